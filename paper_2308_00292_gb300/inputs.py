@@ -1,0 +1,79 @@
+"""Seeded synthetic point clouds shaped like the paper's workloads.
+
+This module holds no arithmetic of the method: it only draws points and
+charges.  It is the one module the CUDA path's tests/benchmark and the CPU
+oracle both consume.  The paper measures only on synthetic distributions
+(uniform cube, sphere surface, Sec. 5 and Table 2), so every workload here is
+synthetic; NumPy's PCG64 generator (``default_rng(seed)``) in float64.
+
+Workloads:
+  uniform_cube  -- points U[0,1)^3, charges U[-1,1]             (C1 / D1 shape)
+  clustered     -- 50 Gaussian clusters + 10% background, net-zero normal
+                   charges                                       (C2 shape)
+  sphere        -- points on a sphere of radius 0.45, charges U[-1,1]
+                                                                 (Table 2 shape)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def uniform_cube(n: int, seed: int = 1, lo: float = 0.0, hi: float = 1.0):
+    """n points uniform in [lo, hi)^3 and charges uniform in [-1, 1]."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(lo, hi, size=(n, 3))
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return x, q
+
+
+def clustered(n: int, seed: int = 2, nclusters: int = 50, background: float = 0.10,
+              sigma_lo: float = 1e-3, sigma_hi: float = 1e-1):
+    """Mixture of Gaussian clusters plus a uniform background in [0,1)^3.
+
+    Cluster centres U[0.1, 0.9]^3, widths log-uniform in [sigma_lo, sigma_hi],
+    equal weights; points falling outside [0,1)^3 are redrawn.  Charges are
+    standard normal shifted to a zero net charge.
+    """
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.1, 0.9, size=(nclusters, 3))
+    sig = np.exp(rng.uniform(np.log(sigma_lo), np.log(sigma_hi), size=nclusters))
+    nb = int(round(background * n))
+    nc = n - nb
+    which = rng.integers(0, nclusters, size=nc)
+    x = np.empty((n, 3))
+    pts = centres[which] + sig[which, None] * rng.standard_normal((nc, 3))
+    bad = np.any((pts < 0.0) | (pts >= 1.0), axis=1)
+    while bad.any():
+        k = int(bad.sum())
+        pts[bad] = centres[which[bad]] + sig[which[bad], None] * rng.standard_normal((k, 3))
+        bad = np.any((pts < 0.0) | (pts >= 1.0), axis=1)
+    x[:nc] = pts
+    x[nc:] = rng.uniform(0.0, 1.0, size=(nb, 3))
+    perm = rng.permutation(n)
+    x = x[perm]
+    q = rng.standard_normal(n)
+    q -= q.mean()
+    return x, q
+
+
+def sphere(n: int, seed: int = 5, radius: float = 0.45):
+    """n points on the sphere |x| = radius (normalised Gaussian directions)."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    x = radius * d
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return x, q
+
+
+# The configurations the library is measured on (sizes, distributions, seeds).
+CONFIGS = {
+    "laplace3d_uniform_n2e4": dict(gen="uniform_cube", n=20000, seed=1, eps=1e-6, leaf_cap=280),
+    "laplace3d_clustered_n1e7": dict(gen="clustered", n=10_000_000, seed=2, eps=1e-6, leaf_cap=200),
+    "laplace3d_clustered_n1e7_eps1e-9": dict(gen="clustered", n=10_000_000, seed=2, eps=1e-9, leaf_cap=200),
+    "laplace3d_sphere_n4e6": dict(gen="sphere", n=4_000_000, seed=5, eps=1e-6, leaf_cap=280),
+}
+
+
+def make(gen: str, n: int, seed: int, **_):
+    return {"uniform_cube": uniform_cube, "clustered": clustered, "sphere": sphere}[gen](n, seed=seed)
