@@ -1,0 +1,288 @@
+#!/usr/bin/env python3
+"""Benchmark of the discrete DMK evaluation pass (3D Laplace) on GB300.
+
+One step = one full evaluation pass (unit-box map, tree build, upward pass,
+plane-wave downward pass, leaf evaluation, residual near field, unpermute) of
+a synthetic point cloud already resident in HBM.  Default workload: N = 1e7
+points, 50 Gaussian clusters plus 10% uniform background, net-zero normal
+charges, eps = 1e-6, leaf capacity 200, mixed precision.  The FP64 path is
+timed on the same input for the mixed-vs-FP64 comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own independent cloud (different
+seed): the method has no exchange step on one node, so scaling is weak and
+there is no collective on the data path (only a barrier and a max-reduction
+of the timings).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D Laplace DMK points/s at rel-L2 1e-6, mixed-prec vs FP64 path, 1 GB300"
+UNIT = "points/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="laplace3d_clustered_n1e7")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def near_flops_per_pair(qdeg: int) -> int:
+    # per candidate pair: 3 differences, r^2 (3 mul + 2 add), x = 2 r^2/R^2 - 1 (2),
+    # Horner q(x) (2 per degree), rsqrt (1), 1/r - q/R (2), charge times value and sum (2)
+    return 3 + 5 + 2 + 2 * qdeg + 1 + 2 + 2
+
+
+def cpu_baseline(cfg: dict, n_sample: int, seed_offset: int = 1000):
+    """The oracle's plain FP64 DMK on a bounded sample of the same workload."""
+    import oracle
+    from paper_2308_00292_gb300 import inputs
+    oracle.build()
+    x, q = inputs.make(cfg["gen"], n_sample, cfg["seed"] + seed_offset)
+    t0 = time.perf_counter()
+    oracle.dmk(x, q, eps=cfg["eps"], leaf_cap=cfg["leaf_cap"])
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d points of the %s workload (seed %d), eps %g, leaf cap %d, plain FP64 C oracle DMK, %.1f s"
+                      % (n_sample, cfg["gen"], cfg["seed"] + seed_offset, cfg["eps"], cfg["leaf_cap"], dt)}
+
+
+def run_reference(args, rank, world):
+    from paper_2308_00292_gb300 import inputs
+    if rank != 0:
+        return
+    cfg = inputs.CONFIGS[args.config]
+    n_sample = args.cpu_sample
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass  # the oracle has no warm state; one untimed sample builds the library
+    base = cpu_baseline(cfg, min(n_sample, 20000))
+    times = []
+    for k in range(args.steps):
+        b = cpu_baseline(cfg, n_sample, seed_offset=1000 + k)
+        times.append(n_sample / b["value"])
+    tot = sum(times)
+    value = n_sample * args.steps / tot
+    cb = dict(base)
+    cb["value"] = value
+    cb["sample"] = "%d points of the %s workload per step, plain FP64 C oracle DMK" % (n_sample, cfg["gen"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, cfg, ours=False),
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, cfg, ours=True):
+    return {"workload": args.config, "n_points": cfg["n"], "distribution": cfg["gen"], "eps": cfg["eps"],
+            "leaf_cap": cfg["leaf_cap"], "precision": "mixed" if ours else "fp64", "seed": cfg["seed"],
+            "l2": "inputs larger than L2 (%.0f MB of points and charges per rank)" % (cfg["n"] * 32 / 1e6),
+            "parallelism": "independent replica per GPU" if args.gpus > 1 else "single GPU"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2308_00292_gb300 import dmk, inputs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    cfg = inputs.CONFIGS[args.config]
+    x, q = inputs.make(cfg["gen"], cfg["n"], cfg["seed"] + 17 * rank)
+    n = x.shape[0]
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    plan = dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"])
+    for _ in range(args.warmup):
+        plan.eval(xd, qd, out=out)
+    barrier()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phase = {"t_tree_ms": 0.0, "t_upward_ms": 0.0, "t_downward_ms": 0.0, "t_near_ms": 0.0}
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.eval(xd, qd, out=out)
+        st = plan.stats()
+        for k in phase:
+            phase[k] += st[k]
+        launches += st["n_launches"]
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = plan.stats()
+    prm = plan.params()
+    value = n * world / (ms / 1e3)
+
+    # end to end through the host entry point: pinned inputs, H2D + eval + D2H per step
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    qh = torch.from_numpy(q).pin_memory().numpy()
+    uh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    plan.eval_host(xh, qh, out=uh)
+    barrier()
+    ke = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        plan.eval_host(xh, qh, out=uh)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
+           "d2h_bytes_per_step": int(uh.nbytes), "ms_per_step": e2e_ms}
+    plan.close()
+
+    # the FP64 path on the same input
+    fp64 = None
+    if not args.skip_fp64:
+        p64 = dmk.Plan(cfg["eps"], precision=dmk.DMK_FP64, leaf_cap=cfg["leaf_cap"])
+        p64.eval(xd, qd, out=out)
+        barrier()
+        k64 = 2
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k64):
+            p64.eval(xd, qd, out=out)
+        f1.record(stream)
+        barrier()
+        ms64 = f0.elapsed_time(f1) / k64
+        s64 = p64.stats()
+        fp64 = {"value": n * world / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                "phases_ms": {k: round(s64[k], 3) for k in phase},
+                "mixed_speedup": ms64 / ms}
+        p64.close()
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    per_step = {k: v / args.steps for k, v in phase.items()}
+    pairs = stats["near_pairs"]
+    fpp = near_flops_per_pair(prm["q_degree"])
+    sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else 1440.0
+    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    t_near = per_step["t_near_ms"] / 1e3
+    achieved = pairs * fpp / t_near / 1e12 if t_near > 0 else 0.0
+    roofline = {"kernel": "k_near (residual near field)", "bound": "alu", "achieved": achieved,
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                "work": "%d candidate pairs x %d FP32 flops per pair per launch" % (pairs, fpp),
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz sampled SM clock" % sm_mhz}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
+            "config": config_dict(args, cfg), "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "clocks": clocks, "phases_ms": {k: round(v, 3) for k, v in per_step.items()},
+            "fp64_path": fp64,
+            "tree": {"levels": stats["n_levels"], "boxes": stats["n_boxes"], "leaves": stats["n_leaves"],
+                     "fout": stats["n_fout"], "near_pairs": pairs, "balance_rounds": stats["balance_rounds"]}}
+    if not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * dmk.h -- C ABI of libdmk, a GB300 (sm_103a) implementation of the discrete
+ * evaluation pass of the dual-space multilevel kernel-splitting (DMK) method
+ * of Jiang & Greengard, arXiv 2308.00292.
+ *
+ * The library computes, for targets x_i and sources y_j with charges rho_j,
+ *
+ *     u_i = sum_{j : y_j != x_i} K(x_i - y_j) rho_j            (eq. discretesum)
+ *
+ * with K(r) = 1/r, the 3D Laplace kernel without the 1/(4 pi) factor
+ * (eq. laplacesum); coincident source/target pairs contribute zero, as in the
+ * self-interaction remark of Sec. 3.1.  The requested precision eps is the
+ * "prescribed precision" of Sec. 3.4 (Step 0 comment); the error is measured
+ * as the relative l2 norm over all targets.
+ *
+ * Every computation runs in CUDA kernels on the device; there is no CPU
+ * fallback.  All functions return a dmk_status code; on failure
+ * dmk_last_error_detail() gives a thread-local description.
+ */
+#ifndef DMK_H
+#define DMK_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DMK_API __attribute__((visibility("default")))
+#else
+#define DMK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef enum {
+    DMK_OK = 0,
+    DMK_ERR_INVALID_ARG = 1,  /* null pointer, negative size, non-finite
+                                 coordinate, eps outside [1e-12, 1e-2], ... */
+    DMK_ERR_UNSUPPORTED = 2,  /* kernel / dimension / option not implemented */
+    DMK_ERR_OOM = 3,          /* device or host allocation failed */
+    DMK_ERR_CUDA = 4,         /* a CUDA runtime call failed (no device, ...) */
+    DMK_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired */
+    DMK_ERR_DEPTH = 6,        /* the tree would exceed the maximum depth */
+    DMK_ERR_INTERNAL = 7      /* internal consistency check failed */
+} dmk_status;
+
+/* ---- kernels and precision ---------------------------------------------- */
+typedef enum {
+    DMK_LAPLACE = 0,       /* 1/r in 3D (Sec. 3); the only kernel implemented */
+    DMK_YUKAWA = 1,        /* reserved: exp(-lambda r)/r (Sec. 4) */
+    DMK_LOG2D = 2,         /* reserved: log r in 2D (Sec. 4) */
+    DMK_SQRTLAPLACE = 3    /* reserved: 1/r^2 in 3D (Sec. 4) */
+} dmk_kernel;
+
+typedef enum {
+    DMK_FP64 = 0,   /* every step in double precision */
+    DMK_MIXED = 1   /* transforms, expansions and residual sums in single
+                       precision; potentials accumulated in double */
+} dmk_precision;
+
+/* Flags for dmk_opts.flags. */
+enum {
+    DMK_FLAG_FAR_ONLY = 1,    /* return only the far part (windowed + difference
+                                 kernels, eqs. farpotential): a diagnostic */
+    DMK_FLAG_NEAR_ONLY = 2,   /* return only the residual-kernel part and the
+                                 self corrections (eq. nearpotential, Step 5) */
+    DMK_FLAG_HOST_ONLY = 4    /* dmk_plan: build the host-side tables only and
+                                 touch no device (for inspecting the plan); such
+                                 a plan cannot be evaluated */
+};
+
+/* Options; a zero-initialised struct selects the defaults. */
+typedef struct {
+    int leaf_cap;        /* n_s: a box with more points is subdivided
+                            (default 280 at eps >= 1e-6, 800 below, Sec. 5.1.1) */
+    int precision;       /* dmk_precision (default DMK_FP64) */
+    double kernel_param; /* reserved (Yukawa lambda) */
+    int flags;           /* DMK_FLAG_* */
+    int max_level;       /* deepest tree level, 1..20 (default 20) */
+    int p;               /* override: Chebyshev order per dimension (Table 1) */
+    int nf;              /* override: Fourier modes m in [-nf, nf]^3 (Table 1) */
+} dmk_opts;
+
+typedef struct dmk_plan_s *dmk_plan_t;
+
+/*
+ * dmk_plan -- choose the method parameters for eps and build the plan tables
+ * (Step 1 "Precomputation" of Sec. 3.4): c, p and N1 = 2 nf + 1 from Table 1,
+ * the PSWF psi_0^c (App. A.5), the 1-D Chebyshev / plane-wave operators, the
+ * diagonal-translation weights (eqs. diagonaltranslation, wlmdef) and the
+ * windowed root kernel weights (Sec. 3.6, eq. windowedkernelft2), and copy
+ * them to the current CUDA device.
+ *
+ *   kernel  must be DMK_LAPLACE and dim must be 3 (else DMK_ERR_UNSUPPORTED);
+ *   eps     in [1e-12, 1e-2] (else DMK_ERR_INVALID_ARG);
+ *   opts    may be NULL (defaults);
+ *   out     receives the plan; the caller releases it with dmk_plan_destroy.
+ */
+DMK_API int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_plan_t *out);
+
+/*
+ * dmk_eval -- one evaluation pass (Steps 0, 2-5 of Sec. 3.4) on device data.
+ *
+ *   sources     device pointer, n_src x 3 doubles, row-major (x, y, z per point)
+ *   n_src       number of sources (>= 0)
+ *   charges     device pointer, n_src doubles
+ *   targets     device pointer, n_tgt x 3 doubles; may be the same pointer as
+ *               sources (with n_tgt == n_src), in which case every source is
+ *               also a target and its own term is excluded
+ *   n_tgt       number of targets (>= 0)
+ *   potentials  device pointer, n_tgt doubles, caller-allocated, overwritten
+ *   cuda_stream cudaStream_t to run on (NULL = legacy default stream)
+ *
+ * Inputs may lie anywhere in R^3 (they are mapped to the unit box and the
+ * potentials scaled back, Sec. 3.1).  The library never writes the inputs and
+ * never frees caller memory; its scratch (tree, expansions) belongs to the
+ * plan, grows on demand and is reused by later calls.  A plan must not be
+ * used by two calls at the same time.  The call synchronises cuda_stream
+ * before it returns.  On error the potentials are unspecified.
+ */
+DMK_API int dmk_eval(dmk_plan_t plan,
+             const double *sources, int64_t n_src, const double *charges,
+             const double *targets, int64_t n_tgt, double *potentials,
+             void *cuda_stream);
+
+/*
+ * dmk_eval_host -- dmk_eval on host arrays: copies the inputs to the device,
+ * evaluates, and copies the potentials back (same argument meaning, host
+ * pointers; pinned host memory makes the copies faster).  The device copies
+ * live in the plan's scratch.
+ */
+DMK_API int dmk_eval_host(dmk_plan_t plan,
+                  const double *sources, int64_t n_src, const double *charges,
+                  const double *targets, int64_t n_tgt, double *potentials,
+                  void *cuda_stream);
+
+/* Release a plan and all its device memory.  NULL is accepted. */
+DMK_API int dmk_plan_destroy(dmk_plan_t plan);
+
+/* Static description of a status code. */
+DMK_API const char *dmk_error_string(int code);
+
+/* Thread-local detail of the last failure in this thread ("" if none). */
+DMK_API const char *dmk_last_error_detail(void);
+
+/* ---- introspection (diagnostics and tests) -------------------------------- */
+
+/* Method parameters chosen by dmk_plan. */
+typedef struct {
+    double eps, c;          /* precision, PSWF bandwidth */
+    int p, nf, n0;          /* Chebyshev order, difference / root Fourier half-widths */
+    int leaf_cap, max_level, precision;
+    int q_degree;           /* degree of the residual-kernel polynomial in r^2 */
+    double psi0_over_c0;    /* psi(0)/c_0: the self term at R = 1 */
+} dmk_plan_params;
+
+DMK_API int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out);
+
+/* Copy a host-side plan table into out (capacity n doubles); returns the
+ * table's length through *len.  which:
+ *   0  psi_0^c on the grid x_k = k / 64, k = 0..256, normalised psi(0) = 1
+ *   1  translation weights w(s), s = |m|^2 = 0..3 nf^2, at box side R = 1
+ *   2  root weights wW(s), s = 0..3 n0^2, and (first) the root spacing hW
+ *   3  residual polynomial: Chebyshev coefficients of q(t) = Phi(sqrt t)/sqrt t
+ *      on t in [0, 1] */
+DMK_API int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len);
+
+/* Statistics of the last dmk_eval. */
+typedef struct {
+    int64_t n_points;       /* points in the tree (union of sources and targets) */
+    int32_t n_levels;       /* L_max + 1 */
+    int64_t n_boxes, n_leaves, n_fout, n_fin;
+    int64_t near_pairs;     /* candidate source-target pairs of the residual sum */
+    int32_t balance_rounds; /* rebuilds needed by the level restriction */
+    float t_tree_ms, t_upward_ms, t_downward_ms, t_near_ms, t_total_ms;
+    int64_t n_launches;     /* kernels of this library launched by the call */
+} dmk_eval_stats;
+
+DMK_API int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out);
+
+/* Tree of the last dmk_eval, for parity checks.  For every point of the
+ * (source u target) set, in input order (sources, then targets when they are
+ * a separate array): leaf_level[i] and leaf_cell[i], the Morton interleave of
+ * the leaf's cell indices at its level (bit 3b + d = bit b of axis d).  Host
+ * arrays of n_points entries (see dmk_get_stats). */
+DMK_API int dmk_get_tree(dmk_plan_t plan, int32_t *leaf_level, int64_t *leaf_cell, int64_t n_points);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMK_H */

@@ -1,0 +1,335 @@
+// api.cu -- the C ABI of libdmk (include/dmk.h): plan construction (Step 1 of
+// Sec. 3.4), one evaluation pass (Steps 0 and 2-5), statistics and tree export.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "dmk.h"
+#include "passes.h"
+
+namespace dmk {
+std::atomic<long long> g_launches{0};
+}
+
+namespace {
+thread_local std::string g_detail;
+
+int fail(int code, const std::string &msg) {
+    g_detail = msg;
+    return code;
+}
+}  // namespace
+
+struct dmk_plan_s {
+    int kernel = 0, dim = 3;
+    double eps = 0;
+    dmk_opts opts{};
+    dmk::Tables tb;
+    bool host_only = false;
+    int device = 0;
+    int precision = 0;
+    int leaf_cap = 280, max_level = 20;
+    int qdeg = 0;
+    dmk::Workspace ws;
+    dmk::DBuf tab;  // device tables (working precision)
+    dmk::DevTables<double> dt_d{};
+    dmk::DevTables<float> dt_f{};
+    std::unique_ptr<dmk::TreeBuilder> tree;
+    dmk::PassBufs bufs;
+    dmk::DBuf h_src, h_q, h_tgt, h_pot;  // device copies for dmk_eval_host
+    dmk_eval_stats stats{};
+    cudaEvent_t ev[6] = {};
+    bool events = false;
+    size_t smem_limit = 0;
+    int num_sms = 0;
+    ~dmk_plan_s() {
+        if (events)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+template <typename T>
+int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
+    const dmk::Tables &tb = pl->tb;
+    const int p = tb.p, nf = tb.nf, N1 = 2 * nf + 1, n0 = tb.n0, NW = 2 * n0 + 1;
+    std::vector<T> h;
+    auto push = [&](const std::vector<double> &v) {
+        size_t off = h.size();
+        for (double x : v) h.push_back((T)x);
+        while (h.size() % 32) h.push_back((T)0);
+        return off;
+    };
+    std::vector<double> A2(tb.A[0]);
+    A2.insert(A2.end(), tb.A[1].begin(), tb.A[1].end());
+    size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(tb.FWr), oFWi = push(tb.FWi);
+    size_t ow = push(tb.w), owW = push(tb.wW), oq = push(tb.qmono);
+    if (pl->ws.ensure(pl->tab, (int64_t)h.size() * sizeof(T))) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
+    if (cudaMemcpy(pl->tab.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(DMK_ERR_CUDA, "copying the plan tables to the device failed");
+    const T *base = (const T *)pl->tab.p;
+    dt.p = p;
+    dt.nf = nf;
+    dt.N1 = N1;
+    dt.nh = nf + 1;
+    dt.n0 = n0;
+    dt.NW = NW;
+    dt.nhW = n0 + 1;
+    dt.qdeg = (int)tb.qmono.size() - 1;
+    dt.A = base + oA;
+    dt.Fr = base + oFr;
+    dt.Fi = base + oFi;
+    dt.FWr = base + oFWr;
+    dt.FWi = base + oFWi;
+    dt.w = base + ow;
+    dt.wW = base + owW;
+    dt.qmono = base + oq;
+    return DMK_OK;
+}
+
+bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 28 || p == 38; }
+
+int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
+                double *pot, cudaStream_t st) {
+    if (nt == 0) return DMK_OK;
+    if (cudaSetDevice(pl->device) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaSetDevice failed");
+    if (ns == 0) {
+        if (cudaMemsetAsync(pot, 0, (size_t)nt * sizeof(double), st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "clearing the potentials failed");
+        pl->stats = dmk_eval_stats{};
+        return DMK_OK;
+    }
+    const bool same = (tgt == src && nt == ns);
+    const int64_t n = same ? ns : ns + nt;
+    if (n >= (int64_t)INT32_MAX / 2) return fail(DMK_ERR_UNSUPPORTED, "more than 2^30 points");
+    if (!pl->tree) pl->tree.reset(new dmk::TreeBuilder(pl->ws));
+    std::string err;
+    const bool single = pl->precision == DMK_MIXED;
+    const long long launches0 = dmk::g_launches.load();
+    cudaEventRecord(pl->ev[0], st);
+    int rc = pl->tree->build(src, ns, q, same ? nullptr : tgt, same ? 0 : nt, same, pl->leaf_cap, pl->max_level,
+                             single ? 1 : 0, st, err);
+    if (rc) return fail(rc, "tree: " + err);
+    dmk::PassCtx cx{};
+    cx.tree = pl->tree.get();
+    cx.bufs = &pl->bufs;
+    cx.ws = &pl->ws;
+    cx.tables = single ? (const void *)&pl->dt_f : (const void *)&pl->dt_d;
+    cx.single = single;
+    cx.p = pl->tb.p;
+    cx.mode = (pl->opts.flags & DMK_FLAG_FAR_ONLY) ? 1 : ((pl->opts.flags & DMK_FLAG_NEAR_ONLY) ? 2 : 0);
+    cx.total_sources = ns;
+    cx.pot = pot;
+    cx.st = st;
+    for (int i = 0; i < 6; ++i) cx.ev[i] = pl->ev[i];
+    cx.smem_limit = pl->smem_limit;
+    cx.num_sms = pl->num_sms;
+    rc = dmk::run_passes(cx, err);
+    if (rc) return fail(rc, "passes: " + err);
+    cudaEventRecord(pl->ev[5], st);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("device execution failed: ") + cudaGetErrorString(ce));
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(ce));
+    dmk_eval_stats &s = pl->stats;
+    s = dmk_eval_stats{};
+    s.n_points = n;
+    s.n_levels = pl->tree->nlev;
+    s.n_boxes = pl->tree->nb;
+    s.n_leaves = pl->tree->nleaves;
+    s.near_pairs = pl->tree->near_pairs;
+    s.balance_rounds = pl->tree->rounds;
+    s.n_fout = pl->tree->root_leaf ? 0 : pl->tree->nslots;
+    s.n_fin = pl->tree->ntleaves;
+    float t01 = 0, t12 = 0, t23 = 0, t34 = 0, t05 = 0;
+    cudaEventElapsedTime(&t01, pl->ev[0], pl->ev[1]);
+    cudaEventElapsedTime(&t12, pl->ev[1], pl->ev[2]);
+    cudaEventElapsedTime(&t23, pl->ev[2], pl->ev[3]);
+    cudaEventElapsedTime(&t34, pl->ev[3], pl->ev[4]);
+    cudaEventElapsedTime(&t05, pl->ev[0], pl->ev[5]);
+    s.t_tree_ms = t01;
+    s.t_upward_ms = t12;
+    s.t_downward_ms = t23;
+    s.t_near_ms = t34;
+    s.t_total_ms = t05;
+    s.n_launches = dmk::g_launches.load() - launches0;
+    return DMK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dmk_error_string(int code) {
+    switch (code) {
+    case DMK_OK: return "success";
+    case DMK_ERR_INVALID_ARG: return "invalid argument";
+    case DMK_ERR_UNSUPPORTED: return "unsupported kernel, dimension or option";
+    case DMK_ERR_OOM: return "out of memory";
+    case DMK_ERR_CUDA: return "CUDA error";
+    case DMK_ERR_TIMEOUT: return "device wait timed out";
+    case DMK_ERR_DEPTH: return "tree depth limit exceeded";
+    case DMK_ERR_INTERNAL: return "internal error";
+    default: return "unknown status code";
+    }
+}
+
+const char *dmk_last_error_detail(void) { return g_detail.c_str(); }
+
+int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_plan_t *out) {
+    g_detail.clear();
+    if (!out) return fail(DMK_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(eps >= 1e-12 && eps <= 1e-2)) return fail(DMK_ERR_INVALID_ARG, "eps must lie in [1e-12, 1e-2]");
+    if (kernel != DMK_LAPLACE) return fail(DMK_ERR_UNSUPPORTED, "only DMK_LAPLACE is implemented");
+    if (dim != 3) return fail(DMK_ERR_UNSUPPORTED, "DMK_LAPLACE is implemented in 3 dimensions");
+    dmk_opts o{};
+    if (opts) o = *opts;
+    if (o.leaf_cap < 0 || o.precision < 0 || o.precision > 1 || o.max_level < 0 || o.max_level > dmk::kMaxLevel ||
+        o.nf < 0 || o.nf > dmk::kMaxNf || !valid_p(o.p) || (o.flags & ~7))
+        return fail(DMK_ERR_INVALID_ARG, "option out of range");
+    if ((o.flags & DMK_FLAG_FAR_ONLY) && (o.flags & DMK_FLAG_NEAR_ONLY))
+        return fail(DMK_ERR_INVALID_ARG, "DMK_FLAG_FAR_ONLY and DMK_FLAG_NEAR_ONLY are exclusive");
+    std::unique_ptr<dmk_plan_s> pl(new (std::nothrow) dmk_plan_s());
+    if (!pl) return fail(DMK_ERR_OOM, "host allocation failed");
+    pl->kernel = kernel;
+    pl->dim = dim;
+    pl->eps = eps;
+    pl->opts = o;
+    pl->precision = o.precision;
+    pl->leaf_cap = o.leaf_cap > 0 ? o.leaf_cap : (eps >= 1e-6 * (1 - 1e-12) ? 280 : 800);
+    pl->max_level = o.max_level > 0 ? o.max_level : dmk::kMaxLevel;
+    std::string err;
+    if (dmk::build_tables(eps, o.p, o.nf, pl->tb, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
+    pl->qdeg = (int)pl->tb.qmono.size() - 1;
+    if (pl->qdeg >= 64) return fail(DMK_ERR_INTERNAL, "residual polynomial degree above 63");
+    pl->host_only = (o.flags & DMK_FLAG_HOST_ONLY) != 0;
+    if (!pl->host_only) {
+        if (cudaGetDevice(&pl->device) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DMK_ERR_CUDA, "no CUDA device available");
+        }
+        int smem = 0, sms = 0;
+        if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DMK_ERR_CUDA, "querying the device failed");
+        }
+        pl->smem_limit = (size_t)smem;
+        pl->num_sms = sms;
+        for (auto &e : pl->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaEventCreate failed");
+        pl->events = true;
+        int rc = pl->precision == DMK_MIXED ? upload_tables<float>(pl.get(), pl->dt_f)
+                                            : upload_tables<double>(pl.get(), pl->dt_d);
+        if (rc) return rc;
+    }
+    *out = pl.release();
+    return DMK_OK;
+}
+
+int dmk_plan_destroy(dmk_plan_t plan) {
+    delete plan;
+    return DMK_OK;
+}
+
+int dmk_eval(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges, const double *targets,
+             int64_t n_tgt, double *potentials, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
+    if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials)))
+        return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    return eval_device(plan, sources, n_src, charges, targets, n_tgt, potentials, (cudaStream_t)cuda_stream);
+}
+
+int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
+                  const double *targets, int64_t n_tgt, double *potentials, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
+    if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials)))
+        return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    if (n_tgt == 0) return DMK_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaSetDevice failed");
+    const bool same = (targets == sources && n_tgt == n_src);
+    dmk::Workspace &ws = plan->ws;
+    if (ws.ensure(plan->h_src, std::max<int64_t>(n_src, 1) * 24) || ws.ensure(plan->h_q, std::max<int64_t>(n_src, 1) * 8) ||
+        ws.ensure(plan->h_pot, n_tgt * 8) || (!same && ws.ensure(plan->h_tgt, n_tgt * 24)))
+        return fail(DMK_ERR_OOM, "device allocation failed (host-call buffers)");
+    if (n_src > 0 &&
+        (cudaMemcpyAsync(plan->h_src.p, sources, (size_t)n_src * 24, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(plan->h_q.p, charges, (size_t)n_src * 8, cudaMemcpyHostToDevice, st) != cudaSuccess))
+        return fail(DMK_ERR_CUDA, "host-to-device copy failed");
+    if (!same && cudaMemcpyAsync(plan->h_tgt.p, targets, (size_t)n_tgt * 24, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(DMK_ERR_CUDA, "host-to-device copy failed");
+    const double *dsrc = (const double *)plan->h_src.p;
+    const double *dtgt = same ? dsrc : (const double *)plan->h_tgt.p;
+    int rc = eval_device(plan, dsrc, n_src, (const double *)plan->h_q.p, dtgt, n_tgt, (double *)plan->h_pot.p, st);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(potentials, plan->h_pot.p, (size_t)n_tgt * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(DMK_ERR_CUDA, "device-to-host copy failed");
+    return DMK_OK;
+}
+
+int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
+    if (!plan || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    out->eps = plan->eps;
+    out->c = plan->tb.c;
+    out->p = plan->tb.p;
+    out->nf = plan->tb.nf;
+    out->n0 = plan->tb.n0;
+    out->leaf_cap = plan->leaf_cap;
+    out->max_level = plan->max_level;
+    out->precision = plan->precision;
+    out->q_degree = plan->qdeg;
+    out->psi0_over_c0 = plan->tb.psi0_over_c0;
+    return DMK_OK;
+}
+
+int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len) {
+    if (!plan || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    std::vector<double> v;
+    switch (which) {
+    case 0: v = plan->tb.psi_grid; break;
+    case 1: v = plan->tb.w; break;
+    case 2:
+        v.push_back(plan->tb.hW);
+        v.insert(v.end(), plan->tb.wW.begin(), plan->tb.wW.end());
+        break;
+    case 3: v = plan->tb.qcheb; break;
+    default: return fail(DMK_ERR_INVALID_ARG, "unknown table");
+    }
+    *len = (int64_t)v.size();
+    if (out) {
+        if (n < (int64_t)v.size()) return fail(DMK_ERR_INVALID_ARG, "output too small");
+        std::memcpy(out, v.data(), v.size() * sizeof(double));
+    }
+    return DMK_OK;
+}
+
+int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out) {
+    if (!plan || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    *out = plan->stats;
+    return DMK_OK;
+}
+
+int dmk_get_tree(dmk_plan_t plan, int32_t *leaf_level, int64_t *leaf_cell, int64_t n_points) {
+    if (!plan || !leaf_level || !leaf_cell) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (!plan->tree || plan->tree->n != n_points)
+        return fail(DMK_ERR_INVALID_ARG, "n_points does not match the last evaluation");
+    std::string err;
+    int rc = plan->tree->export_leaves(leaf_level, leaf_cell, 0, err);
+    if (rc) return fail(rc, err);
+    return DMK_OK;
+}
+
+}  // extern "C"

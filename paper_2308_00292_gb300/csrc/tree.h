@@ -1,0 +1,107 @@
+// tree.h -- device buffers and the tree builder of libdmk (internal).
+#pragma once
+
+#include "dmk.h"
+#include "dmk_internal.h"
+
+namespace dmk {
+
+enum {
+    DMK_ERR_INVALID_ARG_I = DMK_ERR_INVALID_ARG,
+    DMK_ERR_OOM_I = DMK_ERR_OOM,
+    DMK_ERR_CUDA_I = DMK_ERR_CUDA,
+    DMK_ERR_INTERNAL_I = DMK_ERR_INTERNAL,
+};
+
+// A device allocation that grows on demand (contents are not preserved).
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+struct Workspace {
+    size_t live = 0;
+    // returns 0 on success
+    int ensure(DBuf &b, int64_t bytes) {
+        if (bytes <= 0) bytes = 16;
+        if (b.p && (int64_t)b.bytes >= bytes) return 0;
+        if (b.p) {
+            cudaFree(b.p);
+            live -= b.bytes;
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        size_t want = (size_t)bytes;
+        if (cudaMalloc(&b.p, want) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return 1;
+        }
+        b.bytes = want;
+        live += want;
+        return 0;
+    }
+    void release(DBuf &b) {
+        if (b.p) {
+            cudaFree(b.p);
+            live -= b.bytes;
+        }
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+};
+
+struct Frame {
+    double lo[3];
+    double S;
+};
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+uint64_t host_morton_encode(uint32_t ix, uint32_t iy, uint32_t iz);
+
+class TreeBuilder {
+public:
+    explicit TreeBuilder(Workspace &w) : ws(w) {}
+    // Build the tree of the union of sources and targets (targets ignored
+    // when same).  point_prec: 1 -> float4 leaf-local coordinates, 0 -> double4.
+    int build(const double *src, int64_t ns, const double *charges, const double *tgt, int64_t nt, bool same,
+              int leaf_cap, int max_level, int point_prec, cudaStream_t st, std::string &err);
+    TreeView view() const;
+    int export_leaves(int32_t *lev, int64_t *cell, cudaStream_t st, std::string &err);
+
+    Workspace &ws;
+    int64_t n = 0;
+    bool same = true;
+    int nb = 0, nlev = 0, nslots = 0, nleaves = 0, ntleaves = 0, rounds = 0, near_list_len = 0;
+    bool root_leaf = false;
+    int64_t near_pairs = 0;
+    int lt_start[kMaxLevel + 2] = {0}, lt_count[kMaxLevel + 2] = {0};
+    Frame h_frame{};
+    const uint64_t *sorted_keys = nullptr;
+    const uint32_t *sorted_idx = nullptr;
+
+    // points (sorted)
+    DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, pscan0, pscan1, scan_tmp;
+    DBuf bbox_part, frame, flags, forced;
+    // boxes
+    int64_t box_cap = 0;
+    DBuf bkey, blevel, bstart, bcount, bparent, bchild0, bcmask, bflags, bnsrc, bntgt, bcol, bslot;
+    DBuf bscr0, bscr1, bscr2, slot2box;
+    DBuf lvl_off9, lvl_cnt, lvl_excl;
+    // near-field lists
+    DBuf tleaves, nl_cnt, nl_off, nl_src, pairs;
+
+private:
+    int grow_boxes(int64_t need, cudaStream_t st, std::string &err);
+};
+
+}  // namespace dmk

@@ -1,0 +1,186 @@
+"""ctypes binding of libdmk (``include/dmk.h``): argument marshalling only.
+
+Every step of the evaluation runs in the library's CUDA kernels.  Device
+arrays are passed as torch CUDA tensors (float64, contiguous, shape [n, 3] for
+points) and evaluated with ``dmk_eval`` on torch's current stream; host arrays
+(NumPy) go through ``dmk_eval_host``, which copies in and out.
+
+If ``libdmk.so`` is missing this module raises on import of the library:
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdmk.so")
+
+DMK_LAPLACE = 0
+DMK_FP64 = 0
+DMK_MIXED = 1
+FLAG_FAR_ONLY = 1
+FLAG_NEAR_ONLY = 2
+FLAG_HOST_ONLY = 4
+
+ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "DMK_ERR_OOM", 4: "DMK_ERR_CUDA",
+          5: "DMK_ERR_TIMEOUT", 6: "DMK_ERR_DEPTH", 7: "DMK_ERR_INTERNAL"}
+
+EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
+            "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("leaf_cap", ctypes.c_int), ("precision", ctypes.c_int), ("kernel_param", ctypes.c_double),
+                ("flags", ctypes.c_int), ("max_level", ctypes.c_int), ("p", ctypes.c_int), ("nf", ctypes.c_int)]
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("c", ctypes.c_double), ("p", ctypes.c_int), ("nf", ctypes.c_int),
+                ("n0", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_level", ctypes.c_int),
+                ("precision", ctypes.c_int), ("q_degree", ctypes.c_int), ("psi0_over_c0", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_fout", ctypes.c_int64), ("n_fin", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("balance_rounds", ctypes.c_int32),
+                ("t_tree_ms", ctypes.c_float), ("t_upward_ms", ctypes.c_float),
+                ("t_downward_ms", ctypes.c_float), ("t_near_ms", ctypes.c_float), ("t_total_ms", ctypes.c_float),
+                ("n_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DMKError(RuntimeError):
+    def __init__(self, code, detail):
+        super().__init__("%s: %s" % (ERRORS.get(code, code), detail))
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libdmk.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise OSError("libdmk.so not built: run paper_2308_00292_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+            L.dmk_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
+                                   ctypes.POINTER(vp)]
+            L.dmk_eval.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
+            L.dmk_eval_host.argtypes = [vp, dp, i64, dp, dp, i64, dp, vp]
+            L.dmk_plan_destroy.argtypes = [vp]
+            L.dmk_error_string.argtypes = [ctypes.c_int]
+            L.dmk_error_string.restype = ctypes.c_char_p
+            L.dmk_last_error_detail.argtypes = []
+            L.dmk_last_error_detail.restype = ctypes.c_char_p
+            L.dmk_plan_get_params.argtypes = [vp, ctypes.POINTER(PlanParams)]
+            L.dmk_plan_get_table.argtypes = [vp, ctypes.c_int, dp, i64, ctypes.POINTER(i64)]
+            L.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+            L.dmk_get_tree.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), i64]
+            for name in EXPORTED:
+                getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        detail = lib().dmk_last_error_detail().decode()
+        raise DMKError(rc, detail)
+
+
+class Plan:
+    """A DMK plan: ``Plan(eps, precision=DMK_MIXED, leaf_cap=200)``."""
+
+    def __init__(self, eps=1e-6, precision=DMK_FP64, leaf_cap=0, flags=0, max_level=0, p=0, nf=0, kernel=DMK_LAPLACE,
+                 dim=3):
+        self._h = ctypes.c_void_p()
+        o = Opts(leaf_cap, precision, 0.0, flags, max_level, p, nf)
+        _check(lib().dmk_plan(kernel, dim, eps, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().dmk_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- eval
+    def eval(self, sources, charges, targets=None, out=None, stream=None):
+        """Potentials at the targets (every source when targets is None).
+
+        torch CUDA tensors -> dmk_eval on the device (result is a tensor);
+        NumPy arrays -> dmk_eval_host (result is an ndarray)."""
+        if isinstance(sources, np.ndarray):
+            return self.eval_host(sources, charges, targets, out)
+        import torch
+        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
+        ns = sources.shape[0]
+        tgt = sources if targets is None else targets
+        nt = tgt.shape[0]
+        if out is None:
+            out = torch.empty(nt, dtype=torch.float64, device=sources.device)
+        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+        _check(lib().dmk_eval(self._h, sources.data_ptr(), ns, charges.data_ptr(), tgt.data_ptr(), nt,
+                              out.data_ptr(), st))
+        return out
+
+    def eval_host(self, sources, charges, targets=None, out=None, stream=0):
+        src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+        q = np.ascontiguousarray(charges, dtype=np.float64)
+        tgt = src if targets is None else np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+        if out is None:
+            out = np.empty(tgt.shape[0])
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(lib().dmk_eval_host(self._h, src.ctypes.data_as(dp), src.shape[0], q.ctypes.data_as(dp),
+                                   tgt.ctypes.data_as(dp), tgt.shape[0], out.ctypes.data_as(dp), stream))
+        return out
+
+    # ---------------------------------------------------------------- introspection
+    def params(self) -> dict:
+        p = PlanParams()
+        _check(lib().dmk_plan_get_params(self._h, ctypes.byref(p)))
+        return {k: getattr(p, k) for k, _ in p._fields_}
+
+    def table(self, which: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().dmk_plan_get_table(self._h, which, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().dmk_plan_get_table(self._h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        n.value, ctypes.byref(n)))
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().dmk_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def tree(self):
+        """(leaf_level, leaf_cell) of every point of the last evaluation."""
+        n = self.stats()["n_points"]
+        lev = np.zeros(n, dtype=np.int32)
+        cell = np.zeros(n, dtype=np.int64)
+        _check(lib().dmk_get_tree(self._h, lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n))
+        return lev, cell

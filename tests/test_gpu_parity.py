@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tree: bit-exact (leaf level and leaf cell of every point).  Potentials: the
+FP64 path against the oracle's DMK on the same tree and against the direct
+sum (rel-L2 <= eps, the bar of eq. discretesum at the prescribed precision);
+the mixed path (single-precision transforms and residual sums) against the
+direct sum at 1e-6.
+
+Tolerances against the oracle's DMK (same tree, same method parameters):
+the far part (plane waves, Chebyshev transforms) differs only by rounding
+order: rel-L2 1e-12.  The near part differs by the residual polynomial: the
+library evaluates Phi(r/R)/r with a Chebyshev fit in r^2 truncated at
+1e-3 eps * psi(0)/c_0 (the oracle integrates the Legendre series exactly),
+so |near - near_oracle| <= 1e-3 eps * max|near|, and the total agrees to
+1e-2 eps in rel-L2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2308_00292_gb300 import inputs  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def dmk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_00292_gb300 import dmk as m
+    m.lib()
+    return m
+
+
+def run(dmk, x, q, y=None, **kw):
+    with dmk.Plan(**kw) as plan:
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+        yd = None if y is None else torch.from_numpy(np.ascontiguousarray(y)).cuda()
+        u = plan.eval(xd, qd, yd).cpu().numpy()
+        lev, cell = plan.tree()
+        st = plan.stats()
+    return u, lev, cell, st
+
+
+CASES = {
+    "uniform": lambda: inputs.uniform_cube(6000, seed=201),
+    "clustered": lambda: inputs.clustered(8000, seed=202, nclusters=6),
+    "sphere": lambda: inputs.sphere(5000, seed=203),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_tree_bit_exact(dmk, oracle_mod, case):
+    x, q = CASES[case]()
+    _, lev, cell, st = run(dmk, x, q, eps=1e-6, leaf_cap=60)
+    olev, ocell = oracle_mod.tree(x, eps=1e-6, leaf_cap=60)
+    assert np.array_equal(lev, olev)
+    assert np.array_equal(cell, ocell)
+    assert st["n_levels"] == olev.max() + 1
+
+
+def test_tree_bit_exact_adversarial(dmk, oracle_mod):
+    rng = np.random.default_rng(204)
+    x = np.vstack([0.25 + 1e-6 * rng.standard_normal((900, 3)), rng.uniform(0, 1, (700, 3))])
+    x[:50] = x[0]           # duplicates beyond the leaf capacity
+    x[900:950, 2] = 1.0     # max face
+    x[950:960] = 0.5        # internal box corners
+    q = rng.standard_normal(len(x))
+    _, lev, cell, _ = run(dmk, x, q, eps=1e-6, leaf_cap=30)
+    olev, ocell = oracle_mod.tree(x, eps=1e-6, leaf_cap=30)
+    assert np.array_equal(lev, olev) and np.array_equal(cell, ocell)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+@pytest.mark.parametrize("case", ["uniform", "clustered"])
+def test_fp64_matches_oracle(dmk, oracle_mod, eps, case):
+    x, q = CASES[case]()
+    u, _, _, _ = run(dmk, x, q, eps=eps, leaf_cap=60, precision=dmk.DMK_FP64)
+    ref = oracle_mod.dmk(x, q, eps=eps, leaf_cap=60)
+    assert rel(u, ref) < 1e-2 * eps
+    assert rel(u, oracle_mod.direct(x, q)) < eps
+
+
+def test_fp64_far_and_near_parts(dmk, oracle_mod):
+    x, q = CASES["clustered"]()
+    _, far, near = oracle_mod.dmk(x, q, eps=1e-6, leaf_cap=60, parts=True)
+    uf, _, _, _ = run(dmk, x, q, eps=1e-6, leaf_cap=60, flags=dmk.FLAG_FAR_ONLY)
+    un, _, _, _ = run(dmk, x, q, eps=1e-6, leaf_cap=60, flags=dmk.FLAG_NEAR_ONLY)
+    assert rel(uf, far) < 1e-12
+    assert np.max(np.abs(un - near)) < 1e-3 * 1e-6 * np.max(np.abs(near))
+
+
+def test_config_uniform_n2e4(dmk, oracle_mod):
+    """N = 2e4 uniform in the unit cube, eps = 1e-6, n_s = 280, FP64 (seeded)."""
+    cfg = inputs.CONFIGS["laplace3d_uniform_n2e4"]
+    x, q = inputs.make(**cfg)
+    u, _, _, _ = run(dmk, x, q, eps=cfg["eps"], leaf_cap=cfg["leaf_cap"], precision=dmk.DMK_FP64)
+    ref = oracle_mod.direct(x, q)
+    assert rel(u, ref) < 1e-6
+    assert rel(u, oracle_mod.dmk(x, q, eps=cfg["eps"], leaf_cap=cfg["leaf_cap"])) < 1e-8
+    um, _, _, _ = run(dmk, x, q, eps=cfg["eps"], leaf_cap=cfg["leaf_cap"], precision=dmk.DMK_MIXED)
+    assert rel(um, ref) < 1e-6
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_accuracy(dmk, oracle_mod, case):
+    x, q = CASES[case]()
+    u, _, _, _ = run(dmk, x, q, eps=1e-6, leaf_cap=60, precision=dmk.DMK_MIXED)
+    assert rel(u, oracle_mod.direct(x, q)) < 1e-6
+
+
+def test_separate_targets(dmk, oracle_mod):
+    x, q = inputs.clustered(5000, seed=205, nclusters=4)
+    y, _ = inputs.uniform_cube(3000, seed=206)
+    y[:20] = x[:20]
+    for prec in (dmk.DMK_FP64, dmk.DMK_MIXED):
+        u, lev, cell, _ = run(dmk, x, q, y, eps=1e-6, leaf_cap=50, precision=prec)
+        assert rel(u, oracle_mod.direct(x, q, y)) < 1e-6
+    olev, ocell = oracle_mod.tree(x, y, eps=1e-6, leaf_cap=50)
+    assert np.array_equal(lev, olev) and np.array_equal(cell, ocell)
+
+
+def test_edge_cases(dmk, oracle_mod):
+    # one point, two points, everything in the root leaf
+    for n in (1, 2, 3, 150):
+        x, q = inputs.uniform_cube(n, seed=207 + n)
+        u, lev, _, _ = run(dmk, x, q, eps=1e-9, leaf_cap=280)
+        ref = oracle_mod.direct(x, q)
+        scale = max(np.linalg.norm(ref), 1.0)
+        assert np.linalg.norm(u - ref) <= 1e-8 * scale
+        assert np.all(lev == 0)
+    # far-away inputs and duplicates
+    x, q = inputs.uniform_cube(3000, seed=211)
+    x = 1e3 + 5.0 * x
+    x[10:40] = x[10]
+    u, _, _, _ = run(dmk, x, q, eps=1e-6, leaf_cap=40)
+    assert rel(u, oracle_mod.direct(x, q)) < 1e-6
+
+
+def test_empty_inputs(dmk):
+    with dmk.Plan(1e-6) as plan:
+        x = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+        q = torch.zeros(0, dtype=torch.float64, device="cuda")
+        y = torch.rand((5, 3), dtype=torch.float64, device="cuda")
+        out = torch.full((5,), 7.0, dtype=torch.float64, device="cuda")
+        plan.eval(x, q, y, out=out)
+        assert torch.all(out == 0)
+        plan.eval(y, torch.ones(5, dtype=torch.float64, device="cuda"), x,
+                  out=torch.zeros(0, dtype=torch.float64, device="cuda"))
+
+
+def test_host_entry_point_matches_device(dmk):
+    x, q = inputs.clustered(6000, seed=212, nclusters=3)
+    with dmk.Plan(1e-6, precision=dmk.DMK_MIXED, leaf_cap=80) as plan:
+        a = plan.eval_host(x, q)
+        b = plan.eval(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_nonfinite_input_rejected(dmk):
+    x = torch.rand((100, 3), dtype=torch.float64, device="cuda")
+    x[7, 1] = float("nan")
+    with dmk.Plan(1e-6) as plan:
+        with pytest.raises(dmk.DMKError) as ei:
+            plan.eval(x, torch.ones(100, dtype=torch.float64, device="cuda"))
+        assert ei.value.code == 1
+
+
+def test_repeated_calls_are_deterministic(dmk):
+    x, q = inputs.clustered(20000, seed=213, nclusters=8)
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    with dmk.Plan(1e-6, precision=dmk.DMK_MIXED, leaf_cap=120) as plan:
+        a = plan.eval(xd, qd).cpu().numpy()
+        b = plan.eval(xd, qd).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_full_size_clustered_sampled(dmk, oracle_mod):
+    """N = 1e7, 50 Gaussian clusters + 10% background, net-zero charges, leaf
+    capacity 200, eps = 1e-6 -- the benchmark's launch configuration.  The
+    direct sum is computed for 256 sampled targets (seed 3) against all 1e7
+    sources; rel-L2 over the sample <= 1e-6 for both precisions."""
+    cfg = inputs.CONFIGS["laplace3d_clustered_n1e7"]
+    x, q = inputs.make(**cfg)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(x.shape[0], 256, replace=False)
+    ref = oracle_mod.direct(x, q, x[idx])
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    for prec in (dmk.DMK_MIXED, dmk.DMK_FP64):
+        with dmk.Plan(cfg["eps"], precision=prec, leaf_cap=cfg["leaf_cap"]) as plan:
+            u = plan.eval(xd, qd).cpu().numpy()
+        assert np.all(np.isfinite(u))
+        assert rel(u[idx], ref) < 1e-6, (prec, rel(u[idx], ref))
