@@ -90,7 +90,7 @@ int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
     return DMK_OK;
 }
 
-bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 28 || p == 38; }
+bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 19 || p == 28 || p == 38; }
 
 int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
                 double *pot, cudaStream_t st) {
@@ -204,7 +204,13 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     pl->leaf_cap = o.leaf_cap > 0 ? o.leaf_cap : (eps >= 1e-6 * (1 - 1e-12) ? 280 : 800);
     pl->max_level = o.max_level > 0 ? o.max_level : dmk::kMaxLevel;
     std::string err;
-    if (dmk::build_tables(eps, o.p, o.nf, pl->tb, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
+    // Single precision cannot deliver eps below ~1e-7.  At the 1e-6 row of
+    // Table 1 the method error of p = 18 alone reaches ~0.5-1e-6 on clustered
+    // clouds, so the mixed path takes p = 19 to leave room for its rounding.
+    if (o.precision == DMK_MIXED && eps < 1e-7) return fail(DMK_ERR_UNSUPPORTED, "DMK_MIXED needs eps >= 1e-7");
+    int p_req = o.p;
+    if (p_req == 0 && o.precision == DMK_MIXED && eps < 1e-3 * (1 - 1e-12)) p_req = 19;
+    if (dmk::build_tables(eps, p_req, o.nf, pl->tb, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
     pl->qdeg = (int)pl->tb.qmono.size() - 1;
     if (pl->qdeg >= 64) return fail(DMK_ERR_INTERNAL, "residual polynomial degree above 63");
     pl->host_only = (o.flags & DMK_FLAG_HOST_ONLY) != 0;

@@ -1,7 +1,7 @@
 // passes.cu -- the upward pass, the plane-wave (dual-space) downward pass and
 // the residual near field of the discrete DMK algorithm (Steps 2-5 of Sec. 3.4
-// of arXiv 2308.00292), templated on the working precision T and the
-// Chebyshev order P.
+// of arXiv 2308.00292), templated on the working precision T, the Chebyshev
+// order P and the Fourier half-width NF (the (P, NF) pairs of Table 1).
 //
 // Representations (all per box, box side R, Chebyshev coordinate
 // xi = 2 (x - c_B) / R):
@@ -14,6 +14,14 @@
 //   local       Lambda[a][b][c], Chebyshev coefficients of the far field in the
 //               box (eq. localexpansion).
 //
+// Parity of the 1-D plane-wave matrix.  F[m][n] = sum_j exp(-i theta m t_j)
+// Vinv[n][j] is real and even in m for even n and imaginary and odd in m for
+// odd n (the Chebyshev nodes are symmetric and T_n has the parity of n).  Every
+// contraction with F or with G = conj(F)^T therefore splits into an even part
+// over m >= 0 and an odd part over m > 0, which the kernels use: the mode
+// products touch only non-negative modes and real coefficients.  hs[n][m'] is
+// Re F[m'][n] for even n and Im F[m'][n] for odd n, m' = 0..NF.
+//
 // Kernels:
 //   k_upward   level by level, finest first: moments of a non-leaf box from the
 //              sources of its leaf children (anterpolation onto the parent grid,
@@ -23,10 +31,11 @@
 //   k_root     the windowed kernel W_0 at the root (eq. windowedkernelft2)
 //   k_local    level by level, coarsest first, every box with targets:
 //              Lambda = T_p2c(Lambda_parent) (Lemma ptoclemma) plus, for F_in
-//              boxes, the incoming expansion of eq. diagonaltranslation formed
-//              one m_y slice at a time and converted straight to Chebyshev
-//              coefficients (T_pw2poly); leaves then evaluate Lambda at their
-//              targets (Step 3 "Evaluate local expansions")
+//              boxes, the incoming expansion of eq. diagonaltranslation (the
+//              phases are cube roots of unity because h_l R_l = 2 pi / 3) and its
+//              conversion to Chebyshev coefficients (T_pw2poly); leaves then
+//              evaluate Lambda at their targets (Step 3 "Evaluate local
+//              expansions")
 //   k_near     residual kernels R_{L(j)} over the interaction lists (Step 4),
 //              including the self correction of Step 5 (r = 0 terms)
 #include "passes.h"
@@ -37,7 +46,7 @@
 namespace dmk {
 
 constexpr int kThreads = 256;
-constexpr int kCH = 32;  // points per staging chunk
+constexpr int kCH = 32;  // points per staging chunk in k_upward
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
@@ -62,6 +71,22 @@ template <typename U>
 __device__ __forceinline__ U *buf_ptr(const BufLayout &lay, int i, char *sm, char *slab) {
     return lay.in_smem[i] ? reinterpret_cast<U *>(sm + lay.off[i])
                           : reinterpret_cast<U *>(slab + (size_t)blockIdx.x * lay.slab_bytes + lay.off[i]);
+}
+
+template <typename C2, typename T>
+__device__ __forceinline__ void cfma(C2 &acc, T h, const C2 &v) {
+    acc.x += h * v.x;
+    acc.y += h * v.y;
+}
+
+// hs[n][m'] = Re F[m'][n] (n even) or Im F[m'][n] (n odd), m' = 0..NF
+template <typename T, int P, int NF>
+__device__ __forceinline__ void load_hs(const DevTables<T> &tb, T *hs) {
+    constexpr int NH = NF + 1;
+    for (int i = threadIdx.x; i < P * NH; i += blockDim.x) {
+        const int n = i / NH, m = i % NH;
+        hs[i] = (n & 1) ? tb.Fi[(m + NF) * P + n] : tb.Fr[(m + NF) * P + n];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -181,27 +206,22 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
 }
 
 // ---------------------------------------------------------------------------
-// Outgoing expansions (Step 3, T_prox2pw)
+// Outgoing expansions (Step 3, T_prox2pw), parity-split
 // ---------------------------------------------------------------------------
-template <typename T, int P>
+template <typename T, int P, int NF>
 __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> tb, int nslots,
                                                       const int32_t *slot2box, const T *M,
                                                       typename Cplx<T>::type *Phi, BufLayout lay, char *slab) {
     using C2 = typename Cplx<T>::type;
     extern __shared__ __align__(128) char sm[];
-    constexpr int P3 = P * P * P;
-    const int nf = tb.nf, N1 = tb.N1, nh = tb.nh;
+    constexpr int P3 = P * P * P, NH = NF + 1, N1 = 2 * NF + 1;
     T *Mb = buf_ptr<T>(lay, 0, sm, slab);
-    C2 *T1 = buf_ptr<C2>(lay, 1, sm, slab);   // [a][b][mz]
-    C2 *T2 = buf_ptr<C2>(lay, 2, sm, slab);   // [a][mz] for one my
-    T *Fs = buf_ptr<T>(lay, 3, sm, slab);     // Fr [N1][P], then Fi
+    C2 *T1 = buf_ptr<C2>(lay, 1, sm, slab);  // [a][b][mz]
+    C2 *T2 = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my + NF][mz]
+    T *hs = buf_ptr<T>(lay, 3, sm, slab);    // [n][m']
     const int tid = threadIdx.x;
-    for (int i = tid; i < N1 * P; i += kThreads) {
-        Fs[i] = tb.Fr[i];
-        Fs[N1 * P + i] = tb.Fi[i];
-    }
-    const T *Fr = Fs, *Fi = Fs + N1 * P;
-    const size_t stride = (size_t)N1 * N1 * nh;
+    load_hs<T, P, NF>(tb, hs);
+    const size_t stride = (size_t)N1 * N1 * NH;
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
         const int B = slot2box[slot];
         if (!(tv.bflags[B] & BF_FOUT)) continue;
@@ -209,45 +229,53 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
         const T *Ms = M + (size_t)slot * P3;
         for (int i = tid; i < P3; i += kThreads) Mb[i] = Ms[i];
         __syncthreads();
-        for (int i = tid; i < P * P * nh; i += kThreads) {
-            const int mz = i % nh, ab = i / nh;
-            const T *fr = Fr + (mz + nf) * P, *fi = Fi + (mz + nf) * P;
-            T re = 0, im = 0;
-#pragma unroll 6
+        // z: T1[a][b][mz] = sum_{c even} Fr M + i sum_{c odd} Fi M, mz >= 0
+        for (int ab = tid; ab < P * P; ab += kThreads) {
+            T E[NH], O[NH];
+#pragma unroll
+            for (int m = 0; m < NH; ++m) E[m] = O[m] = (T)0;
+            const T *row = Mb + ab * P;
+#pragma unroll 2
             for (int c = 0; c < P; ++c) {
-                const T m = Mb[ab * P + c];
-                re += fr[c] * m;
-                im += fi[c] * m;
+                const T v = row[c];
+                const T *h = hs + c * NH;
+                if (c & 1) {
+#pragma unroll
+                    for (int m = 0; m < NH; ++m) O[m] += h[m] * v;
+                } else {
+#pragma unroll
+                    for (int m = 0; m < NH; ++m) E[m] += h[m] * v;
+                }
             }
-            T1[i] = C2{re, im};
+#pragma unroll
+            for (int m = 0; m < NH; ++m) T1[ab * NH + m] = C2{E[m], O[m]};
         }
         __syncthreads();
+        // y: T2[a][+-my'][mz] = E +- i O
+        for (int it = tid; it < P * NH * NH; it += kThreads) {
+            const int a = it / (NH * NH), r = it % (NH * NH), myp = r / NH, mz = r % NH;
+            C2 E{0, 0}, O{0, 0};
+            for (int b = 0; b < P; ++b) {
+                const C2 t = T1[(a * P + b) * NH + mz];
+                const T h = hs[b * NH + myp];
+                if (b & 1) cfma(O, h, t); else cfma(E, h, t);
+            }
+            T2[(a * N1 + NF + myp) * NH + mz] = C2{E.x - O.y, E.y + O.x};
+            if (myp > 0) T2[(a * N1 + NF - myp) * NH + mz] = C2{E.x + O.y, E.y - O.x};
+        }
+        __syncthreads();
+        // x: Phi[my][+-mx'][mz] = E +- i O
         C2 *out = Phi + (size_t)slot * stride;
-        for (int my = 0; my < N1; ++my) {
-            const T *fr = Fr + my * P, *fi = Fi + my * P;
-            for (int i = tid; i < P * nh; i += kThreads) {
-                const int a = i / nh, mz = i % nh;
-                T re = 0, im = 0;
-                for (int b = 0; b < P; ++b) {
-                    const C2 t = T1[(a * P + b) * nh + mz];
-                    re += fr[b] * t.x - fi[b] * t.y;
-                    im += fr[b] * t.y + fi[b] * t.x;
-                }
-                T2[i] = C2{re, im};
+        for (int it = tid; it < N1 * NH * NH; it += kThreads) {
+            const int my = it / (NH * NH), r = it % (NH * NH), mxp = r / NH, mz = r % NH;
+            C2 E{0, 0}, O{0, 0};
+            for (int a = 0; a < P; ++a) {
+                const C2 t = T2[(a * N1 + my) * NH + mz];
+                const T h = hs[a * NH + mxp];
+                if (a & 1) cfma(O, h, t); else cfma(E, h, t);
             }
-            __syncthreads();
-            for (int i = tid; i < N1 * nh; i += kThreads) {
-                const int mx = i / nh, mz = i % nh;
-                const T *gr = Fr + mx * P, *gi = Fi + mx * P;
-                T re = 0, im = 0;
-                for (int a = 0; a < P; ++a) {
-                    const C2 t = T2[a * nh + mz];
-                    re += gr[a] * t.x - gi[a] * t.y;
-                    im += gr[a] * t.y + gi[a] * t.x;
-                }
-                out[(size_t)(my * N1 + mx) * nh + mz] = C2{re, im};
-            }
-            __syncthreads();
+            out[(size_t)(my * N1 + NF + mxp) * NH + mz] = C2{E.x - O.y, E.y + O.x};
+            if (mxp > 0) out[(size_t)(my * N1 + NF - mxp) * NH + mz] = C2{E.x + O.y, E.y - O.x};
         }
     }
 }
@@ -346,32 +374,40 @@ __global__ void __launch_bounds__(kThreads) k_root(TreeView tv, DevTables<T> tb,
 }
 
 // ---------------------------------------------------------------------------
-// Local expansions and leaf evaluation (Step 3)
+// Local expansions and leaf evaluation (Step 3), parity-split
 // ---------------------------------------------------------------------------
-template <typename T, int P>
-__global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb, int level, int lstart, int lcount,
-                                                    const typename Cplx<T>::type *Phi, T *Lam, const T *LamW,
-                                                    double *ufar, BufLayout lay, char *slab) {
+constexpr int kLThreads = 512;
+constexpr int kECH = 64;  // targets per evaluation chunk (8 threads per target)
+
+template <int P, int NF> struct LocalShape {
+    static constexpr int NH = NF + 1, N1 = 2 * NF + 1;
+    static constexpr int AG = (P + 6) / 7, AC = (P + AG - 1) / AG;  // phase B: a-groups, a per group
+    static constexpr int BG = (P + 7) / 8, BC = (P + BG - 1) / BG;  // phase C
+    static constexpr int CG = (P + 8) / 9, CC = (P + CG - 1) / CG;  // phase D
+};
+
+template <typename T, int P, int NF>
+__global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T> tb, int level, int lstart,
+                                                        int lcount, const typename Cplx<T>::type *Phi, T *Lam,
+                                                        const T *LamW, double *ufar, BufLayout lay, char *slab) {
     using C2 = typename Cplx<T>::type;
+    using S = LocalShape<P, NF>;
+    constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P;
     extern __shared__ __align__(128) char sm[];
-    constexpr int P3 = P * P * P;
-    const int nf = tb.nf, N1 = tb.N1, nh = tb.nh;
     T *Ls = buf_ptr<T>(lay, 0, sm, slab);
-    C2 *T1 = buf_ptr<C2>(lay, 1, sm, slab);  // [a][my][mz]; also p2c scratch b0
-    C2 *T2 = buf_ptr<C2>(lay, 2, sm, slab);  // [a][b][mz]; also p2c scratch b1
-    C2 *Ps = buf_ptr<C2>(lay, 3, sm, slab);  // [mx][mz] one my slice of Psi
-    T *Fs = buf_ptr<T>(lay, 4, sm, slab);    // Fr [N1][P], Fi
-    T *ev = buf_ptr<T>(lay, 5, sm, slab);    // [3][kCH][P]
+    C2 *PsE = buf_ptr<C2>(lay, 1, sm, slab);  // [my + NF][mx'][mz]; PsO follows
+    C2 *PsO = PsE + N1 * NH * NH;
+    C2 *T2 = PsE;                              // [a][b][mz], reuses the Psi buffers
+    C2 *T1e = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my'][mz]; T1o follows
+    C2 *T1o = T1e + P * NH * NH;
+    T *hs = buf_ptr<T>(lay, 3, sm, slab);
+    T *ev = buf_ptr<T>(lay, 4, sm, slab);     // [3][kECH][P]
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
     const int tid = threadIdx.x;
-    for (int i = tid; i < N1 * P; i += kThreads) {
-        Fs[i] = tb.Fr[i];
-        Fs[N1 * P + i] = tb.Fi[i];
-    }
-    const T *Fr = Fs, *Fi = Fs + N1 * P;
-    const size_t pstride = (size_t)N1 * N1 * nh;
+    load_hs<T, P, NF>(tb, hs);
+    const size_t pstride = (size_t)N1 * N1 * NH;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
     for (int it = blockIdx.x; it < lcount; it += gridDim.x) {
@@ -379,35 +415,35 @@ __global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb
         if (tv.bntgt[B] == 0) continue;
         const uint8_t fl = tv.bflags[B];
         __syncthreads();
-        // ---- parent's local expansion, re-centred (T_p2c) or the root term
+        // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
         if (level == 0) {
-            for (int i = tid; i < P3; i += kThreads) Ls[i] = LamW[i];
+            for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[i];
         } else {
-            T *b0 = reinterpret_cast<T *>(T1);
-            T *b1 = reinterpret_cast<T *>(T2);
+            T *b0 = reinterpret_cast<T *>(PsE);
+            T *b1 = reinterpret_cast<T *>(PsO);
             const int Pb = tv.bparent[B];
             const T *Lp = Lam + (size_t)tv.bslot[Pb] * P3;
-            for (int i = tid; i < P3; i += kThreads) b0[i] = Lp[i];
+            for (int i = tid; i < P3; i += kLThreads) b0[i] = Lp[i];
             __syncthreads();
             const int oc = (int)(tv.bkey[B] & 7ull);
             const T *Ax = tb.A + (oc & 1) * P * P;
             const T *Ay = tb.A + ((oc >> 1) & 1) * P * P;
             const T *Az = tb.A + ((oc >> 2) & 1) * P * P;
-            for (int i = tid; i < P3; i += kThreads) {
+            for (int i = tid; i < P3; i += kLThreads) {
                 const int m = i % P, ab = i / P;
                 T s = 0;
                 for (int n = m; n < P; ++n) s += Az[n * P + m] * b0[ab * P + n];
                 b1[i] = s;
             }
             __syncthreads();
-            for (int i = tid; i < P3; i += kThreads) {
+            for (int i = tid; i < P3; i += kLThreads) {
                 const int c = i % P, m = (i / P) % P, a = i / (P * P);
                 T s = 0;
                 for (int n = m; n < P; ++n) s += Ay[n * P + m] * b1[(a * P + n) * P + c];
                 b0[i] = s;
             }
             __syncthreads();
-            for (int i = tid; i < P3; i += kThreads) {
+            for (int i = tid; i < P3; i += kLThreads) {
                 const int bc = i % (P * P), m = i / (P * P);
                 T s = 0;
                 for (int n = m; n < P; ++n) s += Ax[n * P + m] * b0[n * P * P + bc];
@@ -420,84 +456,152 @@ __global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb
             if (tid == 0) {
                 int nc = 0;
                 for (int k = 0; k < 27; ++k) {
-                    const int S = tv.bcol[(size_t)B * 27 + k];
-                    if (S < 0 || !(tv.bflags[S] & BF_FOUT)) continue;
-                    s_cslot[nc] = tv.bslot[S];
-                    // delta = (c_B - c_S) / R = -(dx, dy, dz)
-                    s_cd[nc][0] = 1 - k / 9;
-                    s_cd[nc][1] = 1 - (k / 3) % 3;
-                    s_cd[nc][2] = 1 - k % 3;
+                    const int Sb = tv.bcol[(size_t)B * 27 + k];
+                    if (Sb < 0 || !(tv.bflags[Sb] & BF_FOUT)) continue;
+                    s_cslot[nc] = tv.bslot[Sb];
+                    // delta = (c_B - c_S) / R = -(dx, dy, dz), stored mod 3 as 0..2
+                    s_cd[nc][0] = (1 - k / 9 + 3) % 3;
+                    s_cd[nc][1] = (1 - (k / 3) % 3 + 3) % 3;
+                    s_cd[nc][2] = (1 - k % 3 + 3) % 3;
                     ++nc;
                 }
                 s_ncol = nc;
             }
             __syncthreads();
             const int ncol = s_ncol;
-            for (int my = 0; my < N1; ++my) {
-                const int myv = my - nf;
-                for (int i = tid; i < N1 * nh; i += kThreads) {
-                    const int mx = i / nh, mz = i % nh, mxv = mx - nf;
-                    T re = 0, im = 0;
-                    for (int j = 0; j < ncol; ++j) {
-                        int ph = mxv * s_cd[j][0] + myv * s_cd[j][1] + mz * s_cd[j][2];
-                        ph = ((ph % 3) + 3) % 3;
-                        const C2 v = Phi[(size_t)s_cslot[j] * pstride + (size_t)(my * N1 + mx) * nh + mz];
-                        // multiply by exp(2 pi i ph / 3)
-                        if (ph == 0) {
-                            re += v.x;
-                            im += v.y;
-                        } else if (ph == 1) {
-                            re += (T)-0.5 * v.x - kH * v.y;
-                            im += kH * v.x + (T)-0.5 * v.y;
-                        } else {
-                            re += (T)-0.5 * v.x + kH * v.y;
-                            im += -kH * v.x + (T)-0.5 * v.y;
-                        }
+            // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x
+            for (int i = tid; i < N1 * NH * NH; i += kLThreads) {
+                const int my = i / (NH * NH), r = i % (NH * NH), mxp = r / NH, mz = r % NH;
+                const int myv = my - NF;
+                const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3, rz = mz % 3;
+                C2 Tp{0, 0}, Up{0, 0}, Dp{0, 0}, Tm{0, 0}, Um{0, 0}, Dm{0, 0};
+                const size_t off_p = (size_t)(my * N1 + NF + mxp) * NH + mz;
+                const size_t off_m = (size_t)(my * N1 + NF - mxp) * NH + mz;
+                for (int j = 0; j < ncol; ++j) {
+                    const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
+                    const int kyz = ry * s_cd[j][1] + rz * s_cd[j][2];
+                    const int kp = (rxp * s_cd[j][0] + kyz) % 3;
+                    const int km = (rxm * s_cd[j][0] + kyz) % 3;
+                    const C2 vp = ph[off_p];
+                    Tp.x += vp.x; Tp.y += vp.y;
+                    const T up = kp ? (T)1 : (T)0, dp = kp == 1 ? (T)1 : (kp == 2 ? (T)-1 : (T)0);
+                    cfma(Up, up, vp);
+                    cfma(Dp, dp, vp);
+                    if (mxp > 0) {
+                        const C2 vm = ph[off_m];
+                        Tm.x += vm.x; Tm.y += vm.y;
+                        const T um = km ? (T)1 : (T)0, dm = km == 1 ? (T)1 : (km == 2 ? (T)-1 : (T)0);
+                        cfma(Um, um, vm);
+                        cfma(Dm, dm, vm);
                     }
-                    const T w = tb.w[mxv * mxv + myv * myv + mz * mz] * invR;
-                    Ps[i] = C2{re * w, im * w};
                 }
-                __syncthreads();
-                for (int i = tid; i < P * nh; i += kThreads) {
-                    const int a = i / nh, mz = i % nh;
-                    T re = 0, im = 0;
-                    for (int mx = 0; mx < N1; ++mx) {
-                        const C2 t = Ps[mx * nh + mz];
-                        const T gr = Fr[mx * P + a], gi = Fi[mx * P + a];  // G = gr - i gi
-                        re += gr * t.x + gi * t.y;
-                        im += gr * t.y - gi * t.x;
-                    }
-                    T1[(a * N1 + my) * nh + mz] = C2{re, im};
+                const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
+                // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
+                const C2 psp{w * (Tp.x - (T)1.5 * Up.x - kH * Dp.y), w * (Tp.y - (T)1.5 * Up.y + kH * Dp.x)};
+                const size_t o = (size_t)(my * NH + mxp) * NH + mz;
+                if (mxp > 0) {
+                    const C2 psm{w * (Tm.x - (T)1.5 * Um.x - kH * Dm.y), w * (Tm.y - (T)1.5 * Um.y + kH * Dm.x)};
+                    PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
+                    PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
+                } else {
+                    PsE[o] = psp;
+                    PsO[o] = C2{0, 0};
                 }
-                __syncthreads();
-            }
-            for (int i = tid; i < P * P * nh; i += kThreads) {
-                const int mz = i % nh, b = (i / nh) % P, a = i / (nh * P);
-                T re = 0, im = 0;
-                for (int my = 0; my < N1; ++my) {
-                    const C2 t = T1[(a * N1 + my) * nh + mz];
-                    const T gr = Fr[my * P + b], gi = Fi[my * P + b];
-                    re += gr * t.x + gi * t.y;
-                    im += gr * t.y - gi * t.x;
-                }
-                T2[i] = C2{re, im};
             }
             __syncthreads();
-            for (int i = tid; i < P3; i += kThreads) {
-                const int c = i % P, ab = i / P;
-                T s = 0;
-                for (int mz = 0; mz < nh; ++mz) {
-                    const C2 t = T2[ab * nh + mz];
-                    const T cz = mz == 0 ? (T)1 : (T)2;
-                    s += cz * (Fr[(mz + nf) * P + c] * t.x + Fi[(mz + nf) * P + c] * t.y);
+            // phase B: contract m_x -> a, for m_y = +-my'; fold into even/odd in m_y
+            for (int i = tid; i < NH * NH * S::AG; i += kLThreads) {
+                const int ag = i / (NH * NH), r = i % (NH * NH), myp = r / NH, mz = r % NH;
+                C2 ap[S::AC], am[S::AC];
+#pragma unroll
+                for (int k = 0; k < S::AC; ++k) ap[k] = am[k] = C2{0, 0};
+                const int rp = (NF + myp) * NH, rm = (NF - myp) * NH;
+                for (int mxp = 0; mxp <= NF; ++mxp) {
+                    const C2 ep = PsE[(rp + mxp) * NH + mz], em = PsE[(rm + mxp) * NH + mz];
+                    const C2 op = PsO[(rp + mxp) * NH + mz], om = PsO[(rm + mxp) * NH + mz];
+#pragma unroll
+                    for (int k = 0; k < S::AC; ++k) {
+                        const int a = ag + S::AG * k;
+                        if (a < P) {
+                            const T h = hs[a * NH + mxp];
+                            if (a & 1) { cfma(ap[k], h, op); cfma(am[k], h, om); }
+                            else { cfma(ap[k], h, ep); cfma(am[k], h, em); }
+                        }
+                    }
                 }
-                Ls[i] += s;
+#pragma unroll
+                for (int k = 0; k < S::AC; ++k) {
+                    const int a = ag + S::AG * k;
+                    if (a >= P) continue;
+                    C2 vp = ap[k], vm = am[k];
+                    if (a & 1) {  // times -i
+                        vp = C2{vp.y, -vp.x};
+                        vm = C2{vm.y, -vm.x};
+                    }
+                    const int o = (a * NH + myp) * NH + mz;
+                    if (myp > 0) {
+                        T1e[o] = C2{vp.x + vm.x, vp.y + vm.y};
+                        T1o[o] = C2{vp.x - vm.x, vp.y - vm.y};
+                    } else {
+                        T1e[o] = vp;
+                        T1o[o] = C2{0, 0};
+                    }
+                }
+            }
+            __syncthreads();
+            // phase C: contract m_y -> b
+            for (int i = tid; i < P * NH * S::BG; i += kLThreads) {
+                const int bg = i / (P * NH), r = i % (P * NH), a = r / NH, mz = r % NH;
+                C2 acc[S::BC];
+#pragma unroll
+                for (int k = 0; k < S::BC; ++k) acc[k] = C2{0, 0};
+                for (int myp = 0; myp <= NF; ++myp) {
+                    const C2 te = T1e[(a * NH + myp) * NH + mz], to = T1o[(a * NH + myp) * NH + mz];
+#pragma unroll
+                    for (int k = 0; k < S::BC; ++k) {
+                        const int b = bg + S::BG * k;
+                        if (b < P) {
+                            const T h = hs[b * NH + myp];
+                            if (b & 1) cfma(acc[k], h, to); else cfma(acc[k], h, te);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < S::BC; ++k) {
+                    const int b = bg + S::BG * k;
+                    if (b >= P) continue;
+                    C2 v = acc[k];
+                    if (b & 1) v = C2{v.y, -v.x};
+                    T2[(a * P + b) * NH + mz] = v;
+                }
+            }
+            __syncthreads();
+            // phase D: contract m_z -> c (real part; m_z < 0 through Hermitian symmetry)
+            for (int i = tid; i < P * P * S::CG; i += kLThreads) {
+                const int cg = i / (P * P), ab = i % (P * P);
+                T acc[S::CC];
+#pragma unroll
+                for (int k = 0; k < S::CC; ++k) acc[k] = (T)0;
+                for (int mz = 0; mz <= NF; ++mz) {
+                    const C2 t = T2[ab * NH + mz];
+                    const T cz = mz ? (T)2 : (T)1;
+#pragma unroll
+                    for (int k = 0; k < S::CC; ++k) {
+                        const int c = cg + S::CG * k;
+                        if (c < P) acc[k] += cz * hs[c * NH + mz] * ((c & 1) ? t.y : t.x);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < S::CC; ++k) {
+                    const int c = cg + S::CG * k;
+                    if (c < P) Ls[ab * P + c] += acc[k];
+                }
             }
             __syncthreads();
         }
         if (!(fl & BF_LEAF)) {
             T *Lo = Lam + (size_t)tv.bslot[B] * P3;
-            for (int i = tid; i < P3; i += kThreads) Lo[i] = Ls[i];
+            for (int i = tid; i < P3; i += kLThreads) Lo[i] = Ls[i];
             continue;
         }
         // ---- leaf: evaluate the local expansion at its targets
@@ -506,11 +610,11 @@ __global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb
         const double R = level_R(level), s2R = 2.0 / R;
         const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
         const int s = tv.bstart[B], e = s + tv.bcount[B];
-        for (int p0 = s; p0 < e; p0 += kCH) {
-            const int np = min(kCH, e - p0);
-            for (int t = tid; t < 3 * kCH; t += kThreads) {
-                const int ax = t / kCH, j = t % kCH;
-                T *o = ev + (ax * kCH + j) * P;
+        for (int p0 = s; p0 < e; p0 += kECH) {
+            const int np = min(kECH, e - p0);
+            for (int t = tid; t < 3 * kECH; t += kLThreads) {
+                const int ax = t / kECH, j = t % kECH;
+                T *o = ev + (ax * kECH + j) * P;
                 if (j < np) {
                     const int kk = p0 + j;
                     const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
@@ -532,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb
             }
             __syncthreads();
             const int j = tid >> 3, g = tid & 7;
-            const T *tx = ev + j * P, *ty = ev + (kCH + j) * P, *tz = ev + (2 * kCH + j) * P;
+            const T *tx = ev + j * P, *ty = ev + (kECH + j) * P, *tz = ev + (2 * kECH + j) * P;
             T sum = 0;
             for (int a = g; a < P; a += 8) {
                 T sa = 0;
@@ -557,24 +661,37 @@ __global__ void __launch_bounds__(kThreads) k_local(TreeView tv, DevTables<T> tb
 // ---------------------------------------------------------------------------
 // Residual near field (Steps 4 and 5)
 // ---------------------------------------------------------------------------
+// One warp per target leaf, taken from an atomic work counter.  Lanes map to
+// (target, source subset) pairs: G lanes share a target and split its sources
+// when the leaf holds fewer than 32 targets.  Sources are read straight from
+// global memory (all lanes of a group read the same address, served by L1).
+// In single precision the coordinates are hi + lo pairs, relative to the leaf
+// centres, and the exact dyadic centre offset is added with a TwoSum, so the
+// difference of two nearby points keeps full relative precision; the sum over
+// a source leaf is compensated (Kahan) and then accumulated in double.
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-constexpr int kNearThreads = 128;
-constexpr int kNearChunk = 256;
+constexpr int kNearThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, const int32_t *tleaves,
                                                        const int32_t *nl_off, const int32_t *nl_src,
-                                                       const typename Vec4<T>::type *plocal, const T *qmono,
-                                                       int qdeg, double *unear) {
+                                                       const typename Vec4<T>::type *__restrict__ plocal,
+                                                       const float4 *__restrict__ plocal_lo, const T *qmono,
+                                                       int qdeg, double *unear, int *counter) {
     using V4 = typename Vec4<T>::type;
-    __shared__ V4 s_src[kNearChunk];
+    constexpr bool kHiLo = sizeof(T) == 4;
     __shared__ T s_q[64];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i <= qdeg; i += kNearThreads) s_q[i] = qmono[i];
-    for (int it = blockIdx.x; it < ntl; it += gridDim.x) {
+    __syncthreads();
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= ntl) break;
         const int Tb = tleaves[it];
         const int a = tv.blevel[Tb];
         int tx, ty, tz;
@@ -582,50 +699,68 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
         const double Ra = level_R(a);
         const double cT[3] = {(tx + 0.5) * Ra, (ty + 0.5) * Ra, (tz + 0.5) * Ra};
         const int ts = tv.bstart[Tb], nt = tv.bcount[Tb];
-        const int G = nt > 64 ? 1 : (nt > 32 ? 2 : 4);
-        const int per = kNearThreads / G;
+        const int G = nt >= 32 ? 1 : (nt >= 16 ? 2 : (nt >= 8 ? 4 : 8));
+        const int per = 32 / G;
         const int l0 = nl_off[it], l1 = nl_off[it + 1];
         for (int t0 = 0; t0 < nt; t0 += per) {
-            const int j = t0 + tid / G, g = tid % G;
+            const int j = t0 + lane / G, g = lane % G;
             const bool valid = j < nt;
             V4 xt;
-            if (valid) xt = plocal[ts + j];
-            else { xt.x = 0; xt.y = 0; xt.z = 0; xt.w = 0; }
+            float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                xt = plocal[ts + j];
+                if (kHiLo) xl = plocal_lo[ts + j];
+            } else {
+                xt.x = xt.y = xt.z = xt.w = (T)0;
+            }
             double acc = 0.0;
             for (int li = l0; li < l1; ++li) {
-                const int S = nl_src[li];
-                const int b = tv.blevel[S];
+                const int Sb = nl_src[li];
+                const int b = tv.blevel[Sb];
                 int sx, sy, sz;
-                morton_decode_d(tv.bkey[S], sx, sy, sz);
+                morton_decode_d(tv.bkey[Sb], sx, sy, sz);
                 const double Rb = level_R(b);
-                // exact dyadic centre difference
+                // exact dyadic centre difference, added to the target's local coordinate
                 const T dcx = (T)(cT[0] - (sx + 0.5) * Rb);
                 const T dcy = (T)(cT[1] - (sy + 0.5) * Rb);
                 const T dcz = (T)(cT[2] - (sz + 0.5) * Rb);
-                const T px = xt.x + dcx, py = xt.y + dcy, pz = xt.z + dcz;
+                T px = xt.x + dcx, py = xt.y + dcy, pz = xt.z + dcz;
+                T pxl = (T)0, pyl = (T)0, pzl = (T)0;
+                if (kHiLo) {  // TwoSum error terms plus the lo parts
+                    T bb = px - xt.x;
+                    pxl = ((xt.x - (px - bb)) + (dcx - bb)) + (T)xl.x;
+                    bb = py - xt.y;
+                    pyl = ((xt.y - (py - bb)) + (dcy - bb)) + (T)xl.y;
+                    bb = pz - xt.z;
+                    pzl = ((xt.z - (pz - bb)) + (dcz - bb)) + (T)xl.z;
+                }
                 const T invRb = (T)(double)(1u << b);
                 const T invRb2 = invRb * invRb;
                 const T Rb2 = (T)(Rb * Rb);
-                const int ss = tv.bstart[S], ns = tv.bcount[S];
-                for (int c0 = 0; c0 < ns; c0 += kNearChunk) {
-                    const int nc = min(kNearChunk, ns - c0);
-                    __syncthreads();
-                    for (int i = tid; i < nc; i += kNearThreads) s_src[i] = plocal[ss + c0 + i];
-                    __syncthreads();
-                    T part = 0;
-                    for (int jj = g; jj < nc; jj += G) {
-                        const V4 y = s_src[jj];
-                        const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        const T x = (T)2 * r2 * invRb2 - (T)1;
-                        T qv = s_q[qdeg];
-                        for (int d = qdeg - 1; d >= 0; --d) qv = qv * x + s_q[d];
-                        const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                        const T v = rinv - qv * invRb;
-                        part += (r2 < Rb2) ? y.w * v : (T)0;
+                const int ss = tv.bstart[Sb], ns = tv.bcount[Sb];
+                T part = 0, comp = 0;
+                for (int jj = g; jj < ns; jj += G) {
+                    const V4 y = plocal[ss + jj];
+                    T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
+                    if (kHiLo) {
+                        const float4 yl = plocal_lo[ss + jj];
+                        dx += pxl - (T)yl.x;
+                        dy += pyl - (T)yl.y;
+                        dz += pzl - (T)yl.z;
                     }
-                    acc += (double)part;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const T x = (T)2 * r2 * invRb2 - (T)1;
+                    T qv = s_q[qdeg];
+                    for (int d = qdeg - 1; d >= 0; --d) qv = qv * x + s_q[d];
+                    const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
+                    const T v = rinv - qv * invRb;
+                    const T term = (r2 < Rb2) ? y.w * v : (T)0;
+                    const T yk = term - comp;
+                    const T tk = part + yk;
+                    comp = (tk - part) - yk;
+                    part = tk;
                 }
+                acc += (double)part - (double)comp;
             }
             for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (valid && g == 0 && (tv.pflag[ts + j] & 2)) unear[ts + j] = acc;
@@ -675,16 +810,16 @@ static BufLayout make_layout(const std::vector<size_t> &sizes, size_t smem_limit
         }                                                                  \
     } while (0)
 
-template <typename T, int P>
+template <typename T, int P, int NF>
 static int run_passes_P(PassCtx &cx, std::string &err) {
     using C2 = typename Cplx<T>::type;
-    constexpr int P3 = P * P * P;
+    constexpr int P3 = P * P * P, NH = NF + 1, N1 = 2 * NF + 1;
     TreeView tv = cx.tree->view();
     const DevTables<T> &tb = *reinterpret_cast<const DevTables<T> *>(cx.tables);
+    if (tb.nf != NF || tb.p != P) { err = "table shape mismatch"; return DMK_ERR_INTERNAL; }
     cudaStream_t st = cx.st;
     Workspace &ws = *cx.ws;
     const int nslots = cx.tree->nslots;
-    const int N1 = tb.N1, nh = tb.nh;
     const size_t smem_limit = cx.smem_limit;
     const int64_t n = tv.n;
     const int maxgrid = cx.num_sms * 8;
@@ -692,7 +827,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     if (ws.ensure(cx.bufs->M, (int64_t)nslots * P3 * sizeof(T)) ||
         ws.ensure(cx.bufs->Lam, (int64_t)nslots * P3 * sizeof(T)) ||
         ws.ensure(cx.bufs->LamW, (int64_t)P3 * sizeof(T)) || ws.ensure(cx.bufs->ufar, n * 8) ||
-        ws.ensure(cx.bufs->unear, n * 8)) {
+        ws.ensure(cx.bufs->unear, n * 8) || ws.ensure(cx.bufs->counter, 64)) {
         err = "device allocation failed (expansions)";
         return DMK_ERR_OOM;
     }
@@ -703,6 +838,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     double *unear = (double *)cx.bufs->unear.p;
     PCK(cudaMemsetAsync(ufar, 0, n * 8, st));
     PCK(cudaMemsetAsync(unear, 0, n * 8, st));
+    PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 64, st));
 
     // ---- upward pass (finest level first)
     cudaEventRecord(cx.ev[1], st);
@@ -724,21 +860,22 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     }
     // ---- outgoing expansions of every F_out box
     cudaEventRecord(cx.ev[2], st);
-    if (ws.ensure(cx.bufs->Phi, (int64_t)nslots * N1 * N1 * nh * sizeof(C2))) {
+    if (ws.ensure(cx.bufs->Phi, (int64_t)nslots * N1 * N1 * NH * sizeof(C2))) {
         err = "device allocation failed (plane waves)";
         return DMK_ERR_OOM;
     }
     C2 *Phi = (C2 *)cx.bufs->Phi.p;
     if (!cx.tree->root_leaf && nslots > 0) {
-        BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * P * nh * sizeof(C2), (size_t)P * nh * sizeof(C2),
-                                     (size_t)2 * N1 * P * sizeof(T)},
+        BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * P * NH * sizeof(C2), (size_t)P * N1 * NH * sizeof(C2),
+                                     (size_t)P * NH * sizeof(T)},
                                     smem_limit);
-        PCK(cudaFuncSetAttribute(k_prox2pw<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
+        PCK(cudaFuncSetAttribute(k_prox2pw<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lay.smem_bytes));
         int grid = std::min(nslots, maxgrid);
         if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
         ::dmk::launch_tick();
-        k_prox2pw<T, P><<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, nslots, (const int32_t *)cx.tree->slot2box.p,
-                                                                M, Phi, lay, (char *)cx.bufs->slab.p);
+        k_prox2pw<T, P, NF><<<grid, kThreads, lay.smem_bytes, st>>>(
+            tv, tb, nslots, (const int32_t *)cx.tree->slot2box.p, M, Phi, lay, (char *)cx.bufs->slab.p);
         PCK(cudaGetLastError());
     }
     // ---- root windowed term
@@ -753,33 +890,33 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     }
     // ---- local expansions, coarsest level first; leaves evaluate
     {
-        BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * N1 * nh * sizeof(C2),
-                                     (size_t)P * P * nh * sizeof(C2), (size_t)N1 * nh * sizeof(C2),
-                                     (size_t)2 * N1 * P * sizeof(T), 3 * kCH * P * sizeof(T)},
+        BufLayout lay = make_layout({P3 * sizeof(T), (size_t)2 * N1 * NH * NH * sizeof(C2),
+                                     (size_t)2 * P * NH * NH * sizeof(C2), (size_t)P * NH * sizeof(T),
+                                     (size_t)3 * kECH * P * sizeof(T)},
                                     smem_limit - 2048);
-        // the p2c scratch aliases the T1 / T2 buffers; they must hold P^3 values each
-        PCK(cudaFuncSetAttribute(k_local<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
+        PCK(cudaFuncSetAttribute(k_local<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         for (int l = 0; l < tv.nlev; ++l) {
             int lc = tv.lev_count[l];
-            int grid = std::min(lc, maxgrid);
+            int grid = std::min(lc, cx.num_sms * 2);
             if (grid <= 0) continue;
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
-            k_local<T, P><<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, l, tv.lev_start[l], lc, Phi, Lam, LamW,
-                                                                  ufar, lay, (char *)cx.bufs->slab.p);
+            k_local<T, P, NF><<<grid, kLThreads, lay.smem_bytes, st>>>(tv, tb, l, tv.lev_start[l], lc, Phi, Lam,
+                                                                       LamW, ufar, lay, (char *)cx.bufs->slab.p);
         }
         PCK(cudaGetLastError());
     }
     // ---- residual near field and self corrections
     cudaEventRecord(cx.ev[3], st);
     if (cx.tree->ntleaves > 0) {
-        int grid = std::min(cx.tree->ntleaves, cx.num_sms * 16);
+        int grid = std::min((cx.tree->ntleaves + 7) / 8, cx.num_sms * 8);
         ::dmk::launch_tick();
         k_near<T><<<grid, kNearThreads, 0, st>>>(tv, cx.tree->ntleaves, (const int32_t *)cx.tree->tleaves.p,
                                                  (const int32_t *)cx.tree->nl_off.p,
                                                  (const int32_t *)cx.tree->nl_src.p,
-                                                 (const typename Vec4<T>::type *)cx.tree->plocal.p, tb.qmono, tb.qdeg,
-                                                 unear);
+                                                 (const typename Vec4<T>::type *)cx.tree->plocal.p,
+                                                 (const float4 *)cx.tree->plocal_lo.p, tb.qmono, tb.qdeg, unear,
+                                                 (int *)cx.bufs->counter.p);
         PCK(cudaGetLastError());
     }
     cudaEventRecord(cx.ev[4], st);
@@ -793,13 +930,14 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
 
 template <typename T>
 static int run_passes_T(PassCtx &cx, std::string &err) {
-    switch (cx.p) {
-    case 9: return run_passes_P<T, 9>(cx, err);
-    case 18: return run_passes_P<T, 18>(cx, err);
-    case 28: return run_passes_P<T, 28>(cx, err);
-    case 38: return run_passes_P<T, 38>(cx, err);
-    default: err = "Chebyshev order must be one of 9, 18, 28, 38 (Table 1)"; return DMK_ERR_UNSUPPORTED;
-    }
+    const DevTables<T> &tb = *reinterpret_cast<const DevTables<T> *>(cx.tables);
+    if (cx.p == 9 && tb.nf == 6) return run_passes_P<T, 9, 6>(cx, err);
+    if (cx.p == 18 && tb.nf == 12) return run_passes_P<T, 18, 12>(cx, err);
+    if (cx.p == 19 && tb.nf == 12) return run_passes_P<T, 19, 12>(cx, err);
+    if (cx.p == 28 && tb.nf == 19) return run_passes_P<T, 28, 19>(cx, err);
+    if (cx.p == 38 && tb.nf == 26) return run_passes_P<T, 38, 26>(cx, err);
+    err = "(p, nf) must be one of (9,6), (18,12), (19,12), (28,19), (38,26)";
+    return DMK_ERR_UNSUPPORTED;
 }
 
 int run_passes(PassCtx &cx, std::string &err) {

@@ -15,7 +15,7 @@ struct BufLayout {
 };
 
 struct PassBufs {
-    DBuf M, Lam, LamW, Phi, ufar, unear, slab, rootscr;
+    DBuf M, Lam, LamW, Phi, ufar, unear, slab, rootscr, counter;
 };
 
 struct PassCtx {

@@ -372,12 +372,14 @@ __global__ void k_slot2box(int nb, const int32_t *bslot, int32_t *slot2box) {
     if (s >= 0) slot2box[s] = b;
 }
 
-// leaf index and leaf-local coordinates of every point
+// leaf index and leaf-local coordinates of every point; in single precision
+// the coordinates are split into hi + lo parts (double-float) so that
+// differences of nearby points keep their relative precision
 template <typename T>
 __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel, const int32_t *bstart,
                               const int32_t *bcount, const uint8_t *bflags, const double *ux, const double *uy,
                               const double *uz, const double *q, const uint8_t *pflag, int32_t *pleaf,
-                              typename Vec4<T>::type *plocal) {
+                              typename Vec4<T>::type *plocal, float4 *plocal_lo) {
     int b = blockIdx.x;
     if (b >= nb || !(bflags[b] & BF_LEAF)) return;
     int l = blevel[b];
@@ -389,11 +391,20 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
     for (int32_t k = s + threadIdx.x; k < e; k += blockDim.x) {
         pleaf[k] = b;
         typename Vec4<T>::type v;
-        v.x = (T)(ux[k] - cx);
-        v.y = (T)(uy[k] - cy);
-        v.z = (T)(uz[k] - cz);
+        const double dx = ux[k] - cx, dy = uy[k] - cy, dz = uz[k] - cz;
+        v.x = (T)dx;
+        v.y = (T)dy;
+        v.z = (T)dz;
         v.w = (pflag[k] & 1) ? (T)q[k] : (T)0;
         plocal[k] = v;
+        if (plocal_lo) {
+            float4 lo;
+            lo.x = (float)(dx - (double)v.x);
+            lo.y = (float)(dy - (double)v.y);
+            lo.z = (float)(dz - (double)v.z);
+            lo.w = 0.f;
+            plocal_lo[k] = lo;
+        }
     }
 }
 
@@ -566,6 +577,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         ws.ensure(sort_tmp, radix_tmp_bytes(N)) || ws.ensure(ux, N * 8) || ws.ensure(uy, N * 8) ||
         ws.ensure(uz, N * 8) || ws.ensure(q, N * 8) || ws.ensure(pflag, N) || ws.ensure(pout, N * 4) ||
         ws.ensure(pleaf, N * 4) || ws.ensure(plocal, N * (point_prec ? 16 : 32)) ||
+        ws.ensure(plocal_lo, point_prec ? N * 16 : 16) ||
         ws.ensure(pscan0, (N + 1) * 4) || ws.ensure(pscan1, (N + 1) * 4) ||
         ws.ensure(scan_tmp, scan_tmp_bytes(std::max<int64_t>(N + 1, 1 << 20)))) {
         err = "device allocation failed (points)";
@@ -759,7 +771,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
                                                  (const uint8_t *)bflags.p, (const double *)ux.p,
                                                  (const double *)uy.p, (const double *)uz.p, (const double *)q.p,
                                                  (const uint8_t *)pflag.p, (int32_t *)pleaf.p,
-                                                 (float4 *)plocal.p);
+                                                 (float4 *)plocal.p, (float4 *)plocal_lo.p);
         }
     else
         { ::dmk::launch_tick();
@@ -768,7 +780,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
                                                   (const uint8_t *)bflags.p, (const double *)ux.p,
                                                   (const double *)uy.p, (const double *)uz.p, (const double *)q.p,
                                                   (const uint8_t *)pflag.p, (int32_t *)pleaf.p,
-                                                  (double4_32a *)plocal.p);
+                                                  (double4_32a *)plocal.p, nullptr);
         }
 
     // ---- near-field lists over target leaves

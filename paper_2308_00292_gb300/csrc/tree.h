@@ -90,7 +90,8 @@ public:
     const uint32_t *sorted_idx = nullptr;
 
     // points (sorted)
-    DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, pscan0, pscan1, scan_tmp;
+    DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, plocal_lo, pscan0, pscan1,
+        scan_tmp;
     DBuf bbox_part, frame, flags, forced;
     // boxes
     int64_t box_cap = 0;
