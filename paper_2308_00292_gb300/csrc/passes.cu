@@ -89,6 +89,71 @@ __device__ __forceinline__ void load_hs(const DevTables<T> &tb, T *hs) {
     }
 }
 
+// four consecutive values (16-byte aligned) from shared memory
+template <typename T> __device__ __forceinline__ void ld4(const T *p, T (&v)[4]);
+template <> __device__ __forceinline__ void ld4<float>(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <> __device__ __forceinline__ void ld4<double>(const double *p, double (&v)[4]) {
+    const double2 t0 = *reinterpret_cast<const double2 *>(p), t1 = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+// padded row strides of the upward pass's staging buffers (multiples of 4)
+template <int P> struct UpShape {
+    static constexpr int PS = (P + 3) & ~3, YS = (P * P + 3) & ~3;
+};
+
+// One axis of the child-to-parent moment shift on a P^3 array:
+// out[.., n, ..] (+)= sum_{m <= n} A[n][m] in[.., m, ..] along axis AX (0 = z,
+// the fastest index, 1 = y, 2 = x); two rows per thread, A from shared memory.
+template <typename T, int P, int AX, int NT, bool ACC>
+__device__ __forceinline__ void shift_up(const T *__restrict__ A, const T *in, T *out) {
+    constexpr int s = AX == 0 ? 1 : (AX == 1 ? P : P * P);
+    if constexpr (P > 20) {  // large orders: one output per thread (registers)
+        for (int i = threadIdx.x; i < P * P * P; i += NT) {
+            const int n = AX == 0 ? i % P : (AX == 1 ? (i / P) % P : i / (P * P));
+            const int b = i - n * s;
+            T acc = 0;
+            for (int m = 0; m <= n; ++m) acc += A[n * P + m] * in[b + m * s];
+            if (ACC) out[i] += acc; else out[i] = acc;
+        }
+        return;
+    }
+    constexpr bool TWO = true;
+    constexpr int RR = P * P, H = TWO ? (RR + 1) / 2 : RR;
+    auto base = [](int r) { return AX == 0 ? r * P : (AX == 1 ? (r / P) * P * P + r % P : r); };
+    for (int t = threadIdx.x; t < H; t += NT) {
+        const int r0 = t, r1 = t + H;
+        const bool has1 = TWO && r1 < RR;
+        const int b0 = base(r0), b1 = has1 ? base(r1) : b0;
+        T o0[P], o1[P];
+#pragma unroll
+        for (int n = 0; n < P; ++n) o0[n] = o1[n] = (T)0;
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            const T v0 = in[b0 + m * s], v1 = in[b1 + m * s];
+#pragma unroll
+            for (int n = m; n < P; ++n) {
+                const T a = A[n * P + m];
+                o0[n] += a * v0;
+                if (TWO) o1[n] += a * v1;
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < P; ++n) {
+            if (ACC) out[b0 + n * s] += o0[n]; else out[b0 + n * s] = o0[n];
+        }
+        if (has1) {
+#pragma unroll
+            for (int n = 0; n < P; ++n) {
+                if (ACC) out[b1 + n * s] += o1[n]; else out[b1 + n * s] = o1[n];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Upward pass (Step 2)
 // ---------------------------------------------------------------------------
@@ -97,11 +162,19 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
                                                      BufLayout lay, char *slab) {
     extern __shared__ __align__(128) char sm[];
     constexpr int P3 = P * P * P;
+    constexpr int PS = UpShape<P>::PS, YS = UpShape<P>::YS;
+    constexpr int NAG = (P + 3) / 4, NBCG = (P * P + 3) / 4;
     T *acc = buf_ptr<T>(lay, 0, sm, slab);
-    T *b0 = buf_ptr<T>(lay, 1, sm, slab);
-    T *b1 = buf_ptr<T>(lay, 2, sm, slab);
-    T *stg = buf_ptr<T>(lay, 3, sm, slab);  // [3][kCH][P]
+    // scratch shared by the two phases: staging + Y for the sources of leaf
+    // children, then two P^3 buffers for the moment shifts of non-leaf children
+    T *scr = buf_ptr<T>(lay, 1, sm, slab);
+    T *As = buf_ptr<T>(lay, 2, sm, slab);   // shift matrices A_{-1}, A_{+1}
+    T *stg = scr;                           // [3][kCH][PS]
+    T *Y = scr + 3 * kCH * PS;              // [kCH][YS]
+    T *b0 = scr, *b1 = scr + P3;
+    __shared__ int s_lstart[8], s_lpre[9];
     const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * P * P; i += kThreads) As[i] = tb.A[i];
     for (int it = blockIdx.x; it < lcount; it += gridDim.x) {
         const int B = lstart + it;
         const bool selfleaf = (tv.bflags[B] & BF_LEAF) != 0;
@@ -116,23 +189,35 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         __syncthreads();
         const int c0 = tv.bchild0[B];
         const unsigned cm = selfleaf ? 1u : tv.bcmask[B];
-        int k = 0;
-        for (int oc = 0; oc < 8; ++oc) {
-            if (!(cm & (1u << oc))) continue;
-            const int D = selfleaf ? B : c0 + k;
-            ++k;
-            if (tv.bnsrc[D] == 0) continue;
-            const bool dleaf = selfleaf || (tv.bflags[D] & BF_LEAF);
-            if (dleaf) {
-                // anterpolation of the leaf's sources onto this box's grid
-                const int s = tv.bstart[D], e = s + tv.bcount[D];
-                for (int p0 = s; p0 < e; p0 += kCH) {
-                    const int np = min(kCH, e - p0);
+        // point ranges of the leaf children (with sources), streamed as one sequence
+        if (tid == 0) {
+            int k = 0, nl = 0, tot = 0;
+            for (int oc = 0; oc < 8; ++oc) {
+                if (!(cm & (1u << oc))) continue;
+                const int D = selfleaf ? B : c0 + k;
+                ++k;
+                if (tv.bnsrc[D] == 0 || !(selfleaf || (tv.bflags[D] & BF_LEAF))) continue;
+                s_lstart[nl] = tv.bstart[D];
+                s_lpre[nl] = tot;
+                tot += tv.bcount[D];
+                ++nl;
+            }
+            for (int q = nl; q < 9; ++q) s_lpre[q] = tot;
+        }
+        __syncthreads();
+        const int ntot = s_lpre[8];
+        {
+            {
+                // anterpolation of the leaf children's sources onto this box's grid
+                for (int p0 = 0; p0 < ntot; p0 += kCH) {
+                    const int np = min(kCH, ntot - p0);
                     for (int t = tid; t < 3 * kCH; t += kThreads) {
                         const int ax = t / kCH, j = t % kCH;
-                        T *o = stg + (ax * kCH + j) * P;
+                        T *o = stg + (ax * kCH + j) * PS;
                         if (j < np) {
-                            const int kk = p0 + j;
+                            int seg = 0;
+                            while (seg < 7 && s_lpre[seg + 1] <= p0 + j) ++seg;
+                            const int kk = s_lstart[seg] + (p0 + j - s_lpre[seg]);
                             const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
                             const T xi = (T)((u - cc[ax]) * s2R);
                             const T w = ax == 0 ? (T)tv.q[kk] : (T)1;
@@ -152,50 +237,59 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
                         }
                     }
                     __syncthreads();
-                    for (int pr = tid; pr < P * P; pr += kThreads) {
-                        const int b = pr / P, c = pr % P;
-                        T r[P];
+                    // M[a][bc] += sum_j X[j][a] Y[j][bc], X = rho T_a(x), Y = T_b(y) T_c(z)
+                    for (int i = tid; i < kCH * YS; i += kThreads) {
+                        const int j = i / YS, bc = i % YS;
+                        Y[i] = bc < P * P ? stg[(kCH + j) * PS + bc / P] * stg[(2 * kCH + j) * PS + bc % P] : (T)0;
+                    }
+                    __syncthreads();
+                    for (int tile = tid; tile < NAG * NBCG; tile += kThreads) {
+                        const int ag = tile / NBCG, bg = tile % NBCG;
+                        T r[4][4];
 #pragma unroll
-                        for (int a = 0; a < P; ++a) r[a] = (T)0;
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) r[i][k] = (T)0;
                         for (int j = 0; j < np; ++j) {
-                            const T w = stg[(kCH + j) * P + b] * stg[(2 * kCH + j) * P + c];
-                            const T *tx = stg + j * P;
+                            T x[4], y[4];
+                            ld4(stg + j * PS + ag * 4, x);
+                            ld4(Y + j * YS + bg * 4, y);
 #pragma unroll
-                            for (int a = 0; a < P; ++a) r[a] += tx[a] * w;
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) r[i][k] += x[i] * y[k];
                         }
 #pragma unroll
-                        for (int a = 0; a < P; ++a) acc[(a * P + b) * P + c] += r[a];
+                        for (int i = 0; i < 4; ++i) {
+                            const int a = ag * 4 + i;
+                            if (a >= P) continue;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int bc = bg * 4 + k;
+                                if (bc < P * P) acc[a * P * P + bc] += r[i][k];
+                            }
+                        }
                     }
                     __syncthreads();
                 }
-            } else {
+            }
+        }
+        int k = 0;
+        for (int oc = 0; oc < 8 && !selfleaf; ++oc) {
+            if (!(cm & (1u << oc))) continue;
+            const int D = c0 + k;
+            ++k;
+            if (tv.bnsrc[D] == 0 || (tv.bflags[D] & BF_LEAF)) continue;
+            {
                 // T_c2p: parent moments from child moments, exact
                 const T *Mc = M + (size_t)tv.bslot[D] * P3;
                 for (int i = tid; i < P3; i += kThreads) b0[i] = Mc[i];
                 __syncthreads();
-                const T *Ax = tb.A + (oc & 1) * P * P;
-                const T *Ay = tb.A + ((oc >> 1) & 1) * P * P;
-                const T *Az = tb.A + ((oc >> 2) & 1) * P * P;
-                for (int i = tid; i < P3; i += kThreads) {
-                    const int n = i % P, ab = i / P;
-                    T s = (T)0;
-                    for (int m = 0; m <= n; ++m) s += Az[n * P + m] * b0[ab * P + m];
-                    b1[i] = s;
-                }
+                shift_up<T, P, 0, kThreads, false>(As + ((oc >> 2) & 1) * P * P, b0, b1);
                 __syncthreads();
-                for (int i = tid; i < P3; i += kThreads) {
-                    const int c = i % P, n = (i / P) % P, a = i / (P * P);
-                    T s = (T)0;
-                    for (int m = 0; m <= n; ++m) s += Ay[n * P + m] * b1[(a * P + m) * P + c];
-                    b0[i] = s;
-                }
+                shift_up<T, P, 1, kThreads, false>(As + ((oc >> 1) & 1) * P * P, b1, b0);
                 __syncthreads();
-                for (int i = tid; i < P3; i += kThreads) {
-                    const int bc = i % (P * P), n = i / (P * P);
-                    T s = (T)0;
-                    for (int m = 0; m <= n; ++m) s += Ax[n * P + m] * b0[m * P * P + bc];
-                    acc[i] += s;
-                }
+                shift_up<T, P, 2, kThreads, true>(As + (oc & 1) * P * P, b0, acc);
                 __syncthreads();
             }
         }
@@ -377,7 +471,53 @@ __global__ void __launch_bounds__(kThreads) k_root(TreeView tv, DevTables<T> tb,
 // Local expansions and leaf evaluation (Step 3), parity-split
 // ---------------------------------------------------------------------------
 constexpr int kLThreads = 512;
-constexpr int kECH = 64;  // targets per evaluation chunk (8 threads per target)
+constexpr int kECH = 32;  // targets per evaluation chunk
+
+// One axis of a Chebyshev re-expansion on a P^3 array: out[.., m, ..] =
+// sum_{n >= m} A[n][m] in[.., n, ..] along axis AX (0 = z, the fastest index,
+// 1 = y, 2 = x).  Each thread owns two rows (P outputs each) in registers and
+// reads A from shared memory once per pair of multiply-adds.
+template <typename T, int P, int AX, int NT>
+__device__ __forceinline__ void shift_pass(const T *__restrict__ A, const T *in, T *out) {
+    constexpr int s = AX == 0 ? 1 : (AX == 1 ? P : P * P);
+    if constexpr (P > 20) {  // large orders: one output per thread (registers)
+        for (int i = threadIdx.x; i < P * P * P; i += NT) {
+            const int m = AX == 0 ? i % P : (AX == 1 ? (i / P) % P : i / (P * P));
+            const int b = i - m * s;
+            T acc = 0;
+            for (int n = m; n < P; ++n) acc += A[n * P + m] * in[b + n * s];
+            out[i] = acc;
+        }
+        return;
+    }
+    constexpr bool TWO = true;
+    constexpr int RR = P * P, H = TWO ? (RR + 1) / 2 : RR;
+    auto base = [](int r) { return AX == 0 ? r * P : (AX == 1 ? (r / P) * P * P + r % P : r); };
+    for (int t = threadIdx.x; t < H; t += NT) {
+        const int r0 = t, r1 = t + H;
+        const bool has1 = TWO && r1 < RR;
+        const int b0 = base(r0), b1 = has1 ? base(r1) : b0;
+        T o0[P], o1[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) o0[m] = o1[m] = (T)0;
+#pragma unroll
+        for (int n = 0; n < P; ++n) {
+            const T v0 = in[b0 + n * s], v1 = in[b1 + n * s];
+#pragma unroll
+            for (int m = 0; m <= n; ++m) {
+                const T a = A[n * P + m];
+                o0[m] += a * v0;
+                if (TWO) o1[m] += a * v1;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < P; ++m) out[b0 + m * s] = o0[m];
+        if (has1) {
+#pragma unroll
+            for (int m = 0; m < P; ++m) out[b1 + m * s] = o1[m];
+        }
+    }
+}
 
 template <int P, int NF> struct LocalShape {
     static constexpr int NH = NF + 1, N1 = 2 * NF + 1;
@@ -402,11 +542,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     C2 *T1o = T1e + P * NH * NH;
     T *hs = buf_ptr<T>(lay, 3, sm, slab);
     T *ev = buf_ptr<T>(lay, 4, sm, slab);     // [3][kECH][P]
+    T *As = buf_ptr<T>(lay, 5, sm, slab);     // shift matrices A_{-1}, A_{+1}
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
     const int tid = threadIdx.x;
     load_hs<T, P, NF>(tb, hs);
+    for (int i = tid; i < 2 * P * P; i += kLThreads) As[i] = tb.A[i];
     const size_t pstride = (size_t)N1 * N1 * NH;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
@@ -426,29 +568,12 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             for (int i = tid; i < P3; i += kLThreads) b0[i] = Lp[i];
             __syncthreads();
             const int oc = (int)(tv.bkey[B] & 7ull);
-            const T *Ax = tb.A + (oc & 1) * P * P;
-            const T *Ay = tb.A + ((oc >> 1) & 1) * P * P;
-            const T *Az = tb.A + ((oc >> 2) & 1) * P * P;
-            for (int i = tid; i < P3; i += kLThreads) {
-                const int m = i % P, ab = i / P;
-                T s = 0;
-                for (int n = m; n < P; ++n) s += Az[n * P + m] * b0[ab * P + n];
-                b1[i] = s;
-            }
+            // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
+            shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, b0, b1);
             __syncthreads();
-            for (int i = tid; i < P3; i += kLThreads) {
-                const int c = i % P, m = (i / P) % P, a = i / (P * P);
-                T s = 0;
-                for (int n = m; n < P; ++n) s += Ay[n * P + m] * b1[(a * P + n) * P + c];
-                b0[i] = s;
-            }
+            shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
             __syncthreads();
-            for (int i = tid; i < P3; i += kLThreads) {
-                const int bc = i % (P * P), m = i / (P * P);
-                T s = 0;
-                for (int n = m; n < P; ++n) s += Ax[n * P + m] * b0[n * P * P + bc];
-                Ls[i] = s;
-            }
+            shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
         }
         __syncthreads();
         // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients
@@ -635,24 +760,57 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 }
             }
             __syncthreads();
-            const int j = tid >> 3, g = tid & 7;
-            const T *tx = ev + j * P, *ty = ev + (kECH + j) * P, *tz = ev + (2 * kECH + j) * P;
-            T sum = 0;
-            for (int a = g; a < P; a += 8) {
-                T sa = 0;
-                for (int b = 0; b < P; ++b) {
-                    const T *row = Ls + (a * P + b) * P;
-                    T sbc = 0;
+            // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
+            {
+                T *W = reinterpret_cast<T *>(PsE);
+                const T *tzs = ev + 2 * kECH * P;
+                constexpr int NABG = (P * P + 3) / 4;
+                for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
+                    const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
+                    T acc[4][4];
 #pragma unroll
-                    for (int c = 0; c < P; ++c) sbc += row[c] * tz[c];
-                    sa += ty[b] * sbc;
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[i][k] = (T)0;
+#pragma unroll
+                    for (int c = 0; c < P; ++c) {
+                        T l[4], z[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int ab = abg * 4 + i;
+                            l[i] = ab < P * P ? Ls[ab * P + c] : (T)0;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) z[k] = tzs[(jg * 4 + k) * P + c];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) acc[i][k] += l[i] * z[k];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int ab = abg * 4 + i;
+                        if (ab < P * P)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) W[(jg * 4 + k) * (P * P) + ab] = acc[i][k];
+                    }
                 }
-                sum += tx[a] * sa;
+                __syncthreads();
+                // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
+                const int j = tid >> 4, g = tid & 15;
+                const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
+                const T *Wj = W + j * (P * P);
+                T sum = 0;
+                for (int a = g; a < P; a += 16) {
+                    T sa = 0;
+#pragma unroll
+                    for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
+                    sum += tx[a] * sa;
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
             }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
             __syncthreads();
         }
     }
@@ -675,7 +833,7 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 
 constexpr int kNearThreads = 256;
 
-template <typename T>
+template <typename T, int QD>
 __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, const int32_t *tleaves,
                                                        const int32_t *nl_off, const int32_t *nl_src,
                                                        const typename Vec4<T>::type *__restrict__ plocal,
@@ -683,10 +841,12 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                                                        int qdeg, double *unear, int *counter) {
     using V4 = typename Vec4<T>::type;
     constexpr bool kHiLo = sizeof(T) == 4;
-    __shared__ T s_q[64];
+    // residual polynomial coefficients in registers (degree QD known at compile time)
+    T qc[QD + 1];
+#pragma unroll
+    for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
+    (void)qdeg;
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int i = tid; i <= qdeg; i += kNearThreads) s_q[i] = qmono[i];
-    __syncthreads();
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(counter, 1);
@@ -738,27 +898,48 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                 const T invRb2 = invRb * invRb;
                 const T Rb2 = (T)(Rb * Rb);
                 const int ss = tv.bstart[Sb], ns = tv.bcount[Sb];
+                // screening radius: a little above R_b so that rounding in the
+                // coarse distance below never drops a pair inside the support
+                const T Rb2_screen = Rb2 * (T)1.0009765625;
                 T part = 0, comp = 0;
-                for (int jj = g; jj < ns; jj += G) {
-                    const V4 y = plocal[ss + jj];
-                    T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
-                    if (kHiLo) {
-                        const float4 yl = plocal_lo[ss + jj];
-                        dx += pxl - (T)yl.x;
-                        dy += pyl - (T)yl.y;
-                        dz += pzl - (T)yl.z;
+                for (int c0 = 0; c0 < ns; c0 += 32 * G) {
+                    // pass 1: coarse distance of 32 sources per lane -> bitmask
+                    unsigned mask = 0;
+#pragma unroll 8
+                    for (int k = 0; k < 32; ++k) {
+                        const int jj = c0 + g + G * k;
+                        if (jj < ns) {
+                            const V4 y = plocal[ss + jj];
+                            const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
+                            if (dx * dx + dy * dy + dz * dz < Rb2_screen) mask |= 1u << k;
+                        }
                     }
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    const T x = (T)2 * r2 * invRb2 - (T)1;
-                    T qv = s_q[qdeg];
-                    for (int d = qdeg - 1; d >= 0; --d) qv = qv * x + s_q[d];
-                    const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                    const T v = rinv - qv * invRb;
-                    const T term = (r2 < Rb2) ? y.w * v : (T)0;
-                    const T yk = term - comp;
-                    const T tk = part + yk;
-                    comp = (tk - part) - yk;
-                    part = tk;
+                    // pass 2: the residual kernel on the pairs inside the support
+                    while (mask) {
+                        const int k = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int jj = c0 + g + G * k;
+                        const V4 y = plocal[ss + jj];
+                        T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
+                        if (kHiLo) {
+                            const float4 yl = plocal_lo[ss + jj];
+                            dx += pxl - (T)yl.x;
+                            dy += pyl - (T)yl.y;
+                            dz += pzl - (T)yl.z;
+                        }
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        const T x = (T)2 * r2 * invRb2 - (T)1;
+                        T qv = qc[QD];
+#pragma unroll
+                        for (int d = QD - 1; d >= 0; --d) qv = qv * x + qc[d];
+                        const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
+                        const T v = rinv - qv * invRb;
+                        const T term = (r2 < Rb2) ? y.w * v : (T)0;
+                        const T yk = term - comp;
+                        const T tk = part + yk;
+                        comp = (tk - part) - yk;
+                        part = tk;
+                    }
                 }
                 acc += (double)part - (double)comp;
             }
@@ -775,6 +956,32 @@ __global__ void k_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout,
     // mode 0: both parts, 1: far part only, 2: near part only
     double v = (mode == 2 ? 0.0 : ufar[k]) + (mode == 1 ? 0.0 : unear[k]);
     pot[pout[k]] = v / frame->S;
+}
+
+// launch k_near with the residual polynomial degree as a template argument
+template <typename T, int QD>
+static void launch_near_qd(int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
+                           const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
+                           const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
+    k_near<T, QD><<<grid, kNearThreads, 0, st>>>(tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, QD,
+                                                  unear, counter);
+}
+
+template <typename T>
+static int launch_near(int qdeg, int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
+                       const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
+                       const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
+    switch (qdeg) {
+#define DMK_NEAR_CASE(d) \
+    case d: launch_near_qd<T, d>(grid, st, tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, unear, counter); return 0;
+        DMK_NEAR_CASE(2) DMK_NEAR_CASE(3) DMK_NEAR_CASE(4) DMK_NEAR_CASE(5) DMK_NEAR_CASE(6) DMK_NEAR_CASE(7)
+        DMK_NEAR_CASE(8) DMK_NEAR_CASE(9) DMK_NEAR_CASE(10) DMK_NEAR_CASE(11) DMK_NEAR_CASE(12) DMK_NEAR_CASE(13)
+        DMK_NEAR_CASE(14) DMK_NEAR_CASE(15) DMK_NEAR_CASE(16) DMK_NEAR_CASE(17) DMK_NEAR_CASE(18) DMK_NEAR_CASE(19)
+        DMK_NEAR_CASE(20) DMK_NEAR_CASE(21) DMK_NEAR_CASE(22) DMK_NEAR_CASE(23) DMK_NEAR_CASE(24) DMK_NEAR_CASE(25)
+        DMK_NEAR_CASE(26) DMK_NEAR_CASE(27) DMK_NEAR_CASE(28) DMK_NEAR_CASE(29) DMK_NEAR_CASE(30)
+#undef DMK_NEAR_CASE
+    default: return 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -843,8 +1050,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     // ---- upward pass (finest level first)
     cudaEventRecord(cx.ev[1], st);
     {
-        BufLayout lay = make_layout({P3 * sizeof(T), P3 * sizeof(T), P3 * sizeof(T), 3 * kCH * P * sizeof(T)},
-                                    smem_limit);
+        const size_t scr = std::max((size_t)2 * P3, (size_t)kCH * (3 * UpShape<P>::PS + UpShape<P>::YS)) * sizeof(T);
+        BufLayout lay = make_layout({P3 * sizeof(T), scr, (size_t)2 * P * P * sizeof(T)}, smem_limit - 1024);
         PCK(cudaFuncSetAttribute(k_upward<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         const int lmax = tv.nlev - 1;
         for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0; --l) {
@@ -890,9 +1097,13 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     }
     // ---- local expansions, coarsest level first; leaves evaluate
     {
-        BufLayout lay = make_layout({P3 * sizeof(T), (size_t)2 * N1 * NH * NH * sizeof(C2),
-                                     (size_t)2 * P * NH * NH * sizeof(C2), (size_t)P * NH * sizeof(T),
-                                     (size_t)3 * kECH * P * sizeof(T)},
+        // buffer 1 holds the incoming expansion, the p2c scratch (2 P^3) and the
+        // evaluation intermediate W (kECH P^2)
+        const size_t psi_bytes = std::max({(size_t)2 * N1 * NH * NH * sizeof(C2), (size_t)2 * P3 * sizeof(T),
+                                           (size_t)kECH * P * P * sizeof(T)});
+        BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, (size_t)2 * P * NH * NH * sizeof(C2),
+                                     (size_t)P * NH * sizeof(T), (size_t)3 * kECH * P * sizeof(T),
+                                     (size_t)2 * P * P * sizeof(T)},
                                     smem_limit - 2048);
         PCK(cudaFuncSetAttribute(k_local<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         for (int l = 0; l < tv.nlev; ++l) {
@@ -911,12 +1122,12 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     if (cx.tree->ntleaves > 0) {
         int grid = std::min((cx.tree->ntleaves + 7) / 8, cx.num_sms * 8);
         ::dmk::launch_tick();
-        k_near<T><<<grid, kNearThreads, 0, st>>>(tv, cx.tree->ntleaves, (const int32_t *)cx.tree->tleaves.p,
-                                                 (const int32_t *)cx.tree->nl_off.p,
-                                                 (const int32_t *)cx.tree->nl_src.p,
-                                                 (const typename Vec4<T>::type *)cx.tree->plocal.p,
-                                                 (const float4 *)cx.tree->plocal_lo.p, tb.qmono, tb.qdeg, unear,
-                                                 (int *)cx.bufs->counter.p);
+        int rc_near = launch_near<T>(tb.qdeg, grid, st, tv, cx.tree->ntleaves, (const int32_t *)cx.tree->tleaves.p,
+                                     (const int32_t *)cx.tree->nl_off.p, (const int32_t *)cx.tree->nl_src.p,
+                                     (const typename Vec4<T>::type *)cx.tree->plocal.p,
+                                     (const float4 *)cx.tree->plocal_lo.p, tb.qmono, unear,
+                                     (int *)cx.bufs->counter.p);
+        if (rc_near) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
         PCK(cudaGetLastError());
     }
     cudaEventRecord(cx.ev[4], st);
