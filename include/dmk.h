@@ -135,6 +135,30 @@ DMK_API int dmk_eval_host(dmk_plan_t plan,
                   const double *targets, int64_t n_tgt, double *potentials,
                   void *cuda_stream);
 
+/*
+ * dmk_direct_noalloc -- the direct sum u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j|
+ * in double precision, performing no device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate while
+ * they run -- work captured into a CUDA graph that must not call cudaMalloc,
+ * applications that give all device memory to their own pool, loops that
+ * cannot absorb the synchronisation an allocation can cause -- and that
+ * therefore cannot use dmk_eval, whose scratch grows with the input.
+ *
+ *   arguments   as in dmk_eval (device pointers, row-major points); targets
+ *               may equal sources; coincident pairs contribute zero
+ *   limits      n_tgt <= 16384 (larger -> DMK_ERR_INVALID_ARG), any n_src;
+ *               cost O(n_src * n_tgt)
+ *   scratch     a fixed 2 MiB device array inside the library, shared by all
+ *               calls: calls that overlap on the device race and must be
+ *               serialised by the caller.  The first call on each device looks
+ *               up the array's address (no allocation); make that first call
+ *               before any stream capture.
+ *   stream      asynchronous with respect to the host; runs on cuda_stream
+ */
+DMK_API int dmk_direct_noalloc(const double *sources, int64_t n_src, const double *charges,
+                               const double *targets, int64_t n_tgt, double *potentials,
+                               void *cuda_stream);
+
 /* Release a plan and all its device memory.  NULL is accepted. */
 DMK_API int dmk_plan_destroy(dmk_plan_t plan);
 

@@ -15,6 +15,14 @@ std::atomic<long long> g_launches{0};
 
 namespace {
 thread_local std::string g_detail;
+}
+
+namespace dmk {
+// lets entry points defined in other translation units report a detail
+void set_error_detail(const std::string &m) { g_detail = m; }
+}
+
+namespace {
 
 int fail(int code, const std::string &msg) {
     g_detail = msg;

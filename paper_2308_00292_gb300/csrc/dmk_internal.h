@@ -10,6 +10,9 @@
 
 namespace dmk {
 
+// Record the thread-local detail returned by dmk_last_error_detail().
+void set_error_detail(const std::string &m);
+
 // Number of kernels this library has launched (reported per evaluation).
 extern std::atomic<long long> g_launches;
 inline void launch_tick() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -30,7 +30,8 @@ ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "D
           5: "DMK_ERR_TIMEOUT", 6: "DMK_ERR_DEPTH", 7: "DMK_ERR_INTERNAL"}
 
 EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
-            "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree"]
+            "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree",
+            "dmk_direct_noalloc"]
 
 
 class Opts(ctypes.Structure):
@@ -88,6 +89,7 @@ def lib():
             L.dmk_plan_get_table.argtypes = [vp, ctypes.c_int, dp, i64, ctypes.POINTER(i64)]
             L.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.dmk_get_tree.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), i64]
+            L.dmk_direct_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp]
             for name in EXPORTED:
                 getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
             _lib = L
