@@ -199,6 +199,10 @@ typedef struct {
     int32_t balance_rounds; /* rebuilds needed by the level restriction */
     float t_tree_ms, t_upward_ms, t_downward_ms, t_near_ms, t_total_ms;
     int64_t n_launches;     /* kernels of this library launched by the call */
+    int64_t near_pairs_inside; /* candidate pairs closer than the residual support R_L */
+    int64_t local_flops;    /* algorithmic flops of the local-expansion pass (p2c,
+                               translation, plane waves to Chebyshev, leaf evaluation) */
+    float t_local_ms;       /* device time of the local-expansion pass alone */
 } dmk_eval_stats;
 
 DMK_API int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out);

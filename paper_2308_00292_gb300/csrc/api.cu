@@ -48,7 +48,7 @@ struct dmk_plan_s {
     dmk::PassBufs bufs;
     dmk::DBuf h_src, h_q, h_tgt, h_pot;  // device copies for dmk_eval_host
     dmk_eval_stats stats{};
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[7] = {};
     bool events = false;
     size_t smem_limit = 0;
     int num_sms = 0;
@@ -133,7 +133,7 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     cx.total_sources = ns;
     cx.pot = pot;
     cx.st = st;
-    for (int i = 0; i < 6; ++i) cx.ev[i] = pl->ev[i];
+    for (int i = 0; i < 7; ++i) cx.ev[i] = pl->ev[i];
     cx.smem_limit = pl->smem_limit;
     cx.num_sms = pl->num_sms;
     rc = dmk::run_passes(cx, err);
@@ -164,7 +164,20 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     s.t_downward_ms = t23;
     s.t_near_ms = t34;
     s.t_total_ms = t05;
+    float t63 = 0;
+    cudaEventElapsedTime(&t63, pl->ev[6], pl->ev[3]);
+    s.t_local_ms = t63;
     s.n_launches = dmk::g_launches.load() - launches0;
+    if (pl->tree->ntleaves > 0 && pl->bufs.counter.p) {
+        unsigned long long inside = 0;
+        if (cudaMemcpy(&inside, (char *)pl->bufs.counter.p + 8, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
+            s.near_pairs_inside = (int64_t)inside;
+    }
+    if (pl->bufs.counter.p) {
+        unsigned long long f = 0;
+        if (cudaMemcpy(&f, (char *)pl->bufs.counter.p + 16, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
+            s.local_flops = (int64_t)f;
+    }
     return DMK_OK;
 }
 

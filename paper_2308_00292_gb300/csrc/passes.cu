@@ -529,7 +529,8 @@ template <int P, int NF> struct LocalShape {
 template <typename T, int P, int NF>
 __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T> tb, int level, int lstart,
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
-                                                        const T *LamW, double *ufar, BufLayout lay, char *slab) {
+                                                        const T *LamW, double *ufar, BufLayout lay, char *slab,
+                                                        unsigned long long *flops) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
     constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P;
@@ -724,6 +725,17 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             }
             __syncthreads();
         }
+        if (tid == 0) {
+            // algorithmic flops of this box: p2c (3 triangular passes), the
+            // translation (one complex multiply-add per mode and colleague) and
+            // the three parity-split contractions, and the leaf evaluation
+            unsigned long long f = level > 0 ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
+            if (fl & BF_FIN)
+                f += 8ull * N1 * N1 * NH * s_ncol + 8ull * P * NH * NH * NH + 4ull * P * P * NH * NH +
+                     2ull * P * P * P * NH;
+            if (fl & BF_LEAF) f += 2ull * (P * P * P + P * P + P) * tv.bntgt[B];
+            atomicAdd(flops, f);
+        }
         if (!(fl & BF_LEAF)) {
             T *Lo = Lam + (size_t)tv.bslot[B] * P3;
             for (int i = tid; i < P3; i += kLThreads) Lo[i] = Ls[i];
@@ -827,6 +839,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
 // centres, and the exact dyadic centre offset is added with a TwoSum, so the
 // difference of two nearby points keeps full relative precision; the sum over
 // a source leaf is compensated (Kahan) and then accumulated in double.
+template <typename T> __device__ __forceinline__ T ldexp_t(T x, int e);
+template <> __device__ __forceinline__ float ldexp_t<float>(float x, int e) { return ldexpf(x, e); }
+template <> __device__ __forceinline__ double ldexp_t<double>(double x, int e) { return ldexp(x, e); }
+// centre coordinate (2 i + 1) 2^-(l+1) of cell i at level l, exact
+template <typename T> __device__ __forceinline__ T dyadic_centre(int i, int l) {
+    return ldexp_t<T>((T)(2 * i + 1), -(l + 1));
+}
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
@@ -847,17 +866,27 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
     for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
     (void)qdeg;
     const int tid = threadIdx.x, lane = tid & 31;
+    // pairs inside the support of the residual kernel (statistics); the
+    // counter sits 8 bytes after the work counter
+    unsigned inside32 = 0;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(counter, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= ntl) break;
+        if (it >= ntl) {
+#pragma unroll
+            unsigned long long inside = inside32;
+            for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(0xffffffffu, inside, o);
+            if (lane == 0 && inside) atomicAdd(reinterpret_cast<unsigned long long *>(counter + 2), inside);
+            break;
+        }
         const int Tb = tleaves[it];
         const int a = tv.blevel[Tb];
         int tx, ty, tz;
         morton_decode_d(tv.bkey[Tb], tx, ty, tz);
-        const double Ra = level_R(a);
-        const double cT[3] = {(tx + 0.5) * Ra, (ty + 0.5) * Ra, (tz + 0.5) * Ra};
+        // box centres (2i + 1) 2^-(l+1) are exact in T; so are their differences
+        // (at most ~22 significant bits for the level gaps of a balanced tree)
+        const T cTx = dyadic_centre<T>(tx, a), cTy = dyadic_centre<T>(ty, a), cTz = dyadic_centre<T>(tz, a);
         const int ts = tv.bstart[Tb], nt = tv.bcount[Tb];
         const int G = nt >= 32 ? 1 : (nt >= 16 ? 2 : (nt >= 8 ? 4 : 8));
         const int per = 32 / G;
@@ -879,11 +908,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                 const int b = tv.blevel[Sb];
                 int sx, sy, sz;
                 morton_decode_d(tv.bkey[Sb], sx, sy, sz);
-                const double Rb = level_R(b);
                 // exact dyadic centre difference, added to the target's local coordinate
-                const T dcx = (T)(cT[0] - (sx + 0.5) * Rb);
-                const T dcy = (T)(cT[1] - (sy + 0.5) * Rb);
-                const T dcz = (T)(cT[2] - (sz + 0.5) * Rb);
+                const T dcx = cTx - dyadic_centre<T>(sx, b);
+                const T dcy = cTy - dyadic_centre<T>(sy, b);
+                const T dcz = cTz - dyadic_centre<T>(sz, b);
                 T px = xt.x + dcx, py = xt.y + dcy, pz = xt.z + dcz;
                 T pxl = (T)0, pyl = (T)0, pzl = (T)0;
                 if (kHiLo) {  // TwoSum error terms plus the lo parts
@@ -894,9 +922,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                     bb = pz - xt.z;
                     pzl = ((xt.z - (pz - bb)) + (dcz - bb)) + (T)xl.z;
                 }
-                const T invRb = (T)(double)(1u << b);
+                const T invRb = ldexp_t<T>((T)1, b);
                 const T invRb2 = invRb * invRb;
-                const T Rb2 = (T)(Rb * Rb);
+                const T Rb2 = ldexp_t<T>((T)1, -2 * b);
                 const int ss = tv.bstart[Sb], ns = tv.bcount[Sb];
                 // screening radius: a little above R_b so that rounding in the
                 // coarse distance below never drops a pair inside the support
@@ -905,13 +933,23 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                 for (int c0 = 0; c0 < ns; c0 += 32 * G) {
                     // pass 1: coarse distance of 32 sources per lane -> bitmask
                     unsigned mask = 0;
+                    if (G == 1 && c0 + 32 <= ns) {  // full chunk, one lane per target
+                        const V4 *yp = plocal + ss + c0;
 #pragma unroll 8
-                    for (int k = 0; k < 32; ++k) {
-                        const int jj = c0 + g + G * k;
-                        if (jj < ns) {
-                            const V4 y = plocal[ss + jj];
+                        for (int k = 0; k < 32; ++k) {
+                            const V4 y = yp[k];
                             const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
                             if (dx * dx + dy * dy + dz * dz < Rb2_screen) mask |= 1u << k;
+                        }
+                    } else {
+#pragma unroll 8
+                        for (int k = 0; k < 32; ++k) {
+                            const int jj = c0 + g + G * k;
+                            if (jj < ns) {
+                                const V4 y = plocal[ss + jj];
+                                const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
+                                if (dx * dx + dy * dy + dz * dz < Rb2_screen) mask |= 1u << k;
+                            }
                         }
                     }
                     // pass 2: the residual kernel on the pairs inside the support
@@ -935,6 +973,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                         const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
                         const T v = rinv - qv * invRb;
                         const T term = (r2 < Rb2) ? y.w * v : (T)0;
+                        inside32 += (r2 < Rb2) ? 1u : 0u;
                         const T yk = term - comp;
                         const T tk = part + yk;
                         comp = (tk - part) - yk;
@@ -1101,6 +1140,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         // evaluation intermediate W (kECH P^2)
         const size_t psi_bytes = std::max({(size_t)2 * N1 * NH * NH * sizeof(C2), (size_t)2 * P3 * sizeof(T),
                                            (size_t)kECH * P * P * sizeof(T)});
+        cudaEventRecord(cx.ev[6], st);
         BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, (size_t)2 * P * NH * NH * sizeof(C2),
                                      (size_t)P * NH * sizeof(T), (size_t)3 * kECH * P * sizeof(T),
                                      (size_t)2 * P * P * sizeof(T)},
@@ -1113,7 +1153,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
             k_local<T, P, NF><<<grid, kLThreads, lay.smem_bytes, st>>>(tv, tb, l, tv.lev_start[l], lc, Phi, Lam,
-                                                                       LamW, ufar, lay, (char *)cx.bufs->slab.p);
+                                                                       LamW, ufar, lay, (char *)cx.bufs->slab.p,
+                                                                       (unsigned long long *)cx.bufs->counter.p + 2);
         }
         PCK(cudaGetLastError());
     }

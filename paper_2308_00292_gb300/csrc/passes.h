@@ -29,7 +29,7 @@ struct PassCtx {
     int64_t total_sources;
     double *pot;
     cudaStream_t st;
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[7];  // 0 start, 1 upward, 2 plane waves, 6 local, 3 near, 4 finalize, 5 end
     size_t smem_limit;
     int num_sms;
 };

@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("balance_rounds", ctypes.c_int32),
                 ("t_tree_ms", ctypes.c_float), ("t_upward_ms", ctypes.c_float),
                 ("t_downward_ms", ctypes.c_float), ("t_near_ms", ctypes.c_float), ("t_total_ms", ctypes.c_float),
-                ("n_launches", ctypes.c_int64)]
+                ("n_launches", ctypes.c_int64), ("near_pairs_inside", ctypes.c_int64),
+                ("local_flops", ctypes.c_int64), ("t_local_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
