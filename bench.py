@@ -102,10 +102,51 @@ class ClockSampler:
 NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares, 2 adds
 
 
+# DRAM bytes per algorithmic unit, from one ncu capture of every k_local and
+# k_near launch of an evaluation of the 2e6-point clustered workload (profiles/
+# dram_traffic_laplace3d_clustered_n2e6.md), valid only for the kernel source
+# it was taken on.
+TRAFFIC_SOURCE = "paper_2308_00292_gb300/csrc/passes.cu"
+TRAFFIC_SHA256 = "ade2dcc1ddae58fd82829432e21c836d850c9f31fb619ce682cc7c68023701fb"
+TRAFFIC_PER_UNIT = {"k_local": (1031.5e6 + 132.3e6) / 8.406e10,  # bytes per algorithmic flop
+                    "k_near": (74.8e6 + 6.1e6) / 4.693e9}        # bytes per candidate pair
+
+
+def traffic_per_unit(kernel: str):
+    """DRAM bytes per unit of work of a kernel, or None if its source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_SOURCE), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC_PER_UNIT.get(kernel) if sha == TRAFFIC_SHA256 else None
+
+
 def near_flops_per_pair(qdeg: int) -> int:
     # a pair inside the support: the distance (8), x = 2 r^2/R^2 - 1 (2),
     # Horner q(x) (2 per degree), rsqrt (1), 1/r - q/R (2), charge times value and sum (2)
     return NEAR_SCREEN_FLOPS + 2 + 2 * qdeg + 1 + 2 + 2
+
+
+def rank_seed(cfg: dict, rank: int) -> int:
+    """Seed of the independent cloud a rank evaluates (replicas, weak scaling)."""
+    return cfg["seed"] + 17 * rank
+
+
+def max_over_ranks(v: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time: an all-reduce(MAX) of one number (no data-path collective)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job points/s: the points of all ranks over the slowest rank's time."""
+    return n_per_rank * world / (ms / 1e3)
 
 
 def cpu_baseline(cfg: dict, n_sample: int, seed_offset: int = 1000):
@@ -129,8 +170,7 @@ def run_reference(args, rank, world):
         return
     cfg = inputs.CONFIGS[args.config]
     n_sample = args.cpu_sample
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass  # the oracle has no warm state; one untimed sample builds the library
+    # untimed: builds the oracle and touches its code once (it keeps no state)
     base = cpu_baseline(cfg, min(n_sample, 20000))
     times = []
     for k in range(args.steps):
@@ -144,15 +184,15 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args, cfg, ours=False),
+            "data": "synthetic", "config": config_dict(args, cfg),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(args, cfg, ours=True):
+def config_dict(args, cfg):
     return {"workload": args.config, "n_points": cfg["n"], "distribution": cfg["gen"], "eps": cfg["eps"],
-            "leaf_cap": cfg["leaf_cap"], "precision": "mixed" if ours else "fp64", "seed": cfg["seed"],
+            "leaf_cap": cfg["leaf_cap"], "precision": "mixed", "seed": cfg["seed"],
             "l2": "inputs larger than L2 (%.0f MB of points and charges per rank)" % (cfg["n"] * 32 / 1e6),
             "parallelism": "independent replica per GPU" if args.gpus > 1 else "single GPU"}
 
@@ -168,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     cfg = inputs.CONFIGS[args.config]
-    x, q = inputs.make(cfg["gen"], cfg["n"], cfg["seed"] + 17 * rank)
+    x, q = inputs.make(cfg["gen"], cfg["n"], rank_seed(cfg, rank))
     n = x.shape[0]
     xd = torch.from_numpy(x).cuda()
     qd = torch.from_numpy(q).cuda()
@@ -201,14 +241,10 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     stats = plan.stats()
     prm = plan.params()
-    value = n * world / (ms / 1e3)
+    value = job_throughput(n, world, ms)
 
     # end to end through the host entry point: pinned inputs, H2D + eval + D2H per step
     e2e = None
@@ -223,12 +259,8 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(ke):
             plan.eval_host(xh, qh, out=uh)
         barrier()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": n * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / ke, dist, "cuda")
+        e2e = {"value": job_throughput(n, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                "d2h_bytes_per_step": int(uh.nbytes), "ms_per_step": e2e_ms}
     plan.close()
 
@@ -245,9 +277,9 @@ def run_ours(args, rank, world, local_rank):
             p64.eval(xd, qd, out=out)
         f1.record(stream)
         barrier()
-        ms64 = f0.elapsed_time(f1) / k64
+        ms64 = max_over_ranks(f0.elapsed_time(f1) / k64, dist, "cuda")
         s64 = p64.stats()
-        fp64 = {"value": n * world / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+        fp64 = {"value": job_throughput(n, world, ms64), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
                 "phases_ms": {k: round(s64[k], 3) for k in phase},
                 "mixed_speedup": ms64 / ms}
         p64.close()
@@ -266,8 +298,11 @@ def run_ours(args, rank, world, local_rank):
     kernels = {}
     t_near = per_step["t_near_ms"] / 1e3
     a_near = near_flops / t_near / 1e12 if t_near > 0 else 0.0
+    tn, tl = traffic_per_unit("k_near"), traffic_per_unit("k_local")
     kernels["k_near"] = {"kernel": "k_near (residual near field, Steps 4-5)", "bound": "alu", "achieved": a_near,
-                         "peak": peak_fp32, "unit": "TFLOP/s", "frac": a_near / peak_fp32, "traffic": None,
+                         "peak": peak_fp32, "unit": "TFLOP/s", "frac": a_near / peak_fp32,
+                         "traffic": tn * pairs if tn is not None else None,
+                         "traffic_basis": "DRAM bytes per launch: ncu capture at 2e6 points scaled by candidate pairs",
                          "work": "%d candidate pairs x %d flops (distance screen) + %d pairs inside R_L x %d flops "
                                  "(residual kernel) per launch" % (pairs, NEAR_SCREEN_FLOPS, inside,
                                                                    fpp - NEAR_SCREEN_FLOPS),
@@ -276,7 +311,10 @@ def run_ours(args, rank, world, local_rank):
     a_loc = stats["local_flops"] / t_loc / 1e12 if t_loc > 0 else 0.0
     kernels["k_local"] = {"kernel": "k_local (local expansions, translation, leaf evaluation; one launch per level)",
                           "bound": "alu", "achieved": a_loc, "peak": peak_fp32, "unit": "TFLOP/s",
-                          "frac": a_loc / peak_fp32, "traffic": None,
+                          "frac": a_loc / peak_fp32,
+                          "traffic": tl * stats["local_flops"] if tl is not None else None,
+                          "traffic_basis": "DRAM bytes per evaluation (all launches): ncu capture at 2e6 points "
+                                           "scaled by algorithmic flops",
                           "work": "%d algorithmic flops per evaluation over %d launches" % (stats["local_flops"],
                                                                                              stats["n_levels"]),
                           "ms_per_eval": per_step["t_local_ms"], "peak_basis": basis}

@@ -16,7 +16,7 @@
  *   5. the level-restricted adaptive tree (Sec. 3.2, Step 0)
  *   6. the DMK algorithm, Steps 0-5 of Sec. 3.4
  *
- * Readings of the paper taken here (each is listed in the design doc):
+ * Readings of the paper taken here:
  *   - Fourier spacing h_l = 2 pi / (3 R_l): the difference kernel D_l has
  *     support radius R_l and colleague separations reach 2 R_l per
  *     coordinate, so its periodic images must sit 3 R_l apart (Poisson
