@@ -168,15 +168,20 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     cudaEventElapsedTime(&t63, pl->ev[6], pl->ev[3]);
     s.t_local_ms = t63;
     s.n_launches = dmk::g_launches.load() - launches0;
-    if (pl->tree->ntleaves > 0 && pl->bufs.counter.p) {
-        unsigned long long inside = 0;
-        if (cudaMemcpy(&inside, (char *)pl->bufs.counter.p + 8, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
-            s.near_pairs_inside = (int64_t)inside;
-    }
     if (pl->bufs.counter.p) {
-        unsigned long long f = 0;
-        if (cudaMemcpy(&f, (char *)pl->bufs.counter.p + 16, 8, cudaMemcpyDeviceToHost) == cudaSuccess)
-            s.local_flops = (int64_t)f;
+        // device words: [0] near work queue, [8] near pairs inside R_L,
+        // [16] local-pass flops, [24] a tensor-core wait that gave up
+        unsigned char w[32] = {0};
+        if (cudaMemcpy(w, pl->bufs.counter.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "reading the device status words failed");
+        unsigned long long inside = 0, f = 0;
+        int timeout = 0;
+        memcpy(&inside, w + 8, 8);
+        memcpy(&f, w + 16, 8);
+        memcpy(&timeout, w + 24, 4);
+        if (pl->tree->ntleaves > 0) s.near_pairs_inside = (int64_t)inside;
+        s.local_flops = (int64_t)f;
+        if (timeout) return fail(DMK_ERR_TIMEOUT, "a tensor-core completion wait gave up (local pass)");
     }
     return DMK_OK;
 }

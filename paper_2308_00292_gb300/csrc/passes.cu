@@ -39,6 +39,7 @@
 //   k_near     residual kernels R_{L(j)} over the interaction lists (Step 4),
 //              including the self correction of Step 5 (r = 0 terms)
 #include "passes.h"
+#include "tc.h"
 
 #include <algorithm>
 #include <cstdio>
@@ -524,16 +525,77 @@ template <int P, int NF> struct LocalShape {
     static constexpr int AG = (P + 6) / 7, AC = (P + AG - 1) / AG;  // phase B: a-groups, a per group
     static constexpr int BG = (P + 7) / 8, BC = (P + BG - 1) / BG;  // phase C
     static constexpr int CG = (P + 8) / 9, CC = (P + CG - 1) / CG;  // phase D
+    // tensor-core leaf evaluation D[j][ab] = sum_c T_c(z_j) Lambda[ab][c]:
+    // 128 targets per tile (M), ab padded to NP (N, multiple of 16, split into
+    // at most two MMAs of <= 256 columns), c padded to KP (K, multiple of 8)
+    static constexpr int TM = 128;
+    static constexpr int NP = (P * P + 15) / 16 * 16, KP = (P + 7) / 8 * 8;
+    static constexpr int NA = NP <= 256 ? NP : (NP / 2 + 15) / 16 * 16, NB = NP - NA;
+    static constexpr int TCOLS = NP <= 128 ? 128 : (NP <= 256 ? 256 : 512);
+    static constexpr bool TC_OK = NP <= 512 && NA <= 256 && NB <= 256;  // accumulator fits in TMEM
+    // shared memory of the tensor-core evaluation: buffer 1 holds B_hi, A_hi,
+    // A_lo, buffer 2 holds B_lo (floats)
+    static constexpr int TC_BUF1 = NP * KP + 2 * TM * KP, TC_BUF2 = NP * KP;
 };
+
+// asynchronous 8-byte global -> shared copies (Ampere-style cp.async)
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// T_0(x) .. T_{P-1}(x) by the three-term recurrence
+template <int P> __device__ __forceinline__ void cheb_row(float x, float (&t)[P]) {
+    t[0] = 1.f;
+    if (P > 1) t[1] = x;
+#pragma unroll
+    for (int n = 2; n < P; ++n) t[n] = 2.f * x * t[n - 1] - t[n - 2];
+}
+
+// sum over the accumulator columns n = 8 C0 .. 8 C1 - 1 (n = a P + b) of this
+// thread's TMEM lane: T_a(x) T_b(y) D[n], up to six 8-column chunks per wait
+template <int P, int C0, int C1>
+__device__ __forceinline__ float eval_part(uint32_t trow, const float (&tx)[P], const float (&ty)[P]) {
+    constexpr int B = 6;
+    float sum = 0.f, acc = 0.f;
+#pragma unroll
+    for (int c = C0; c < C1; c += B) {
+        float d[B][8];
+#pragma unroll
+        for (int g = 0; g < B; ++g)
+            if (c + g < C1) tc::ld_x8(trow + (uint32_t)((c + g) * 8), d[g]);
+        tc::ld_wait();
+#pragma unroll
+        for (int g = 0; g < B; ++g)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int n = (c + g) * 8 + q;
+                if (c + g < C1 && n < P * P) {
+                    acc += ty[n % P] * d[g][q];
+                    if (n % P == P - 1) {
+                        sum += tx[n / P] * acc;
+                        acc = 0.f;
+                    }
+                }
+            }
+    }
+    // a row a cut by the end of the range
+    constexpr int nlast = (8 * C1 < P * P ? 8 * C1 : P * P) - 1;
+    if (nlast >= 8 * C0 && nlast % P != P - 1) sum += tx[nlast / P] * acc;
+    return sum;
+}
 
 template <typename T, int P, int NF>
 __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T> tb, int level, int lstart,
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
                                                         const T *LamW, double *ufar, BufLayout lay, char *slab,
-                                                        unsigned long long *flops) {
+                                                        unsigned long long *flops, int *tc_err, int *run_ctr) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
     constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P;
+    // single precision evaluates the leaves on the tensor cores (3xTF32)
+    constexpr bool kTC = sizeof(T) == 4 && S::TC_OK;
     extern __shared__ __align__(128) char sm[];
     T *Ls = buf_ptr<T>(lay, 0, sm, slab);
     C2 *PsE = buf_ptr<C2>(lay, 1, sm, slab);  // [my + NF][mx'][mz]; PsO follows
@@ -547,17 +609,61 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
-    const int tid = threadIdx.x;
+    __shared__ __align__(8) uint64_t s_bar;  // MMA completion
+    __shared__ uint32_t s_tmem;              // TMEM accumulator base
+    __shared__ int s_pending;                // an MMA batch outlived its wait
+    __shared__ float s_red[3][128];          // partial leaf sums of column groups 1..3
+    __shared__ float2 s_ud[27 * 27];         // translation phases per colleague and residue class
+    __shared__ double s_xyz[3][128];         // a leaf's first 128 points, fetched while its expansion forms
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint32_t phase = 0;
+    if constexpr (kTC) {
+        if (warp == 0) tc::tmem_alloc(&s_tmem, S::TCOLS);
+        if (tid == 0) {
+            tc::mbar_init(&s_bar, 1);
+            s_pending = 0;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     load_hs<T, P, NF>(tb, hs);
     for (int i = tid; i < 2 * P * P; i += kLThreads) As[i] = tb.A[i];
     const size_t pstride = (size_t)N1 * N1 * NH;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
-    for (int it = blockIdx.x; it < lcount; it += gridDim.x) {
+    T *Pl = buf_ptr<T>(lay, 6, sm, slab);     // the parent's Lambda, kept for its next children
+    int cur_parent = -1;
+    // runs of 8 consecutive boxes, taken from a work counter: siblings are
+    // adjacent in Morton order and share the parent's expansion
+    __shared__ int s_run;
+    for (int it = 0, it_end = 0;; ++it) {
+        if (it >= it_end) {
+            __syncthreads();
+            if (tid == 0) s_run = atomicAdd(run_ctr, 1);
+            __syncthreads();
+            it = s_run * 8;
+            it_end = min(it + 8, lcount);
+            if (it >= lcount) break;
+        }
         const int B = lstart + it;
         if (tv.bntgt[B] == 0) continue;
         const uint8_t fl = tv.bflags[B];
         __syncthreads();
+        if constexpr (kTC) {
+            if (fl & BF_LEAF) {
+                const int s0 = tv.bstart[B], n0 = min(S::TM, tv.bcount[B]);
+                for (int t = tid; t < 3 * S::TM; t += kLThreads) {
+                    const int ax = t / S::TM, j = t % S::TM;
+                    if (j < n0) cp_async8(&s_xyz[ax][j], (ax == 0 ? tv.ux : (ax == 1 ? tv.uy : tv.uz)) + s0 + j);
+                }
+                cp_async_commit();
+            }
+        }
+        // A leaf without incoming expansion keeps its parent's Lambda: T_p2c is
+        // an exact re-expansion, so the leaf evaluates the parent's polynomial in
+        // the parent's coordinates instead (tensor-core path)
+        const bool in_parent = kTC && level > 0 && (fl & BF_LEAF) && !(fl & BF_FIN);
         // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
         if (level == 0) {
             for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[i];
@@ -565,16 +671,21 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             T *b0 = reinterpret_cast<T *>(PsE);
             T *b1 = reinterpret_cast<T *>(PsO);
             const int Pb = tv.bparent[B];
-            const T *Lp = Lam + (size_t)tv.bslot[Pb] * P3;
-            for (int i = tid; i < P3; i += kLThreads) b0[i] = Lp[i];
-            __syncthreads();
-            const int oc = (int)(tv.bkey[B] & 7ull);
-            // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
-            shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, b0, b1);
-            __syncthreads();
-            shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
-            __syncthreads();
-            shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
+            if (Pb != cur_parent) {
+                const T *Lp = Lam + (size_t)tv.bslot[Pb] * P3;
+                for (int i = tid; i < P3; i += kLThreads) Pl[i] = Lp[i];
+                cur_parent = Pb;
+                __syncthreads();
+            }
+            if (!in_parent) {
+                const int oc = (int)(tv.bkey[B] & 7ull);
+                // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
+                shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, Pl, b1);
+                __syncthreads();
+                shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
+                __syncthreads();
+                shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
+            }
         }
         __syncthreads();
         // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients
@@ -595,30 +706,45 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             }
             __syncthreads();
             const int ncol = s_ncol;
+            // phase of colleague j for modes of residue class r = (m_x, m_y, m_z) mod 3
+            // (r = r_x + 3 r_y + 9 r_z): omega^k with k = r . delta_j mod 3, kept as
+            // (k != 0, +1 / -1 / 0 for k = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3/2) D
+            for (int t = tid; t < 27 * ncol; t += kLThreads) {
+                const int j = t / 27, r = t % 27;
+                const int k = ((r % 3) * s_cd[j][0] + ((r / 3) % 3) * s_cd[j][1] + (r / 9) * s_cd[j][2]) % 3;
+                s_ud[t] = make_float2(k ? 1.f : 0.f, k == 1 ? 1.f : (k == 2 ? -1.f : 0.f));
+            }
+            __syncthreads();
             // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x
             for (int i = tid; i < N1 * NH * NH; i += kLThreads) {
                 const int my = i / (NH * NH), r = i % (NH * NH), mxp = r / NH, mz = r % NH;
                 const int myv = my - NF;
                 const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3, rz = mz % 3;
+                const float2 *udp = s_ud + rxp + 3 * ry + 9 * rz, *udm = s_ud + rxm + 3 * ry + 9 * rz;
                 C2 Tp{0, 0}, Up{0, 0}, Dp{0, 0}, Tm{0, 0}, Um{0, 0}, Dm{0, 0};
                 const size_t off_p = (size_t)(my * N1 + NF + mxp) * NH + mz;
                 const size_t off_m = (size_t)(my * N1 + NF - mxp) * NH + mz;
-                for (int j = 0; j < ncol; ++j) {
-                    const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
-                    const int kyz = ry * s_cd[j][1] + rz * s_cd[j][2];
-                    const int kp = (rxp * s_cd[j][0] + kyz) % 3;
-                    const int km = (rxm * s_cd[j][0] + kyz) % 3;
-                    const C2 vp = ph[off_p];
-                    Tp.x += vp.x; Tp.y += vp.y;
-                    const T up = kp ? (T)1 : (T)0, dp = kp == 1 ? (T)1 : (kp == 2 ? (T)-1 : (T)0);
-                    cfma(Up, up, vp);
-                    cfma(Dp, dp, vp);
-                    if (mxp > 0) {
-                        const C2 vm = ph[off_m];
+                if (mxp > 0) {
+#pragma unroll 3
+                    for (int j = 0; j < ncol; ++j) {
+                        const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
+                        const C2 vp = ph[off_p], vm = ph[off_m];
+                        const float2 cp = udp[27 * j], cm = udm[27 * j];
+                        Tp.x += vp.x; Tp.y += vp.y;
+                        cfma(Up, (T)cp.x, vp);
+                        cfma(Dp, (T)cp.y, vp);
                         Tm.x += vm.x; Tm.y += vm.y;
-                        const T um = km ? (T)1 : (T)0, dm = km == 1 ? (T)1 : (km == 2 ? (T)-1 : (T)0);
-                        cfma(Um, um, vm);
-                        cfma(Dm, dm, vm);
+                        cfma(Um, (T)cm.x, vm);
+                        cfma(Dm, (T)cm.y, vm);
+                    }
+                } else {
+#pragma unroll 3
+                    for (int j = 0; j < ncol; ++j) {
+                        const C2 vp = Phi[(size_t)s_cslot[j] * pstride + off_p];
+                        const float2 cp = udp[27 * j];
+                        Tp.x += vp.x; Tp.y += vp.y;
+                        cfma(Up, (T)cp.x, vp);
+                        cfma(Dp, (T)cp.y, vp);
                     }
                 }
                 const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
@@ -729,7 +855,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             // algorithmic flops of this box: p2c (3 triangular passes), the
             // translation (one complex multiply-add per mode and colleague) and
             // the three parity-split contractions, and the leaf evaluation
-            unsigned long long f = level > 0 ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
+            unsigned long long f = level > 0 && !in_parent ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
             if (fl & BF_FIN)
                 f += 8ull * N1 * N1 * NH * s_ncol + 8ull * P * NH * NH * NH + 4ull * P * P * NH * NH +
                      2ull * P * P * P * NH;
@@ -744,101 +870,243 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
         // ---- leaf: evaluate the local expansion at its targets
         int ix, iy, iz;
         morton_decode_d(tv.bkey[B], ix, iy, iz);
-        const double R = level_R(level), s2R = 2.0 / R;
+        const int le = in_parent ? level - 1 : level;  // level of the expansion's box
+        if (in_parent) {
+            ix >>= 1;
+            iy >>= 1;
+            iz >>= 1;
+        }
+        const double R = level_R(le), s2R = 2.0 / R;
         const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
+        const T *Lev = in_parent ? Pl : Ls;
         const int s = tv.bstart[B], e = s + tv.bcount[B];
-        for (int p0 = s; p0 < e; p0 += kECH) {
-            const int np = min(kECH, e - p0);
-            for (int t = tid; t < 3 * kECH; t += kLThreads) {
-                const int ax = t / kECH, j = t % kECH;
-                T *o = ev + (ax * kECH + j) * P;
-                if (j < np) {
-                    const int kk = p0 + j;
-                    const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
-                    const T xi = (T)((u - cc[ax]) * s2R);
-                    T t0 = (T)1, t1 = xi;
-                    o[0] = (T)1;
-                    if (P > 1) o[1] = xi;
+        if constexpr (kTC) {
+            // Tensor cores: D[j][ab] = sum_c T_c(z_j) Lambda[ab][c] for 128 targets
+            // at a time (targets on the TMEM lanes), then each target's own thread
+            // forms u_j = sum_a T_a(x_j) sum_b T_b(y_j) D[j][ab].  Operands are
+            // split into TF32 hi + lo and D = A_lo B_hi + A_hi B_lo + A_hi B_hi.
+            float *Bh = reinterpret_cast<float *>(PsE);
+            float *Ah = Bh + S::NP * S::KP;
+            float *Al = Ah + S::TM * S::KP;
+            float *Bl = reinterpret_cast<float *>(T1e);
+            // B operand: row ab, column c of Lambda; one float4 (4 columns) per step
+            for (int t = tid; t < S::NP * S::KP / 4; t += kLThreads) {
+                const int r = t & 7, k4 = (t >> 3) % (S::KP / 4), n = ((t >> 3) / (S::KP / 4)) * 8 + r;
+                float h[4], l[4];
 #pragma unroll
-                    for (int n = 2; n < P; ++n) {
-                        T t2 = (T)2 * xi * t1 - t0;
-                        o[n] = t2;
-                        t0 = t1;
-                        t1 = t2;
-                    }
-                } else {
-#pragma unroll
-                    for (int n = 0; n < P; ++n) o[n] = (T)0;
+                for (int q = 0; q < 4; ++q) {
+                    const int k = 4 * k4 + q;
+                    const float v = (n < P * P && k < P) ? (float)Lev[n * P + k] : 0.f;
+                    tc::split_tf32(v, h[q], l[q]);
                 }
+                reinterpret_cast<float4 *>(Bh)[t] = make_float4(h[0], h[1], h[2], h[3]);
+                reinterpret_cast<float4 *>(Bl)[t] = make_float4(l[0], l[1], l[2], l[3]);
             }
+            cp_async_wait_all();
             __syncthreads();
-            // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
-            {
-                T *W = reinterpret_cast<T *>(PsE);
-                const T *tzs = ev + 2 * kECH * P;
-                constexpr int NABG = (P * P + 3) / 4;
-                for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
-                    const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
-                    T acc[4][4];
+            for (int p0 = s; p0 < e; p0 += S::TM) {
+                const int np = min(S::TM, e - p0);
+                const bool first = p0 == s;  // points already in s_xyz
+                // coordinates of this thread's epilogue target
+                const int jq = min(tid & (S::TM - 1), np - 1);
+                const double xq = first ? s_xyz[0][jq] : tv.ux[p0 + jq];
+                const double yq = first ? s_xyz[1][jq] : tv.uy[p0 + jq];
+                if (tid < S::TM) {
+                    // A operand row j = T_c(z_j), c < P (zero rows past the leaf's points)
+                    const int j = tid;
+                    float tz[S::KP];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int n = 0; n < S::KP; ++n) tz[n] = 0.f;
+                    if (j < np) {
+                        const float zi = (float)(((first ? s_xyz[2][j] : tv.uz[p0 + j]) - cc[2]) * s2R);
+                        tz[0] = 1.f;
+                        if (P > 1) tz[1] = zi;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[i][k] = (T)0;
-#pragma unroll
-                    for (int c = 0; c < P; ++c) {
-                        T l[4], z[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int ab = abg * 4 + i;
-                            l[i] = ab < P * P ? Ls[ab * P + c] : (T)0;
-                        }
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) z[k] = tzs[(jg * 4 + k) * P + c];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) acc[i][k] += l[i] * z[k];
+                        for (int n = 2; n < P; ++n) tz[n] = 2.f * zi * tz[n - 1] - tz[n - 2];
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int ab = abg * 4 + i;
-                        if (ab < P * P)
+                    for (int k4 = 0; k4 < S::KP / 4; ++k4) {
+                        float h[4], l[4];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) W[(jg * 4 + k) * (P * P) + ab] = acc[i][k];
+                        for (int q = 0; q < 4; ++q) tc::split_tf32(tz[4 * k4 + q], h[q], l[q]);
+                        const int o = ((j >> 3) * (S::KP / 4) + k4) * 8 + (j & 7);
+                        reinterpret_cast<float4 *>(Ah)[o] = make_float4(h[0], h[1], h[2], h[3]);
+                        reinterpret_cast<float4 *>(Al)[o] = make_float4(l[0], l[1], l[2], l[3]);
+                    }
+                }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (tid == 0) {
+                    constexpr uint32_t lbo = 128, sbo = S::KP * 32;
+                    const uint32_t aH = tc::smem_addr(Ah), aL = tc::smem_addr(Al);
+                    const uint32_t bH = tc::smem_addr(Bh), bL = tc::smem_addr(Bl);
+#pragma unroll
+                    for (int h = 0; h < (S::NB > 0 ? 2 : 1); ++h) {
+                        const int n0 = h ? S::NA : 0;
+                        const uint32_t id = tc::idesc_tf32(S::TM, h ? S::NB : S::NA);
+                        const uint32_t boff = (uint32_t)(n0 / 8) * sbo, dcol = s_tmem + (uint32_t)n0;
+#pragma unroll
+                        for (int ks = 0; ks < S::KP / 8; ++ks) {
+                            const uint32_t ko = (uint32_t)ks * 256;
+                            tc::mma_tf32(dcol, tc::sdesc(aL + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id,
+                                         ks > 0);
+                            tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bL + boff + ko, lbo, sbo), id,
+                                         true);
+                            tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id,
+                                         true);
+                        }
+                    }
+                    tc::commit(&s_bar);
+                }
+                {
+                    // every warp waits; warps w, w + 4, w + 8, w + 12 share TMEM lanes
+                    // 32 (w mod 4) .. + 31 (targets j) and split the ab columns
+                    bool ok = tc::mbar_wait(&s_bar, phase, 2000000000ll);  // about 1 s
+                    ok = __all_sync(0xffffffffu, ok);
+                    tc::fence_after_sync();
+                    const int j = tid & (S::TM - 1), cg = tid >> 7;
+                    float part = 0.f;
+                    if (ok) {
+                        float tx[P], ty[P];
+                        cheb_row<P>((float)((xq - cc[0]) * s2R), tx);
+                        cheb_row<P>((float)((yq - cc[1]) * s2R), ty);
+                        const uint32_t trow = s_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+                        constexpr int NC = S::NP / 8;  // 8-column chunks
+                        switch (cg) {
+                        case 0: part = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
+                        case 1: part = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
+                        case 2: part = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
+                        default: part = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
+                        }
+                    } else if ((tid & 31) == 0) {
+                        atomicExch(tc_err, 1);
+                        s_pending = 1;
+                    }
+                    if (cg > 0) s_red[cg - 1][j] = part;
+                    tc::fence_before_sync();
+                    __syncthreads();
+                    if (cg == 0 && j < np && (tv.pflag[p0 + j] & 2))
+                        ufar[p0 + j] = (double)(part + s_red[0][j] + s_red[1][j] + s_red[2][j]);
+                }
+                phase ^= 1u;
+            }
+        } else {
+            for (int p0 = s; p0 < e; p0 += kECH) {
+                const int np = min(kECH, e - p0);
+                for (int t = tid; t < 3 * kECH; t += kLThreads) {
+                    const int ax = t / kECH, j = t % kECH;
+                    T *o = ev + (ax * kECH + j) * P;
+                    if (j < np) {
+                        const int kk = p0 + j;
+                        const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
+                        const T xi = (T)((u - cc[ax]) * s2R);
+                        T t0 = (T)1, t1 = xi;
+                        o[0] = (T)1;
+                        if (P > 1) o[1] = xi;
+#pragma unroll
+                        for (int n = 2; n < P; ++n) {
+                            T t2 = (T)2 * xi * t1 - t0;
+                            o[n] = t2;
+                            t0 = t1;
+                            t1 = t2;
+                        }
+                    } else {
+#pragma unroll
+                        for (int n = 0; n < P; ++n) o[n] = (T)0;
                     }
                 }
                 __syncthreads();
-                // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
-                const int j = tid >> 4, g = tid & 15;
-                const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
-                const T *Wj = W + j * (P * P);
-                T sum = 0;
-                for (int a = g; a < P; a += 16) {
-                    T sa = 0;
+                // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
+                {
+                    T *W = reinterpret_cast<T *>(PsE);
+                    const T *tzs = ev + 2 * kECH * P;
+                    constexpr int NABG = (P * P + 3) / 4;
+                    for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
+                        const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
+                        T acc[4][4];
 #pragma unroll
-                    for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
-                    sum += tx[a] * sa;
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) acc[i][k] = (T)0;
+#pragma unroll
+                        for (int c = 0; c < P; ++c) {
+                            T l[4], z[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int ab = abg * 4 + i;
+                                l[i] = ab < P * P ? Ls[ab * P + c] : (T)0;
+                            }
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) z[k] = tzs[(jg * 4 + k) * P + c];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) acc[i][k] += l[i] * z[k];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int ab = abg * 4 + i;
+                            if (ab < P * P)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) W[(jg * 4 + k) * (P * P) + ab] = acc[i][k];
+                        }
+                    }
+                    __syncthreads();
+                    // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
+                    const int j = tid >> 4, g = tid & 15;
+                    const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
+                    const T *Wj = W + j * (P * P);
+                    T sum = 0;
+                    for (int a = g; a < P; a += 16) {
+                        T sa = 0;
+#pragma unroll
+                        for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
+                        sum += tx[a] * sa;
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
                 }
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
+                __syncthreads();
             }
-            __syncthreads();
         }
+    }
+    if constexpr (kTC) {
+        // an MMA batch that outlived its wait must finish before TMEM is freed
+        if (s_pending && tid < 32) {
+            const bool done = tc::mbar_wait(&s_bar, phase ^ 1u, 2000000000ll);
+            (void)done;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(s_tmem, S::TCOLS);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Residual near field (Steps 4 and 5)
 // ---------------------------------------------------------------------------
-// One warp per target leaf, taken from an atomic work counter.  Lanes map to
-// (target, source subset) pairs: G lanes share a target and split its sources
-// when the leaf holds fewer than 32 targets.  Sources are read straight from
-// global memory (all lanes of a group read the same address, served by L1).
-// In single precision the coordinates are hi + lo pairs, relative to the leaf
-// centres, and the exact dyadic centre offset is added with a TwoSum, so the
-// difference of two nearby points keeps full relative precision; the sum over
-// a source leaf is compensated (Kahan) and then accumulated in double.
+// One warp per target leaf, taken from an atomic work counter.  The leaf's
+// points are taken in groups of up to 32 targets; when the leaf holds fewer
+// than 32 points, G adjacent lanes share a target and split its candidates.
+// For each group:
+//   1. the source leaves of the interaction list are read 32 at a time, one
+//      per lane, and a leaf whose box lies farther than R_b from the group's
+//      bounding box is dropped;
+//   2. the sources of the kept leaves form one flat stream, staged in shared
+//      memory kNC at a time and moved to the target leaf's frame;
+//   3. each lane screens its target against 32 staged sources and marks those
+//      closer than R_b; the marked pairs of the warp are compacted into a
+//      queue and evaluated 32 at a time, one pair per lane;
+//   4. values are summed per target by a segmented warp reduction (a fixed
+//      order: the result is deterministic) into double accumulators.
+// In single precision coordinates are hi + lo pairs relative to the leaf
+// centres; the exact dyadic offset between the two leaf centres is added to
+// the source with a TwoSum, so differences of nearby points keep their full
+// relative precision.
 template <typename T> __device__ __forceinline__ T ldexp_t(T x, int e);
 template <> __device__ __forceinline__ float ldexp_t<float>(float x, int e) { return ldexpf(x, e); }
 template <> __device__ __forceinline__ double ldexp_t<double>(double x, int e) { return ldexp(x, e); }
@@ -850,7 +1118,38 @@ template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
-constexpr int kNearThreads = 256;
+constexpr int kNearThreads = 128;
+constexpr int kNC = 128;  // staged sources per chunk
+
+// the screening radius^2 of a staged source is R_b^2 (1 + 2^-10) with
+// R_b = 2^-b: its exponent gives R_b^2, 1/R_b and 1/R_b^2 exactly
+__device__ __forceinline__ void level_scales(float w, float &R2, float &invR, float &invR2) {
+    const int bits = __float_as_int(w), E = (bits >> 23) & 255, b = (127 - E) >> 1;
+    R2 = __int_as_float(bits & 0x7f800000);
+    invR2 = __int_as_float((254 - E) << 23);
+    invR = __int_as_float((127 + b) << 23);
+}
+__device__ __forceinline__ void level_scales(double w, double &R2, double &invR, double &invR2) {
+    const long long bits = __double_as_longlong(w);
+    const int E = (int)((bits >> 52) & 2047), b = (1023 - E) >> 1;
+    R2 = __longlong_as_double(bits & 0x7ff0000000000000ll);
+    invR2 = __longlong_as_double((long long)(2046 - E) << 52);
+    invR = __longlong_as_double((long long)(1023 + b) << 52);
+}
+
+// per-warp shared memory of k_near
+template <typename T> struct NearWarp {
+    using V4 = typename Vec4<T>::type;
+    V4 sh[kNC];        // staged sources: x, y, z in the target leaf's frame (hi), screening radius^2
+    float4 sl[kNC];    // single precision: lo parts of x, y, z and the charge
+    T sq[kNC];         // double precision: the charge
+    V4 th[32];         // the group's targets (hi) and
+    float4 tl[32];     // their lo parts
+    double acc[32];    // per-target sums
+    T lox[32], loy[32], loz[32], lr2[32];  // kept source leaves: centre offset, screening radius^2
+    int lss[32], loff[33];                 // first point, offset in the stream
+    uint16_t q[32 * 32];                   // marked pairs: (target << 7) | staged source
+};
 
 template <typename T, int QD>
 __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, const int32_t *tleaves,
@@ -860,23 +1159,27 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                                                        int qdeg, double *unear, int *counter) {
     using V4 = typename Vec4<T>::type;
     constexpr bool kHiLo = sizeof(T) == 4;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(32) char nsm[];
+    NearWarp<T> &W = reinterpret_cast<NearWarp<T> *>(nsm)[threadIdx.x >> 5];
     // residual polynomial coefficients in registers (degree QD known at compile time)
     T qc[QD + 1];
 #pragma unroll
     for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
     (void)qdeg;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int lane = threadIdx.x & 31;
+    const T kBig = (T)1e30;
     // pairs inside the support of the residual kernel (statistics); the
     // counter sits 8 bytes after the work counter
     unsigned inside32 = 0;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(counter, 1);
-        it = __shfl_sync(0xffffffffu, it, 0);
+        it = __shfl_sync(FULL, it, 0);
         if (it >= ntl) {
-#pragma unroll
             unsigned long long inside = inside32;
-            for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(0xffffffffu, inside, o);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(FULL, inside, o);
             if (lane == 0 && inside) atomicAdd(reinterpret_cast<unsigned long long *>(counter + 2), inside);
             break;
         }
@@ -889,101 +1192,197 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
         const T cTx = dyadic_centre<T>(tx, a), cTy = dyadic_centre<T>(ty, a), cTz = dyadic_centre<T>(tz, a);
         const int ts = tv.bstart[Tb], nt = tv.bcount[Tb];
         const int G = nt >= 32 ? 1 : (nt >= 16 ? 2 : (nt >= 8 ? 4 : 8));
-        const int per = 32 / G;
+        const int per = 32 / G, t = lane / G, sub = lane % G;
         const int l0 = nl_off[it], l1 = nl_off[it + 1];
-        for (int t0 = 0; t0 < nt; t0 += per) {
-            const int j = t0 + lane / G, g = lane % G;
-            const bool valid = j < nt;
-            V4 xt;
-            float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) {
-                xt = plocal[ts + j];
-                if (kHiLo) xl = plocal_lo[ts + j];
-            } else {
-                xt.x = xt.y = xt.z = xt.w = (T)0;
+        for (int j0 = 0; j0 < nt; j0 += per) {
+            const int ng = min(per, nt - j0);
+            // the group's targets and their bounding box
+            T bl[3] = {kBig, kBig, kBig}, bh[3] = {-kBig, -kBig, -kBig};
+            if (lane < ng) {
+                const V4 v = plocal[ts + j0 + lane];
+                W.th[lane] = v;
+                if (kHiLo) W.tl[lane] = plocal_lo[ts + j0 + lane];
+                bl[0] = bh[0] = v.x;
+                bl[1] = bh[1] = v.y;
+                bl[2] = bh[2] = v.z;
             }
-            double acc = 0.0;
-            for (int li = l0; li < l1; ++li) {
-                const int Sb = nl_src[li];
-                const int b = tv.blevel[Sb];
-                int sx, sy, sz;
-                morton_decode_d(tv.bkey[Sb], sx, sy, sz);
-                // exact dyadic centre difference, added to the target's local coordinate
-                const T dcx = cTx - dyadic_centre<T>(sx, b);
-                const T dcy = cTy - dyadic_centre<T>(sy, b);
-                const T dcz = cTz - dyadic_centre<T>(sz, b);
-                T px = xt.x + dcx, py = xt.y + dcy, pz = xt.z + dcz;
-                T pxl = (T)0, pyl = (T)0, pzl = (T)0;
-                if (kHiLo) {  // TwoSum error terms plus the lo parts
-                    T bb = px - xt.x;
-                    pxl = ((xt.x - (px - bb)) + (dcx - bb)) + (T)xl.x;
-                    bb = py - xt.y;
-                    pyl = ((xt.y - (py - bb)) + (dcy - bb)) + (T)xl.y;
-                    bb = pz - xt.z;
-                    pzl = ((xt.z - (pz - bb)) + (dcz - bb)) + (T)xl.z;
+            W.acc[lane] = 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    bl[d] = min(bl[d], __shfl_xor_sync(FULL, bl[d], o));
+                    bh[d] = max(bh[d], __shfl_xor_sync(FULL, bh[d], o));
                 }
-                const T invRb = ldexp_t<T>((T)1, b);
-                const T invRb2 = invRb * invRb;
-                const T Rb2 = ldexp_t<T>((T)1, -2 * b);
-                const int ss = tv.bstart[Sb], ns = tv.bcount[Sb];
-                // screening radius: a little above R_b so that rounding in the
-                // coarse distance below never drops a pair inside the support
-                const T Rb2_screen = Rb2 * (T)1.0009765625;
-                T part = 0, comp = 0;
-                for (int c0 = 0; c0 < ns; c0 += 32 * G) {
-                    // pass 1: coarse distance of 32 sources per lane -> bitmask
-                    unsigned mask = 0;
-                    if (G == 1 && c0 + 32 <= ns) {  // full chunk, one lane per target
-                        const V4 *yp = plocal + ss + c0;
-#pragma unroll 8
-                        for (int k = 0; k < 32; ++k) {
-                            const V4 y = yp[k];
-                            const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
-                            if (dx * dx + dy * dy + dz * dz < Rb2_screen) mask |= 1u << k;
+            __syncwarp();
+            const bool tvalid = t < ng;
+            const V4 xt = W.th[tvalid ? t : 0];
+            for (int lb = l0; lb < l1; lb += 32) {
+                // 1. up to 32 source leaves, one per lane; drop those out of reach
+                const int li = lb + lane;
+                bool keep = false;
+                int ns = 0, ss = 0;
+                T ox = 0, oy = 0, oz = 0, r2s = 0;
+                if (li < l1) {
+                    const int Sb = nl_src[li];
+                    const int b = tv.blevel[Sb];
+                    int sx, sy, sz;
+                    morton_decode_d(tv.bkey[Sb], sx, sy, sz);
+                    ox = dyadic_centre<T>(sx, b) - cTx;
+                    oy = dyadic_centre<T>(sy, b) - cTy;
+                    oz = dyadic_centre<T>(sz, b) - cTz;
+                    const T Rb = ldexp_t<T>((T)1, -b), hb = (T)0.5 * Rb;
+                    ss = tv.bstart[Sb];
+                    ns = tv.bcount[Sb];
+                    // distance between the leaf's box and the group's bounding box
+                    const T gx = max((T)0, max(bl[0] - (ox + hb), (ox - hb) - bh[0]));
+                    const T gy = max((T)0, max(bl[1] - (oy + hb), (oy - hb) - bh[1]));
+                    const T gz = max((T)0, max(bl[2] - (oz + hb), (oz - hb) - bh[2]));
+                    keep = ns > 0 && gx * gx + gy * gy + gz * gz <= Rb * Rb * (T)1.0078125;
+                    r2s = Rb * Rb * (T)1.0009765625;
+                }
+                const unsigned kb = __ballot_sync(FULL, keep);
+                const int nk = __popc(kb);
+                if (nk == 0) continue;
+                const int slot = __popc(kb & ((1u << lane) - 1u));
+                int cum = keep ? ns : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(FULL, cum, o);
+                    if (lane >= o) cum += v;
+                }
+                if (keep) {
+                    W.lox[slot] = ox;
+                    W.loy[slot] = oy;
+                    W.loz[slot] = oz;
+                    W.lr2[slot] = r2s;
+                    W.lss[slot] = ss;
+                    W.loff[slot + 1] = cum;
+                }
+                if (lane == 0) W.loff[0] = 0;
+                const int stream = __shfl_sync(FULL, cum, 31);
+                __syncwarp();
+                for (int c0 = 0; c0 < stream; c0 += kNC) {
+                    // 2. stage kNC sources of the stream in the target leaf's frame
+                    const int fill = min(kNC, stream - c0);
+                    for (int k = lane; k < fill; k += 32) {
+                        const int pos = c0 + k;
+                        int lo = 0, hi = nk;  // leaf: loff[lo] <= pos < loff[lo + 1]
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (W.loff[mid] <= pos) lo = mid; else hi = mid;
                         }
-                    } else {
+                        const int src = W.lss[lo] + pos - W.loff[lo];
+                        const V4 y = plocal[src];
+                        const T ax = W.lox[lo], ay = W.loy[lo], az = W.loz[lo];
+                        V4 hv;
+                        hv.x = y.x + ax;
+                        hv.y = y.y + ay;
+                        hv.z = y.z + az;
+                        hv.w = W.lr2[lo];
+                        W.sh[k] = hv;
+                        if (kHiLo) {  // TwoSum error terms plus the lo parts
+                            const float4 yl = plocal_lo[src];
+                            float4 lv;
+                            T bb = hv.x - y.x;
+                            lv.x = (float)(((y.x - (hv.x - bb)) + (ax - bb)) + (T)yl.x);
+                            bb = hv.y - y.y;
+                            lv.y = (float)(((y.y - (hv.y - bb)) + (ay - bb)) + (T)yl.y);
+                            bb = hv.z - y.z;
+                            lv.z = (float)(((y.z - (hv.z - bb)) + (az - bb)) + (T)yl.z);
+                            lv.w = (float)y.w;
+                            W.sl[k] = lv;
+                        } else {
+                            W.sq[k] = y.w;
+                        }
+                    }
+                    __syncwarp();
+                    // 3. screening, 32 candidates per lane: k = u0 + sub + G i
+                    for (int u0 = 0; u0 < fill; u0 += 32 * G) {
+                        unsigned mask = 0;
+                        if (tvalid) {
+                            if (u0 + 32 * G <= fill) {
 #pragma unroll 8
-                        for (int k = 0; k < 32; ++k) {
-                            const int jj = c0 + g + G * k;
-                            if (jj < ns) {
-                                const V4 y = plocal[ss + jj];
-                                const T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
-                                if (dx * dx + dy * dy + dz * dz < Rb2_screen) mask |= 1u << k;
+                                for (int i = 0; i < 32; ++i) {
+                                    const V4 y = W.sh[u0 + sub + G * i];
+                                    const T dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
+                                    if (dx * dx + dy * dy + dz * dz < y.w) mask |= 1u << i;
+                                }
+                            } else {
+                                for (int i = 0; i < 32; ++i) {
+                                    const int k = u0 + sub + G * i;
+                                    if (k >= fill) break;
+                                    const V4 y = W.sh[k];
+                                    const T dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
+                                    if (dx * dx + dy * dy + dz * dz < y.w) mask |= 1u << i;
+                                }
                             }
                         }
-                    }
-                    // pass 2: the residual kernel on the pairs inside the support
-                    while (mask) {
-                        const int k = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const int jj = c0 + g + G * k;
-                        const V4 y = plocal[ss + jj];
-                        T dx = px - y.x, dy = py - y.y, dz = pz - y.z;
-                        if (kHiLo) {
-                            const float4 yl = plocal_lo[ss + jj];
-                            dx += pxl - (T)yl.x;
-                            dy += pyl - (T)yl.y;
-                            dz += pzl - (T)yl.z;
-                        }
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        const T x = (T)2 * r2 * invRb2 - (T)1;
-                        T qv = qc[QD];
+                        // compaction: the warp's marked pairs, in lane order (targets ascending)
+                        const int cnt = __popc(mask);
+                        int pre = cnt;
 #pragma unroll
-                        for (int d = QD - 1; d >= 0; --d) qv = qv * x + qc[d];
-                        const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                        const T v = rinv - qv * invRb;
-                        const T term = (r2 < Rb2) ? y.w * v : (T)0;
-                        inside32 += (r2 < Rb2) ? 1u : 0u;
-                        const T yk = term - comp;
-                        const T tk = part + yk;
-                        comp = (tk - part) - yk;
-                        part = tk;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int v = __shfl_up_sync(FULL, pre, o);
+                            if (lane >= o) pre += v;
+                        }
+                        const int total = __shfl_sync(FULL, pre, 31);
+                        int o = pre - cnt;
+                        while (mask) {
+                            const int i = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            W.q[o++] = (uint16_t)((t << 7) | (u0 + sub + G * i));
+                        }
+                        __syncwarp();
+                        // the residual kernel, one marked pair per lane
+                        for (int r0 = 0; r0 < total; r0 += 32) {
+                            const int e = r0 + lane;
+                            int key = -1 - lane;
+                            T val = 0;
+                            if (e < total) {
+                                const int ent = W.q[e], tt = ent >> 7, k = ent & 127;
+                                key = tt;
+                                const V4 y = W.sh[k], x = W.th[tt];
+                                T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                                T qj;
+                                if (kHiLo) {
+                                    const float4 yl = W.sl[k], xl = W.tl[tt];
+                                    dx += (T)xl.x - (T)yl.x;
+                                    dy += (T)xl.y - (T)yl.y;
+                                    dz += (T)xl.z - (T)yl.z;
+                                    qj = (T)yl.w;
+                                } else {
+                                    qj = W.sq[k];
+                                }
+                                T R2, invR, invR2;
+                                level_scales(y.w, R2, invR, invR2);
+                                const T r2 = dx * dx + dy * dy + dz * dz;
+                                const T xx = (T)2 * r2 * invR2 - (T)1;
+                                T qv = qc[QD];
+#pragma unroll
+                                for (int d = QD - 1; d >= 0; --d) qv = qv * xx + qc[d];
+                                const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
+                                const bool in = r2 < R2;
+                                val = in ? qj * (rinv - qv * invR) : (T)0;
+                                inside32 += in ? 1u : 0u;
+                            }
+                            // 4. segmented sum over lanes with the same target
+#pragma unroll
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const T vu = __shfl_up_sync(FULL, val, d);
+                                const int ku = __shfl_up_sync(FULL, key, d);
+                                if (lane >= d && ku == key) val += vu;
+                            }
+                            const int kn = __shfl_down_sync(FULL, key, 1);
+                            if (e < total && (lane == 31 || kn != key)) W.acc[key] += (double)val;
+                            __syncwarp();
+                        }
                     }
+                    __syncwarp();
                 }
-                acc += (double)part - (double)comp;
             }
-            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (valid && g == 0 && (tv.pflag[ts + j] & 2)) unear[ts + j] = acc;
+            if (lane < ng && (tv.pflag[ts + j0 + lane] & 2)) unear[ts + j0 + lane] = W.acc[lane];
+            __syncwarp();
         }
     }
 }
@@ -997,13 +1396,18 @@ __global__ void k_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout,
     pot[pout[k]] = v / frame->S;
 }
 
-// launch k_near with the residual polynomial degree as a template argument
+// launch k_near with the residual polynomial degree as a template argument;
+// returns 1 for a degree outside 2..30, 2 for a failed launch
 template <typename T, int QD>
-static void launch_near_qd(int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
-                           const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
-                           const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
-    k_near<T, QD><<<grid, kNearThreads, 0, st>>>(tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, QD,
-                                                  unear, counter);
+static cudaError_t launch_near_qd(int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
+                                  const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
+                                  const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
+    constexpr size_t smem = (size_t)(kNearThreads / 32) * sizeof(NearWarp<T>);
+    cudaError_t e = cudaFuncSetAttribute(k_near<T, QD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_near<T, QD><<<grid, kNearThreads, smem, st>>>(tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, QD,
+                                                     unear, counter);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1012,7 +1416,9 @@ static int launch_near(int qdeg, int grid, cudaStream_t st, TreeView tv, int ntl
                        const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
     switch (qdeg) {
 #define DMK_NEAR_CASE(d) \
-    case d: launch_near_qd<T, d>(grid, st, tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, unear, counter); return 0;
+    case d: \
+        return launch_near_qd<T, d>(grid, st, tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, unear, \
+                                    counter) == cudaSuccess ? 0 : 2;
         DMK_NEAR_CASE(2) DMK_NEAR_CASE(3) DMK_NEAR_CASE(4) DMK_NEAR_CASE(5) DMK_NEAR_CASE(6) DMK_NEAR_CASE(7)
         DMK_NEAR_CASE(8) DMK_NEAR_CASE(9) DMK_NEAR_CASE(10) DMK_NEAR_CASE(11) DMK_NEAR_CASE(12) DMK_NEAR_CASE(13)
         DMK_NEAR_CASE(14) DMK_NEAR_CASE(15) DMK_NEAR_CASE(16) DMK_NEAR_CASE(17) DMK_NEAR_CASE(18) DMK_NEAR_CASE(19)
@@ -1073,7 +1479,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     if (ws.ensure(cx.bufs->M, (int64_t)nslots * P3 * sizeof(T)) ||
         ws.ensure(cx.bufs->Lam, (int64_t)nslots * P3 * sizeof(T)) ||
         ws.ensure(cx.bufs->LamW, (int64_t)P3 * sizeof(T)) || ws.ensure(cx.bufs->ufar, n * 8) ||
-        ws.ensure(cx.bufs->unear, n * 8) || ws.ensure(cx.bufs->counter, 64)) {
+        ws.ensure(cx.bufs->unear, n * 8) || ws.ensure(cx.bufs->counter, 256)) {
         err = "device allocation failed (expansions)";
         return DMK_ERR_OOM;
     }
@@ -1084,7 +1490,9 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     double *unear = (double *)cx.bufs->unear.p;
     PCK(cudaMemsetAsync(ufar, 0, n * 8, st));
     PCK(cudaMemsetAsync(unear, 0, n * 8, st));
-    PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 64, st));
+    // device words: [0] near work queue, [2..3] pairs inside R_L, [4..5] local
+    // flops, [6] tensor-core wait error, [32 + l] level-l work queue of k_local
+    PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 256, st));
 
     // ---- upward pass (finest level first)
     cudaEventRecord(cx.ev[1], st);
@@ -1137,38 +1545,51 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     // ---- local expansions, coarsest level first; leaves evaluate
     {
         // buffer 1 holds the incoming expansion, the p2c scratch (2 P^3) and the
-        // evaluation intermediate W (kECH P^2)
+        // evaluation intermediate W (kECH P^2) or the tensor-core operands
+        using LS = LocalShape<P, NF>;
+        const bool tcore = sizeof(T) == 4 && LS::TC_OK;
         const size_t psi_bytes = std::max({(size_t)2 * N1 * NH * NH * sizeof(C2), (size_t)2 * P3 * sizeof(T),
-                                           (size_t)kECH * P * P * sizeof(T)});
+                                           (size_t)kECH * P * P * sizeof(T),
+                                           tcore ? (size_t)LS::TC_BUF1 * sizeof(float) : (size_t)0});
+        const size_t t1_bytes = std::max((size_t)2 * P * NH * NH * sizeof(C2),
+                                         tcore ? (size_t)LS::TC_BUF2 * sizeof(float) : (size_t)0);
         cudaEventRecord(cx.ev[6], st);
-        BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, (size_t)2 * P * NH * NH * sizeof(C2),
-                                     (size_t)P * NH * sizeof(T), (size_t)3 * kECH * P * sizeof(T),
-                                     (size_t)2 * P * P * sizeof(T)},
-                                    smem_limit - 2048);
+        BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, t1_bytes, (size_t)P * NH * sizeof(T),
+                                     (size_t)3 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
+                                     P3 * sizeof(T)},
+                                    smem_limit - 12288);
+        if (tcore && !(lay.in_smem[1] && lay.in_smem[2])) {
+            err = "tensor-core operands do not fit in shared memory";
+            return DMK_ERR_INTERNAL;
+        }
         PCK(cudaFuncSetAttribute(k_local<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         for (int l = 0; l < tv.nlev; ++l) {
             int lc = tv.lev_count[l];
-            int grid = std::min(lc, cx.num_sms * 2);
+            int grid = std::min((lc + 7) / 8, cx.num_sms);
             if (grid <= 0) continue;
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
             k_local<T, P, NF><<<grid, kLThreads, lay.smem_bytes, st>>>(tv, tb, l, tv.lev_start[l], lc, Phi, Lam,
                                                                        LamW, ufar, lay, (char *)cx.bufs->slab.p,
-                                                                       (unsigned long long *)cx.bufs->counter.p + 2);
+                                                                       (unsigned long long *)cx.bufs->counter.p + 2,
+                                                                       (int *)cx.bufs->counter.p + 6,
+                                                                       (int *)cx.bufs->counter.p + 32 + l);
         }
         PCK(cudaGetLastError());
     }
     // ---- residual near field and self corrections
     cudaEventRecord(cx.ev[3], st);
     if (cx.tree->ntleaves > 0) {
-        int grid = std::min((cx.tree->ntleaves + 7) / 8, cx.num_sms * 8);
+        const int wpb = kNearThreads / 32;
+        int grid = std::min((cx.tree->ntleaves + wpb - 1) / wpb, cx.num_sms * 8);
         ::dmk::launch_tick();
         int rc_near = launch_near<T>(tb.qdeg, grid, st, tv, cx.tree->ntleaves, (const int32_t *)cx.tree->tleaves.p,
                                      (const int32_t *)cx.tree->nl_off.p, (const int32_t *)cx.tree->nl_src.p,
                                      (const typename Vec4<T>::type *)cx.tree->plocal.p,
                                      (const float4 *)cx.tree->plocal_lo.p, tb.qmono, unear,
                                      (int *)cx.bufs->counter.p);
-        if (rc_near) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
+        if (rc_near == 1) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
+        if (rc_near) { err = "near-field launch failed"; return DMK_ERR_CUDA; }
         PCK(cudaGetLastError());
     }
     cudaEventRecord(cx.ev[4], st);
