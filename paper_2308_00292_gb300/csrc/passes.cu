@@ -10,7 +10,8 @@
 //               rho~ = V^-T M, so M carries the same information; the library
 //               folds V^-T into the plane-wave matrix F.
 //   outgoing    Phi[my][mx][mz], m in [-nf, nf]^2 x [0, nf]: the half spectrum of
-//               eq. outgoingexpansion2 (Phi_{-m} = conj(Phi_m) for real charges).
+//               eq. outgoingexpansion2 (Phi_{-m} = conj(Phi_m) for real charges);
+//               the m_z index is padded to an even count (nz_pad).
 //   local       Lambda[a][b][c], Chebyshev coefficients of the far field in the
 //               box (eq. localexpansion).
 //
@@ -72,6 +73,19 @@ template <typename U>
 __device__ __forceinline__ U *buf_ptr(const BufLayout &lay, int i, char *sm, char *slab) {
     return lay.in_smem[i] ? reinterpret_cast<U *>(sm + lay.off[i])
                           : reinterpret_cast<U *>(slab + (size_t)blockIdx.x * lay.slab_bytes + lay.off[i]);
+}
+
+// the stored half spectrum pads m_z to an even count so that two adjacent
+// modes form one aligned 16-byte (single) or 32-byte (double) pair
+template <int NF> __host__ __device__ constexpr int nz_pad() { return (NF + 2) & ~1; }
+
+template <typename C2> struct C2x2 { C2 a, b; };
+__device__ __forceinline__ C2x2<float2> ld_pair(const float2 *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ C2x2<double2> ld_pair(const double2 *p) {
+    return {p[0], p[1]};
 }
 
 template <typename C2, typename T>
@@ -316,7 +330,8 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
     T *hs = buf_ptr<T>(lay, 3, sm, slab);    // [n][m']
     const int tid = threadIdx.x;
     load_hs<T, P, NF>(tb, hs);
-    const size_t stride = (size_t)N1 * N1 * NH;
+    constexpr int NHP = nz_pad<NF>();
+    const size_t stride = (size_t)N1 * N1 * NHP;
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
         const int B = slot2box[slot];
         if (!(tv.bflags[B] & BF_FOUT)) continue;
@@ -369,8 +384,8 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
                 const T h = hs[a * NH + mxp];
                 if (a & 1) cfma(O, h, t); else cfma(E, h, t);
             }
-            out[(size_t)(my * N1 + NF + mxp) * NH + mz] = C2{E.x - O.y, E.y + O.x};
-            if (mxp > 0) out[(size_t)(my * N1 + NF - mxp) * NH + mz] = C2{E.x + O.y, E.y - O.x};
+            out[(size_t)(my * N1 + NF + mxp) * NHP + mz] = C2{E.x - O.y, E.y + O.x};
+            if (mxp > 0) out[(size_t)(my * N1 + NF - mxp) * NHP + mz] = C2{E.x + O.y, E.y - O.x};
         }
     }
 }
@@ -593,13 +608,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                                                         unsigned long long *flops, int *tc_err, int *run_ctr) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
-    constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P;
+    constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P, NHP = nz_pad<NF>();
     // single precision evaluates the leaves on the tensor cores (3xTF32)
     constexpr bool kTC = sizeof(T) == 4 && S::TC_OK;
     extern __shared__ __align__(128) char sm[];
     T *Ls = buf_ptr<T>(lay, 0, sm, slab);
     C2 *PsE = buf_ptr<C2>(lay, 1, sm, slab);  // [my + NF][mx'][mz]; PsO follows
-    C2 *PsO = PsE + N1 * NH * NH;
+    C2 *PsO = PsE + N1 * NH * NHP;
     C2 *T2 = PsE;                              // [a][b][mz], reuses the Psi buffers
     C2 *T1e = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my'][mz]; T1o follows
     C2 *T1o = T1e + P * NH * NH;
@@ -629,7 +644,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     }
     load_hs<T, P, NF>(tb, hs);
     for (int i = tid; i < 2 * P * P; i += kLThreads) As[i] = tb.A[i];
-    const size_t pstride = (size_t)N1 * N1 * NH;
+    const size_t pstride = (size_t)N1 * N1 * NHP;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
     T *Pl = buf_ptr<T>(lay, 6, sm, slab);     // the parent's Lambda, kept for its next children
@@ -715,49 +730,71 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 s_ud[t] = make_float2(k ? 1.f : 0.f, k == 1 ? 1.f : (k == 2 ? -1.f : 0.f));
             }
             __syncthreads();
-            // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x
-            for (int i = tid; i < N1 * NH * NH; i += kLThreads) {
-                const int my = i / (NH * NH), r = i % (NH * NH), mxp = r / NH, mz = r % NH;
+            // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x;
+            // a thread takes two adjacent m_z (one 16-byte load per colleague and sign
+            // of m_x), four colleagues per step for memory-level parallelism
+            for (int i = tid; i < N1 * NH * (NHP / 2); i += kLThreads) {
+                const int my = i / (NH * (NHP / 2)), r = i % (NH * (NHP / 2)), mxp = r / (NHP / 2);
+                const int mz0 = 2 * (r % (NHP / 2));
                 const int myv = my - NF;
-                const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3, rz = mz % 3;
-                const float2 *udp = s_ud + rxp + 3 * ry + 9 * rz, *udm = s_ud + rxm + 3 * ry + 9 * rz;
-                C2 Tp{0, 0}, Up{0, 0}, Dp{0, 0}, Tm{0, 0}, Um{0, 0}, Dm{0, 0};
-                const size_t off_p = (size_t)(my * N1 + NF + mxp) * NH + mz;
-                const size_t off_m = (size_t)(my * N1 + NF - mxp) * NH + mz;
+                const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3;
+                const int rz0 = mz0 % 3, rz1 = (mz0 + 1) % 3;
+                const float2 *udp0 = s_ud + rxp + 3 * ry + 9 * rz0, *udp1 = s_ud + rxp + 3 * ry + 9 * rz1;
+                const float2 *udm0 = s_ud + rxm + 3 * ry + 9 * rz0, *udm1 = s_ud + rxm + 3 * ry + 9 * rz1;
+                C2 Tp[2] = {}, Up[2] = {}, Dp[2] = {}, Tm[2] = {}, Um[2] = {}, Dm[2] = {};
+                const size_t off_p = (size_t)(my * N1 + NF + mxp) * NHP + mz0;
+                const size_t off_m = (size_t)(my * N1 + NF - mxp) * NHP + mz0;
                 if (mxp > 0) {
-#pragma unroll 3
+#pragma unroll 4
                     for (int j = 0; j < ncol; ++j) {
                         const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
-                        const C2 vp = ph[off_p], vm = ph[off_m];
-                        const float2 cp = udp[27 * j], cm = udm[27 * j];
-                        Tp.x += vp.x; Tp.y += vp.y;
-                        cfma(Up, (T)cp.x, vp);
-                        cfma(Dp, (T)cp.y, vp);
-                        Tm.x += vm.x; Tm.y += vm.y;
-                        cfma(Um, (T)cm.x, vm);
-                        cfma(Dm, (T)cm.y, vm);
+                        const C2x2<C2> vp = ld_pair(ph + off_p), vm = ld_pair(ph + off_m);
+                        const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
+                        const float2 cm0 = udm0[27 * j], cm1 = udm1[27 * j];
+                        Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
+                        Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
+                        cfma(Up[0], (T)cp0.x, vp.a);
+                        cfma(Dp[0], (T)cp0.y, vp.a);
+                        cfma(Up[1], (T)cp1.x, vp.b);
+                        cfma(Dp[1], (T)cp1.y, vp.b);
+                        Tm[0].x += vm.a.x; Tm[0].y += vm.a.y;
+                        Tm[1].x += vm.b.x; Tm[1].y += vm.b.y;
+                        cfma(Um[0], (T)cm0.x, vm.a);
+                        cfma(Dm[0], (T)cm0.y, vm.a);
+                        cfma(Um[1], (T)cm1.x, vm.b);
+                        cfma(Dm[1], (T)cm1.y, vm.b);
                     }
                 } else {
-#pragma unroll 3
+#pragma unroll 4
                     for (int j = 0; j < ncol; ++j) {
-                        const C2 vp = Phi[(size_t)s_cslot[j] * pstride + off_p];
-                        const float2 cp = udp[27 * j];
-                        Tp.x += vp.x; Tp.y += vp.y;
-                        cfma(Up, (T)cp.x, vp);
-                        cfma(Dp, (T)cp.y, vp);
+                        const C2x2<C2> vp = ld_pair(Phi + (size_t)s_cslot[j] * pstride + off_p);
+                        const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
+                        Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
+                        Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
+                        cfma(Up[0], (T)cp0.x, vp.a);
+                        cfma(Dp[0], (T)cp0.y, vp.a);
+                        cfma(Up[1], (T)cp1.x, vp.b);
+                        cfma(Dp[1], (T)cp1.y, vp.b);
                     }
                 }
-                const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
-                // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
-                const C2 psp{w * (Tp.x - (T)1.5 * Up.x - kH * Dp.y), w * (Tp.y - (T)1.5 * Up.y + kH * Dp.x)};
-                const size_t o = (size_t)(my * NH + mxp) * NH + mz;
-                if (mxp > 0) {
-                    const C2 psm{w * (Tm.x - (T)1.5 * Um.x - kH * Dm.y), w * (Tm.y - (T)1.5 * Um.y + kH * Dm.x)};
-                    PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
-                    PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
-                } else {
-                    PsE[o] = psp;
-                    PsO[o] = C2{0, 0};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int mz = mz0 + h;
+                    if (mz >= NH) continue;
+                    const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
+                    // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
+                    const C2 psp{w * (Tp[h].x - (T)1.5 * Up[h].x - kH * Dp[h].y),
+                                 w * (Tp[h].y - (T)1.5 * Up[h].y + kH * Dp[h].x)};
+                    const size_t o = (size_t)(my * NH + mxp) * NHP + mz;
+                    if (mxp > 0) {
+                        const C2 psm{w * (Tm[h].x - (T)1.5 * Um[h].x - kH * Dm[h].y),
+                                     w * (Tm[h].y - (T)1.5 * Um[h].y + kH * Dm[h].x)};
+                        PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
+                        PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
+                    } else {
+                        PsE[o] = psp;
+                        PsO[o] = C2{0, 0};
+                    }
                 }
             }
             __syncthreads();
@@ -769,8 +806,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 for (int k = 0; k < S::AC; ++k) ap[k] = am[k] = C2{0, 0};
                 const int rp = (NF + myp) * NH, rm = (NF - myp) * NH;
                 for (int mxp = 0; mxp <= NF; ++mxp) {
-                    const C2 ep = PsE[(rp + mxp) * NH + mz], em = PsE[(rm + mxp) * NH + mz];
-                    const C2 op = PsO[(rp + mxp) * NH + mz], om = PsO[(rm + mxp) * NH + mz];
+                    const C2 ep = PsE[(rp + mxp) * NHP + mz], em = PsE[(rm + mxp) * NHP + mz];
+                    const C2 op = PsO[(rp + mxp) * NHP + mz], om = PsO[(rm + mxp) * NHP + mz];
 #pragma unroll
                     for (int k = 0; k < S::AC; ++k) {
                         const int a = ag + S::AG * k;
@@ -1121,35 +1158,66 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 constexpr int kNearThreads = 128;
 constexpr int kNC = 128;  // staged sources per chunk
 
-// the screening radius^2 of a staged source is R_b^2 (1 + 2^-10) with
-// R_b = 2^-b: its exponent gives R_b^2, 1/R_b and 1/R_b^2 exactly
-__device__ __forceinline__ void level_scales(float w, float &R2, float &invR, float &invR2) {
-    const int bits = __float_as_int(w), E = (bits >> 23) & 255, b = (127 - E) >> 1;
-    R2 = __int_as_float(bits & 0x7f800000);
-    invR2 = __int_as_float((254 - E) << 23);
-    invR = __int_as_float((127 + b) << 23);
-}
-__device__ __forceinline__ void level_scales(double w, double &R2, double &invR, double &invR2) {
-    const long long bits = __double_as_longlong(w);
-    const int E = (int)((bits >> 52) & 2047), b = (1023 - E) >> 1;
-    R2 = __longlong_as_double(bits & 0x7ff0000000000000ll);
-    invR2 = __longlong_as_double((long long)(2046 - E) << 52);
-    invR = __longlong_as_double((long long)(1023 + b) << 52);
-}
-
 // per-warp shared memory of k_near
 template <typename T> struct NearWarp {
     using V4 = typename Vec4<T>::type;
-    V4 sh[kNC];        // staged sources: x, y, z in the target leaf's frame (hi), screening radius^2
+    V4 sh[kNC];        // staged sources: x, y, z in the target leaf's frame (hi) and
+                       // |s|^2 - R_b^2 (1 + 2^-9) carrying the leaf level b in its low bits
     float4 sl[kNC];    // single precision: lo parts of x, y, z and the charge
     T sq[kNC];         // double precision: the charge
     V4 th[32];         // the group's targets (hi) and
     float4 tl[32];     // their lo parts
     double acc[32];    // per-target sums
-    T lox[32], loy[32], loz[32], lr2[32];  // kept source leaves: centre offset, screening radius^2
-    int lss[32], loff[33];                 // first point, offset in the stream
-    uint16_t q[32 * 32];                   // marked pairs: (target << 7) | staged source
+    T lox[32], loy[32], loz[32];            // kept source leaves: centre offset,
+    int lb_[32];                            // level
+    int lss[32], loff[33];                  // first point, offset in the stream
+    int fkey[32];                           // per lane: target of its first segment
+    T fsum[32];                             // and that segment's sum
+    uint16_t q[32 * 32];                    // marked pairs: (target << 7) | staged source
 };
+
+// the staged threshold |s|^2 - R_b^2 (1 + 2^-9) keeps the level b of the
+// source's leaf in its five low mantissa bits (a change of at most 2^-18 of
+// its value, well inside the margin); 1 / R_b = 2^b
+__device__ __forceinline__ float pack_level(float thr, int b) {
+    return __int_as_float((__float_as_int(thr) & ~31) | b);
+}
+__device__ __forceinline__ double pack_level(double thr, int b) {
+    return __longlong_as_double((__double_as_longlong(thr) & ~31ll) | b);
+}
+__device__ __forceinline__ float inv_radius(float thr) {
+    return __int_as_float((127 + (__float_as_int(thr) & 31)) << 23);
+}
+__device__ __forceinline__ double inv_radius(double thr) {
+    return __longlong_as_double((long long)(1023 + (int)(__double_as_longlong(thr) & 31)) << 52);
+}
+
+// screening of 32 staged sources k = u0 + sub + G i against this lane's
+// target: bit i set when |t - s|^2 < R_b^2 (1 + 2^-9), with the difference
+// formed as (-2 t) . s + (|s|^2 - R_b^2 (1 + 2^-9)) + |t|^2; its cancellation
+// error (~1e-6 R_b^2) is far below the 2^-9 margin, so no pair inside the
+// support is dropped (the exact test follows in the evaluation)
+template <typename T, int G, bool FULL_UNIT>
+__device__ __forceinline__ unsigned screen_unit(const typename Vec4<T>::type *sh, int u0, int sub, int fill, T t2x,
+                                                T t2y, T t2z, T ntt) {
+    unsigned mask = 0;
+    const typename Vec4<T>::type *p = sh + u0 + sub;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        if (!FULL_UNIT && u0 + sub + G * i >= fill) break;
+        const typename Vec4<T>::type y = p[G * i];
+        const T d = fma(t2x, y.x, fma(t2y, y.y, fma(t2z, y.z, y.w)));
+        if (d < ntt) mask |= 1u << i;
+    }
+    return mask;
+}
+
+template <typename T, int G>
+__device__ __forceinline__ unsigned screen_g(const typename Vec4<T>::type *sh, int u0, int sub, int fill, T t2x,
+                                             T t2y, T t2z, T ntt) {
+    return u0 + 32 * G <= fill ? screen_unit<T, G, true>(sh, u0, sub, fill, t2x, t2y, t2z, ntt)
+                               : screen_unit<T, G, false>(sh, u0, sub, fill, t2x, t2y, t2z, ntt);
+}
 
 template <typename T, int QD>
 __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, const int32_t *tleaves,
@@ -1217,15 +1285,18 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
             __syncwarp();
             const bool tvalid = t < ng;
             const V4 xt = W.th[tvalid ? t : 0];
+            const T t2x = (T)-2 * xt.x, t2y = (T)-2 * xt.y, t2z = (T)-2 * xt.z;
+            const T ntt = -(xt.x * xt.x + xt.y * xt.y + xt.z * xt.z);
             for (int lb = l0; lb < l1; lb += 32) {
                 // 1. up to 32 source leaves, one per lane; drop those out of reach
                 const int li = lb + lane;
                 bool keep = false;
                 int ns = 0, ss = 0;
-                T ox = 0, oy = 0, oz = 0, r2s = 0;
+                T ox = 0, oy = 0, oz = 0;
+                int b = 0;
                 if (li < l1) {
                     const int Sb = nl_src[li];
-                    const int b = tv.blevel[Sb];
+                    b = tv.blevel[Sb];
                     int sx, sy, sz;
                     morton_decode_d(tv.bkey[Sb], sx, sy, sz);
                     ox = dyadic_centre<T>(sx, b) - cTx;
@@ -1239,7 +1310,6 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                     const T gy = max((T)0, max(bl[1] - (oy + hb), (oy - hb) - bh[1]));
                     const T gz = max((T)0, max(bl[2] - (oz + hb), (oz - hb) - bh[2]));
                     keep = ns > 0 && gx * gx + gy * gy + gz * gz <= Rb * Rb * (T)1.0078125;
-                    r2s = Rb * Rb * (T)1.0009765625;
                 }
                 const unsigned kb = __ballot_sync(FULL, keep);
                 const int nk = __popc(kb);
@@ -1255,31 +1325,30 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                     W.lox[slot] = ox;
                     W.loy[slot] = oy;
                     W.loz[slot] = oz;
-                    W.lr2[slot] = r2s;
+                    W.lb_[slot] = b;
                     W.lss[slot] = ss;
                     W.loff[slot + 1] = cum;
                 }
                 if (lane == 0) W.loff[0] = 0;
                 const int stream = __shfl_sync(FULL, cum, 31);
                 __syncwarp();
+                int lf = 0;  // leaf of this lane's next staged position (positions only grow)
                 for (int c0 = 0; c0 < stream; c0 += kNC) {
                     // 2. stage kNC sources of the stream in the target leaf's frame
                     const int fill = min(kNC, stream - c0);
                     for (int k = lane; k < fill; k += 32) {
                         const int pos = c0 + k;
-                        int lo = 0, hi = nk;  // leaf: loff[lo] <= pos < loff[lo + 1]
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (W.loff[mid] <= pos) lo = mid; else hi = mid;
-                        }
-                        const int src = W.lss[lo] + pos - W.loff[lo];
+                        while (W.loff[lf + 1] <= pos) ++lf;
+                        const int src = W.lss[lf] + pos - W.loff[lf];
                         const V4 y = plocal[src];
-                        const T ax = W.lox[lo], ay = W.loy[lo], az = W.loz[lo];
+                        const T ax = W.lox[lf], ay = W.loy[lf], az = W.loz[lf];
+                        const int lev = W.lb_[lf];
                         V4 hv;
                         hv.x = y.x + ax;
                         hv.y = y.y + ay;
                         hv.z = y.z + az;
-                        hv.w = W.lr2[lo];
+                        const T Rb2 = ldexp_t<T>((T)1.001953125, -2 * lev);  // R_b^2 (1 + 2^-9)
+                        hv.w = pack_level(hv.x * hv.x + hv.y * hv.y + hv.z * hv.z - Rb2, lev);
                         W.sh[k] = hv;
                         if (kHiLo) {  // TwoSum error terms plus the lo parts
                             const float4 yl = plocal_lo[src];
@@ -1301,21 +1370,11 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                     for (int u0 = 0; u0 < fill; u0 += 32 * G) {
                         unsigned mask = 0;
                         if (tvalid) {
-                            if (u0 + 32 * G <= fill) {
-#pragma unroll 8
-                                for (int i = 0; i < 32; ++i) {
-                                    const V4 y = W.sh[u0 + sub + G * i];
-                                    const T dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
-                                    if (dx * dx + dy * dy + dz * dz < y.w) mask |= 1u << i;
-                                }
-                            } else {
-                                for (int i = 0; i < 32; ++i) {
-                                    const int k = u0 + sub + G * i;
-                                    if (k >= fill) break;
-                                    const V4 y = W.sh[k];
-                                    const T dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
-                                    if (dx * dx + dy * dy + dz * dz < y.w) mask |= 1u << i;
-                                }
+                            switch (G) {
+                            case 1: mask = screen_g<T, 1>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
+                            case 2: mask = screen_g<T, 2>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
+                            case 4: mask = screen_g<T, 4>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
+                            default: mask = screen_g<T, 8>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
                             }
                         }
                         // compaction: the warp's marked pairs, in lane order (targets ascending)
@@ -1334,49 +1393,80 @@ __global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, con
                             W.q[o++] = (uint16_t)((t << 7) | (u0 + sub + G * i));
                         }
                         __syncwarp();
-                        // the residual kernel, one marked pair per lane
-                        for (int r0 = 0; r0 < total; r0 += 32) {
-                            const int e = r0 + lane;
-                            int key = -1 - lane;
-                            T val = 0;
-                            if (e < total) {
-                                const int ent = W.q[e], tt = ent >> 7, k = ent & 127;
-                                key = tt;
-                                const V4 y = W.sh[k], x = W.th[tt];
-                                T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
-                                T qj;
-                                if (kHiLo) {
-                                    const float4 yl = W.sl[k], xl = W.tl[tt];
-                                    dx += (T)xl.x - (T)yl.x;
-                                    dy += (T)xl.y - (T)yl.y;
-                                    dz += (T)xl.z - (T)yl.z;
-                                    qj = (T)yl.w;
-                                } else {
-                                    qj = W.sq[k];
+                        if (total == 0) continue;
+                        // the residual kernel: lane L takes the marked pairs [L n, (L + 1) n)
+                        // in order, so it meets each target in one run; a run that starts
+                        // inside the lane's block belongs to this lane alone and goes to
+                        // the target's sum directly, the run at the block start may be
+                        // shared with earlier lanes and is combined below in lane order
+                        const int nper = (total + 31) >> 5;
+                        const int e0 = min(lane * nper, total), e1 = min(e0 + nper, total);
+                        int cur = -1, first = -1;
+                        T part = 0, fpart = 0;
+                        V4 x = W.th[0];
+                        float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int e = e0; e < e1; ++e) {
+                            const int ent = W.q[e], tt = ent >> 7, k = ent & 127;
+                            if (tt != cur) {  // a new run: flush the previous one, load the target
+                                if (cur >= 0) {
+                                    if (first < 0) {
+                                        first = cur;
+                                        fpart = part;
+                                    } else {
+                                        W.acc[cur] += (double)part;
+                                    }
                                 }
-                                T R2, invR, invR2;
-                                level_scales(y.w, R2, invR, invR2);
-                                const T r2 = dx * dx + dy * dy + dz * dz;
-                                const T xx = (T)2 * r2 * invR2 - (T)1;
-                                T qv = qc[QD];
-#pragma unroll
-                                for (int d = QD - 1; d >= 0; --d) qv = qv * xx + qc[d];
-                                const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                                const bool in = r2 < R2;
-                                val = in ? qj * (rinv - qv * invR) : (T)0;
-                                inside32 += in ? 1u : 0u;
+                                cur = tt;
+                                part = 0;
+                                x = W.th[tt];
+                                if (kHiLo) xl = W.tl[tt];
                             }
-                            // 4. segmented sum over lanes with the same target
-#pragma unroll
-                            for (int d = 1; d < 32; d <<= 1) {
-                                const T vu = __shfl_up_sync(FULL, val, d);
-                                const int ku = __shfl_up_sync(FULL, key, d);
-                                if (lane >= d && ku == key) val += vu;
+                            const V4 y = W.sh[k];
+                            T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                            T qj;
+                            if (kHiLo) {
+                                const float4 yl = W.sl[k];
+                                dx += (T)xl.x - (T)yl.x;
+                                dy += (T)xl.y - (T)yl.y;
+                                dz += (T)xl.z - (T)yl.z;
+                                qj = (T)yl.w;
+                            } else {
+                                qj = W.sq[k];
                             }
-                            const int kn = __shfl_down_sync(FULL, key, 1);
-                            if (e < total && (lane == 31 || kn != key)) W.acc[key] += (double)val;
-                            __syncwarp();
+                            const T iR = inv_radius(y.w), iR2 = iR * iR;
+                            const T r2 = dx * dx + dy * dy + dz * dz;
+                            const T xx = (T)2 * r2 * iR2 - (T)1;  // r < R_b  <=>  xx < 1
+                            T qv = qc[QD];
+#pragma unroll
+                            for (int d = QD - 1; d >= 0; --d) qv = qv * xx + qc[d];
+                            const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
+                            const bool in = xx < (T)1;
+                            const T val = in ? qj * (rinv - qv * iR) : (T)0;
+                            inside32 += in ? 1u : 0u;
+                            part += val;
                         }
+                        if (cur >= 0) {
+                            if (first < 0) {
+                                first = cur;
+                                fpart = part;
+                            } else {
+                                W.acc[cur] += (double)part;
+                            }
+                        }
+                        // first runs: a segmented sum over lanes with the same target
+                        // (lanes without pairs carry no key)
+                        int key = first >= 0 ? first : -1 - lane;
+                        T v = fpart;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const T vu = __shfl_up_sync(FULL, v, d);
+                            const int ku = __shfl_up_sync(FULL, key, d);
+                            if (lane >= d && ku == key) v += vu;
+                        }
+                        const int kn = __shfl_down_sync(FULL, key, 1);
+                        __syncwarp();
+                        if (first >= 0 && (lane == 31 || kn != key)) W.acc[key] += (double)v;
+                        __syncwarp();
                     }
                     __syncwarp();
                 }
@@ -1514,7 +1604,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     }
     // ---- outgoing expansions of every F_out box
     cudaEventRecord(cx.ev[2], st);
-    if (ws.ensure(cx.bufs->Phi, (int64_t)nslots * N1 * N1 * NH * sizeof(C2))) {
+    if (ws.ensure(cx.bufs->Phi, (int64_t)nslots * N1 * N1 * nz_pad<NF>() * sizeof(C2))) {
         err = "device allocation failed (plane waves)";
         return DMK_ERR_OOM;
     }
@@ -1548,7 +1638,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         // evaluation intermediate W (kECH P^2) or the tensor-core operands
         using LS = LocalShape<P, NF>;
         const bool tcore = sizeof(T) == 4 && LS::TC_OK;
-        const size_t psi_bytes = std::max({(size_t)2 * N1 * NH * NH * sizeof(C2), (size_t)2 * P3 * sizeof(T),
+        const size_t psi_bytes = std::max({(size_t)2 * N1 * NH * nz_pad<NF>() * sizeof(C2), (size_t)2 * P3 * sizeof(T),
                                            (size_t)kECH * P * P * sizeof(T),
                                            tcore ? (size_t)LS::TC_BUF1 * sizeof(float) : (size_t)0});
         const size_t t1_bytes = std::max((size_t)2 * P * NH * NH * sizeof(C2),

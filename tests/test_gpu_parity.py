@@ -54,6 +54,30 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_near_pair_count_matches_kdtree(dmk, oracle_mod, precision):
+    """Every pair closer than R_L of its source leaf (Step 4's support of the
+    residual kernel, r = 0 included) is reached by the interaction lists and
+    counted once: the near kernel's count equals a k-d tree count on the
+    oracle's (bit-identical) tree.  Single precision may flip pairs within
+    rounding of the boundary r = R_L."""
+    spatial = pytest.importorskip("scipy.spatial")
+    x, q = inputs.clustered(20000, seed=204, nclusters=8)
+    _, lev, _, st = run(dmk, x, q, eps=1e-6, leaf_cap=120, precision=precision)
+    lo = x.min(axis=0)
+    S = (x.max(axis=0) - lo).max()
+    u = (x - lo) / S
+    everyone = spatial.cKDTree(u)
+    expected = 0
+    for L in np.unique(lev):
+        expected += int(spatial.cKDTree(u[lev == L]).count_neighbors(everyone, 2.0 ** -int(L)))
+    got = st["near_pairs_inside"]
+    if precision == 0:
+        assert got == expected
+    else:
+        assert abs(got - expected) <= 1e-6 * expected + 10
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_tree_bit_exact(dmk, oracle_mod, case):
     x, q = CASES[case]()
