@@ -601,6 +601,152 @@ __device__ __forceinline__ float eval_part(uint32_t trow, const float (&tx)[P], 
     return sum;
 }
 
+// Shared state of the tensor-core leaf evaluation.
+struct TcEval {
+    float *Bh, *Bl, *Ah, *Al;  // operands (K-major, TF32 hi and lo)
+    uint64_t *bar;             // MMA completion
+    uint32_t tmem;             // accumulator base
+    int *pending;              // an MMA batch outlived its wait
+    float (*red)[128];         // partial sums of column groups 1..3
+    int *err;                  // device error word
+};
+
+// point of position gp in a table of point ranges (starts rs, prefix offsets ro)
+__device__ __forceinline__ int range_point(const int *rs, const int *ro, int gp) {
+    int r = 0;
+    while (gp >= ro[r + 1]) ++r;
+    return rs[r] + gp - ro[r];
+}
+
+// Tensor cores: evaluate the Chebyshev expansion Lev (P^3, box centre cc,
+// scale s2R = 2 / R) at the points of nr ranges: D[j][ab] = sum_c T_c(z_j)
+// Lev[ab][c] for 128 points at a time (points on the TMEM lanes), then each
+// point's threads form u_j = sum_a T_a(x_j) sum_b T_b(y_j) D[j][ab].  Operands
+// are split into TF32 hi + lo and D = A_lo B_hi + A_hi B_lo + A_hi B_hi.  The
+// first 128 points' coordinates are in xyz (fetched by cp.async).  Called by
+// the whole CTA.
+template <int P, int NF>
+__device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)[3], double s2R, const int *rs,
+                        const int *ro, int nr, const double (*xyz)[128], const TcEval &st, uint32_t &phase,
+                        double *ufar) {
+    using S = LocalShape<P, NF>;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ntot = ro[nr];
+    // B operand: row ab, column c of Lev; one float4 (4 columns) per step
+    for (int t = tid; t < S::NP * S::KP / 4; t += kLThreads) {
+        const int r = t & 7, k4 = (t >> 3) % (S::KP / 4), n = ((t >> 3) / (S::KP / 4)) * 8 + r;
+        float h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * k4 + q;
+            const float v = (n < P * P && k < P) ? Lev[n * P + k] : 0.f;
+            tc::split_tf32(v, h[q], l[q]);
+        }
+        reinterpret_cast<float4 *>(st.Bh)[t] = make_float4(h[0], h[1], h[2], h[3]);
+        reinterpret_cast<float4 *>(st.Bl)[t] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int p0 = 0; p0 < ntot; p0 += S::TM) {
+        const int np = min(S::TM, ntot - p0);
+        const bool first = p0 == 0;  // coordinates already in xyz
+        // this thread's epilogue point
+        const int jq = min(tid & (S::TM - 1), np - 1);
+        const int pq = range_point(rs, ro, p0 + jq);
+        const double xq = first ? xyz[0][jq] : tv.ux[pq];
+        const double yq = first ? xyz[1][jq] : tv.uy[pq];
+        if (tid < S::TM) {
+            // A operand row j = T_c(z_j), c < P (zero rows past the points)
+            const int j = tid;
+            float tz[S::KP];
+#pragma unroll
+            for (int n = 0; n < S::KP; ++n) tz[n] = 0.f;
+            if (j < np) {
+                const float zi = (float)(((first ? xyz[2][j] : tv.uz[pq]) - cc[2]) * s2R);
+                tz[0] = 1.f;
+                if (P > 1) tz[1] = zi;
+#pragma unroll
+                for (int n = 2; n < P; ++n) tz[n] = 2.f * zi * tz[n - 1] - tz[n - 2];
+            }
+#pragma unroll
+            for (int k4 = 0; k4 < S::KP / 4; ++k4) {
+                float h[4], l[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tc::split_tf32(tz[4 * k4 + q], h[q], l[q]);
+                const int o = ((j >> 3) * (S::KP / 4) + k4) * 8 + (j & 7);
+                reinterpret_cast<float4 *>(st.Ah)[o] = make_float4(h[0], h[1], h[2], h[3]);
+                reinterpret_cast<float4 *>(st.Al)[o] = make_float4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t lbo = 128, sbo = S::KP * 32;
+            const uint32_t aH = tc::smem_addr(st.Ah), aL = tc::smem_addr(st.Al);
+            const uint32_t bH = tc::smem_addr(st.Bh), bL = tc::smem_addr(st.Bl);
+#pragma unroll
+            for (int h = 0; h < (S::NB > 0 ? 2 : 1); ++h) {
+                const int n0 = h ? S::NA : 0;
+                const uint32_t id = tc::idesc_tf32(S::TM, h ? S::NB : S::NA);
+                const uint32_t boff = (uint32_t)(n0 / 8) * sbo, dcol = st.tmem + (uint32_t)n0;
+#pragma unroll
+                for (int ks = 0; ks < S::KP / 8; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256;
+                    tc::mma_tf32(dcol, tc::sdesc(aL + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id, ks > 0);
+                    tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bL + boff + ko, lbo, sbo), id, true);
+                    tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id, true);
+                }
+            }
+            tc::commit(st.bar);
+        }
+        // every warp waits; warps w, w + 4, w + 8, w + 12 share TMEM lanes
+        // 32 (w mod 4) .. + 31 (points j) and split the ab columns
+        bool ok = tc::mbar_wait(st.bar, phase, 2000000000ll);  // about 1 s
+        ok = __all_sync(0xffffffffu, ok);
+        tc::fence_after_sync();
+        const int j = tid & (S::TM - 1), cg = tid >> 7;
+        float part = 0.f;
+        if (ok) {
+            float tx[P], ty[P];
+            cheb_row<P>((float)((xq - cc[0]) * s2R), tx);
+            cheb_row<P>((float)((yq - cc[1]) * s2R), ty);
+            const uint32_t trow = st.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+            constexpr int NC = S::NP / 8;  // 8-column chunks
+            switch (cg) {
+            case 0: part = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
+            case 1: part = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
+            case 2: part = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
+            default: part = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
+            }
+        } else if ((tid & 31) == 0) {
+            atomicExch(st.err, 1);
+            *st.pending = 1;
+        }
+        if (cg > 0) st.red[cg - 1][j] = part;
+        tc::fence_before_sync();
+        __syncthreads();
+        if (cg == 0 && j < np && (tv.pflag[pq] & 2))
+            ufar[pq] = (double)(part + st.red[0][j] + st.red[1][j] + st.red[2][j]);
+        phase ^= 1u;
+    }
+}
+
+// cp.async of the coordinates of the first 128 points of a range table
+__device__ __forceinline__ void fetch_xyz(const TreeView &tv, const int *rs, const int *ro, int nr,
+                                          double (*xyz)[128]) {
+    const int n0 = min(128, ro[nr]);
+    for (int t = threadIdx.x; t < 3 * 128; t += blockDim.x) {
+        const int ax = t >> 7, j = t & 127;
+        if (j < n0) {
+            const int pt = range_point(rs, ro, j);
+            cp_async8(&xyz[ax][j], (ax == 0 ? tv.ux : (ax == 1 ? tv.uy : tv.uz)) + pt);
+        }
+    }
+    cp_async_commit();
+}
+
 template <typename T, int P, int NF>
 __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T> tb, int level, int lstart,
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
@@ -649,464 +795,418 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
     T *Pl = buf_ptr<T>(lay, 6, sm, slab);     // the parent's Lambda, kept for its next children
     int cur_parent = -1;
-    // runs of 8 consecutive boxes, taken from a work counter: siblings are
-    // adjacent in Morton order and share the parent's expansion
     __shared__ int s_run;
-    for (int it = 0, it_end = 0;; ++it) {
-        if (it >= it_end) {
-            __syncthreads();
-            if (tid == 0) s_run = atomicAdd(run_ctr, 1);
-            __syncthreads();
-            it = s_run * 8;
-            it_end = min(it + 8, lcount);
-            if (it >= lcount) break;
-        }
-        const int B = lstart + it;
-        if (tv.bntgt[B] == 0) continue;
-        const uint8_t fl = tv.bflags[B];
+    __shared__ int s_grs[8], s_gro[9], s_gnr, s_gntgt;  // a sibling group's leaves evaluated in the parent
+    __shared__ int s_brs[1], s_bro[2];                  // one leaf
+    __shared__ double s_gxyz[3][128];                   // the group's first 128 points
+    TcEval st{};
+    if constexpr (kTC) {
+        st.Bh = reinterpret_cast<float *>(PsE);
+        st.Ah = st.Bh + S::NP * S::KP;
+        st.Al = st.Ah + S::TM * S::KP;
+        st.Bl = reinterpret_cast<float *>(T1e);
+        st.bar = &s_bar;
+        st.tmem = s_tmem;
+        st.pending = &s_pending;
+        st.red = s_red;
+        st.err = tc_err;
+    }
+    auto parent_of = [&](int i) { return level > 0 ? tv.bparent[lstart + i] : -1; };
+    // runs of 8 consecutive boxes from a work counter, moved to whole sibling
+    // groups (children of one parent are adjacent in Morton order): a run
+    // leaves a group that started in the previous run to that run's CTA and
+    // finishes the group it ends in
+    for (;;) {
         __syncthreads();
-        if constexpr (kTC) {
-            if (fl & BF_LEAF) {
-                const int s0 = tv.bstart[B], n0 = min(S::TM, tv.bcount[B]);
-                for (int t = tid; t < 3 * S::TM; t += kLThreads) {
-                    const int ax = t / S::TM, j = t % S::TM;
-                    if (j < n0) cp_async8(&s_xyz[ax][j], (ax == 0 ? tv.ux : (ax == 1 ? tv.uy : tv.uz)) + s0 + j);
-                }
-                cp_async_commit();
-            }
-        }
-        // A leaf without incoming expansion keeps its parent's Lambda: T_p2c is
-        // an exact re-expansion, so the leaf evaluates the parent's polynomial in
-        // the parent's coordinates instead (tensor-core path)
-        const bool in_parent = kTC && level > 0 && (fl & BF_LEAF) && !(fl & BF_FIN);
-        // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
-        if (level == 0) {
-            for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[i];
-        } else {
-            T *b0 = reinterpret_cast<T *>(PsE);
-            T *b1 = reinterpret_cast<T *>(PsO);
-            const int Pb = tv.bparent[B];
-            if (Pb != cur_parent) {
-                const T *Lp = Lam + (size_t)tv.bslot[Pb] * P3;
-                for (int i = tid; i < P3; i += kLThreads) Pl[i] = Lp[i];
-                cur_parent = Pb;
-                __syncthreads();
-            }
-            if (!in_parent) {
-                const int oc = (int)(tv.bkey[B] & 7ull);
-                // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
-                shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, Pl, b1);
-                __syncthreads();
-                shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
-                __syncthreads();
-                shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
-            }
-        }
+        if (tid == 0) s_run = atomicAdd(run_ctr, 1);
         __syncthreads();
-        // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients
-        if (fl & BF_FIN) {
-            if (tid == 0) {
-                int nc = 0;
-                for (int k = 0; k < 27; ++k) {
-                    const int Sb = tv.bcol[(size_t)B * 27 + k];
-                    if (Sb < 0 || !(tv.bflags[Sb] & BF_FOUT)) continue;
-                    s_cslot[nc] = tv.bslot[Sb];
-                    // delta = (c_B - c_S) / R = -(dx, dy, dz), stored mod 3 as 0..2
-                    s_cd[nc][0] = (1 - k / 9 + 3) % 3;
-                    s_cd[nc][1] = (1 - (k / 3) % 3 + 3) % 3;
-                    s_cd[nc][2] = (1 - k % 3 + 3) % 3;
-                    ++nc;
-                }
-                s_ncol = nc;
+        const int r0 = s_run * 8;
+        if (r0 >= lcount) break;
+        const int r1 = min(r0 + 8, lcount);
+        int a0 = r0, a1 = r1;
+        if (level > 0) {
+            if (r0 > 0) {
+                const int pp = parent_of(r0 - 1);
+                while (a0 < r1 && parent_of(a0) == pp) ++a0;
             }
-            __syncthreads();
-            const int ncol = s_ncol;
-            // phase of colleague j for modes of residue class r = (m_x, m_y, m_z) mod 3
-            // (r = r_x + 3 r_y + 9 r_z): omega^k with k = r . delta_j mod 3, kept as
-            // (k != 0, +1 / -1 / 0 for k = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3/2) D
-            for (int t = tid; t < 27 * ncol; t += kLThreads) {
-                const int j = t / 27, r = t % 27;
-                const int k = ((r % 3) * s_cd[j][0] + ((r / 3) % 3) * s_cd[j][1] + (r / 9) * s_cd[j][2]) % 3;
-                s_ud[t] = make_float2(k ? 1.f : 0.f, k == 1 ? 1.f : (k == 2 ? -1.f : 0.f));
-            }
-            __syncthreads();
-            // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x;
-            // a thread takes two adjacent m_z (one 16-byte load per colleague and sign
-            // of m_x), four colleagues per step for memory-level parallelism
-            for (int i = tid; i < N1 * NH * (NHP / 2); i += kLThreads) {
-                const int my = i / (NH * (NHP / 2)), r = i % (NH * (NHP / 2)), mxp = r / (NHP / 2);
-                const int mz0 = 2 * (r % (NHP / 2));
-                const int myv = my - NF;
-                const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3;
-                const int rz0 = mz0 % 3, rz1 = (mz0 + 1) % 3;
-                const float2 *udp0 = s_ud + rxp + 3 * ry + 9 * rz0, *udp1 = s_ud + rxp + 3 * ry + 9 * rz1;
-                const float2 *udm0 = s_ud + rxm + 3 * ry + 9 * rz0, *udm1 = s_ud + rxm + 3 * ry + 9 * rz1;
-                C2 Tp[2] = {}, Up[2] = {}, Dp[2] = {}, Tm[2] = {}, Um[2] = {}, Dm[2] = {};
-                const size_t off_p = (size_t)(my * N1 + NF + mxp) * NHP + mz0;
-                const size_t off_m = (size_t)(my * N1 + NF - mxp) * NHP + mz0;
-                if (mxp > 0) {
-#pragma unroll 4
-                    for (int j = 0; j < ncol; ++j) {
-                        const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
-                        const C2x2<C2> vp = ld_pair(ph + off_p), vm = ld_pair(ph + off_m);
-                        const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
-                        const float2 cm0 = udm0[27 * j], cm1 = udm1[27 * j];
-                        Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
-                        Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
-                        cfma(Up[0], (T)cp0.x, vp.a);
-                        cfma(Dp[0], (T)cp0.y, vp.a);
-                        cfma(Up[1], (T)cp1.x, vp.b);
-                        cfma(Dp[1], (T)cp1.y, vp.b);
-                        Tm[0].x += vm.a.x; Tm[0].y += vm.a.y;
-                        Tm[1].x += vm.b.x; Tm[1].y += vm.b.y;
-                        cfma(Um[0], (T)cm0.x, vm.a);
-                        cfma(Dm[0], (T)cm0.y, vm.a);
-                        cfma(Um[1], (T)cm1.x, vm.b);
-                        cfma(Dm[1], (T)cm1.y, vm.b);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int j = 0; j < ncol; ++j) {
-                        const C2x2<C2> vp = ld_pair(Phi + (size_t)s_cslot[j] * pstride + off_p);
-                        const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
-                        Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
-                        Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
-                        cfma(Up[0], (T)cp0.x, vp.a);
-                        cfma(Dp[0], (T)cp0.y, vp.a);
-                        cfma(Up[1], (T)cp1.x, vp.b);
-                        cfma(Dp[1], (T)cp1.y, vp.b);
-                    }
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int mz = mz0 + h;
-                    if (mz >= NH) continue;
-                    const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
-                    // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
-                    const C2 psp{w * (Tp[h].x - (T)1.5 * Up[h].x - kH * Dp[h].y),
-                                 w * (Tp[h].y - (T)1.5 * Up[h].y + kH * Dp[h].x)};
-                    const size_t o = (size_t)(my * NH + mxp) * NHP + mz;
-                    if (mxp > 0) {
-                        const C2 psm{w * (Tm[h].x - (T)1.5 * Um[h].x - kH * Dm[h].y),
-                                     w * (Tm[h].y - (T)1.5 * Um[h].y + kH * Dm[h].x)};
-                        PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
-                        PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
-                    } else {
-                        PsE[o] = psp;
-                        PsO[o] = C2{0, 0};
-                    }
-                }
-            }
-            __syncthreads();
-            // phase B: contract m_x -> a, for m_y = +-my'; fold into even/odd in m_y
-            for (int i = tid; i < NH * NH * S::AG; i += kLThreads) {
-                const int ag = i / (NH * NH), r = i % (NH * NH), myp = r / NH, mz = r % NH;
-                C2 ap[S::AC], am[S::AC];
-#pragma unroll
-                for (int k = 0; k < S::AC; ++k) ap[k] = am[k] = C2{0, 0};
-                const int rp = (NF + myp) * NH, rm = (NF - myp) * NH;
-                for (int mxp = 0; mxp <= NF; ++mxp) {
-                    const C2 ep = PsE[(rp + mxp) * NHP + mz], em = PsE[(rm + mxp) * NHP + mz];
-                    const C2 op = PsO[(rp + mxp) * NHP + mz], om = PsO[(rm + mxp) * NHP + mz];
-#pragma unroll
-                    for (int k = 0; k < S::AC; ++k) {
-                        const int a = ag + S::AG * k;
-                        if (a < P) {
-                            const T h = hs[a * NH + mxp];
-                            if (a & 1) { cfma(ap[k], h, op); cfma(am[k], h, om); }
-                            else { cfma(ap[k], h, ep); cfma(am[k], h, em); }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < S::AC; ++k) {
-                    const int a = ag + S::AG * k;
-                    if (a >= P) continue;
-                    C2 vp = ap[k], vm = am[k];
-                    if (a & 1) {  // times -i
-                        vp = C2{vp.y, -vp.x};
-                        vm = C2{vm.y, -vm.x};
-                    }
-                    const int o = (a * NH + myp) * NH + mz;
-                    if (myp > 0) {
-                        T1e[o] = C2{vp.x + vm.x, vp.y + vm.y};
-                        T1o[o] = C2{vp.x - vm.x, vp.y - vm.y};
-                    } else {
-                        T1e[o] = vp;
-                        T1o[o] = C2{0, 0};
-                    }
-                }
-            }
-            __syncthreads();
-            // phase C: contract m_y -> b
-            for (int i = tid; i < P * NH * S::BG; i += kLThreads) {
-                const int bg = i / (P * NH), r = i % (P * NH), a = r / NH, mz = r % NH;
-                C2 acc[S::BC];
-#pragma unroll
-                for (int k = 0; k < S::BC; ++k) acc[k] = C2{0, 0};
-                for (int myp = 0; myp <= NF; ++myp) {
-                    const C2 te = T1e[(a * NH + myp) * NH + mz], to = T1o[(a * NH + myp) * NH + mz];
-#pragma unroll
-                    for (int k = 0; k < S::BC; ++k) {
-                        const int b = bg + S::BG * k;
-                        if (b < P) {
-                            const T h = hs[b * NH + myp];
-                            if (b & 1) cfma(acc[k], h, to); else cfma(acc[k], h, te);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < S::BC; ++k) {
-                    const int b = bg + S::BG * k;
-                    if (b >= P) continue;
-                    C2 v = acc[k];
-                    if (b & 1) v = C2{v.y, -v.x};
-                    T2[(a * P + b) * NH + mz] = v;
-                }
-            }
-            __syncthreads();
-            // phase D: contract m_z -> c (real part; m_z < 0 through Hermitian symmetry)
-            for (int i = tid; i < P * P * S::CG; i += kLThreads) {
-                const int cg = i / (P * P), ab = i % (P * P);
-                T acc[S::CC];
-#pragma unroll
-                for (int k = 0; k < S::CC; ++k) acc[k] = (T)0;
-                for (int mz = 0; mz <= NF; ++mz) {
-                    const C2 t = T2[ab * NH + mz];
-                    const T cz = mz ? (T)2 : (T)1;
-#pragma unroll
-                    for (int k = 0; k < S::CC; ++k) {
-                        const int c = cg + S::CG * k;
-                        if (c < P) acc[k] += cz * hs[c * NH + mz] * ((c & 1) ? t.y : t.x);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < S::CC; ++k) {
-                    const int c = cg + S::CG * k;
-                    if (c < P) Ls[ab * P + c] += acc[k];
-                }
-            }
-            __syncthreads();
+            while (a1 < lcount && parent_of(a1) == parent_of(a1 - 1)) ++a1;
         }
-        if (tid == 0) {
-            // algorithmic flops of this box: p2c (3 triangular passes), the
-            // translation (one complex multiply-add per mode and colleague) and
-            // the three parity-split contractions, and the leaf evaluation
-            unsigned long long f = level > 0 && !in_parent ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
-            if (fl & BF_FIN)
-                f += 8ull * N1 * N1 * NH * s_ncol + 8ull * P * NH * NH * NH + 4ull * P * P * NH * NH +
-                     2ull * P * P * P * NH;
-            if (fl & BF_LEAF) f += 2ull * (P * P * P + P * P + P) * tv.bntgt[B];
-            atomicAdd(flops, f);
-        }
-        if (!(fl & BF_LEAF)) {
-            T *Lo = Lam + (size_t)tv.bslot[B] * P3;
-            for (int i = tid; i < P3; i += kLThreads) Lo[i] = Ls[i];
-            continue;
-        }
-        // ---- leaf: evaluate the local expansion at its targets
-        int ix, iy, iz;
-        morton_decode_d(tv.bkey[B], ix, iy, iz);
-        const int le = in_parent ? level - 1 : level;  // level of the expansion's box
-        if (in_parent) {
-            ix >>= 1;
-            iy >>= 1;
-            iz >>= 1;
-        }
-        const double R = level_R(le), s2R = 2.0 / R;
-        const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
-        const T *Lev = in_parent ? Pl : Ls;
-        const int s = tv.bstart[B], e = s + tv.bcount[B];
-        if constexpr (kTC) {
-            // Tensor cores: D[j][ab] = sum_c T_c(z_j) Lambda[ab][c] for 128 targets
-            // at a time (targets on the TMEM lanes), then each target's own thread
-            // forms u_j = sum_a T_a(x_j) sum_b T_b(y_j) D[j][ab].  Operands are
-            // split into TF32 hi + lo and D = A_lo B_hi + A_hi B_lo + A_hi B_hi.
-            float *Bh = reinterpret_cast<float *>(PsE);
-            float *Ah = Bh + S::NP * S::KP;
-            float *Al = Ah + S::TM * S::KP;
-            float *Bl = reinterpret_cast<float *>(T1e);
-            // B operand: row ab, column c of Lambda; one float4 (4 columns) per step
-            for (int t = tid; t < S::NP * S::KP / 4; t += kLThreads) {
-                const int r = t & 7, k4 = (t >> 3) % (S::KP / 4), n = ((t >> 3) / (S::KP / 4)) * 8 + r;
-                float h[4], l[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = 4 * k4 + q;
-                    const float v = (n < P * P && k < P) ? (float)Lev[n * P + k] : 0.f;
-                    tc::split_tf32(v, h[q], l[q]);
-                }
-                reinterpret_cast<float4 *>(Bh)[t] = make_float4(h[0], h[1], h[2], h[3]);
-                reinterpret_cast<float4 *>(Bl)[t] = make_float4(l[0], l[1], l[2], l[3]);
-            }
-            cp_async_wait_all();
-            __syncthreads();
-            for (int p0 = s; p0 < e; p0 += S::TM) {
-                const int np = min(S::TM, e - p0);
-                const bool first = p0 == s;  // points already in s_xyz
-                // coordinates of this thread's epilogue target
-                const int jq = min(tid & (S::TM - 1), np - 1);
-                const double xq = first ? s_xyz[0][jq] : tv.ux[p0 + jq];
-                const double yq = first ? s_xyz[1][jq] : tv.uy[p0 + jq];
-                if (tid < S::TM) {
-                    // A operand row j = T_c(z_j), c < P (zero rows past the leaf's points)
-                    const int j = tid;
-                    float tz[S::KP];
-#pragma unroll
-                    for (int n = 0; n < S::KP; ++n) tz[n] = 0.f;
-                    if (j < np) {
-                        const float zi = (float)(((first ? s_xyz[2][j] : tv.uz[p0 + j]) - cc[2]) * s2R);
-                        tz[0] = 1.f;
-                        if (P > 1) tz[1] = zi;
-#pragma unroll
-                        for (int n = 2; n < P; ++n) tz[n] = 2.f * zi * tz[n - 1] - tz[n - 2];
-                    }
-#pragma unroll
-                    for (int k4 = 0; k4 < S::KP / 4; ++k4) {
-                        float h[4], l[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) tc::split_tf32(tz[4 * k4 + q], h[q], l[q]);
-                        const int o = ((j >> 3) * (S::KP / 4) + k4) * 8 + (j & 7);
-                        reinterpret_cast<float4 *>(Ah)[o] = make_float4(h[0], h[1], h[2], h[3]);
-                        reinterpret_cast<float4 *>(Al)[o] = make_float4(l[0], l[1], l[2], l[3]);
-                    }
-                }
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
+        for (int g0 = a0, g1 = a0; g0 < a1; g0 = g1) {
+            const int Pg = parent_of(g0);
+            g1 = g0 + 1;
+            while (level > 0 && g1 < a1 && parent_of(g1) == Pg) ++g1;
+            // leaves without incoming expansion keep their parent's Lambda: T_p2c is
+            // an exact re-expansion, so they evaluate the parent's polynomial in the
+            // parent's coordinates, all of the group's together (tensor-core path)
+            int gnr = 0;
+            if (kTC && level > 0) {
                 __syncthreads();
-                tc::fence_after_sync();
                 if (tid == 0) {
-                    constexpr uint32_t lbo = 128, sbo = S::KP * 32;
-                    const uint32_t aH = tc::smem_addr(Ah), aL = tc::smem_addr(Al);
-                    const uint32_t bH = tc::smem_addr(Bh), bL = tc::smem_addr(Bl);
-#pragma unroll
-                    for (int h = 0; h < (S::NB > 0 ? 2 : 1); ++h) {
-                        const int n0 = h ? S::NA : 0;
-                        const uint32_t id = tc::idesc_tf32(S::TM, h ? S::NB : S::NA);
-                        const uint32_t boff = (uint32_t)(n0 / 8) * sbo, dcol = s_tmem + (uint32_t)n0;
-#pragma unroll
-                        for (int ks = 0; ks < S::KP / 8; ++ks) {
-                            const uint32_t ko = (uint32_t)ks * 256;
-                            tc::mma_tf32(dcol, tc::sdesc(aL + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id,
-                                         ks > 0);
-                            tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bL + boff + ko, lbo, sbo), id,
-                                         true);
-                            tc::mma_tf32(dcol, tc::sdesc(aH + ko, lbo, sbo), tc::sdesc(bH + boff + ko, lbo, sbo), id,
-                                         true);
-                        }
+                    int n = 0, off = 0, nt = 0;
+                    for (int i = g0; i < g1; ++i) {
+                        const int b = lstart + i;
+                        const uint8_t f = tv.bflags[b];
+                        if (!(f & BF_LEAF) || (f & BF_FIN) || tv.bntgt[b] == 0) continue;
+                        s_grs[n] = tv.bstart[b];
+                        s_gro[n] = off;
+                        off += tv.bcount[b];
+                        nt += tv.bntgt[b];
+                        ++n;
                     }
-                    tc::commit(&s_bar);
-                }
-                {
-                    // every warp waits; warps w, w + 4, w + 8, w + 12 share TMEM lanes
-                    // 32 (w mod 4) .. + 31 (targets j) and split the ab columns
-                    bool ok = tc::mbar_wait(&s_bar, phase, 2000000000ll);  // about 1 s
-                    ok = __all_sync(0xffffffffu, ok);
-                    tc::fence_after_sync();
-                    const int j = tid & (S::TM - 1), cg = tid >> 7;
-                    float part = 0.f;
-                    if (ok) {
-                        float tx[P], ty[P];
-                        cheb_row<P>((float)((xq - cc[0]) * s2R), tx);
-                        cheb_row<P>((float)((yq - cc[1]) * s2R), ty);
-                        const uint32_t trow = s_tmem + ((uint32_t)((warp & 3) * 32) << 16);
-                        constexpr int NC = S::NP / 8;  // 8-column chunks
-                        switch (cg) {
-                        case 0: part = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
-                        case 1: part = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
-                        case 2: part = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
-                        default: part = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
-                        }
-                    } else if ((tid & 31) == 0) {
-                        atomicExch(tc_err, 1);
-                        s_pending = 1;
-                    }
-                    if (cg > 0) s_red[cg - 1][j] = part;
-                    tc::fence_before_sync();
-                    __syncthreads();
-                    if (cg == 0 && j < np && (tv.pflag[p0 + j] & 2))
-                        ufar[p0 + j] = (double)(part + s_red[0][j] + s_red[1][j] + s_red[2][j]);
-                }
-                phase ^= 1u;
-            }
-        } else {
-            for (int p0 = s; p0 < e; p0 += kECH) {
-                const int np = min(kECH, e - p0);
-                for (int t = tid; t < 3 * kECH; t += kLThreads) {
-                    const int ax = t / kECH, j = t % kECH;
-                    T *o = ev + (ax * kECH + j) * P;
-                    if (j < np) {
-                        const int kk = p0 + j;
-                        const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
-                        const T xi = (T)((u - cc[ax]) * s2R);
-                        T t0 = (T)1, t1 = xi;
-                        o[0] = (T)1;
-                        if (P > 1) o[1] = xi;
-#pragma unroll
-                        for (int n = 2; n < P; ++n) {
-                            T t2 = (T)2 * xi * t1 - t0;
-                            o[n] = t2;
-                            t0 = t1;
-                            t1 = t2;
-                        }
-                    } else {
-#pragma unroll
-                        for (int n = 0; n < P; ++n) o[n] = (T)0;
-                    }
+                    s_gro[n] = off;
+                    s_gnr = n;
+                    s_gntgt = nt;
                 }
                 __syncthreads();
-                // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
-                {
-                    T *W = reinterpret_cast<T *>(PsE);
-                    const T *tzs = ev + 2 * kECH * P;
-                    constexpr int NABG = (P * P + 3) / 4;
-                    for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
-                        const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
-                        T acc[4][4];
+                gnr = s_gnr;
+                if (gnr > 0) fetch_xyz(tv, s_grs, s_gro, gnr, s_gxyz);
+            }
+            for (int it = g0; it < g1; ++it) {
+                const int B = lstart + it;
+                if (tv.bntgt[B] == 0) continue;
+                const uint8_t fl = tv.bflags[B];
+                if (kTC && level > 0 && (fl & BF_LEAF) && !(fl & BF_FIN)) continue;  // in the group
+                __syncthreads();
+                if constexpr (kTC) {
+                    if (fl & BF_LEAF) {
+                        if (tid == 0) {
+                            s_brs[0] = tv.bstart[B];
+                            s_bro[0] = 0;
+                            s_bro[1] = tv.bcount[B];
+                        }
+                        __syncthreads();
+                        fetch_xyz(tv, s_brs, s_bro, 1, s_xyz);
+                    }
+                }
+                // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
+                if (level == 0) {
+                    for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[i];
+                } else {
+                    T *b0 = reinterpret_cast<T *>(PsE);
+                    T *b1 = reinterpret_cast<T *>(PsO);
+                    const int Pb = tv.bparent[B];
+                    if (Pb != cur_parent) {
+                        const T *Lp = Lam + (size_t)tv.bslot[Pb] * P3;
+                        for (int i = tid; i < P3; i += kLThreads) Pl[i] = Lp[i];
+                        cur_parent = Pb;
+                        __syncthreads();
+                    }
+                    const int oc = (int)(tv.bkey[B] & 7ull);
+                    // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
+                    shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, Pl, b1);
+                    __syncthreads();
+                    shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
+                    __syncthreads();
+                    shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
+                }
+                __syncthreads();
+                // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients
+                if (fl & BF_FIN) {
+                    if (tid == 0) {
+                        int nc = 0;
+                        for (int k = 0; k < 27; ++k) {
+                            const int Sb = tv.bcol[(size_t)B * 27 + k];
+                            if (Sb < 0 || !(tv.bflags[Sb] & BF_FOUT)) continue;
+                            s_cslot[nc] = tv.bslot[Sb];
+                            // delta = (c_B - c_S) / R = -(dx, dy, dz), stored mod 3 as 0..2
+                            s_cd[nc][0] = (1 - k / 9 + 3) % 3;
+                            s_cd[nc][1] = (1 - (k / 3) % 3 + 3) % 3;
+                            s_cd[nc][2] = (1 - k % 3 + 3) % 3;
+                            ++nc;
+                        }
+                        s_ncol = nc;
+                    }
+                    __syncthreads();
+                    const int ncol = s_ncol;
+                    // phase of colleague j for modes of residue class r = (m_x, m_y, m_z) mod 3
+                    // (r = r_x + 3 r_y + 9 r_z): omega^k with k = r . delta_j mod 3, kept as
+                    // (k != 0, +1 / -1 / 0 for k = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3/2) D
+                    for (int t = tid; t < 27 * ncol; t += kLThreads) {
+                        const int j = t / 27, r = t % 27;
+                        const int k = ((r % 3) * s_cd[j][0] + ((r / 3) % 3) * s_cd[j][1] + (r / 9) * s_cd[j][2]) % 3;
+                        s_ud[t] = make_float2(k ? 1.f : 0.f, k == 1 ? 1.f : (k == 2 ? -1.f : 0.f));
+                    }
+                    __syncthreads();
+                    // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x;
+                    // a thread takes two adjacent m_z (one 16-byte load per colleague and sign
+                    // of m_x), four colleagues per step for memory-level parallelism
+                    for (int i = tid; i < N1 * NH * (NHP / 2); i += kLThreads) {
+                        const int my = i / (NH * (NHP / 2)), r = i % (NH * (NHP / 2)), mxp = r / (NHP / 2);
+                        const int mz0 = 2 * (r % (NHP / 2));
+                        const int myv = my - NF;
+                        const int rxp = mxp % 3, rxm = (3 - rxp) % 3, ry = (myv % 3 + 3) % 3;
+                        const int rz0 = mz0 % 3, rz1 = (mz0 + 1) % 3;
+                        const float2 *udp0 = s_ud + rxp + 3 * ry + 9 * rz0, *udp1 = s_ud + rxp + 3 * ry + 9 * rz1;
+                        const float2 *udm0 = s_ud + rxm + 3 * ry + 9 * rz0, *udm1 = s_ud + rxm + 3 * ry + 9 * rz1;
+                        C2 Tp[2] = {}, Up[2] = {}, Dp[2] = {}, Tm[2] = {}, Um[2] = {}, Dm[2] = {};
+                        const size_t off_p = (size_t)(my * N1 + NF + mxp) * NHP + mz0;
+                        const size_t off_m = (size_t)(my * N1 + NF - mxp) * NHP + mz0;
+                        if (mxp > 0) {
+#pragma unroll 4
+                            for (int j = 0; j < ncol; ++j) {
+                                const C2 *ph = Phi + (size_t)s_cslot[j] * pstride;
+                                const C2x2<C2> vp = ld_pair(ph + off_p), vm = ld_pair(ph + off_m);
+                                const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
+                                const float2 cm0 = udm0[27 * j], cm1 = udm1[27 * j];
+                                Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
+                                Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
+                                cfma(Up[0], (T)cp0.x, vp.a);
+                                cfma(Dp[0], (T)cp0.y, vp.a);
+                                cfma(Up[1], (T)cp1.x, vp.b);
+                                cfma(Dp[1], (T)cp1.y, vp.b);
+                                Tm[0].x += vm.a.x; Tm[0].y += vm.a.y;
+                                Tm[1].x += vm.b.x; Tm[1].y += vm.b.y;
+                                cfma(Um[0], (T)cm0.x, vm.a);
+                                cfma(Dm[0], (T)cm0.y, vm.a);
+                                cfma(Um[1], (T)cm1.x, vm.b);
+                                cfma(Dm[1], (T)cm1.y, vm.b);
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int j = 0; j < ncol; ++j) {
+                                const C2x2<C2> vp = ld_pair(Phi + (size_t)s_cslot[j] * pstride + off_p);
+                                const float2 cp0 = udp0[27 * j], cp1 = udp1[27 * j];
+                                Tp[0].x += vp.a.x; Tp[0].y += vp.a.y;
+                                Tp[1].x += vp.b.x; Tp[1].y += vp.b.y;
+                                cfma(Up[0], (T)cp0.x, vp.a);
+                                cfma(Dp[0], (T)cp0.y, vp.a);
+                                cfma(Up[1], (T)cp1.x, vp.b);
+                                cfma(Dp[1], (T)cp1.y, vp.b);
+                            }
+                        }
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
+                        for (int h = 0; h < 2; ++h) {
+                            const int mz = mz0 + h;
+                            if (mz >= NH) continue;
+                            const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
+                            // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
+                            const C2 psp{w * (Tp[h].x - (T)1.5 * Up[h].x - kH * Dp[h].y),
+                                         w * (Tp[h].y - (T)1.5 * Up[h].y + kH * Dp[h].x)};
+                            const size_t o = (size_t)(my * NH + mxp) * NHP + mz;
+                            if (mxp > 0) {
+                                const C2 psm{w * (Tm[h].x - (T)1.5 * Um[h].x - kH * Dm[h].y),
+                                             w * (Tm[h].y - (T)1.5 * Um[h].y + kH * Dm[h].x)};
+                                PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
+                                PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
+                            } else {
+                                PsE[o] = psp;
+                                PsO[o] = C2{0, 0};
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    // phase B: contract m_x -> a, for m_y = +-my'; fold into even/odd in m_y
+                    for (int i = tid; i < NH * NH * S::AG; i += kLThreads) {
+                        const int ag = i / (NH * NH), r = i % (NH * NH), myp = r / NH, mz = r % NH;
+                        C2 ap[S::AC], am[S::AC];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) acc[i][k] = (T)0;
+                        for (int k = 0; k < S::AC; ++k) ap[k] = am[k] = C2{0, 0};
+                        const int rp = (NF + myp) * NH, rm = (NF - myp) * NH;
+                        for (int mxp = 0; mxp <= NF; ++mxp) {
+                            const C2 ep = PsE[(rp + mxp) * NHP + mz], em = PsE[(rm + mxp) * NHP + mz];
+                            const C2 op = PsO[(rp + mxp) * NHP + mz], om = PsO[(rm + mxp) * NHP + mz];
 #pragma unroll
-                        for (int c = 0; c < P; ++c) {
-                            T l[4], z[4];
+                            for (int k = 0; k < S::AC; ++k) {
+                                const int a = ag + S::AG * k;
+                                if (a < P) {
+                                    const T h = hs[a * NH + mxp];
+                                    if (a & 1) { cfma(ap[k], h, op); cfma(am[k], h, om); }
+                                    else { cfma(ap[k], h, ep); cfma(am[k], h, em); }
+                                }
+                            }
+                        }
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const int ab = abg * 4 + i;
-                                l[i] = ab < P * P ? Ls[ab * P + c] : (T)0;
+                        for (int k = 0; k < S::AC; ++k) {
+                            const int a = ag + S::AG * k;
+                            if (a >= P) continue;
+                            C2 vp = ap[k], vm = am[k];
+                            if (a & 1) {  // times -i
+                                vp = C2{vp.y, -vp.x};
+                                vm = C2{vm.y, -vm.x};
+                            }
+                            const int o = (a * NH + myp) * NH + mz;
+                            if (myp > 0) {
+                                T1e[o] = C2{vp.x + vm.x, vp.y + vm.y};
+                                T1o[o] = C2{vp.x - vm.x, vp.y - vm.y};
+                            } else {
+                                T1e[o] = vp;
+                                T1o[o] = C2{0, 0};
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    // phase C: contract m_y -> b
+                    for (int i = tid; i < P * NH * S::BG; i += kLThreads) {
+                        const int bg = i / (P * NH), r = i % (P * NH), a = r / NH, mz = r % NH;
+                        C2 acc[S::BC];
+#pragma unroll
+                        for (int k = 0; k < S::BC; ++k) acc[k] = C2{0, 0};
+                        for (int myp = 0; myp <= NF; ++myp) {
+                            const C2 te = T1e[(a * NH + myp) * NH + mz], to = T1o[(a * NH + myp) * NH + mz];
+#pragma unroll
+                            for (int k = 0; k < S::BC; ++k) {
+                                const int b = bg + S::BG * k;
+                                if (b < P) {
+                                    const T h = hs[b * NH + myp];
+                                    if (b & 1) cfma(acc[k], h, to); else cfma(acc[k], h, te);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < S::BC; ++k) {
+                            const int b = bg + S::BG * k;
+                            if (b >= P) continue;
+                            C2 v = acc[k];
+                            if (b & 1) v = C2{v.y, -v.x};
+                            T2[(a * P + b) * NH + mz] = v;
+                        }
+                    }
+                    __syncthreads();
+                    // phase D: contract m_z -> c (real part; m_z < 0 through Hermitian symmetry)
+                    for (int i = tid; i < P * P * S::CG; i += kLThreads) {
+                        const int cg = i / (P * P), ab = i % (P * P);
+                        T acc[S::CC];
+#pragma unroll
+                        for (int k = 0; k < S::CC; ++k) acc[k] = (T)0;
+                        for (int mz = 0; mz <= NF; ++mz) {
+                            const C2 t = T2[ab * NH + mz];
+                            const T cz = mz ? (T)2 : (T)1;
+#pragma unroll
+                            for (int k = 0; k < S::CC; ++k) {
+                                const int c = cg + S::CG * k;
+                                if (c < P) acc[k] += cz * hs[c * NH + mz] * ((c & 1) ? t.y : t.x);
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < S::CC; ++k) {
+                            const int c = cg + S::CG * k;
+                            if (c < P) Ls[ab * P + c] += acc[k];
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0) {
+                    // algorithmic flops of this box: p2c (3 triangular passes), the
+                    // translation (one complex multiply-add per mode and colleague) and
+                    // the three parity-split contractions, and the leaf evaluation
+                    unsigned long long f = level > 0 ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
+                    if (fl & BF_FIN)
+                        f += 8ull * N1 * N1 * NH * s_ncol + 8ull * P * NH * NH * NH + 4ull * P * P * NH * NH +
+                             2ull * P * P * P * NH;
+                    if (fl & BF_LEAF) f += 2ull * (P * P * P + P * P + P) * tv.bntgt[B];
+                    atomicAdd(flops, f);
+                }
+                if (!(fl & BF_LEAF)) {
+                    T *Lo = Lam + (size_t)tv.bslot[B] * P3;
+                    for (int i = tid; i < P3; i += kLThreads) Lo[i] = Ls[i];
+                    continue;
+                }
+                // ---- leaf: evaluate the local expansion at its targets
+                int ix, iy, iz;
+                morton_decode_d(tv.bkey[B], ix, iy, iz);
+                const double R = level_R(level), s2R = 2.0 / R;
+                const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
+                if constexpr (kTC) {
+                    tc_eval<P, NF>(tv, Ls, cc, s2R, s_brs, s_bro, 1, s_xyz, st, phase, ufar);
+                } else {
+                    const int s = tv.bstart[B], e = s + tv.bcount[B];
+                    for (int p0 = s; p0 < e; p0 += kECH) {
+                        const int np = min(kECH, e - p0);
+                        for (int t = tid; t < 3 * kECH; t += kLThreads) {
+                            const int ax = t / kECH, j = t % kECH;
+                            T *o = ev + (ax * kECH + j) * P;
+                            if (j < np) {
+                                const int kk = p0 + j;
+                                const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
+                                const T xi = (T)((u - cc[ax]) * s2R);
+                                T t0 = (T)1, t1 = xi;
+                                o[0] = (T)1;
+                                if (P > 1) o[1] = xi;
+#pragma unroll
+                                for (int n = 2; n < P; ++n) {
+                                    T t2 = (T)2 * xi * t1 - t0;
+                                    o[n] = t2;
+                                    t0 = t1;
+                                    t1 = t2;
+                                }
+                            } else {
+#pragma unroll
+                                for (int n = 0; n < P; ++n) o[n] = (T)0;
+                            }
+                        }
+                        __syncthreads();
+                        // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
+                        {
+                            T *W = reinterpret_cast<T *>(PsE);
+                            const T *tzs = ev + 2 * kECH * P;
+                            constexpr int NABG = (P * P + 3) / 4;
+                            for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
+                                const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
+                                T acc[4][4];
+#pragma unroll
+                                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) acc[i][k] = (T)0;
+#pragma unroll
+                                for (int c = 0; c < P; ++c) {
+                                    T l[4], z[4];
+#pragma unroll
+                                    for (int i = 0; i < 4; ++i) {
+                                        const int ab = abg * 4 + i;
+                                        l[i] = ab < P * P ? Ls[ab * P + c] : (T)0;
+                                    }
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) z[k] = tzs[(jg * 4 + k) * P + c];
+#pragma unroll
+                                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                        for (int k = 0; k < 4; ++k) acc[i][k] += l[i] * z[k];
+                                }
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    const int ab = abg * 4 + i;
+                                    if (ab < P * P)
+#pragma unroll
+                                        for (int k = 0; k < 4; ++k) W[(jg * 4 + k) * (P * P) + ab] = acc[i][k];
+                                }
+                            }
+                            __syncthreads();
+                            // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
+                            const int j = tid >> 4, g = tid & 15;
+                            const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
+                            const T *Wj = W + j * (P * P);
+                            T sum = 0;
+                            for (int a = g; a < P; a += 16) {
+                                T sa = 0;
+#pragma unroll
+                                for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
+                                sum += tx[a] * sa;
                             }
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) z[k] = tzs[(jg * 4 + k) * P + c];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) acc[i][k] += l[i] * z[k];
+                            for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                            if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
                         }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int ab = abg * 4 + i;
-                            if (ab < P * P)
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) W[(jg * 4 + k) * (P * P) + ab] = acc[i][k];
-                        }
+                        __syncthreads();
+                    }
+                }
+            }
+            if constexpr (kTC) {
+                if (gnr > 0) {
+                    // the group's leaves: the parent's expansion in the parent's frame
+                    if (Pg != cur_parent) {
+                        __syncthreads();
+                        const T *Lp = Lam + (size_t)tv.bslot[Pg] * P3;
+                        for (int i = tid; i < P3; i += kLThreads) Pl[i] = Lp[i];
+                        cur_parent = Pg;
                     }
                     __syncthreads();
-                    // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
-                    const int j = tid >> 4, g = tid & 15;
-                    const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
-                    const T *Wj = W + j * (P * P);
-                    T sum = 0;
-                    for (int a = g; a < P; a += 16) {
-                        T sa = 0;
-#pragma unroll
-                        for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
-                        sum += tx[a] * sa;
-                    }
-#pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                    if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
+                    int ix, iy, iz;
+                    morton_decode_d(tv.bkey[Pg], ix, iy, iz);
+                    const double R = level_R(level - 1), s2R = 2.0 / R;
+                    const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
+                    if (tid == 0) atomicAdd(flops, 2ull * (P * P * P + P * P + P) * (unsigned long long)s_gntgt);
+                    tc_eval<P, NF>(tv, Pl, cc, s2R, s_grs, s_gro, gnr, s_gxyz, st, phase, ufar);
                 }
-                __syncthreads();
             }
         }
     }
@@ -1647,7 +1747,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, t1_bytes, (size_t)P * NH * sizeof(T),
                                      (size_t)3 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
                                      P3 * sizeof(T)},
-                                    smem_limit - 12288);
+                                    smem_limit - 16384);
         if (tcore && !(lay.in_smem[1] && lay.in_smem[2])) {
             err = "tensor-core operands do not fit in shared memory";
             return DMK_ERR_INTERNAL;
