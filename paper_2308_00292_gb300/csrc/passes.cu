@@ -118,6 +118,14 @@ template <> __device__ __forceinline__ void ld4<double>(const double *p, double 
 // padded row strides of the upward pass's staging buffers (multiples of 4)
 template <int P> struct UpShape {
     static constexpr int PS = (P + 3) & ~3, YS = (P * P + 3) & ~3;
+    // tensor-core anterpolation D[bc][a] = sum_j T_b(y_j) T_c(z_j) rho_j T_a(x_j):
+    // bc on MT tiles of 128 TMEM lanes, a padded to NA columns (N), points in
+    // chunks of KC (K); operands TF32 hi + lo
+    static constexpr int MT = (P * P + 127) / 128, NA = (P + 15) / 16 * 16, KC = 16;
+    static constexpr int TCOLS = MT * NA <= 32 ? 32 : (MT * NA <= 64 ? 64 : (MT * NA <= 128 ? 128 : 256));
+    static constexpr bool TC_OK = MT * NA <= 256;
+    static constexpr int A_FL = MT * 128 * KC, B_FL = NA * KC;  // floats per operand part
+    static constexpr int TC_SCR = 2 * A_FL + 2 * B_FL + 3 * KC * PS;
 };
 
 // One axis of the child-to-parent moment shift on a P^3 array:
@@ -172,13 +180,152 @@ __device__ __forceinline__ void shift_up(const T *__restrict__ A, const T *in, T
 // ---------------------------------------------------------------------------
 // Upward pass (Step 2)
 // ---------------------------------------------------------------------------
+// Tensor-core anterpolation of ntot points (ranges lstart / lpre) onto the
+// grid of a box (centre cc, scale s2R): acc[a][b][c] += sum_j rho_j T_a(x_j)
+// T_b(y_j) T_c(z_j) as D[bc][a] = sum_j Y[bc][j] X[a][j] with Y = T_b(y) T_c(z)
+// and X = rho T_a(x), KC points per MMA batch; operands split into TF32 hi +
+// lo (D = A_lo B_hi + A_hi B_lo + A_hi B_hi).  Each batch's D is added to acc
+// by the CUDA cores in round-to-nearest FP32, so no accumulation runs through
+// the tensor core's adder for more than one batch.  Called by the whole CTA.
+template <int P>
+__device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double s2R, const int *lstart,
+                               const int *lpre, int ntot, float *scr, uint32_t tmem, uint64_t *bar, uint32_t &phase,
+                               float *acc, int *tc_err) {
+    using U = UpShape<P>;
+    constexpr int KC = U::KC, PS = U::PS;
+    float *Ah = scr, *Al = Ah + U::A_FL, *Bh = Al + U::A_FL, *Bl = Bh + U::B_FL;
+    float *stg = Bl + U::B_FL;  // [3][KC][PS]: rho T_a(x), T_b(y), T_c(z)
+    const int tid = threadIdx.x;
+    constexpr uint32_t lbo = 128, sbo = KC * 32;
+    bool ok = true;
+    for (int p0 = 0; p0 < ntot; p0 += KC) {
+        const int np = min(KC, ntot - p0);
+        if (tid < 3 * KC) {
+            const int ax = tid / KC, j = tid % KC;
+            float *o = stg + (ax * KC + j) * PS;
+            if (j < np) {
+                int seg = 0;
+                while (seg < 7 && lpre[seg + 1] <= p0 + j) ++seg;
+                const int kk = lstart[seg] + (p0 + j - lpre[seg]);
+                const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
+                const float xi = (float)((u - cc[ax]) * s2R);
+                const float w = ax == 0 ? (float)tv.q[kk] : 1.f;
+                float t0 = 1.f, t1 = xi;
+                o[0] = w;
+                if (P > 1) o[1] = w * xi;
+#pragma unroll
+                for (int n = 2; n < P; ++n) {
+                    const float t2 = 2.f * xi * t1 - t0;
+                    o[n] = w * t2;
+                    t0 = t1;
+                    t1 = t2;
+                }
+            } else {
+#pragma unroll
+                for (int n = 0; n < P; ++n) o[n] = 0.f;
+            }
+        }
+        __syncthreads();
+        // A operand: row bc, column j (K-major core matrices), 4 points per float4
+        for (int t = tid; t < U::A_FL / 4; t += blockDim.x) {
+            const int r8 = t & 7, k4 = (t >> 3) % (KC / 4), bc = ((t >> 3) / (KC / 4)) * 8 + r8;
+            float h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * k4 + q;
+                const float v = bc < P * P ? stg[(KC + j) * PS + bc / P] * stg[(2 * KC + j) * PS + bc % P] : 0.f;
+                tc::split_tf32(v, h[q], l[q]);
+            }
+            reinterpret_cast<float4 *>(Ah)[t] = make_float4(h[0], h[1], h[2], h[3]);
+            reinterpret_cast<float4 *>(Al)[t] = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        // B operand: row a, column j
+        for (int t = tid; t < U::B_FL / 4; t += blockDim.x) {
+            const int r8 = t & 7, k4 = (t >> 3) % (KC / 4), a = ((t >> 3) / (KC / 4)) * 8 + r8;
+            float h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * k4 + q;
+                const float v = a < P ? stg[j * PS + a] : 0.f;
+                tc::split_tf32(v, h[q], l[q]);
+            }
+            reinterpret_cast<float4 *>(Bh)[t] = make_float4(h[0], h[1], h[2], h[3]);
+            reinterpret_cast<float4 *>(Bl)[t] = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t aH = tc::smem_addr(Ah), aL = tc::smem_addr(Al);
+            const uint32_t bH = tc::smem_addr(Bh), bL = tc::smem_addr(Bl);
+            const uint32_t id = tc::idesc_tf32(128, U::NA);
+#pragma unroll
+            for (int mt = 0; mt < U::MT; ++mt) {
+                const uint32_t aoff = (uint32_t)(mt * 128 / 8) * sbo, dcol = tmem + (uint32_t)(mt * U::NA);
+#pragma unroll
+                for (int ks = 0; ks < KC / 8; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256;
+                    tc::mma_tf32(dcol, tc::sdesc(aL + aoff + ko, lbo, sbo), tc::sdesc(bH + ko, lbo, sbo), id, ks > 0);
+                    tc::mma_tf32(dcol, tc::sdesc(aH + aoff + ko, lbo, sbo), tc::sdesc(bL + ko, lbo, sbo), id, true);
+                    tc::mma_tf32(dcol, tc::sdesc(aH + aoff + ko, lbo, sbo), tc::sdesc(bH + ko, lbo, sbo), id, true);
+                }
+            }
+            tc::commit(bar);
+        }
+        // every thread waits for the batch, then adds its share of D to acc:
+        // warp w reads TMEM lanes 32 (w mod 4) .. + 31 of the tiles w / 4, w / 4 + 2, ...
+        ok = tc::mbar_wait(bar, phase, 2000000000ll) && ok;  // about 1 s
+        phase ^= 1u;
+        const bool wok = __all_sync(0xffffffffu, ok);
+        tc::fence_after_sync();
+        if (wok) {
+            const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+            for (int mt = warp >> 2; mt < U::MT; mt += nw >> 2) {
+                const int bc = mt * 128 + (warp & 3) * 32 + lane;
+                const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * U::NA);
+                float d[(P + 7) / 8][8];
+#pragma unroll
+                for (int c8 = 0; c8 < (P + 7) / 8; ++c8) tc::ld_x8(trow + (uint32_t)(c8 * 8), d[c8]);
+                tc::ld_wait();
+                if (bc < P * P) {
+#pragma unroll
+                    for (int c8 = 0; c8 < (P + 7) / 8; ++c8)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int a = c8 * 8 + q;
+                            if (a < P) acc[a * P * P + bc] += d[c8][q];
+                        }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok && (tid & 31) == 0) atomicExch(tc_err, 1);
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> tb, int lstart, int lcount, T *M,
-                                                     BufLayout lay, char *slab) {
+                                                     BufLayout lay, char *slab, int *tc_err) {
     extern __shared__ __align__(128) char sm[];
+    using U = UpShape<P>;
     constexpr int P3 = P * P * P;
-    constexpr int PS = UpShape<P>::PS, YS = UpShape<P>::YS;
+    constexpr int PS = U::PS, YS = U::YS;
     constexpr int NAG = (P + 3) / 4, NBCG = (P * P + 3) / 4;
+    // single precision anterpolates on the tensor cores (3xTF32)
+    constexpr bool kTC = sizeof(T) == 4 && U::TC_OK;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    uint32_t phase = 0;
+    if constexpr (kTC) {
+        if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&s_tmem, U::TCOLS);
+        if (threadIdx.x == 0) tc::mbar_init(&s_bar, 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     T *acc = buf_ptr<T>(lay, 0, sm, slab);
     // scratch shared by the two phases: staging + Y for the sources of leaf
     // children, then two P^3 buffers for the moment shifts of non-leaf children
@@ -221,7 +368,10 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         }
         __syncthreads();
         const int ntot = s_lpre[8];
-        {
+        if constexpr (kTC) {
+            if (ntot > 0) anterpolate_tc<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, scr, s_tmem, &s_bar, phase, acc,
+                                             tc_err);
+        } else {
             {
                 // anterpolation of the leaf children's sources onto this box's grid
                 for (int p0 = 0; p0 < ntot; p0 += kCH) {
@@ -311,6 +461,12 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         T *Mo = M + (size_t)tv.bslot[B] * P3;
         for (int i = tid; i < P3; i += kThreads) Mo[i] = acc[i];
         __syncthreads();
+    }
+    if constexpr (kTC) {
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tmem, U::TCOLS);
     }
 }
 
@@ -1687,8 +1843,13 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     // ---- upward pass (finest level first)
     cudaEventRecord(cx.ev[1], st);
     {
-        const size_t scr = std::max((size_t)2 * P3, (size_t)kCH * (3 * UpShape<P>::PS + UpShape<P>::YS)) * sizeof(T);
+        size_t scr = std::max((size_t)2 * P3, (size_t)kCH * (3 * UpShape<P>::PS + UpShape<P>::YS)) * sizeof(T);
+        if (sizeof(T) == 4 && UpShape<P>::TC_OK) scr = std::max(scr, (size_t)UpShape<P>::TC_SCR * sizeof(float));
         BufLayout lay = make_layout({P3 * sizeof(T), scr, (size_t)2 * P * P * sizeof(T)}, smem_limit - 1024);
+        if (sizeof(T) == 4 && UpShape<P>::TC_OK && !lay.in_smem[1]) {
+            err = "tensor-core operands of the upward pass do not fit in shared memory";
+            return DMK_ERR_INTERNAL;
+        }
         PCK(cudaFuncSetAttribute(k_upward<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         const int lmax = tv.nlev - 1;
         for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0; --l) {
@@ -1698,7 +1859,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
             k_upward<T, P><<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, tv.lev_start[l], lc, M, lay,
-                                                                   (char *)cx.bufs->slab.p);
+                                                                   (char *)cx.bufs->slab.p,
+                                                                   (int *)cx.bufs->counter.p + 6);
         }
         PCK(cudaGetLastError());
     }

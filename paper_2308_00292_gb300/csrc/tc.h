@@ -112,13 +112,18 @@ __device__ __forceinline__ void ld_x8(uint32_t taddr, float (&v)[8]) {
 
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// x = hi + lo: hi is x rounded to a TF32 value (11 significant bits, ties
-// away from zero, by integer arithmetic on the bits) and lo = x - hi exactly;
-// the tensor core reads lo to 11 bits, so hi + lo carries about 22 bits and a
-// product of two splits, dropping lo * lo, about 21
+// round to a TF32 value (11 significant bits, ties away from zero) by integer
+// arithmetic on the bits
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
+// x = hi + lo with hi = TF32(x) and lo = TF32(x - hi): x - hi is exact in
+// FP32 and at most 2^-12 |x|, so hi + lo represents x to about 2^-23
+// relative; a product of two splits without lo * lo keeps about 22 bits
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-    hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
-    lo = x - hi;
+    hi = round_tf32(x);
+    lo = round_tf32(x - hi);
 }
 
 }  // namespace tc
