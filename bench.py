@@ -107,9 +107,9 @@ NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares,
 # dram_traffic_laplace3d_clustered_n2e6.md), valid only for the kernel source
 # it was taken on.
 TRAFFIC_SOURCE = "paper_2308_00292_gb300/csrc/passes.cu"
-TRAFFIC_SHA256 = "ade2dcc1ddae58fd82829432e21c836d850c9f31fb619ce682cc7c68023701fb"
-TRAFFIC_PER_UNIT = {"k_local": (1031.5e6 + 132.3e6) / 8.406e10,  # bytes per algorithmic flop
-                    "k_near": (74.8e6 + 6.1e6) / 4.693e9}        # bytes per candidate pair
+TRAFFIC_SHA256 = "2be5f3a5c84a7a6a9f8edc72e4f7d2d4bd09f5c432dfb6c170e79f6b56896e4c"
+TRAFFIC_PER_UNIT = {"k_local": (847.0e6 + 146.7e6) / 7.106e10,  # bytes per algorithmic flop
+                    "k_near": (74.7e6 + 7.5e6) / 4.693e9}         # bytes per candidate pair
 
 
 def traffic_per_unit(kernel: str):
