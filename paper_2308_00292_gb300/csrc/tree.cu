@@ -305,6 +305,71 @@ __global__ void k_balance(const uint64_t *bkey, const int8_t *blevel, const uint
     }
 }
 
+// The level restriction completed on cell sets, without rebuilding the tree:
+// S = the forced set = every box that splits (the first tree's non-leaf boxes,
+// then the forced ones).  A cell n at level l is a box if its parent is in S
+// and it holds points; a box n that is not in S but shares a boundary point
+// with a member of S one level finer must split.  Every round pushes from all
+// of S (new boxes may neighbour old members); the forced set grows
+// monotonically to the same least fixpoint as check-and-rebuild rounds.
+__global__ void k_collect_nonleaf(const uint64_t *bkey, const int8_t *blevel, const uint8_t *bcmask, int nb,
+                                  uint64_t *forced, uint32_t fcap, uint64_t *slist, int *count, int lcap,
+                                  int *overflow) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || bcmask[b] == 0) return;
+    const uint64_t key = cell_key(blevel[b], bkey[b]);
+    if (hset_insert(forced, fcap, key, overflow)) {
+        const int k = atomicAdd(count, 1);
+        if (k < lcap) slist[k] = key; else atomicExch(overflow, 1);
+    }
+}
+
+// whether cell m at level l holds points (sorted finest-level keys)
+__device__ __forceinline__ bool cell_nonempty(const uint64_t *keys, int64_t n, int l, uint64_t m) {
+    const int shift = 3 * (kMortonBits - l);
+    const uint64_t lo = shift >= 64 ? 0ull : (m << shift);
+    int64_t a = 0, b = n;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (keys[mid] < lo) a = mid + 1; else b = mid;
+    }
+    return a < n && (shift >= 64 ? true : (keys[a] >> shift) == m);
+}
+
+__global__ void k_push_balance(const uint64_t *keys, int64_t n, int max_level, uint64_t *forced, uint32_t fcap,
+                               uint64_t *slist, int ns, int *count, int lcap, int *changed, int *overflow) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const uint64_t sk = slist[i];
+    const int ls = (63 - __clzll((long long)sk)) / 3;
+    if (ls < 1 || ls >= max_level) return;  // a cell at the deepest level never splits
+    int sx, sy, sz;
+    morton_decode(sk ^ (1ull << (3 * ls)), sx, sy, sz);
+    const int l = ls - 1, lim = 1 << l;
+    const int px = sx >> 1, py = sy >> 1, pz = sz >> 1;
+    // level-l cells sharing a boundary point with s: 2 i - 1 <= s <= 2 i + 2 per axis
+    for (int ix = (sx - 1) >> 1; ix <= (sx + 1) >> 1; ++ix) {
+        if (ix < 0 || ix >= lim) continue;
+        for (int iy = (sy - 1) >> 1; iy <= (sy + 1) >> 1; ++iy) {
+            if (iy < 0 || iy >= lim) continue;
+            for (int iz = (sz - 1) >> 1; iz <= (sz + 1) >> 1; ++iz) {
+                if (iz < 0 || iz >= lim) continue;
+                if (ix == px && iy == py && iz == pz) continue;
+                const uint64_t m = morton_encode(ix, iy, iz);
+                const uint64_t key = cell_key(l, m);
+                if (hset_contains(forced, fcap, key)) continue;
+                if (l > 0 && !hset_contains(forced, fcap, cell_key(l - 1, m >> 3))) continue;
+                if (!cell_nonempty(keys, n, l, m)) continue;
+                if (hset_insert(forced, fcap, key, overflow)) {
+                    const int k = atomicAdd(count, 1);
+                    if (k < lcap) slist[k] = key; else atomicExch(overflow, 1);
+                    atomicExch(changed, 1);
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ 5. finish
 __global__ void k_box_finish(int nb, const uint64_t *bkey, const int8_t *blevel, const int32_t *bstart,
                              const int32_t *bcount, const uint8_t *bcmask, const int32_t *psrc, const int32_t *ptgt,
@@ -613,9 +678,9 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     int64_t est = std::max<int64_t>(4096, 16 * (N / std::max(leaf_cap, 1) + 64));
     if (int rc = grow_boxes(est, st, err)) return rc;
     rounds = 0;
-    for (;;) {
-        ++rounds;
-        if (rounds > 64) { err = "level restriction did not converge"; return DMK_ERR_INTERNAL_I; }
+    bool pushed = false;  // the forced set has been completed on the cell sets
+    for (int rebuilds = 0;; ++rebuilds) {
+        if (rebuilds > 64) { err = "level restriction did not converge"; return DMK_ERR_INTERNAL_I; }
         // root
         uint64_t zero64 = 0;
         int8_t zero8 = 0;
@@ -702,6 +767,35 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
             lt.count[l] = l < nlev ? lt_count[l] : 0;
         }
         lt.nlev = nlev;
+        if (!pushed) {
+            // complete the level restriction on the cell sets, then rebuild once
+            pushed = true;
+            const int lcap = (int)fcap;
+            if (ws.ensure(slist, (int64_t)lcap * 8)) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
+            CK(cudaMemsetAsync(d_flags + 1, 0, 3 * sizeof(int), st));  // changed, overflow, count
+            ::dmk::launch_tick();
+            k_collect_nonleaf<<<nblk(nb, 128), 128, 0, st>>>((const uint64_t *)bkey.p, (const int8_t *)blevel.p,
+                                                             (const uint8_t *)bcmask.p, nb, (uint64_t *)forced.p,
+                                                             fcap, (uint64_t *)slist.p, d_flags + 3, lcap,
+                                                             d_flags + 2);
+            int any = 0;
+            for (int pr = 0;; ++pr) {
+                int hc[3];
+                CK(cudaMemcpyAsync(hc, d_flags + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (hc[1]) { err = "forced-split table overflow"; return DMK_ERR_INTERNAL_I; }
+                if ((pr > 0 && !hc[0]) || hc[2] == 0) break;
+                if (pr > 64) { err = "level restriction did not converge"; return DMK_ERR_INTERNAL_I; }
+                any |= hc[0];
+                ++rounds;
+                CK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+                ::dmk::launch_tick();
+                k_push_balance<<<nblk(hc[2], 128), 128, 0, st>>>(skeys, N, max_level, (uint64_t *)forced.p, fcap,
+                                                                 (uint64_t *)slist.p, hc[2], d_flags + 3, lcap,
+                                                                 d_flags + 1, d_flags + 2);
+            }
+            if (any) continue;  // rebuild with the completed forced set
+        }
         CK(cudaMemsetAsync(d_flags + 1, 0, 2 * sizeof(int), st));
         ::dmk::launch_tick();
         k_balance<<<nblk(nb, 128), 128, 0, st>>>((const uint64_t *)bkey.p, (const int8_t *)blevel.p,

@@ -92,7 +92,7 @@ public:
     // points (sorted)
     DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, plocal_lo, pscan0, pscan1,
         scan_tmp;
-    DBuf bbox_part, frame, flags, forced;
+    DBuf bbox_part, frame, flags, forced, slist;
     // boxes
     int64_t box_cap = 0;
     DBuf bkey, blevel, bstart, bcount, bparent, bchild0, bcmask, bflags, bnsrc, bntgt, bcol, bslot;
