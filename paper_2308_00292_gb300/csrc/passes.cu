@@ -198,18 +198,32 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
     const int tid = threadIdx.x;
     constexpr uint32_t lbo = 128, sbo = KC * 32;
     bool ok = true;
+    // threads 0 .. 3 KC - 1 hold one coordinate (and charge) of the next batch,
+    // loaded one batch ahead
+    auto fetch = [&](int p, double &u, double &w) {
+        const int ax = tid / KC, j = tid % KC;
+        u = 0.0;
+        w = 1.0;
+        if (p + j < ntot) {
+            int seg = 0;
+            while (seg < 7 && lpre[seg + 1] <= p + j) ++seg;
+            const int kk = lstart[seg] + (p + j - lpre[seg]);
+            u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
+            if (ax == 0) w = tv.q[kk];
+        }
+    };
+    double un = 0.0, wn = 1.0;
+    if (tid < 3 * KC) fetch(0, un, wn);
     for (int p0 = 0; p0 < ntot; p0 += KC) {
         const int np = min(KC, ntot - p0);
         if (tid < 3 * KC) {
             const int ax = tid / KC, j = tid % KC;
             float *o = stg + (ax * KC + j) * PS;
+            const double u = un, wq = wn;
+            if (p0 + KC < ntot) fetch(p0 + KC, un, wn);
             if (j < np) {
-                int seg = 0;
-                while (seg < 7 && lpre[seg + 1] <= p0 + j) ++seg;
-                const int kk = lstart[seg] + (p0 + j - lpre[seg]);
-                const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
                 const float xi = (float)((u - cc[ax]) * s2R);
-                const float w = ax == 0 ? (float)tv.q[kk] : 1.f;
+                const float w = (float)wq;
                 float t0 = 1.f, t1 = xi;
                 o[0] = w;
                 if (P > 1) o[1] = w * xi;
