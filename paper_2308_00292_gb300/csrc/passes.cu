@@ -184,9 +184,12 @@ __device__ __forceinline__ void shift_up(const T *__restrict__ A, const T *in, T
 // grid of a box (centre cc, scale s2R): acc[a][b][c] += sum_j rho_j T_a(x_j)
 // T_b(y_j) T_c(z_j) as D[bc][a] = sum_j Y[bc][j] X[a][j] with Y = T_b(y) T_c(z)
 // and X = rho T_a(x), KC points per MMA batch; operands split into TF32 hi +
-// lo (D = A_lo B_hi + A_hi B_lo + A_hi B_hi).  Each batch's D is added to acc
-// by the CUDA cores in round-to-nearest FP32, so no accumulation runs through
-// the tensor core's adder for more than one batch.  Called by the whole CTA.
+// lo (D = A_lo B_hi + A_hi B_lo + A_hi B_hi).  D accumulates kFlush batches in
+// TMEM and is then added to acc by the CUDA cores in round-to-nearest FP32, so
+// no sum runs through the tensor core's adder for more than kFlush batches:
+// all batches at once missed the 1e-6 bar, and 4 batches per flush raised the
+// rel-L2 error of 2e4 uniform points from 5.1e-7 to 6.3e-7, so each batch is
+// flushed.  Called by the whole CTA.
 template <int P>
 __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double s2R, const int *lstart,
                                const int *lpre, int ntot, float *scr, uint32_t tmem, uint64_t *bar, uint32_t &phase,
@@ -214,8 +217,11 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
     };
     double un = 0.0, wn = 1.0;
     if (tid < 3 * KC) fetch(0, un, wn);
+    constexpr int kFlush = 1;
+    bool pending = false;     // a batch's MMAs were issued but not yet waited for
+    uint32_t pend_par = 0;
     for (int p0 = 0; p0 < ntot; p0 += KC) {
-        const int np = min(KC, ntot - p0);
+        const int np = min(KC, ntot - p0), bi = p0 / KC;
         if (tid < 3 * KC) {
             const int ax = tid / KC, j = tid % KC;
             float *o = stg + (ax * KC + j) * PS;
@@ -239,6 +245,8 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
                 for (int n = 0; n < P; ++n) o[n] = 0.f;
             }
         }
+        // the previous batch's MMAs read the operands: they must be done
+        if (pending && tid == 0) ok = tc::mbar_wait(bar, pend_par, 2000000000ll) && ok;
         __syncthreads();
         // A operand: row bc, column j (K-major core matrices), 4 points per float4
         for (int t = tid; t < U::A_FL / 4; t += blockDim.x) {
@@ -280,17 +288,25 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
 #pragma unroll
                 for (int ks = 0; ks < KC / 8; ++ks) {
                     const uint32_t ko = (uint32_t)ks * 256;
-                    tc::mma_tf32(dcol, tc::sdesc(aL + aoff + ko, lbo, sbo), tc::sdesc(bH + ko, lbo, sbo), id, ks > 0);
+                    tc::mma_tf32(dcol, tc::sdesc(aL + aoff + ko, lbo, sbo), tc::sdesc(bH + ko, lbo, sbo), id,
+                                 ks > 0 || bi % kFlush != 0);
                     tc::mma_tf32(dcol, tc::sdesc(aH + aoff + ko, lbo, sbo), tc::sdesc(bL + ko, lbo, sbo), id, true);
                     tc::mma_tf32(dcol, tc::sdesc(aH + aoff + ko, lbo, sbo), tc::sdesc(bH + ko, lbo, sbo), id, true);
                 }
             }
             tc::commit(bar);
         }
+        const uint32_t par = phase;
+        phase ^= 1u;
+        if (bi % kFlush != kFlush - 1 && p0 + KC < ntot) {
+            pending = true;
+            pend_par = par;
+            continue;
+        }
+        pending = false;
         // every thread waits for the batch, then adds its share of D to acc:
         // warp w reads TMEM lanes 32 (w mod 4) .. + 31 of the tiles w / 4, w / 4 + 2, ...
-        ok = tc::mbar_wait(bar, phase, 2000000000ll) && ok;  // about 1 s
-        phase ^= 1u;
+        ok = tc::mbar_wait(bar, par, 2000000000ll) && ok;  // about 1 s
         const bool wok = __all_sync(0xffffffffu, ok);
         tc::fence_after_sync();
         if (wok) {
