@@ -136,6 +136,26 @@ DMK_API int dmk_eval_host(dmk_plan_t plan,
                   void *cuda_stream);
 
 /*
+ * dmk_eval_grad -- dmk_eval plus the gradient of the potential at every target,
+ * grad u(x_i) = sum_{j : y_j != x_i} rho_j (y_j - x_i) / |x_i - y_j|^3, from the same
+ * pass differentiated: the Chebyshev local expansions through T_n' = n U_{n-1}
+ * (Sec. 2.1) and the residual kernel through R_L'(r) (x - y) / r (Sec. 3.6).  The
+ * negated gradient times a target's charge is the force on it; the gradient
+ * with respect to a source follows from evaluating with the roles swapped.
+ *
+ *   arguments   as in dmk_eval
+ *   gradients   device pointer, n_tgt x 3 doubles, row-major (d/dx, d/dy, d/dz of
+ *               u at target i), caller-allocated, overwritten
+ *
+ * The gradients carry the method's error relative to their own size (about eps
+ * for the FP64 path); the flags DMK_FLAG_FAR_ONLY / NEAR_ONLY apply to them too.
+ */
+DMK_API int dmk_eval_grad(dmk_plan_t plan,
+                          const double *sources, int64_t n_src, const double *charges,
+                          const double *targets, int64_t n_tgt, double *potentials, double *gradients,
+                          void *cuda_stream);
+
+/*
  * dmk_direct_noalloc -- the direct sum u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j|
  * in double precision, performing no device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate while

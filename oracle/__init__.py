@@ -72,6 +72,10 @@ def _load():
             lib.oracle_direct.restype = None
             lib.oracle_dmk.argtypes = [ctypes.POINTER(Params), dp, dp, i64, dp, i64, dp, dp, dp]
             lib.oracle_dmk.restype = ctypes.c_int
+            lib.oracle_direct_grad.argtypes = [dp, dp, i64, dp, i64, dp, ctypes.c_int]
+            lib.oracle_direct_grad.restype = None
+            lib.oracle_dmk_grad.argtypes = [ctypes.POINTER(Params), dp, dp, i64, dp, i64, dp, dp, dp, dp]
+            lib.oracle_dmk_grad.restype = ctypes.c_int
             lib.oracle_tree.argtypes = [ctypes.POINTER(Params), dp, i64, dp, i64,
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
@@ -122,6 +126,35 @@ def direct(src, rho, tgt=None, nthreads=0) -> np.ndarray:
     out = np.zeros(tgt.shape[0])
     _load().oracle_direct(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], _dp(out), nthreads)
     return out
+
+
+def direct_grad(src, rho, tgt=None, nthreads=0) -> np.ndarray:
+    """O1 gradient in the target position: sum_j rho_j (y_j - x_i) / |x_i - y_j|^3
+    over y_j != x_i, as an (nt, 3) array."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
+    rho = _c64(rho, src.shape[0])
+    tgt = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((tgt.shape[0], 3))
+    _load().oracle_direct_grad(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], _dp(out), nthreads)
+    return out
+
+
+def dmk_grad(src, rho, tgt=None, prm: Params | None = None, parts: bool = False, **kw):
+    """O2 gradient of the potential at the targets, (nt, 3).
+
+    Returns (pot, grad), or (pot, grad, grad_far, grad_near) if parts is True."""
+    prm = prm if prm is not None else params(**kw)
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
+    rho = _c64(rho, src.shape[0])
+    tgt_a = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 3)
+    nt = tgt_a.shape[0]
+    pot = np.zeros(nt)
+    g, gf, gn = np.zeros((nt, 3)), np.zeros((nt, 3)), np.zeros((nt, 3))
+    rc = _load().oracle_dmk_grad(ctypes.byref(prm), _dp(src), _dp(rho), src.shape[0], _dp(tgt_a), nt,
+                                 _dp(pot), _dp(g), _dp(gf), _dp(gn))
+    if rc != 0:
+        raise RuntimeError("oracle_dmk_grad failed with code %d" % rc)
+    return (pot, g, gf, gn) if parts else (pot, g)
 
 
 def dmk(src, rho, tgt=None, prm: Params | None = None, parts: bool = False, **kw):

@@ -105,6 +105,23 @@ static double cheb_t(int n, double x)
     return cos(n * acos(x));
 }
 
+/* derivative T_n'(x) = n U_{n-1}(x), with U_k the Chebyshev polynomials of the
+ * second kind by their three-term recurrence (U_0 = 1, U_1 = 2x) */
+static double cheb_dt(int n, double x)
+{
+    if (n == 0) return 0.0;
+    if (x > 1.0) x = 1.0;
+    if (x < -1.0) x = -1.0;
+    double u0 = 1.0, u1 = 2.0 * x;
+    if (n == 1) return 1.0;
+    for (int k = 2; k < n; ++k) {
+        double u2 = 2.0 * x * u1 - u0;
+        u0 = u1;
+        u1 = u2;
+    }
+    return n * u1;
+}
+
 /* Chebyshev nodes of the first kind r_i = cos(pi (i - 1/2) / p), i = 1..p. */
 static void cheb_nodes(int p, double *t)
 {
@@ -325,6 +342,22 @@ static double split_R(const split_t *sp, int l, double r)
     }
 }
 
+/* d/dr of the residual kernel R_l(r) = 1/r - S_l(r), r > 0:
+ *   PSWF:     -Phi'(r/R)/(R r) - (1 - Phi(r/R))/r^2, Phi'(t) = psi(t)/c_0
+ *   Gaussian: -2 exp(-r^2/sigma^2)/(sqrt(pi) sigma r) - erfc(r/sigma)/r^2 */
+static double split_dR(const split_t *sp, int l, double r)
+{
+    double R = level_R(l);
+    if (sp->prm.splitting == ORACLE_PSWF) {
+        double t = r / R;
+        double dphi = t < 1.0 ? pswf_eval(sp->pswf, t) / sp->pswf->c0 : 0.0;
+        return -dphi / (R * r) - (1.0 - pswf_Phi(sp->pswf, t)) / (r * r);
+    } else {
+        double sg = gauss_sigma(sp, l);
+        return -2.0 * exp(-(r * r) / (sg * sg)) / (sqrt(M_PI) * sg * r) - erfc(r / sg) / (r * r);
+    }
+}
+
 /* Fourier transform of the difference kernel D_l at |k| */
 static double split_Dhat(const split_t *sp, int l, double k)
 {
@@ -461,6 +494,38 @@ void oracle_direct(const double *src, const double *rho, int64_t ns,
             sum = t;
         }
         pot[i] = sum + comp;
+    }
+}
+
+/* O1 gradient: grad u(x_i) = sum_{j : y_j != x_i} rho_j (y_j - x_i) / |x_i - y_j|^3,
+ * the derivative of eq. discretesum in the target position, with compensated
+ * sums per component. */
+void oracle_direct_grad(const double *src, const double *rho, int64_t ns,
+                        const double *tgt, int64_t nt, double *grad, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < nt; ++i) {
+        double sum[3] = {0.0, 0.0, 0.0}, comp[3] = {0.0, 0.0, 0.0};
+        const double *x = &tgt[3 * i];
+        for (int64_t j = 0; j < ns; ++j) {
+            double d[3] = {src[3 * j] - x[0], src[3 * j + 1] - x[1], src[3 * j + 2] - x[2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double f = rho[j] / (r2 * sqrt(r2));
+            for (int a = 0; a < 3; ++a) {
+                double term = f * d[a];
+                double t = sum[a] + term;
+                if (fabs(sum[a]) >= fabs(term)) comp[a] += (sum[a] - t) + term;
+                else comp[a] += (term - t) + sum[a];
+                sum[a] = t;
+            }
+        }
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = sum[a] + comp[a];
     }
 }
 
@@ -1014,6 +1079,36 @@ static double eval_local(const ops_t *o, const obox *b, const double *coef, cons
     return acc;
 }
 
+/* gradient (in unit-box coordinates) of the local expansion at u:
+ * d/du_x sum coef[a][b][c] T_a(xi_x) T_b(xi_y) T_c(xi_z) = (2/R) sum coef T_a' T_b T_c, ... */
+static void eval_local_grad(const ops_t *o, const obox *b, const double *coef, const double *u, double *g)
+{
+    int p = o->p;
+    double R = level_R(b->level);
+    double t[3][64], dt[3][64];
+    double xi[3];
+    xi[0] = 2.0 * (u[0] - (b->ix + 0.5) * R) / R;
+    xi[1] = 2.0 * (u[1] - (b->iy + 0.5) * R) / R;
+    xi[2] = 2.0 * (u[2] - (b->iz + 0.5) * R) / R;
+    for (int d = 0; d < 3; ++d)
+        for (int n = 0; n < p; ++n) {
+            t[d][n] = cheb_t(n, xi[d]);
+            dt[d][n] = cheb_dt(n, xi[d]);
+        }
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int a = 0; a < p; ++a)
+        for (int bb = 0; bb < p; ++bb)
+            for (int c = 0; c < p; ++c) {
+                double v = coef[(a * p + bb) * p + c];
+                gx += v * dt[0][a] * t[1][bb] * t[2][c];
+                gy += v * t[0][a] * dt[1][bb] * t[2][c];
+                gz += v * t[0][a] * t[1][bb] * dt[2][c];
+            }
+    g[0] = 2.0 * gx / R;
+    g[1] = 2.0 * gy / R;
+    g[2] = 2.0 * gz / R;
+}
+
 /* near-field list of a target leaf: source leaves whose Step-4 target set
  * (colleagues' subtrees and coarse neighbours) contains it */
 typedef struct { int *s; int n, cap; } ilist;
@@ -1040,7 +1135,8 @@ static int add_subtree_leaves(const otree *t, int X, int S, ilist *lists)
     return 0;
 }
 
-static int run_dmk(const split_t *sp, const opoints *P, otree *t, double *ufar, double *unear)
+static int run_dmk(const split_t *sp, const opoints *P, otree *t, double *ufar, double *unear,
+                   double *gfar, double *gnear)
 {
     const oracle_params *prm = &sp->prm;
     ops_t o;
@@ -1185,6 +1281,11 @@ static int run_dmk(const split_t *sp, const opoints *P, otree *t, double *ufar, 
                 int64_t pi = t->ord[k];
                 if (!P->is_tgt[pi]) continue;
                 ufar[pi] += eval_local(&o, b, b->local, &P->u[3 * pi]);
+                if (gfar) {
+                    double g[3];
+                    eval_local_grad(&o, b, b->local, &P->u[3 * pi], g);
+                    for (int d = 0; d < 3; ++d) gfar[3 * pi + d] += g[d];
+                }
             }
         }
         /* expansions of this level are no longer needed */
@@ -1228,7 +1329,7 @@ static int run_dmk(const split_t *sp, const opoints *P, otree *t, double *ufar, 
                 int64_t ti = t->ord[k];
                 if (!P->is_tgt[ti]) continue;
                 const double *x = &P->u[3 * ti];
-                double acc = 0.0;
+                double acc = 0.0, gacc[3] = {0.0, 0.0, 0.0};
                 for (int li = 0; li < lists[T].n; ++li) {
                     const obox *bs = &t->b[lists[T].s[li]];
                     double Rb = level_R(bs->level);
@@ -1240,9 +1341,18 @@ static int run_dmk(const split_t *sp, const opoints *P, otree *t, double *ufar, 
                         double r = sqrt(dx * dx + dy * dy + dz * dz);
                         if (r == 0.0 || r >= Rb) continue;
                         acc += P->q[sj] * split_R(sp, bs->level, r);
+                        if (gnear) {
+                            /* grad_x R(|x - y|) = R'(r) (x - y) / r */
+                            double f = P->q[sj] * split_dR(sp, bs->level, r) / r;
+                            gacc[0] += f * dx;
+                            gacc[1] += f * dy;
+                            gacc[2] += f * dz;
+                        }
                     }
                 }
                 unear[ti] += acc;
+                if (gnear)
+                    for (int d = 0; d < 3; ++d) gnear[3 * ti + d] += gacc[d];
             }
         }
     }
@@ -1296,7 +1406,7 @@ int oracle_dmk(const oracle_params *prm_in,
         unear = (double *)malloc((size_t)P.n * sizeof(double));
         if (!ufar || !unear) rc = -1;
     }
-    if (rc == 0) rc = run_dmk(&sp, &P, &t, ufar, unear);
+    if (rc == 0) rc = run_dmk(&sp, &P, &t, ufar, unear, NULL, NULL);
     if (rc == 0) {
         for (int64_t i = 0; i < P.n; ++i) {
             int64_t o = P.out_index[i];
@@ -1308,6 +1418,56 @@ int oracle_dmk(const oracle_params *prm_in,
     }
     free(ufar);
     free(unear);
+    tree_free(&t);
+    points_free(&P);
+    split_free(&sp);
+    return rc;
+}
+
+int oracle_dmk_grad(const oracle_params *prm_in,
+                    const double *src, const double *rho, int64_t ns,
+                    const double *tgt, int64_t nt,
+                    double *pot, double *grad, double *grad_far, double *grad_near)
+{
+    if (ns < 0 || nt < 0) return -1;
+    if (nt == 0) return 0;
+    split_t sp;
+    if (split_init(&sp, prm_in) != 0) return -1;
+#ifdef _OPENMP
+    if (sp.prm.nthreads > 0) omp_set_num_threads(sp.prm.nthreads);
+#endif
+    opoints P;
+    otree t;
+    memset(&t, 0, sizeof(t));
+    int rc = points_init(&P, src, rho, ns, tgt, nt);
+    if (rc == 0) rc = tree_make(&t, &P, &sp.prm);
+    double *ufar = NULL, *unear = NULL, *gf = NULL, *gn = NULL;
+    if (rc == 0) {
+        ufar = (double *)calloc((size_t)P.n, sizeof(double));
+        unear = (double *)calloc((size_t)P.n, sizeof(double));
+        gf = (double *)calloc((size_t)P.n * 3, sizeof(double));
+        gn = (double *)calloc((size_t)P.n * 3, sizeof(double));
+        if (!ufar || !unear || !gf || !gn) rc = -1;
+    }
+    if (rc == 0) rc = run_dmk(&sp, &P, &t, ufar, unear, gf, gn);
+    if (rc == 0) {
+        /* unit-box potentials scale by 1/S, their gradients by 1/S^2 */
+        const double s2 = P.S * P.S;
+        for (int64_t i = 0; i < P.n; ++i) {
+            int64_t o = P.out_index[i];
+            if (o < 0) continue;
+            if (pot) pot[o] = (ufar[i] + unear[i]) / P.S;
+            for (int d = 0; d < 3; ++d) {
+                grad[3 * o + d] = (gf[3 * i + d] + gn[3 * i + d]) / s2;
+                if (grad_far) grad_far[3 * o + d] = gf[3 * i + d] / s2;
+                if (grad_near) grad_near[3 * o + d] = gn[3 * i + d] / s2;
+            }
+        }
+    }
+    free(ufar);
+    free(unear);
+    free(gf);
+    free(gn);
     tree_free(&t);
     points_free(&P);
     split_free(&sp);

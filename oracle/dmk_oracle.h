@@ -71,6 +71,19 @@ int oracle_dmk(const oracle_params *prm,
                const double *tgt, int64_t nt,
                double *pot, double *pot_far, double *pot_near);
 
+/* O1 gradient in the target position: grad[3 i + d] = d/dx_d of u(x_i). */
+void oracle_direct_grad(const double *src, const double *rho, int64_t ns,
+                        const double *tgt, int64_t nt, double *grad, int nthreads);
+
+/* O2 gradient: the plain DMK pass with the derivative of the local expansions
+ * (Chebyshev derivatives T_n' = n U_{n-1}) and of the residual kernel
+ * (R_L'(r) (x - y) / r) at every target; grad (and the optional far / near
+ * parts) hold nt x 3 doubles; pot may be NULL. */
+int oracle_dmk_grad(const oracle_params *prm,
+                    const double *src, const double *rho, int64_t ns,
+                    const double *tgt, int64_t nt,
+                    double *pot, double *grad, double *grad_far, double *grad_near);
+
 /* Tree export for parity checks.  Returns the number of boxes (>= 1) or < 0.
  * For every point of the (source u target) set, in the order sources then
  * (if tgt != src) targets: leaf_level[i], leaf_cell[i] = Morton interleave of

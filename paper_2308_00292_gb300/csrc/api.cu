@@ -101,11 +101,12 @@ int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
 bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 19 || p == 28 || p == 38; }
 
 int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
-                double *pot, cudaStream_t st) {
+                double *pot, double *grad, cudaStream_t st) {
     if (nt == 0) return DMK_OK;
     if (cudaSetDevice(pl->device) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaSetDevice failed");
     if (ns == 0) {
         if (cudaMemsetAsync(pot, 0, (size_t)nt * sizeof(double), st) != cudaSuccess ||
+            (grad && cudaMemsetAsync(grad, 0, (size_t)nt * 3 * sizeof(double), st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail(DMK_ERR_CUDA, "clearing the potentials failed");
         pl->stats = dmk_eval_stats{};
@@ -132,6 +133,7 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     cx.mode = (pl->opts.flags & DMK_FLAG_FAR_ONLY) ? 1 : ((pl->opts.flags & DMK_FLAG_NEAR_ONLY) ? 2 : 0);
     cx.total_sources = ns;
     cx.pot = pot;
+    cx.grad = grad;
     cx.st = st;
     for (int i = 0; i < 7; ++i) cx.ev[i] = pl->ev[i];
     cx.smem_limit = pl->smem_limit;
@@ -277,7 +279,20 @@ int dmk_eval(dmk_plan_t plan, const double *sources, int64_t n_src, const double
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials)))
         return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
-    return eval_device(plan, sources, n_src, charges, targets, n_tgt, potentials, (cudaStream_t)cuda_stream);
+    return eval_device(plan, sources, n_src, charges, targets, n_tgt, potentials, nullptr,
+                       (cudaStream_t)cuda_stream);
+}
+
+int dmk_eval_grad(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
+                  const double *targets, int64_t n_tgt, double *potentials, double *gradients, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
+    if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials || !gradients)))
+        return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    return eval_device(plan, sources, n_src, charges, targets, n_tgt, potentials, gradients,
+                       (cudaStream_t)cuda_stream);
 }
 
 int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
@@ -304,7 +319,8 @@ int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const d
         return fail(DMK_ERR_CUDA, "host-to-device copy failed");
     const double *dsrc = (const double *)plan->h_src.p;
     const double *dtgt = same ? dsrc : (const double *)plan->h_tgt.p;
-    int rc = eval_device(plan, dsrc, n_src, (const double *)plan->h_q.p, dtgt, n_tgt, (double *)plan->h_pot.p, st);
+    int rc = eval_device(plan, dsrc, n_src, (const double *)plan->h_q.p, dtgt, n_tgt, (double *)plan->h_pot.p,
+                         nullptr, st);
     if (rc) return rc;
     if (cudaMemcpyAsync(potentials, plan->h_pot.p, (size_t)n_tgt * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)

@@ -41,6 +41,7 @@
 //              including the self correction of Step 5 (r = 0 terms)
 #include "passes.h"
 #include "tc.h"
+#include "dev_util.h"
 
 #include <algorithm>
 #include <cstdio>
@@ -54,20 +55,6 @@ template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
 
-__device__ __forceinline__ void morton_decode_d(uint64_t m, int &ix, int &iy, int &iz) {
-    auto compact = [](uint64_t x) -> int {
-        x &= 0x1249249249249249ull;
-        x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
-        x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
-        x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
-        x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
-        x = (x ^ (x >> 32)) & 0x1fffffull;
-        return (int)x;
-    };
-    ix = compact(m);
-    iy = compact(m >> 1);
-    iz = compact(m >> 2);
-}
 
 template <typename U>
 __device__ __forceinline__ U *buf_ptr(const BufLayout &lay, int i, char *sm, char *slab) {
@@ -754,6 +741,64 @@ template <int P> __device__ __forceinline__ void cheb_row(float x, float (&t)[P]
     for (int n = 2; n < P; ++n) t[n] = 2.f * x * t[n - 1] - t[n - 2];
 }
 
+// T_n(x) and T_n'(x) by their recurrences (T'_{n+1} = 2 T_n + 2 x T'_n - T'_{n-1})
+template <int P> __device__ __forceinline__ void cheb_row_d(float x, float (&t)[P], float (&dt)[P]) {
+    t[0] = 1.f;
+    dt[0] = 0.f;
+    if (P > 1) {
+        t[1] = x;
+        dt[1] = 1.f;
+    }
+#pragma unroll
+    for (int n = 2; n < P; ++n) {
+        t[n] = 2.f * x * t[n - 1] - t[n - 2];
+        dt[n] = 2.f * t[n - 1] + 2.f * x * dt[n - 1] - dt[n - 2];
+    }
+}
+
+// the same column range for the potential and its x and y derivatives:
+// u = sum T_a T_b D, gx = sum T'_a T_b D, gy = sum T_a T'_b D
+template <int P, int C0, int C1>
+__device__ __forceinline__ void eval_part_g(uint32_t trow, const float (&tx)[P], const float (&ty)[P],
+                                            const float (&dtx)[P], const float (&dty)[P], float &u, float &gx,
+                                            float &gy) {
+    constexpr int B = 4;
+    float su = 0.f, sx = 0.f, sy = 0.f, acc = 0.f, accd = 0.f;
+#pragma unroll
+    for (int c = C0; c < C1; c += B) {
+        float d[B][8];
+#pragma unroll
+        for (int g = 0; g < B; ++g)
+            if (c + g < C1) tc::ld_x8(trow + (uint32_t)((c + g) * 8), d[g]);
+        tc::ld_wait();
+#pragma unroll
+        for (int g = 0; g < B; ++g)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int n = (c + g) * 8 + q;
+                if (c + g < C1 && n < P * P) {
+                    acc += ty[n % P] * d[g][q];
+                    accd += dty[n % P] * d[g][q];
+                    if (n % P == P - 1) {
+                        su += tx[n / P] * acc;
+                        sx += dtx[n / P] * acc;
+                        sy += tx[n / P] * accd;
+                        acc = accd = 0.f;
+                    }
+                }
+            }
+    }
+    constexpr int nlast = (8 * C1 < P * P ? 8 * C1 : P * P) - 1;
+    if (nlast >= 8 * C0 && nlast % P != P - 1) {
+        su += tx[nlast / P] * acc;
+        sx += dtx[nlast / P] * acc;
+        sy += tx[nlast / P] * accd;
+    }
+    u = su;
+    gx = sx;
+    gy = sy;
+}
+
 // sum over the accumulator columns n = 8 C0 .. 8 C1 - 1 (n = a P + b) of this
 // thread's TMEM lane: T_a(x) T_b(y) D[n], up to six 8-column chunks per wait
 template <int P, int C0, int C1>
@@ -793,7 +838,7 @@ struct TcEval {
     uint64_t *bar;             // MMA completion
     uint32_t tmem;             // accumulator base
     int *pending;              // an MMA batch outlived its wait
-    float (*red)[128];         // partial sums of column groups 1..3
+    float *red;                // partial sums of column groups 1..3: [4 values][3][128]
     int *err;                  // device error word
 };
 
@@ -809,12 +854,14 @@ __device__ __forceinline__ int range_point(const int *rs, const int *ro, int gp)
 // Lev[ab][c] for 128 points at a time (points on the TMEM lanes), then each
 // point's threads form u_j = sum_a T_a(x_j) sum_b T_b(y_j) D[j][ab].  Operands
 // are split into TF32 hi + lo and D = A_lo B_hi + A_hi B_lo + A_hi B_hi.  The
-// first 128 points' coordinates are in xyz (fetched by cp.async).  Called by
+// first 128 points' coordinates are in xyz (fetched by cp.async).  With gfar,
+// also the gradient in unit-box coordinates: d/dx and d/dy from the same D with
+// T'_a or T'_b, d/dz from a second MMA with the A operand T'_c(z).  Called by
 // the whole CTA.
 template <int P, int NF>
 __device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)[3], double s2R, const int *rs,
                         const int *ro, int nr, const double (*xyz)[128], const TcEval &st, uint32_t &phase,
-                        double *ufar) {
+                        double *ufar, double *gfar) {
     using S = LocalShape<P, NF>;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ntot = ro[nr];
@@ -841,34 +888,38 @@ __device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)
         const int pq = range_point(rs, ro, p0 + jq);
         const double xq = first ? xyz[0][jq] : tv.ux[pq];
         const double yq = first ? xyz[1][jq] : tv.uy[pq];
-        if (tid < S::TM) {
-            // A operand row j = T_c(z_j), c < P (zero rows past the points)
+        // A operand row j = T_c(z_j) (deriv: T_c'(z_j)), c < P, zero rows past the points
+        auto build_a = [&](bool deriv) {
+            if (tid >= S::TM) return;
             const int j = tid;
-            float tz[S::KP];
+            float tz[S::KP], dz[S::KP];
 #pragma unroll
-            for (int n = 0; n < S::KP; ++n) tz[n] = 0.f;
+            for (int n = 0; n < S::KP; ++n) tz[n] = dz[n] = 0.f;
             if (j < np) {
                 const float zi = (float)(((first ? xyz[2][j] : tv.uz[pq]) - cc[2]) * s2R);
                 tz[0] = 1.f;
-                if (P > 1) tz[1] = zi;
+                if (P > 1) {
+                    tz[1] = zi;
+                    dz[1] = 1.f;
+                }
 #pragma unroll
-                for (int n = 2; n < P; ++n) tz[n] = 2.f * zi * tz[n - 1] - tz[n - 2];
+                for (int n = 2; n < P; ++n) {
+                    tz[n] = 2.f * zi * tz[n - 1] - tz[n - 2];
+                    dz[n] = 2.f * tz[n - 1] + 2.f * zi * dz[n - 1] - dz[n - 2];
+                }
             }
 #pragma unroll
             for (int k4 = 0; k4 < S::KP / 4; ++k4) {
                 float h[4], l[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tc::split_tf32(tz[4 * k4 + q], h[q], l[q]);
+                for (int q = 0; q < 4; ++q) tc::split_tf32(deriv ? dz[4 * k4 + q] : tz[4 * k4 + q], h[q], l[q]);
                 const int o = ((j >> 3) * (S::KP / 4) + k4) * 8 + (j & 7);
                 reinterpret_cast<float4 *>(st.Ah)[o] = make_float4(h[0], h[1], h[2], h[3]);
                 reinterpret_cast<float4 *>(st.Al)[o] = make_float4(l[0], l[1], l[2], l[3]);
             }
-        }
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
+        };
+        auto issue = [&]() {
+            if (tid != 0) return;
             constexpr uint32_t lbo = 128, sbo = S::KP * 32;
             const uint32_t aH = tc::smem_addr(st.Ah), aL = tc::smem_addr(st.Al);
             const uint32_t bH = tc::smem_addr(st.Bh), bL = tc::smem_addr(st.Bl);
@@ -886,36 +937,85 @@ __device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)
                 }
             }
             tc::commit(st.bar);
-        }
+        };
         // every warp waits; warps w, w + 4, w + 8, w + 12 share TMEM lanes
         // 32 (w mod 4) .. + 31 (points j) and split the ab columns
-        bool ok = tc::mbar_wait(st.bar, phase, 2000000000ll);  // about 1 s
-        ok = __all_sync(0xffffffffu, ok);
-        tc::fence_after_sync();
-        const int j = tid & (S::TM - 1), cg = tid >> 7;
-        float part = 0.f;
-        if (ok) {
-            float tx[P], ty[P];
-            cheb_row<P>((float)((xq - cc[0]) * s2R), tx);
-            cheb_row<P>((float)((yq - cc[1]) * s2R), ty);
-            const uint32_t trow = st.tmem + ((uint32_t)((warp & 3) * 32) << 16);
-            constexpr int NC = S::NP / 8;  // 8-column chunks
-            switch (cg) {
-            case 0: part = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
-            case 1: part = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
-            case 2: part = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
-            default: part = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
+        auto wait = [&]() {
+            bool ok = tc::mbar_wait(st.bar, phase, 2000000000ll);  // about 1 s
+            ok = __all_sync(0xffffffffu, ok);
+            tc::fence_after_sync();
+            phase ^= 1u;
+            if (!ok && (tid & 31) == 0) {
+                atomicExch(st.err, 1);
+                *st.pending = 1;
             }
-        } else if ((tid & 31) == 0) {
-            atomicExch(st.err, 1);
-            *st.pending = 1;
-        }
-        if (cg > 0) st.red[cg - 1][j] = part;
+            return ok;
+        };
+        const int j = tid & (S::TM - 1), cg = tid >> 7;
+        const uint32_t trow = st.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        constexpr int NC = S::NP / 8;  // 8-column chunks
+        auto red = [&](int v, int g) -> float & { return st.red[(v * 3 + g) * 128 + j]; };
+        build_a(false);
+        tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
-        if (cg == 0 && j < np && (tv.pflag[pq] & 2))
-            ufar[pq] = (double)(part + st.red[0][j] + st.red[1][j] + st.red[2][j]);
-        phase ^= 1u;
+        tc::fence_after_sync();
+        issue();
+        const bool ok = wait();
+        float tx[P], ty[P], dtx[P], dty[P];
+        cheb_row_d<P>((float)((xq - cc[0]) * s2R), tx, dtx);
+        cheb_row_d<P>((float)((yq - cc[1]) * s2R), ty, dty);
+        float pu = 0.f, pgx = 0.f, pgy = 0.f, pgz = 0.f;
+        if (ok && !gfar) {
+            switch (cg) {
+            case 0: pu = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
+            case 1: pu = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
+            case 2: pu = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
+            default: pu = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
+            }
+        } else if (ok) {
+            switch (cg) {
+            case 0: eval_part_g<P, 0, NC / 4>(trow, tx, ty, dtx, dty, pu, pgx, pgy); break;
+            case 1: eval_part_g<P, NC / 4, NC / 2>(trow, tx, ty, dtx, dty, pu, pgx, pgy); break;
+            case 2: eval_part_g<P, NC / 2, 3 * NC / 4>(trow, tx, ty, dtx, dty, pu, pgx, pgy); break;
+            default: eval_part_g<P, 3 * NC / 4, NC>(trow, tx, ty, dtx, dty, pu, pgx, pgy); break;
+            }
+        }
+        if (gfar) {
+            // d/dz: a second MMA with T_c'(z) once every warp has read the first D
+            build_a(true);
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            issue();
+            if (wait()) {
+                switch (cg) {
+                case 0: pgz = eval_part<P, 0, NC / 4>(trow, tx, ty); break;
+                case 1: pgz = eval_part<P, NC / 4, NC / 2>(trow, tx, ty); break;
+                case 2: pgz = eval_part<P, NC / 2, 3 * NC / 4>(trow, tx, ty); break;
+                default: pgz = eval_part<P, 3 * NC / 4, NC>(trow, tx, ty); break;
+                }
+            }
+        }
+        if (cg > 0) {
+            red(0, cg - 1) = pu;
+            if (gfar) {
+                red(1, cg - 1) = pgx;
+                red(2, cg - 1) = pgy;
+                red(3, cg - 1) = pgz;
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (cg == 0 && j < np && (tv.pflag[pq] & 2)) {
+            ufar[pq] = (double)(pu + red(0, 0) + red(0, 1) + red(0, 2));
+            if (gfar) {
+                gfar[3 * (size_t)pq + 0] = (double)(pgx + red(1, 0) + red(1, 1) + red(1, 2)) * s2R;
+                gfar[3 * (size_t)pq + 1] = (double)(pgy + red(2, 0) + red(2, 1) + red(2, 2)) * s2R;
+                gfar[3 * (size_t)pq + 2] = (double)(pgz + red(3, 0) + red(3, 1) + red(3, 2)) * s2R;
+            }
+        }
     }
 }
 
@@ -937,7 +1037,8 @@ template <typename T, int P, int NF>
 __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T> tb, int level, int lstart,
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
                                                         const T *LamW, double *ufar, BufLayout lay, char *slab,
-                                                        unsigned long long *flops, int *tc_err, int *run_ctr) {
+                                                        unsigned long long *flops, int *tc_err, int *run_ctr,
+                                                        double *gfar) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
     constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P, NHP = nz_pad<NF>();
@@ -951,7 +1052,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     C2 *T1e = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my'][mz]; T1o follows
     C2 *T1o = T1e + P * NH * NH;
     T *hs = buf_ptr<T>(lay, 3, sm, slab);
-    T *ev = buf_ptr<T>(lay, 4, sm, slab);     // [3][kECH][P]
+    T *ev = buf_ptr<T>(lay, 4, sm, slab);     // [2][3][kECH][P]: T_n and T_n' of the evaluation chunk
     T *As = buf_ptr<T>(lay, 5, sm, slab);     // shift matrices A_{-1}, A_{+1}
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
@@ -959,7 +1060,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     __shared__ __align__(8) uint64_t s_bar;  // MMA completion
     __shared__ uint32_t s_tmem;              // TMEM accumulator base
     __shared__ int s_pending;                // an MMA batch outlived its wait
-    __shared__ float s_red[3][128];          // partial leaf sums of column groups 1..3
+    __shared__ float s_red[4 * 3 * 128];     // partial leaf sums (and gradients) of column groups 1..3
     __shared__ float2 s_ud[27 * 27];         // translation phases per colleague and residue class
     __shared__ double s_xyz[3][128];         // a leaf's first 128 points, fetched while its expansion forms
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -1293,38 +1394,49 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 const double R = level_R(level), s2R = 2.0 / R;
                 const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
                 if constexpr (kTC) {
-                    tc_eval<P, NF>(tv, Ls, cc, s2R, s_brs, s_bro, 1, s_xyz, st, phase, ufar);
+                    tc_eval<P, NF>(tv, Ls, cc, s2R, s_brs, s_bro, 1, s_xyz, st, phase, ufar, gfar);
                 } else {
                     const int s = tv.bstart[B], e = s + tv.bcount[B];
+                    T *dev = ev + 3 * kECH * P;  // derivatives T_n' (gradient pass)
                     for (int p0 = s; p0 < e; p0 += kECH) {
                         const int np = min(kECH, e - p0);
                         for (int t = tid; t < 3 * kECH; t += kLThreads) {
                             const int ax = t / kECH, j = t % kECH;
-                            T *o = ev + (ax * kECH + j) * P;
+                            T *o = ev + (ax * kECH + j) * P, *od = dev + (ax * kECH + j) * P;
                             if (j < np) {
                                 const int kk = p0 + j;
                                 const double u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
                                 const T xi = (T)((u - cc[ax]) * s2R);
-                                T t0 = (T)1, t1 = xi;
+                                T t0 = (T)1, t1 = xi, d0 = (T)0, d1 = (T)1;
                                 o[0] = (T)1;
-                                if (P > 1) o[1] = xi;
+                                od[0] = (T)0;
+                                if (P > 1) {
+                                    o[1] = xi;
+                                    od[1] = (T)1;
+                                }
 #pragma unroll
                                 for (int n = 2; n < P; ++n) {
-                                    T t2 = (T)2 * xi * t1 - t0;
+                                    const T t2 = (T)2 * xi * t1 - t0;
+                                    const T d2 = (T)2 * t1 + (T)2 * xi * d1 - d0;
                                     o[n] = t2;
+                                    od[n] = d2;
                                     t0 = t1;
                                     t1 = t2;
+                                    d0 = d1;
+                                    d1 = d2;
                                 }
                             } else {
 #pragma unroll
-                                for (int n = 0; n < P; ++n) o[n] = (T)0;
+                                for (int n = 0; n < P; ++n) o[n] = od[n] = (T)0;
                             }
                         }
                         __syncthreads();
-                        // W[j][ab] = sum_c Lambda[ab][c] T_c(z_j): 4 x 4 register tiles over (ab, j)
-                        {
+                        // pass 0: W = sum_c Lambda T_c(z) -> u, d/dx, d/dy; pass 1 (gradient):
+                        // W = sum_c Lambda T_c'(z) -> d/dz
+                        for (int pass = 0; pass < (gfar ? 2 : 1); ++pass) {
+                            // W[j][ab] = sum_c Lambda[ab][c] Z_c(z_j): 4 x 4 register tiles over (ab, j)
                             T *W = reinterpret_cast<T *>(PsE);
-                            const T *tzs = ev + 2 * kECH * P;
+                            const T *tzs = (pass ? dev : ev) + 2 * kECH * P;
                             constexpr int NABG = (P * P + 3) / 4;
                             for (int tile = tid; tile < NABG * (kECH / 4); tile += kLThreads) {
                                 const int jg = tile % (kECH / 4), abg = tile / (kECH / 4);
@@ -1357,22 +1469,45 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                                 }
                             }
                             __syncthreads();
-                            // u_j = sum_a T_a(x_j) sum_b T_b(y_j) W[j][a][b]: 16 threads per target
+                            // sum_a X_a(x_j) sum_b Y_b(y_j) W[j][a][b]: 16 threads per target
                             const int j = tid >> 4, g = tid & 15;
                             const T *tx = ev + j * P, *ty = ev + (kECH + j) * P;
+                            const T *dtx = dev + j * P, *dty = dev + (kECH + j) * P;
                             const T *Wj = W + j * (P * P);
-                            T sum = 0;
+                            T su = 0, sx = 0, sy = 0;
                             for (int a = g; a < P; a += 16) {
-                                T sa = 0;
+                                T sa = 0, sda = 0;
 #pragma unroll
-                                for (int b = 0; b < P; ++b) sa += ty[b] * Wj[a * P + b];
-                                sum += tx[a] * sa;
+                                for (int b = 0; b < P; ++b) {
+                                    sa += ty[b] * Wj[a * P + b];
+                                    if (gfar && pass == 0) sda += dty[b] * Wj[a * P + b];
+                                }
+                                su += tx[a] * sa;
+                                if (gfar && pass == 0) {
+                                    sx += dtx[a] * sa;
+                                    sy += tx[a] * sda;
+                                }
                             }
 #pragma unroll
-                            for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                            if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) ufar[p0 + j] = (double)sum;
+                            for (int o = 8; o > 0; o >>= 1) {
+                                su += __shfl_xor_sync(0xffffffffu, su, o);
+                                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                            }
+                            if (g == 0 && j < np && (tv.pflag[p0 + j] & 2)) {
+                                const size_t pk = (size_t)(p0 + j);
+                                if (pass == 0) {
+                                    ufar[pk] = (double)su;
+                                    if (gfar) {
+                                        gfar[3 * pk + 0] = (double)sx * s2R;
+                                        gfar[3 * pk + 1] = (double)sy * s2R;
+                                    }
+                                } else {
+                                    gfar[3 * pk + 2] = (double)su * s2R;
+                                }
+                            }
+                            __syncthreads();
                         }
-                        __syncthreads();
                     }
                 }
             }
@@ -1391,7 +1526,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     const double R = level_R(level - 1), s2R = 2.0 / R;
                     const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
                     if (tid == 0) atomicAdd(flops, 2ull * (P * P * P + P * P + P) * (unsigned long long)s_gntgt);
-                    tc_eval<P, NF>(tv, Pl, cc, s2R, s_grs, s_gro, gnr, s_gxyz, st, phase, ufar);
+                    tc_eval<P, NF>(tv, Pl, cc, s2R, s_grs, s_gro, gnr, s_gxyz, st, phase, ufar, gfar);
                 }
             }
         }
@@ -1409,400 +1544,20 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     }
 }
 
-// ---------------------------------------------------------------------------
-// Residual near field (Steps 4 and 5)
-// ---------------------------------------------------------------------------
-// One warp per target leaf, taken from an atomic work counter.  The leaf's
-// points are taken in groups of up to 32 targets; when the leaf holds fewer
-// than 32 points, G adjacent lanes share a target and split its candidates.
-// For each group:
-//   1. the source leaves of the interaction list are read 32 at a time, one
-//      per lane, and a leaf whose box lies farther than R_b from the group's
-//      bounding box is dropped;
-//   2. the sources of the kept leaves form one flat stream, staged in shared
-//      memory kNC at a time and moved to the target leaf's frame;
-//   3. each lane screens its target against 32 staged sources and marks those
-//      closer than R_b; the marked pairs of the warp are compacted into a
-//      queue and evaluated 32 at a time, one pair per lane;
-//   4. values are summed per target by a segmented warp reduction (a fixed
-//      order: the result is deterministic) into double accumulators.
-// In single precision coordinates are hi + lo pairs relative to the leaf
-// centres; the exact dyadic offset between the two leaf centres is added to
-// the source with a TwoSum, so differences of nearby points keep their full
-// relative precision.
-template <typename T> __device__ __forceinline__ T ldexp_t(T x, int e);
-template <> __device__ __forceinline__ float ldexp_t<float>(float x, int e) { return ldexpf(x, e); }
-template <> __device__ __forceinline__ double ldexp_t<double>(double x, int e) { return ldexp(x, e); }
-// centre coordinate (2 i + 1) 2^-(l+1) of cell i at level l, exact
-template <typename T> __device__ __forceinline__ T dyadic_centre(int i, int l) {
-    return ldexp_t<T>((T)(2 * i + 1), -(l + 1));
-}
-template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
-template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
-
-constexpr int kNearThreads = 128;
-constexpr int kNC = 128;  // staged sources per chunk
-
-// per-warp shared memory of k_near
-template <typename T> struct NearWarp {
-    using V4 = typename Vec4<T>::type;
-    V4 sh[kNC];        // staged sources: x, y, z in the target leaf's frame (hi) and
-                       // |s|^2 - R_b^2 (1 + 2^-9) carrying the leaf level b in its low bits
-    float4 sl[kNC];    // single precision: lo parts of x, y, z and the charge
-    T sq[kNC];         // double precision: the charge
-    V4 th[32];         // the group's targets (hi) and
-    float4 tl[32];     // their lo parts
-    double acc[32];    // per-target sums
-    T lox[32], loy[32], loz[32];            // kept source leaves: centre offset,
-    int lb_[32];                            // level
-    int lss[32], loff[33];                  // first point, offset in the stream
-    int fkey[32];                           // per lane: target of its first segment
-    T fsum[32];                             // and that segment's sum
-    uint16_t q[32 * 32];                    // marked pairs: (target << 7) | staged source
-};
-
-// the staged threshold |s|^2 - R_b^2 (1 + 2^-9) keeps the level b of the
-// source's leaf in its five low mantissa bits (a change of at most 2^-18 of
-// its value, well inside the margin); 1 / R_b = 2^b
-__device__ __forceinline__ float pack_level(float thr, int b) {
-    return __int_as_float((__float_as_int(thr) & ~31) | b);
-}
-__device__ __forceinline__ double pack_level(double thr, int b) {
-    return __longlong_as_double((__double_as_longlong(thr) & ~31ll) | b);
-}
-__device__ __forceinline__ float inv_radius(float thr) {
-    return __int_as_float((127 + (__float_as_int(thr) & 31)) << 23);
-}
-__device__ __forceinline__ double inv_radius(double thr) {
-    return __longlong_as_double((long long)(1023 + (int)(__double_as_longlong(thr) & 31)) << 52);
-}
-
-// screening of 32 staged sources k = u0 + sub + G i against this lane's
-// target: bit i set when |t - s|^2 < R_b^2 (1 + 2^-9), with the difference
-// formed as (-2 t) . s + (|s|^2 - R_b^2 (1 + 2^-9)) + |t|^2; its cancellation
-// error (~1e-6 R_b^2) is far below the 2^-9 margin, so no pair inside the
-// support is dropped (the exact test follows in the evaluation)
-template <typename T, int G, bool FULL_UNIT>
-__device__ __forceinline__ unsigned screen_unit(const typename Vec4<T>::type *sh, int u0, int sub, int fill, T t2x,
-                                                T t2y, T t2z, T ntt) {
-    unsigned mask = 0;
-    const typename Vec4<T>::type *p = sh + u0 + sub;
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) {
-        if (!FULL_UNIT && u0 + sub + G * i >= fill) break;
-        const typename Vec4<T>::type y = p[G * i];
-        const T d = fma(t2x, y.x, fma(t2y, y.y, fma(t2z, y.z, y.w)));
-        if (d < ntt) mask |= 1u << i;
-    }
-    return mask;
-}
-
-template <typename T, int G>
-__device__ __forceinline__ unsigned screen_g(const typename Vec4<T>::type *sh, int u0, int sub, int fill, T t2x,
-                                             T t2y, T t2z, T ntt) {
-    return u0 + 32 * G <= fill ? screen_unit<T, G, true>(sh, u0, sub, fill, t2x, t2y, t2z, ntt)
-                               : screen_unit<T, G, false>(sh, u0, sub, fill, t2x, t2y, t2z, ntt);
-}
-
-template <typename T, int QD>
-__global__ void __launch_bounds__(kNearThreads) k_near(TreeView tv, int ntl, const int32_t *tleaves,
-                                                       const int32_t *nl_off, const int32_t *nl_src,
-                                                       const typename Vec4<T>::type *__restrict__ plocal,
-                                                       const float4 *__restrict__ plocal_lo, const T *qmono,
-                                                       int qdeg, double *unear, int *counter) {
-    using V4 = typename Vec4<T>::type;
-    constexpr bool kHiLo = sizeof(T) == 4;
-    constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(32) char nsm[];
-    NearWarp<T> &W = reinterpret_cast<NearWarp<T> *>(nsm)[threadIdx.x >> 5];
-    // residual polynomial coefficients in registers (degree QD known at compile time)
-    T qc[QD + 1];
-#pragma unroll
-    for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
-    (void)qdeg;
-    const int lane = threadIdx.x & 31;
-    const T kBig = (T)1e30;
-    // pairs inside the support of the residual kernel (statistics); the
-    // counter sits 8 bytes after the work counter
-    unsigned inside32 = 0;
-    for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(counter, 1);
-        it = __shfl_sync(FULL, it, 0);
-        if (it >= ntl) {
-            unsigned long long inside = inside32;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(FULL, inside, o);
-            if (lane == 0 && inside) atomicAdd(reinterpret_cast<unsigned long long *>(counter + 2), inside);
-            break;
-        }
-        const int Tb = tleaves[it];
-        const int a = tv.blevel[Tb];
-        int tx, ty, tz;
-        morton_decode_d(tv.bkey[Tb], tx, ty, tz);
-        // box centres (2i + 1) 2^-(l+1) are exact in T; so are their differences
-        // (at most ~22 significant bits for the level gaps of a balanced tree)
-        const T cTx = dyadic_centre<T>(tx, a), cTy = dyadic_centre<T>(ty, a), cTz = dyadic_centre<T>(tz, a);
-        const int ts = tv.bstart[Tb], nt = tv.bcount[Tb];
-        const int G = nt >= 32 ? 1 : (nt >= 16 ? 2 : (nt >= 8 ? 4 : 8));
-        const int per = 32 / G, t = lane / G, sub = lane % G;
-        const int l0 = nl_off[it], l1 = nl_off[it + 1];
-        for (int j0 = 0; j0 < nt; j0 += per) {
-            const int ng = min(per, nt - j0);
-            // the group's targets and their bounding box
-            T bl[3] = {kBig, kBig, kBig}, bh[3] = {-kBig, -kBig, -kBig};
-            if (lane < ng) {
-                const V4 v = plocal[ts + j0 + lane];
-                W.th[lane] = v;
-                if (kHiLo) W.tl[lane] = plocal_lo[ts + j0 + lane];
-                bl[0] = bh[0] = v.x;
-                bl[1] = bh[1] = v.y;
-                bl[2] = bh[2] = v.z;
-            }
-            W.acc[lane] = 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    bl[d] = min(bl[d], __shfl_xor_sync(FULL, bl[d], o));
-                    bh[d] = max(bh[d], __shfl_xor_sync(FULL, bh[d], o));
-                }
-            __syncwarp();
-            const bool tvalid = t < ng;
-            const V4 xt = W.th[tvalid ? t : 0];
-            const T t2x = (T)-2 * xt.x, t2y = (T)-2 * xt.y, t2z = (T)-2 * xt.z;
-            const T ntt = -(xt.x * xt.x + xt.y * xt.y + xt.z * xt.z);
-            for (int lb = l0; lb < l1; lb += 32) {
-                // 1. up to 32 source leaves, one per lane; drop those out of reach
-                const int li = lb + lane;
-                bool keep = false;
-                int ns = 0, ss = 0;
-                T ox = 0, oy = 0, oz = 0;
-                int b = 0;
-                if (li < l1) {
-                    const int Sb = nl_src[li];
-                    b = tv.blevel[Sb];
-                    int sx, sy, sz;
-                    morton_decode_d(tv.bkey[Sb], sx, sy, sz);
-                    ox = dyadic_centre<T>(sx, b) - cTx;
-                    oy = dyadic_centre<T>(sy, b) - cTy;
-                    oz = dyadic_centre<T>(sz, b) - cTz;
-                    const T Rb = ldexp_t<T>((T)1, -b), hb = (T)0.5 * Rb;
-                    ss = tv.bstart[Sb];
-                    ns = tv.bcount[Sb];
-                    // distance between the leaf's box and the group's bounding box
-                    const T gx = max((T)0, max(bl[0] - (ox + hb), (ox - hb) - bh[0]));
-                    const T gy = max((T)0, max(bl[1] - (oy + hb), (oy - hb) - bh[1]));
-                    const T gz = max((T)0, max(bl[2] - (oz + hb), (oz - hb) - bh[2]));
-                    keep = ns > 0 && gx * gx + gy * gy + gz * gz <= Rb * Rb * (T)1.0078125;
-                }
-                const unsigned kb = __ballot_sync(FULL, keep);
-                const int nk = __popc(kb);
-                if (nk == 0) continue;
-                const int slot = __popc(kb & ((1u << lane) - 1u));
-                int cum = keep ? ns : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(FULL, cum, o);
-                    if (lane >= o) cum += v;
-                }
-                if (keep) {
-                    W.lox[slot] = ox;
-                    W.loy[slot] = oy;
-                    W.loz[slot] = oz;
-                    W.lb_[slot] = b;
-                    W.lss[slot] = ss;
-                    W.loff[slot + 1] = cum;
-                }
-                if (lane == 0) W.loff[0] = 0;
-                const int stream = __shfl_sync(FULL, cum, 31);
-                __syncwarp();
-                int lf = 0;  // leaf of this lane's next staged position (positions only grow)
-                for (int c0 = 0; c0 < stream; c0 += kNC) {
-                    // 2. stage kNC sources of the stream in the target leaf's frame
-                    const int fill = min(kNC, stream - c0);
-                    for (int k = lane; k < fill; k += 32) {
-                        const int pos = c0 + k;
-                        while (W.loff[lf + 1] <= pos) ++lf;
-                        const int src = W.lss[lf] + pos - W.loff[lf];
-                        const V4 y = plocal[src];
-                        const T ax = W.lox[lf], ay = W.loy[lf], az = W.loz[lf];
-                        const int lev = W.lb_[lf];
-                        V4 hv;
-                        hv.x = y.x + ax;
-                        hv.y = y.y + ay;
-                        hv.z = y.z + az;
-                        const T Rb2 = ldexp_t<T>((T)1.001953125, -2 * lev);  // R_b^2 (1 + 2^-9)
-                        hv.w = pack_level(hv.x * hv.x + hv.y * hv.y + hv.z * hv.z - Rb2, lev);
-                        W.sh[k] = hv;
-                        if (kHiLo) {  // TwoSum error terms plus the lo parts
-                            const float4 yl = plocal_lo[src];
-                            float4 lv;
-                            T bb = hv.x - y.x;
-                            lv.x = (float)(((y.x - (hv.x - bb)) + (ax - bb)) + (T)yl.x);
-                            bb = hv.y - y.y;
-                            lv.y = (float)(((y.y - (hv.y - bb)) + (ay - bb)) + (T)yl.y);
-                            bb = hv.z - y.z;
-                            lv.z = (float)(((y.z - (hv.z - bb)) + (az - bb)) + (T)yl.z);
-                            lv.w = (float)y.w;
-                            W.sl[k] = lv;
-                        } else {
-                            W.sq[k] = y.w;
-                        }
-                    }
-                    __syncwarp();
-                    // 3. screening, 32 candidates per lane: k = u0 + sub + G i
-                    for (int u0 = 0; u0 < fill; u0 += 32 * G) {
-                        unsigned mask = 0;
-                        if (tvalid) {
-                            switch (G) {
-                            case 1: mask = screen_g<T, 1>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
-                            case 2: mask = screen_g<T, 2>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
-                            case 4: mask = screen_g<T, 4>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
-                            default: mask = screen_g<T, 8>(W.sh, u0, sub, fill, t2x, t2y, t2z, ntt); break;
-                            }
-                        }
-                        // compaction: the warp's marked pairs, in lane order (targets ascending)
-                        const int cnt = __popc(mask);
-                        int pre = cnt;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int v = __shfl_up_sync(FULL, pre, o);
-                            if (lane >= o) pre += v;
-                        }
-                        const int total = __shfl_sync(FULL, pre, 31);
-                        int o = pre - cnt;
-                        while (mask) {
-                            const int i = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            W.q[o++] = (uint16_t)((t << 7) | (u0 + sub + G * i));
-                        }
-                        __syncwarp();
-                        if (total == 0) continue;
-                        // the residual kernel: lane L takes the marked pairs [L n, (L + 1) n)
-                        // in order, so it meets each target in one run; a run that starts
-                        // inside the lane's block belongs to this lane alone and goes to
-                        // the target's sum directly, the run at the block start may be
-                        // shared with earlier lanes and is combined below in lane order
-                        const int nper = (total + 31) >> 5;
-                        const int e0 = min(lane * nper, total), e1 = min(e0 + nper, total);
-                        int cur = -1, first = -1;
-                        T part = 0, fpart = 0;
-                        V4 x = W.th[0];
-                        float4 xl = make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int e = e0; e < e1; ++e) {
-                            const int ent = W.q[e], tt = ent >> 7, k = ent & 127;
-                            if (tt != cur) {  // a new run: flush the previous one, load the target
-                                if (cur >= 0) {
-                                    if (first < 0) {
-                                        first = cur;
-                                        fpart = part;
-                                    } else {
-                                        W.acc[cur] += (double)part;
-                                    }
-                                }
-                                cur = tt;
-                                part = 0;
-                                x = W.th[tt];
-                                if (kHiLo) xl = W.tl[tt];
-                            }
-                            const V4 y = W.sh[k];
-                            T dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
-                            T qj;
-                            if (kHiLo) {
-                                const float4 yl = W.sl[k];
-                                dx += (T)xl.x - (T)yl.x;
-                                dy += (T)xl.y - (T)yl.y;
-                                dz += (T)xl.z - (T)yl.z;
-                                qj = (T)yl.w;
-                            } else {
-                                qj = W.sq[k];
-                            }
-                            const T iR = inv_radius(y.w), iR2 = iR * iR;
-                            const T r2 = dx * dx + dy * dy + dz * dz;
-                            const T xx = (T)2 * r2 * iR2 - (T)1;  // r < R_b  <=>  xx < 1
-                            T qv = qc[QD];
-#pragma unroll
-                            for (int d = QD - 1; d >= 0; --d) qv = qv * xx + qc[d];
-                            const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
-                            const bool in = xx < (T)1;
-                            const T val = in ? qj * (rinv - qv * iR) : (T)0;
-                            inside32 += in ? 1u : 0u;
-                            part += val;
-                        }
-                        if (cur >= 0) {
-                            if (first < 0) {
-                                first = cur;
-                                fpart = part;
-                            } else {
-                                W.acc[cur] += (double)part;
-                            }
-                        }
-                        // first runs: a segmented sum over lanes with the same target
-                        // (lanes without pairs carry no key)
-                        int key = first >= 0 ? first : -1 - lane;
-                        T v = fpart;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const T vu = __shfl_up_sync(FULL, v, d);
-                            const int ku = __shfl_up_sync(FULL, key, d);
-                            if (lane >= d && ku == key) v += vu;
-                        }
-                        const int kn = __shfl_down_sync(FULL, key, 1);
-                        __syncwarp();
-                        if (first >= 0 && (lane == 31 || kn != key)) W.acc[key] += (double)v;
-                        __syncwarp();
-                    }
-                    __syncwarp();
-                }
-            }
-            if (lane < ng && (tv.pflag[ts + j0 + lane] & 2)) unear[ts + j0 + lane] = W.acc[lane];
-            __syncwarp();
-        }
-    }
-}
-
 __global__ void k_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout, const double *ufar,
-                           const double *unear, const Frame *frame, int mode, double *pot) {
+                           const double *unear, const double *gfar, const double *gnear, const Frame *frame,
+                           int mode, double *pot, double *grad) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || !(pflag[k] & 2)) return;
-    // mode 0: both parts, 1: far part only, 2: near part only
-    double v = (mode == 2 ? 0.0 : ufar[k]) + (mode == 1 ? 0.0 : unear[k]);
-    pot[pout[k]] = v / frame->S;
-}
-
-// launch k_near with the residual polynomial degree as a template argument;
-// returns 1 for a degree outside 2..30, 2 for a failed launch
-template <typename T, int QD>
-static cudaError_t launch_near_qd(int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
-                                  const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
-                                  const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
-    constexpr size_t smem = (size_t)(kNearThreads / 32) * sizeof(NearWarp<T>);
-    cudaError_t e = cudaFuncSetAttribute(k_near<T, QD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_near<T, QD><<<grid, kNearThreads, smem, st>>>(tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, QD,
-                                                     unear, counter);
-    return cudaGetLastError();
-}
-
-template <typename T>
-static int launch_near(int qdeg, int grid, cudaStream_t st, TreeView tv, int ntl, const int32_t *tleaves,
-                       const int32_t *nl_off, const int32_t *nl_src, const typename Vec4<T>::type *plocal,
-                       const float4 *plocal_lo, const T *qmono, double *unear, int *counter) {
-    switch (qdeg) {
-#define DMK_NEAR_CASE(d) \
-    case d: \
-        return launch_near_qd<T, d>(grid, st, tv, ntl, tleaves, nl_off, nl_src, plocal, plocal_lo, qmono, unear, \
-                                    counter) == cudaSuccess ? 0 : 2;
-        DMK_NEAR_CASE(2) DMK_NEAR_CASE(3) DMK_NEAR_CASE(4) DMK_NEAR_CASE(5) DMK_NEAR_CASE(6) DMK_NEAR_CASE(7)
-        DMK_NEAR_CASE(8) DMK_NEAR_CASE(9) DMK_NEAR_CASE(10) DMK_NEAR_CASE(11) DMK_NEAR_CASE(12) DMK_NEAR_CASE(13)
-        DMK_NEAR_CASE(14) DMK_NEAR_CASE(15) DMK_NEAR_CASE(16) DMK_NEAR_CASE(17) DMK_NEAR_CASE(18) DMK_NEAR_CASE(19)
-        DMK_NEAR_CASE(20) DMK_NEAR_CASE(21) DMK_NEAR_CASE(22) DMK_NEAR_CASE(23) DMK_NEAR_CASE(24) DMK_NEAR_CASE(25)
-        DMK_NEAR_CASE(26) DMK_NEAR_CASE(27) DMK_NEAR_CASE(28) DMK_NEAR_CASE(29) DMK_NEAR_CASE(30)
-#undef DMK_NEAR_CASE
-    default: return 1;
-    }
+    // mode 0: both parts, 1: far part only, 2: near part only; unit-box
+    // potentials scale by 1/S, their gradients by 1/S^2
+    const double S = frame->S;
+    const double v = (mode == 2 ? 0.0 : ufar[k]) + (mode == 1 ? 0.0 : unear[k]);
+    const int64_t o = pout[k];
+    pot[o] = v / S;
+    if (grad)
+        for (int d = 0; d < 3; ++d)
+            grad[3 * o + d] = ((mode == 2 ? 0.0 : gfar[3 * k + d]) + (mode == 1 ? 0.0 : gnear[3 * k + d])) / (S * S);
 }
 
 // ---------------------------------------------------------------------------
@@ -1866,6 +1621,18 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     double *unear = (double *)cx.bufs->unear.p;
     PCK(cudaMemsetAsync(ufar, 0, n * 8, st));
     PCK(cudaMemsetAsync(unear, 0, n * 8, st));
+    // gradient pass: far and near gradients of every point (n x 3)
+    double *gfar = nullptr, *gnear = nullptr;
+    if (cx.grad) {
+        if (ws.ensure(cx.bufs->gfar, n * 24) || ws.ensure(cx.bufs->gnear, n * 24)) {
+            err = "device allocation failed (gradients)";
+            return DMK_ERR_OOM;
+        }
+        gfar = (double *)cx.bufs->gfar.p;
+        gnear = (double *)cx.bufs->gnear.p;
+        PCK(cudaMemsetAsync(gfar, 0, n * 24, st));
+        PCK(cudaMemsetAsync(gnear, 0, n * 24, st));
+    }
     // device words: [0] near work queue, [2..3] pairs inside R_L, [4..5] local
     // flops, [6] tensor-core wait error, [32 + l] level-l work queue of k_local
     PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 256, st));
@@ -1937,9 +1704,9 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                          tcore ? (size_t)LS::TC_BUF2 * sizeof(float) : (size_t)0);
         cudaEventRecord(cx.ev[6], st);
         BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, t1_bytes, (size_t)P * NH * sizeof(T),
-                                     (size_t)3 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
+                                     (size_t)6 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
                                      P3 * sizeof(T)},
-                                    smem_limit - 16384);
+                                    smem_limit - 20480);
         if (tcore && !(lay.in_smem[1] && lay.in_smem[2])) {
             err = "tensor-core operands do not fit in shared memory";
             return DMK_ERR_INTERNAL;
@@ -1955,21 +1722,26 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                                                        LamW, ufar, lay, (char *)cx.bufs->slab.p,
                                                                        (unsigned long long *)cx.bufs->counter.p + 2,
                                                                        (int *)cx.bufs->counter.p + 6,
-                                                                       (int *)cx.bufs->counter.p + 32 + l);
+                                                                       (int *)cx.bufs->counter.p + 32 + l, gfar);
         }
         PCK(cudaGetLastError());
     }
     // ---- residual near field and self corrections
     cudaEventRecord(cx.ev[3], st);
     if (cx.tree->ntleaves > 0) {
-        const int wpb = kNearThreads / 32;
-        int grid = std::min((cx.tree->ntleaves + wpb - 1) / wpb, cx.num_sms * 8);
-        ::dmk::launch_tick();
-        int rc_near = launch_near<T>(tb.qdeg, grid, st, tv, cx.tree->ntleaves, (const int32_t *)cx.tree->tleaves.p,
-                                     (const int32_t *)cx.tree->nl_off.p, (const int32_t *)cx.tree->nl_src.p,
-                                     (const typename Vec4<T>::type *)cx.tree->plocal.p,
-                                     (const float4 *)cx.tree->plocal_lo.p, tb.qmono, unear,
-                                     (int *)cx.bufs->counter.p);
+        NearArgs na{tv,
+                    cx.tree->ntleaves,
+                    (const int32_t *)cx.tree->tleaves.p,
+                    (const int32_t *)cx.tree->nl_off.p,
+                    (const int32_t *)cx.tree->nl_src.p,
+                    cx.tree->plocal.p,
+                    (const float4 *)cx.tree->plocal_lo.p,
+                    tb.qmono,
+                    tb.qdeg,
+                    unear,
+                    gnear,
+                    (int *)cx.bufs->counter.p};
+        int rc_near = launch_near(sizeof(T) == 4, na, cx.num_sms, st);
         if (rc_near == 1) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
         if (rc_near) { err = "near-field launch failed"; return DMK_ERR_CUDA; }
         PCK(cudaGetLastError());
@@ -1977,8 +1749,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     cudaEventRecord(cx.ev[4], st);
     ::dmk::launch_tick();
     k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)cx.tree->pout.p, ufar,
-                                                           unear, (const Frame *)cx.tree->frame.p, cx.mode,
-                                                           cx.pot);
+                                                           unear, gfar, gnear, (const Frame *)cx.tree->frame.p,
+                                                           cx.mode, cx.pot, cx.grad);
     PCK(cudaGetLastError());
     return 0;
 }

@@ -15,7 +15,7 @@ struct BufLayout {
 };
 
 struct PassBufs {
-    DBuf M, Lam, LamW, Phi, ufar, unear, slab, rootscr, counter;
+    DBuf M, Lam, LamW, Phi, ufar, unear, gfar, gnear, slab, rootscr, counter;
 };
 
 struct PassCtx {
@@ -28,6 +28,7 @@ struct PassCtx {
     int mode;             // 0 all, 1 far only, 2 near only
     int64_t total_sources;
     double *pot;
+    double *grad;         // gradients of the potentials (n_tgt x 3), or null
     cudaStream_t st;
     cudaEvent_t ev[7];  // 0 start, 1 upward, 2 plane waves, 6 local, 3 near, 4 finalize, 5 end
     size_t smem_limit;
@@ -35,5 +36,21 @@ struct PassCtx {
 };
 
 int run_passes(PassCtx &cx, std::string &err);
+
+// The residual near field (near.cu): unear (and gnear, if not null) of every
+// point of the ntl target leaves.  Returns 0, 1 for a polynomial degree outside
+// 2..30, 2 for a failed launch.
+struct NearArgs {
+    TreeView tv;
+    int ntl;
+    const int32_t *tleaves, *nl_off, *nl_src;
+    const void *plocal;         // float4 or double4 leaf-local points
+    const float4 *plocal_lo;    // single precision: lo parts
+    const void *qmono;          // residual polynomial, monomial coefficients (float or double)
+    int qdeg;
+    double *unear, *gnear;
+    int *counter;
+};
+int launch_near(bool single, const NearArgs &a, int num_sms, cudaStream_t st);
 
 }  // namespace dmk

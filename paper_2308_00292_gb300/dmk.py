@@ -29,7 +29,7 @@ FLAG_HOST_ONLY = 4
 ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "DMK_ERR_OOM", 4: "DMK_ERR_CUDA",
           5: "DMK_ERR_TIMEOUT", 6: "DMK_ERR_DEPTH", 7: "DMK_ERR_INTERNAL"}
 
-EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
+EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_grad", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
             "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree",
             "dmk_direct_noalloc"]
 
@@ -80,6 +80,7 @@ def lib():
             L.dmk_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Opts),
                                    ctypes.POINTER(vp)]
             L.dmk_eval.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
+            L.dmk_eval_grad.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, vp]
             L.dmk_eval_host.argtypes = [vp, dp, i64, dp, dp, i64, dp, vp]
             L.dmk_plan_destroy.argtypes = [vp]
             L.dmk_error_string.argtypes = [ctypes.c_int]
@@ -149,6 +150,22 @@ class Plan:
                               out.data_ptr(), st))
         return out
 
+    def eval_grad(self, sources, charges, targets=None, out=None, gout=None, stream=None):
+        """Potentials and their gradients (n_tgt x 3) at the targets, torch CUDA tensors."""
+        import torch
+        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
+        ns = sources.shape[0]
+        tgt = sources if targets is None else targets
+        nt = tgt.shape[0]
+        if out is None:
+            out = torch.empty(nt, dtype=torch.float64, device=sources.device)
+        if gout is None:
+            gout = torch.empty(nt, 3, dtype=torch.float64, device=sources.device)
+        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+        _check(lib().dmk_eval_grad(self._h, sources.data_ptr(), ns, charges.data_ptr(), tgt.data_ptr(), nt,
+                                   out.data_ptr(), gout.data_ptr(), st))
+        return out, gout
+
     def eval_host(self, sources, charges, targets=None, out=None, stream=0):
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         q = np.ascontiguousarray(charges, dtype=np.float64)
@@ -187,3 +204,53 @@ class Plan:
         _check(lib().dmk_get_tree(self._h, lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n))
         return lev, cell
+
+
+def potential(plan: Plan, sources, charges, targets=None):
+    """Differentiable potentials: u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j| at the
+    targets (every source when targets is None), with gradients with respect
+    to the charges and to the source and target positions.
+
+    The backward pass is two more evaluations of the same plan: the kernel is
+    symmetric, so dL/drho_j = v(y_j) and dL/dy_j = rho_j grad v(y_j) for the
+    potential v of charges dL/du at the targets, and dL/dx_i = dL/du_i grad u(x_i).
+    """
+    import torch
+
+    class _Potential(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, src, rho, tgt):
+            same = tgt is None
+            t = src if same else tgt
+            need_pos = ctx.needs_input_grad[0] or (not same and ctx.needs_input_grad[2])
+            if need_pos:
+                u, gu = plan.eval_grad(src.detach().contiguous(), rho.detach().contiguous(),
+                                       None if same else t.detach().contiguous())
+            else:
+                u = plan.eval(src.detach().contiguous(), rho.detach().contiguous(),
+                              None if same else t.detach().contiguous())
+                gu = None
+            ctx.same = same
+            ctx.save_for_backward(src, rho, t, gu if gu is not None else torch.empty(0, device=src.device))
+            ctx.has_gu = gu is not None
+            return u
+
+        @staticmethod
+        def backward(ctx, g):
+            src, rho, t, gu = ctx.saved_tensors
+            g = g.contiguous()
+            # the potential of charges g at the targets, and its gradient, at the sources
+            if ctx.same:
+                v, gv = plan.eval_grad(src.detach().contiguous(), g)
+            else:
+                v, gv = plan.eval_grad(t.detach().contiguous(), g, src.detach().contiguous())
+            d_rho = v if ctx.needs_input_grad[1] else None
+            d_src = rho[:, None] * gv if ctx.needs_input_grad[0] else None
+            d_tgt = None
+            if ctx.same and d_src is not None and ctx.has_gu:
+                d_src = d_src + g[:, None] * gu
+            elif not ctx.same and ctx.needs_input_grad[2] and ctx.has_gu:
+                d_tgt = g[:, None] * gu
+            return d_src, d_rho, d_tgt
+
+    return _Potential.apply(sources, charges, targets)
