@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the host-buffer measurement (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--grad", action="store_true",
+                    help="time the differentiable potential (forward with gradients, backward) instead")
     return ap.parse_args()
 
 
@@ -197,6 +199,45 @@ def config_dict(args, cfg):
             "parallelism": "independent replica per GPU" if args.gpus > 1 else "single GPU"}
 
 
+def run_grad(args):
+    """Forward (potentials and gradients) plus backward (dL/drho, dL/dx) of the
+    differentiable potential, L = sum_i w_i u_i, one GPU, mixed precision."""
+    import numpy as np
+    import torch
+    from paper_2308_00292_gb300 import dmk, inputs
+    cfg = inputs.CONFIGS[args.config]
+    x, q = inputs.make(cfg["gen"], cfg["n"], cfg["seed"])
+    n = x.shape[0]
+    w = torch.from_numpy(np.random.default_rng(cfg["seed"] + 1).standard_normal(n)).cuda()
+    plan = dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"])
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q).cuda()
+
+    def step():
+        xt = xd.clone().requires_grad_(True)
+        qt = qd.clone().requires_grad_(True)
+        (w * dmk.potential(plan, xt, qt)).sum().backward()
+        return xt.grad, qt.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    plan.close()
+    line = {"metric": "3D Laplace DMK potentials + gradients (autograd forward and backward) points/s, 1 GB300",
+            "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64acc", "data": "synthetic", "config": config_dict(args, cfg),
+            "evaluations_per_step": 2}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -340,6 +381,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.grad:
+        run_grad(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -74,6 +74,8 @@ CONFIGS = {
     "laplace3d_sphere_n4e6": dict(gen="sphere", n=4_000_000, seed=5, eps=1e-6, leaf_cap=280),
     # the clustered workload at 2e6 points: small enough for ncu --set full captures
     "laplace3d_clustered_n2e6": dict(gen="clustered", n=2_000_000, seed=2, eps=1e-6, leaf_cap=200),
+    # the differentiable workload: potentials plus gradients in charges and positions
+    "laplace3d_uniform_n2e6": dict(gen="uniform_cube", n=2_000_000, seed=4, eps=1e-6, leaf_cap=200),
 }
 
 
