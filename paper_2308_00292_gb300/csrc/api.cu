@@ -49,12 +49,22 @@ struct dmk_plan_s {
     dmk::DBuf h_src, h_q, h_tgt, h_pot;  // device copies for dmk_eval_host
     dmk_eval_stats stats{};
     cudaEvent_t ev[7] = {};
+    // the near field runs on an internal low-priority stream, concurrently with
+    // the far field on the caller's stream: its short blocks fill the SMs that
+    // the per-level far-field launches leave idle
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, nev[2] = {};
     bool events = false;
     size_t smem_limit = 0;
     int num_sms = 0;
     ~dmk_plan_s() {
-        if (events)
+        if (events) {
             for (auto &e : ev) cudaEventDestroy(e);
+            for (auto &e : nev) cudaEventDestroy(e);
+            cudaEventDestroy(fork);
+            cudaEventDestroy(join);
+        }
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -136,10 +146,19 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     cx.grad = grad;
     cx.st = st;
     for (int i = 0; i < 7; ++i) cx.ev[i] = pl->ev[i];
+    cx.side = pl->side;
+    cx.fork = pl->fork;
+    cx.join = pl->join;
+    cx.nev[0] = pl->nev[0];
+    cx.nev[1] = pl->nev[1];
     cx.smem_limit = pl->smem_limit;
     cx.num_sms = pl->num_sms;
     rc = dmk::run_passes(cx, err);
-    if (rc) return fail(rc, "passes: " + err);
+    if (rc) {
+        // a pass that failed to launch may leave near-field work queued
+        cudaStreamSynchronize(pl->side);
+        return fail(rc, "passes: " + err);
+    }
     cudaEventRecord(pl->ev[5], st);
     cudaError_t ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("device execution failed: ") + cudaGetErrorString(ce));
@@ -166,9 +185,12 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     s.t_downward_ms = t23;
     s.t_near_ms = t34;
     s.t_total_ms = t05;
-    float t63 = 0;
+    float t63 = 0, tn = 0;
     cudaEventElapsedTime(&t63, pl->ev[6], pl->ev[3]);
     s.t_local_ms = t63;
+    // the near field ran on the side stream, overlapping the far field
+    if (cudaEventElapsedTime(&tn, pl->nev[0], pl->nev[1]) == cudaSuccess) s.t_near_ms = tn;
+    else cudaGetLastError();
     s.n_launches = dmk::g_launches.load() - launches0;
     if (pl->bufs.counter.p) {
         // device words: [0] near work queue, [8] near pairs inside R_L,
@@ -257,7 +279,19 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
         pl->num_sms = sms;
         for (auto &e : pl->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaEventCreate failed");
+        for (auto &e : pl->nev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaEventCreate failed");
+        if (cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "cudaEventCreate failed");
         pl->events = true;
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            least = 0;
+        }
+        if (cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, least) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "cudaStreamCreate failed");
         int rc = pl->precision == DMK_MIXED ? upload_tables<float>(pl.get(), pl->dt_f)
                                             : upload_tables<double>(pl.get(), pl->dt_d);
         if (rc) return rc;

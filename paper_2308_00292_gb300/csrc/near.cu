@@ -433,8 +433,11 @@ static int launch_near_t(int grid, cudaStream_t st, const NearArgs &a) {
 }
 
 int launch_near(bool single, const NearArgs &a, int num_sms, cudaStream_t st) {
+    // one warp per target leaf and no persistent blocks: short blocks let the
+    // concurrent far-field kernels take SMs as they free up
     const int wpb = kNearThreads / 32;
-    const int grid = std::min((a.ntl + wpb - 1) / wpb, num_sms * 8);
+    const int grid = (a.ntl + wpb - 1) / wpb;
+    (void)num_sms;
     if (grid <= 0) return 0;
     ::dmk::launch_tick();
     const bool grad = a.gnear != nullptr;

@@ -1637,6 +1637,32 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     // flops, [6] tensor-core wait error, [32 + l] level-l work queue of k_local
     PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 256, st));
 
+    // ---- residual near field and self corrections, on the side stream: it
+    // needs only the tree, and fills the SMs the per-level far-field launches
+    // leave idle
+    PCK(cudaEventRecord(cx.fork, st));
+    PCK(cudaStreamWaitEvent(cx.side, cx.fork, 0));
+    cudaEventRecord(cx.nev[0], cx.side);
+    if (cx.tree->ntleaves > 0) {
+        NearArgs na{tv,
+                    cx.tree->ntleaves,
+                    (const int32_t *)cx.tree->tleaves.p,
+                    (const int32_t *)cx.tree->nl_off.p,
+                    (const int32_t *)cx.tree->nl_src.p,
+                    cx.tree->plocal.p,
+                    (const float4 *)cx.tree->plocal_lo.p,
+                    tb.qmono,
+                    tb.qdeg,
+                    unear,
+                    gnear,
+                    (int *)cx.bufs->counter.p};
+        int rc_near = launch_near(sizeof(T) == 4, na, cx.num_sms, cx.side);
+        if (rc_near == 1) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
+        if (rc_near) { err = "near-field launch failed"; return DMK_ERR_CUDA; }
+        PCK(cudaGetLastError());
+    }
+    cudaEventRecord(cx.nev[1], cx.side);
+    PCK(cudaEventRecord(cx.join, cx.side));
     // ---- upward pass (finest level first)
     cudaEventRecord(cx.ev[1], st);
     {
@@ -1726,26 +1752,9 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         }
         PCK(cudaGetLastError());
     }
-    // ---- residual near field and self corrections
+    // ---- the far field is done; join the near field
     cudaEventRecord(cx.ev[3], st);
-    if (cx.tree->ntleaves > 0) {
-        NearArgs na{tv,
-                    cx.tree->ntleaves,
-                    (const int32_t *)cx.tree->tleaves.p,
-                    (const int32_t *)cx.tree->nl_off.p,
-                    (const int32_t *)cx.tree->nl_src.p,
-                    cx.tree->plocal.p,
-                    (const float4 *)cx.tree->plocal_lo.p,
-                    tb.qmono,
-                    tb.qdeg,
-                    unear,
-                    gnear,
-                    (int *)cx.bufs->counter.p};
-        int rc_near = launch_near(sizeof(T) == 4, na, cx.num_sms, st);
-        if (rc_near == 1) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
-        if (rc_near) { err = "near-field launch failed"; return DMK_ERR_CUDA; }
-        PCK(cudaGetLastError());
-    }
+    PCK(cudaStreamWaitEvent(st, cx.join, 0));
     cudaEventRecord(cx.ev[4], st);
     ::dmk::launch_tick();
     k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)cx.tree->pout.p, ufar,

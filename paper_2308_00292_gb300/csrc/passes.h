@@ -30,7 +30,9 @@ struct PassCtx {
     double *pot;
     double *grad;         // gradients of the potentials (n_tgt x 3), or null
     cudaStream_t st;
-    cudaEvent_t ev[7];  // 0 start, 1 upward, 2 plane waves, 6 local, 3 near, 4 finalize, 5 end
+    cudaEvent_t ev[7];  // 0 start, 1 upward, 2 plane waves, 6 local, 3 far done, 4 finalize, 5 end
+    cudaStream_t side;  // the near field's stream, forked after the tree and joined before finalize
+    cudaEvent_t fork, join, nev[2];  // nev: start and end of the near field on side
     size_t smem_limit;
     int num_sms;
 };
