@@ -136,6 +136,33 @@ DMK_API int dmk_eval_host(dmk_plan_t plan,
                   void *cuda_stream);
 
 /*
+ * dmk_eval_batch -- dmk_eval of many independent systems in one pass.  System s
+ * holds the points offsets[s] .. offsets[s + 1] - 1; they are its sources and
+ * its targets (every point's own term excluded), and no system sees another's
+ * charges.  Each system is mapped to its own unit box (Sec. 3.1), so a level-l
+ * box has side 2^-l in every system and all systems share the plan's tables;
+ * the tree is one forest with a root per system, and every kernel processes
+ * the boxes of all systems of a level together.
+ *
+ *   points      device pointer, total x 3 doubles, row-major, the systems one
+ *               after another (total = offsets[n_systems])
+ *   charges     device pointer, total doubles
+ *   offsets     HOST pointer, n_systems + 1 ascending int64 offsets,
+ *               offsets[0] = 0; empty systems are allowed
+ *   n_systems   1 .. 2^24
+ *   potentials  device pointer, total doubles, caller-allocated, overwritten
+ *   cuda_stream as in dmk_eval
+ *
+ * The system index takes the top bits of the 63-bit point keys: with n_systems
+ * up to 2^k the tree depth is limited to (63 - k) / 3 levels (17 levels for
+ * 4096 systems).  Statistics (dmk_get_stats) cover the whole batch;
+ * dmk_get_tree reports each point's leaf cell within its own system.
+ */
+DMK_API int dmk_eval_batch(dmk_plan_t plan,
+                           const double *points, const double *charges, const int64_t *offsets, int n_systems,
+                           double *potentials, void *cuda_stream);
+
+/*
  * dmk_eval_grad -- dmk_eval plus the gradient of the potential at every target,
  * grad u(x_i) = sum_{j : y_j != x_i} rho_j (y_j - x_i) / |x_i - y_j|^3, from the same
  * pass differentiated: the Chebyshev local expansions through T_n' = n U_{n-1}
@@ -178,6 +205,43 @@ DMK_API int dmk_eval_grad(dmk_plan_t plan,
 DMK_API int dmk_direct_noalloc(const double *sources, int64_t n_src, const double *charges,
                                const double *targets, int64_t n_tgt, double *potentials,
                                void *cuda_stream);
+
+/*
+ * dmk_tune_leaf_cap -- choose the plan's leaf capacity n_s by timing.  The
+ * accuracy of the method is set by p and nf (Table 1) and does not depend on
+ * n_s; n_s only moves work between the residual near field, which grows
+ * linearly with it, and the far field, which grows with the number of boxes
+ * (the balance discussed in Sec. 5.1.1).  The best n_s depends on the point
+ * distribution and the hardware, so it is measured: for every candidate the
+ * plan evaluates the given problem reps + 1 times (the first untimed) and
+ * keeps the smallest device time of one evaluation; the fastest candidate
+ * becomes the plan's leaf capacity for later calls.
+ *
+ *   sources ... n_tgt  a representative problem, as in dmk_eval (device pointers)
+ *   candidates    leaf capacities to try (each 1..2^20), or NULL for the
+ *                 default list 64, 100, 140, 200, 280, 400, 560
+ *   n_candidates  entries of candidates (1..64; ignored when it is NULL)
+ *   reps          timed evaluations per candidate (0 = 3, at most 100)
+ *   best_leaf_cap receives the chosen capacity (may be NULL)
+ *   times_ms      receives one time per candidate, in milliseconds (may be NULL)
+ *   cuda_stream   as in dmk_eval
+ *
+ * On error the plan keeps its previous leaf capacity.  The potentials are
+ * computed into the plan's scratch and discarded.
+ */
+DMK_API int dmk_tune_leaf_cap(dmk_plan_t plan,
+                              const double *sources, int64_t n_src, const double *charges,
+                              const double *targets, int64_t n_tgt,
+                              const int *candidates, int n_candidates, int reps,
+                              int *best_leaf_cap, float *times_ms, void *cuda_stream);
+
+/* dmk_tune_leaf_cap for a batch of systems (arguments as in dmk_eval_batch,
+ * the rest as in dmk_tune_leaf_cap): the capacity that evaluates the whole
+ * batch fastest. */
+DMK_API int dmk_tune_leaf_cap_batch(dmk_plan_t plan,
+                                    const double *points, const double *charges, const int64_t *offsets,
+                                    int n_systems, const int *candidates, int n_candidates, int reps,
+                                    int *best_leaf_cap, float *times_ms, void *cuda_stream);
 
 /* Release a plan and all its device memory.  NULL is accepted. */
 DMK_API int dmk_plan_destroy(dmk_plan_t plan);

@@ -111,7 +111,7 @@ int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
 bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 19 || p == 28 || p == 38; }
 
 int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
-                double *pot, double *grad, cudaStream_t st) {
+                double *pot, double *grad, cudaStream_t st, int nsys = 1, const int64_t *h_off = nullptr) {
     if (nt == 0) return DMK_OK;
     if (cudaSetDevice(pl->device) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaSetDevice failed");
     if (ns == 0) {
@@ -131,7 +131,7 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     const long long launches0 = dmk::g_launches.load();
     cudaEventRecord(pl->ev[0], st);
     int rc = pl->tree->build(src, ns, q, same ? nullptr : tgt, same ? 0 : nt, same, pl->leaf_cap, pl->max_level,
-                             single ? 1 : 0, st, err);
+                             single ? 1 : 0, st, err, nsys, h_off);
     if (rc) return fail(rc, "tree: " + err);
     dmk::PassCtx cx{};
     cx.tree = pl->tree.get();
@@ -329,6 +329,23 @@ int dmk_eval_grad(dmk_plan_t plan, const double *sources, int64_t n_src, const d
                        (cudaStream_t)cuda_stream);
 }
 
+int dmk_eval_batch(dmk_plan_t plan, const double *points, const double *charges, const int64_t *offsets,
+                   int n_systems, double *potentials, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (!offsets || n_systems < 1 || n_systems > (1 << 24))
+        return fail(DMK_ERR_INVALID_ARG, "n_systems must lie in 1..2^24 with an offsets array");
+    if (offsets[0] != 0) return fail(DMK_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int s = 0; s < n_systems; ++s)
+        if (offsets[s + 1] < offsets[s]) return fail(DMK_ERR_INVALID_ARG, "offsets must not decrease");
+    const int64_t total = offsets[n_systems];
+    if (total == 0) return DMK_OK;
+    if (!points || !charges || !potentials) return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    return eval_device(plan, points, total, charges, points, total, potentials, nullptr, (cudaStream_t)cuda_stream,
+                       n_systems, offsets);
+}
+
 int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
                   const double *targets, int64_t n_tgt, double *potentials, void *cuda_stream) {
     g_detail.clear();
@@ -360,6 +377,93 @@ int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const d
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(DMK_ERR_CUDA, "device-to-host copy failed");
     return DMK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// time plan evaluations at each candidate leaf capacity; keep the fastest
+template <typename Eval>
+int tune_leaf_cap(dmk_plan_s *plan, const int *candidates, int n_candidates, int reps, int *best_leaf_cap,
+                  float *times_ms, Eval eval) {
+    // the default candidates bracket the balance point of Sec. 5.1.1: the near
+    // field grows linearly with the cap, the far field with the number of boxes
+    static const int kDefault[] = {64, 100, 140, 200, 280, 400, 560};
+    const int *cand = candidates ? candidates : kDefault;
+    const int nc = candidates ? n_candidates : (int)(sizeof(kDefault) / sizeof(kDefault[0]));
+    if (nc <= 0 || nc > 64) return fail(DMK_ERR_INVALID_ARG, "n_candidates must lie in 1..64");
+    for (int i = 0; i < nc; ++i)
+        if (cand[i] <= 0 || cand[i] > (1 << 20)) return fail(DMK_ERR_INVALID_ARG, "leaf cap out of range");
+    if (reps < 0 || reps > 100) return fail(DMK_ERR_INVALID_ARG, "reps must lie in 0..100");
+    if (reps == 0) reps = 3;
+    const int keep = plan->leaf_cap;
+    int best = -1;
+    float best_ms = 0;
+    for (int i = 0; i < nc; ++i) {
+        plan->leaf_cap = cand[i];
+        // one untimed evaluation grows the scratch for this tree shape
+        float t = 0;
+        for (int r = 0; r <= reps; ++r) {
+            const int rc = eval();
+            if (rc) {
+                plan->leaf_cap = keep;
+                return rc;
+            }
+            if (r == 1 || (r > 1 && plan->stats.t_total_ms < t)) t = plan->stats.t_total_ms;
+        }
+        if (times_ms) times_ms[i] = t;
+        if (best < 0 || t < best_ms) {
+            best = i;
+            best_ms = t;
+        }
+    }
+    plan->leaf_cap = cand[best];
+    if (best_leaf_cap) *best_leaf_cap = cand[best];
+    return DMK_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int dmk_tune_leaf_cap(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
+                      const double *targets, int64_t n_tgt, const int *candidates, int n_candidates, int reps,
+                      int *best_leaf_cap, float *times_ms, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
+    if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && !targets))
+        return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    if (plan->ws.ensure(plan->h_pot, std::max<int64_t>(n_tgt, 1) * 8))
+        return fail(DMK_ERR_OOM, "device allocation failed (tuning)");
+    double *pot = (double *)plan->h_pot.p;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    return tune_leaf_cap(plan, candidates, n_candidates, reps, best_leaf_cap, times_ms, [&]() {
+        return eval_device(plan, sources, n_src, charges, targets, n_tgt, pot, nullptr, st);
+    });
+}
+
+int dmk_tune_leaf_cap_batch(dmk_plan_t plan, const double *points, const double *charges, const int64_t *offsets,
+                            int n_systems, const int *candidates, int n_candidates, int reps, int *best_leaf_cap,
+                            float *times_ms, void *cuda_stream) {
+    g_detail.clear();
+    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
+    if (!offsets || n_systems < 1 || n_systems > (1 << 24) || offsets[0] != 0)
+        return fail(DMK_ERR_INVALID_ARG, "n_systems must lie in 1..2^24 with offsets from 0");
+    for (int s = 0; s < n_systems; ++s)
+        if (offsets[s + 1] < offsets[s]) return fail(DMK_ERR_INVALID_ARG, "offsets must not decrease");
+    const int64_t total = offsets[n_systems];
+    if (total > 0 && (!points || !charges)) return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    if (plan->ws.ensure(plan->h_pot, std::max<int64_t>(total, 1) * 8))
+        return fail(DMK_ERR_OOM, "device allocation failed (tuning)");
+    double *pot = (double *)plan->h_pot.p;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    return tune_leaf_cap(plan, candidates, n_candidates, reps, best_leaf_cap, times_ms, [&]() {
+        return total == 0 ? (int)DMK_OK
+                          : eval_device(plan, points, total, charges, points, total, pot, nullptr, st, n_systems,
+                                        offsets);
+    });
 }
 
 int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {

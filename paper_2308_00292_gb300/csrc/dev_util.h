@@ -21,4 +21,10 @@ __device__ __forceinline__ void morton_decode_d(uint64_t m, int &ix, int &iy, in
     iz = compact(m >> 2);
 }
 
+// cell indices of a box key at level l: the key's low 3 l bits are the Morton
+// code of the cell (the bits above them number the system of a batch)
+__device__ __forceinline__ void box_decode_d(uint64_t key, int l, int &ix, int &iy, int &iz) {
+    morton_decode_d(key & ((1ull << (3 * l)) - 1ull), ix, iy, iz);
+}
+
 }  // namespace dmk

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
         const int Tb = tleaves[it];
         const int a = tv.blevel[Tb];
         int tx, ty, tz;
-        morton_decode_d(tv.bkey[Tb], tx, ty, tz);
+        box_decode_d(tv.bkey[Tb], a, tx, ty, tz);
         // box centres (2i + 1) 2^-(l+1) are exact in T; so are their differences
         // (at most ~22 significant bits for the level gaps of a balanced tree)
         const T cTx = dyadic_centre<T>(tx, a), cTy = dyadic_centre<T>(ty, a), cTz = dyadic_centre<T>(tz, a);
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                     const int Sb = nl_src[li];
                     b = tv.blevel[Sb];
                     int sx, sy, sz;
-                    morton_decode_d(tv.bkey[Sb], sx, sy, sz);
+                    box_decode_d(tv.bkey[Sb], b, sx, sy, sz);
                     ox = dyadic_centre<T>(sx, b) - cTx;
                     oy = dyadic_centre<T>(sy, b) - cTy;
                     oz = dyadic_centre<T>(sz, b) - cTz;

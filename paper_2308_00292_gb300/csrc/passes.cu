@@ -357,12 +357,14 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
     for (int it = blockIdx.x; it < lcount; it += gridDim.x) {
         const int B = lstart + it;
         const bool selfleaf = (tv.bflags[B] & BF_LEAF) != 0;
-        if (selfleaf && !(B == 0 && tv.nlev == 1)) continue;
+        // a leaf's sources go to its parent's grid; a root that is a leaf
+        // anterpolates onto its own grid (for the windowed term W_0)
+        if (selfleaf && tv.blevel[B] != 0) continue;
         if (tv.bnsrc[B] == 0) continue;
         for (int i = tid; i < P3; i += kThreads) acc[i] = (T)0;
         const int l = tv.blevel[B];
         int ix, iy, iz;
-        morton_decode_d(tv.bkey[B], ix, iy, iz);
+        box_decode_d(tv.bkey[B], l, ix, iy, iz);
         const double R = level_R(l), s2R = 2.0 / R;
         const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
         __syncthreads();
@@ -564,20 +566,26 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
 }
 
 // ---------------------------------------------------------------------------
-// Root: windowed kernel W_0 over the unit box (single CTA, global scratch)
+// Roots: windowed kernel W_0 over each system's unit box (global scratch per CTA)
 // ---------------------------------------------------------------------------
 template <typename T, int P>
-__global__ void __launch_bounds__(kThreads) k_root(TreeView tv, DevTables<T> tb, const T *Mroot, int has_sources,
-                                                   T *LamW, typename Cplx<T>::type *scr) {
+__global__ void __launch_bounds__(kThreads) k_root(TreeView tv, DevTables<T> tb, const T *M, int nroots, T *LamW_all,
+                                                   typename Cplx<T>::type *scr_all, size_t scr_elems) {
     using C2 = typename Cplx<T>::type;
     constexpr int P3 = P * P * P;
     const int n0 = tb.n0, NW = tb.NW, nh = tb.nhW;
     const T *Fr = tb.FWr, *Fi = tb.FWi;
     const int tid = threadIdx.x;
-    if (!has_sources) {
+    C2 *scr = scr_all + (size_t)blockIdx.x * scr_elems;
+    // one root (system) per iteration: the roots are boxes 0 .. nroots - 1
+    for (int r = blockIdx.x; r < nroots; r += gridDim.x) {
+    T *LamW = LamW_all + (size_t)r * P3;
+    __syncthreads();
+    if (tv.bnsrc[r] == 0 || tv.bslot[r] < 0) {
         for (int i = tid; i < P3; i += kThreads) LamW[i] = (T)0;
-        return;
+        continue;
     }
+    const T *Mroot = M + (size_t)tv.bslot[r] * P3;
     C2 *T1 = scr;                                  // [a][b][mz]
     C2 *T2 = T1 + P * P * nh;                      // [a][my][mz]
     C2 *Ph = T2 + P * NW * nh;                     // [my][mx][mz]
@@ -653,6 +661,7 @@ __global__ void __launch_bounds__(kThreads) k_root(TreeView tv, DevTables<T> tb,
             s += cz * (Fr[(mz + n0) * P + c] * t.x + Fi[(mz + n0) * P + c] * t.y);
         }
         LamW[i] = s;
+    }
     }
 }
 
@@ -1167,7 +1176,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 }
                 // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
                 if (level == 0) {
-                    for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[i];
+                    // a root: the windowed term of its system (roots are boxes 0 ..)
+                    for (int i = tid; i < P3; i += kLThreads) Ls[i] = LamW[(size_t)B * P3 + i];
                 } else {
                     T *b0 = reinterpret_cast<T *>(PsE);
                     T *b1 = reinterpret_cast<T *>(PsO);
@@ -1390,7 +1400,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 }
                 // ---- leaf: evaluate the local expansion at its targets
                 int ix, iy, iz;
-                morton_decode_d(tv.bkey[B], ix, iy, iz);
+                box_decode_d(tv.bkey[B], level, ix, iy, iz);
                 const double R = level_R(level), s2R = 2.0 / R;
                 const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
                 if constexpr (kTC) {
@@ -1522,7 +1532,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     }
                     __syncthreads();
                     int ix, iy, iz;
-                    morton_decode_d(tv.bkey[Pg], ix, iy, iz);
+                    box_decode_d(tv.bkey[Pg], level - 1, ix, iy, iz);
                     const double R = level_R(level - 1), s2R = 2.0 / R;
                     const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
                     if (tid == 0) atomicAdd(flops, 2ull * (P * P * P + P * P + P) * (unsigned long long)s_gntgt);
@@ -1546,12 +1556,12 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
 
 __global__ void k_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout, const double *ufar,
                            const double *unear, const double *gfar, const double *gnear, const Frame *frame,
-                           int mode, double *pot, double *grad) {
+                           const int32_t *psys, int mode, double *pot, double *grad) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || !(pflag[k] & 2)) return;
     // mode 0: both parts, 1: far part only, 2: near part only; unit-box
-    // potentials scale by 1/S, their gradients by 1/S^2
-    const double S = frame->S;
+    // potentials scale by 1/S, their gradients by 1/S^2 (S of the point's system)
+    const double S = frame[psys ? psys[k] : 0].S;
     const double v = (mode == 2 ? 0.0 : ufar[k]) + (mode == 1 ? 0.0 : unear[k]);
     const int64_t o = pout[k];
     pot[o] = v / S;
@@ -1609,7 +1619,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
 
     if (ws.ensure(cx.bufs->M, (int64_t)nslots * P3 * sizeof(T)) ||
         ws.ensure(cx.bufs->Lam, (int64_t)nslots * P3 * sizeof(T)) ||
-        ws.ensure(cx.bufs->LamW, (int64_t)P3 * sizeof(T)) || ws.ensure(cx.bufs->ufar, n * 8) ||
+        ws.ensure(cx.bufs->LamW, (int64_t)tv.lev_count[0] * P3 * sizeof(T)) || ws.ensure(cx.bufs->ufar, n * 8) ||
         ws.ensure(cx.bufs->unear, n * 8) || ws.ensure(cx.bufs->counter, 256)) {
         err = "device allocation failed (expansions)";
         return DMK_ERR_OOM;
@@ -1707,14 +1717,14 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             tv, tb, nslots, (const int32_t *)cx.tree->slot2box.p, M, Phi, lay, (char *)cx.bufs->slab.p);
         PCK(cudaGetLastError());
     }
-    // ---- root windowed term
+    // ---- root windowed term, for every root (system)
     {
-        const int NW = tb.NW, nhW = tb.nhW;
-        size_t scr = (size_t)(2 * P * P * nhW + 2 * P * NW * nhW + NW * NW * nhW) * sizeof(C2);
-        if (ws.ensure(cx.bufs->rootscr, scr)) { err = "oom root"; return DMK_ERR_OOM; }
-        const int has_src = cx.total_sources > 0 ? 1 : 0;
+        const int NW = tb.NW, nhW = tb.nhW, nroots = tv.lev_count[0];
+        const size_t scr = (size_t)(2 * P * P * nhW + 2 * P * NW * nhW + NW * NW * nhW);
+        const int grid = std::min(nroots, maxgrid);
+        if (ws.ensure(cx.bufs->rootscr, (int64_t)grid * scr * sizeof(C2))) { err = "oom root"; return DMK_ERR_OOM; }
         ::dmk::launch_tick();
-        k_root<T, P><<<1, kThreads, 0, st>>>(tv, tb, M, has_src, LamW, (C2 *)cx.bufs->rootscr.p);
+        k_root<T, P><<<grid, kThreads, 0, st>>>(tv, tb, M, nroots, LamW, (C2 *)cx.bufs->rootscr.p, scr);
         PCK(cudaGetLastError());
     }
     // ---- local expansions, coarsest level first; leaves evaluate
@@ -1759,6 +1769,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     ::dmk::launch_tick();
     k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)cx.tree->pout.p, ufar,
                                                            unear, gfar, gnear, (const Frame *)cx.tree->frame.p,
+                                                           cx.tree->nsys > 1 ? (const int32_t *)cx.tree->psys.p
+                                                                             : nullptr,
                                                            cx.mode, cx.pot, cx.grad);
     PCK(cudaGetLastError());
     return 0;

@@ -14,6 +14,14 @@
 //   5. colleagues (same-level boxes sharing a boundary point, Sec. 3.2),
 //      flags F_leaf / F_out / F_in (Step 0), expansion slots, and the
 //      residual-kernel interaction list of every target leaf (Step 4).
+//
+// A batch of independent systems is built as one forest: every system is
+// mapped to its own unit box, and the system index s prefixes every key.  A
+// point key is (s << 3 kb) | Morton(kb-bit cells); a box key at level l is
+// (s << 3 l) | Morton(level-l cell), so the children's keys (key << 3 | octant)
+// keep the prefix, every level stays sorted by (system, cell), and lookups
+// never cross systems.  The roots (level 0) are the systems, in order.  With
+// one system s = 0, kb = 21 and the keys are plain Morton codes.
 #include "tree.h"
 
 #include <algorithm>
@@ -53,6 +61,16 @@ uint64_t host_morton_encode(uint32_t ix, uint32_t iy, uint32_t iz) { return mort
 
 // key of (level, cell) unique over levels: Morton code with a leading one bit
 __device__ __forceinline__ uint64_t cell_key(int level, uint64_t m) { return m | (1ull << (3 * level)); }
+
+// the Morton cell and the system of a box key at level l
+__device__ __forceinline__ uint64_t key_cell(uint64_t key, int l) { return key & ((1ull << (3 * l)) - 1ull); }
+__device__ __forceinline__ uint64_t key_sys(uint64_t key, int l) { return key >> (3 * l); }
+
+// entry of the forced-split set: the cell key of (level, cell) below bit
+// 3 kb, the system above it
+__device__ __forceinline__ uint64_t forced_key(int level, uint64_t m, uint64_t sys, int kb) {
+    return cell_key(level, m) | (sys << (3 * kb));
+}
 
 // ------------------------------------------------------------------ hash set
 __device__ __forceinline__ uint32_t hash64(uint64_t k) {
@@ -135,42 +153,98 @@ __global__ void k_bbox_final(const double *part, int nblk, Frame *frame) {
     frame->S = S;
 }
 
+// one block per system of a batch: the bounding box of its points -> frame[s]
+__global__ void k_bbox_sys(const double *src, const int64_t *off, Frame *frame, int *bad) {
+    const int sy = blockIdx.x;
+    const int64_t a = off[sy], b = off[sy + 1];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nonfinite = 0;
+    for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = src[3 * i + d];
+            if (!isfinite(v)) nonfinite = 1;
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+    }
+    if (nonfinite) atomicExch(bad, 1);
+    __shared__ double s[6][256];
+    for (int d = 0; d < 3; ++d) {
+        s[d][threadIdx.x] = mn[d];
+        s[3 + d][threadIdx.x] = mx[d];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int d = 0; d < 3; ++d) {
+                s[d][threadIdx.x] = fmin(s[d][threadIdx.x], s[d][threadIdx.x + o]);
+                s[3 + d][threadIdx.x] = fmax(s[3 + d][threadIdx.x], s[3 + d][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        for (int d = 0; d < 3; ++d) S = fmax(S, s[3 + d][0] - s[d][0]);
+        if (!(S > 0.0)) S = 1.0;
+        for (int d = 0; d < 3; ++d) frame[sy].lo[d] = b > a ? s[d][0] : 0.0;
+        frame[sy].S = S;
+    }
+}
+
 // ------------------------------------------------------------------ 2. keys
 __device__ __forceinline__ double unit_coord(double x, double lo, double S) {
     // one IEEE subtraction and one IEEE division (nothing to contract)
     return __ddiv_rn(__dsub_rn(x, lo), S);
 }
-__device__ __forceinline__ uint32_t fine_cell(double u) {
-    double f = floor(u * 2097152.0);  // exact scaling by 2^21
-    if (f > 2097151.0) f = 2097151.0;
+// cell of u in [0, 1] at kb bits (exact scaling by 2^kb)
+__device__ __forceinline__ uint32_t fine_cell(double u, int kb) {
+    const double top = (double)(1u << kb);
+    double f = floor(u * top);
+    if (f > top - 1.0) f = top - 1.0;
     if (f < 0.0) f = 0.0;
     return (uint32_t)f;
 }
 
+// system of input point i (off: nsys + 1 ascending offsets; NULL = one system)
+__device__ __forceinline__ int point_sys(const int64_t *off, int nsys, int64_t i) {
+    if (!off) return 0;
+    int lo = 0, hi = nsys - 1;  // last s with off[s] <= i
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (off[m] <= i) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
+
 __global__ void k_make_keys(const double *src, int64_t ns, const double *tgt, int64_t n, const Frame *frame,
-                            uint64_t *keys, uint32_t *idx) {
+                            const int64_t *off, int nsys, int kb, uint64_t *keys, uint32_t *idx) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *x = i < ns ? src + 3 * i : tgt + 3 * (i - ns);
-    double S = frame->S;
-    uint32_t c0 = fine_cell(unit_coord(x[0], frame->lo[0], S));
-    uint32_t c1 = fine_cell(unit_coord(x[1], frame->lo[1], S));
-    uint32_t c2 = fine_cell(unit_coord(x[2], frame->lo[2], S));
-    keys[i] = morton_encode(c0, c1, c2);
+    const int sy = point_sys(off, nsys, i);
+    const Frame f = frame[sy];
+    uint32_t c0 = fine_cell(unit_coord(x[0], f.lo[0], f.S), kb);
+    uint32_t c1 = fine_cell(unit_coord(x[1], f.lo[1], f.S), kb);
+    uint32_t c2 = fine_cell(unit_coord(x[2], f.lo[2], f.S), kb);
+    keys[i] = morton_encode(c0, c1, c2) | ((uint64_t)sy << (3 * kb));
     idx[i] = (uint32_t)i;
 }
 
 __global__ void k_gather_points(const double *src, const double *charges, int64_t ns, const double *tgt, int64_t n,
-                                int same, const Frame *frame, const uint32_t *idx, double *ux, double *uy,
-                                double *uz, double *q, uint8_t *pflag, int32_t *pout) {
+                                int same, const Frame *frame, const uint64_t *skeys, int kb, const uint32_t *idx,
+                                double *ux, double *uy, double *uz, double *q, uint8_t *pflag, int32_t *pout,
+                                int32_t *psys) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int64_t i = idx[k];
     const double *x = i < ns ? src + 3 * i : tgt + 3 * (i - ns);
-    double S = frame->S;
-    ux[k] = unit_coord(x[0], frame->lo[0], S);
-    uy[k] = unit_coord(x[1], frame->lo[1], S);
-    uz[k] = unit_coord(x[2], frame->lo[2], S);
+    const int sy = (int)(skeys[k] >> (3 * kb));
+    if (psys) psys[k] = sy;
+    const Frame f = frame[sy];
+    ux[k] = unit_coord(x[0], f.lo[0], f.S);
+    uy[k] = unit_coord(x[1], f.lo[1], f.S);
+    uz[k] = unit_coord(x[2], f.lo[2], f.S);
     if (same) {
         q[k] = charges[i];
         pflag[k] = 3;
@@ -196,7 +270,20 @@ struct LevelArgs {
     int32_t *off9, *cnt, *excl;
     const uint64_t *forced;
     uint32_t fcap;
+    int kb;  // bits per axis of the point keys
 };
+
+// the roots of a batch: box s is system s (points off[s] .. off[s + 1])
+__global__ void k_roots(int nsys, const int64_t *off, uint64_t *bkey, int8_t *blevel, int32_t *bstart,
+                        int32_t *bcount, int32_t *bparent) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    bkey[s] = (uint64_t)s;
+    blevel[s] = 0;
+    bstart[s] = (int32_t)off[s];
+    bcount[s] = (int32_t)(off[s + 1] - off[s]);
+    bparent[s] = -1;
+}
 
 __global__ void k_level_split(LevelArgs a, int level, int lstart, int lcount, int leaf_cap, int max_level) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,13 +292,15 @@ __global__ void k_level_split(LevelArgs a, int level, int lstart, int lcount, in
     int32_t s = a.bstart[b], c = a.bcount[b], e = s + c;
     bool split = false;
     if (level < max_level) {
+        const uint64_t k = a.bkey[b];
         if (c > leaf_cap && a.keys[s] != a.keys[e - 1]) split = true;
-        else if (hset_contains(a.forced, a.fcap, cell_key(level, a.bkey[b]))) split = true;
+        else if (hset_contains(a.forced, a.fcap, forced_key(level, key_cell(k, level), key_sys(k, level), a.kb)))
+            split = true;
     }
     int32_t *off = a.off9 + (int64_t)i * 9;
     int n = 0;
     if (split) {
-        int shift = 3 * (kMortonBits - 1 - level);
+        int shift = 3 * (a.kb - 1 - level);
         off[0] = s;
         int32_t lo = s;
         for (int oc = 1; oc < 8; ++oc) {
@@ -276,14 +365,16 @@ struct LevelTable {
 
 // ------------------------------------------------------------------ 4. balance
 __global__ void k_balance(const uint64_t *bkey, const int8_t *blevel, const uint8_t *bcmask, int nb, LevelTable lt,
-                          uint64_t *forced, uint32_t fcap, int *changed, int *overflow) {
+                          uint64_t *forced, uint32_t fcap, int kb, int *changed, int *overflow) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     if (bcmask[b] != 0) return;  // not a leaf
     int l = blevel[b];
     if (l + 1 >= lt.nlev) return;
     int ix, iy, iz;
-    morton_decode(bkey[b], ix, iy, iz);
+    const uint64_t cell = key_cell(bkey[b], l), sy = key_sys(bkey[b], l);
+    morton_decode(cell, ix, iy, iz);
+    const uint64_t pre1 = sy << (3 * (l + 1));
     int lim = 1 << (l + 1);
     int ns = lt.start[l + 1], nc = lt.count[l + 1];
     for (int jx = 2 * ix - 1; jx <= 2 * ix + 2; ++jx) {
@@ -294,9 +385,9 @@ __global__ void k_balance(const uint64_t *bkey, const int8_t *blevel, const uint
                 if (jz < 0 || jz >= lim) continue;
                 bool inside = (jx >> 1) == ix && (jy >> 1) == iy && (jz >> 1) == iz;
                 if (inside) continue;
-                int c = find_box(bkey, ns, nc, morton_encode(jx, jy, jz));
+                int c = find_box(bkey, ns, nc, pre1 | morton_encode(jx, jy, jz));
                 if (c >= 0 && bcmask[c] != 0) {
-                    hset_insert(forced, fcap, cell_key(l, bkey[b]), overflow);
+                    hset_insert(forced, fcap, forced_key(l, cell, sy, kb), overflow);
                     atomicExch(changed, 1);
                     return;
                 }
@@ -313,38 +404,44 @@ __global__ void k_balance(const uint64_t *bkey, const int8_t *blevel, const uint
 // of S (new boxes may neighbour old members); the forced set grows
 // monotonically to the same least fixpoint as check-and-rebuild rounds.
 __global__ void k_collect_nonleaf(const uint64_t *bkey, const int8_t *blevel, const uint8_t *bcmask, int nb,
-                                  uint64_t *forced, uint32_t fcap, uint64_t *slist, int *count, int lcap,
+                                  uint64_t *forced, uint32_t fcap, int kb, uint64_t *slist, int *count, int lcap,
                                   int *overflow) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb || bcmask[b] == 0) return;
-    const uint64_t key = cell_key(blevel[b], bkey[b]);
+    const int l = blevel[b];
+    const uint64_t key = forced_key(l, key_cell(bkey[b], l), key_sys(bkey[b], l), kb);
     if (hset_insert(forced, fcap, key, overflow)) {
         const int k = atomicAdd(count, 1);
         if (k < lcap) slist[k] = key; else atomicExch(overflow, 1);
     }
 }
 
-// whether cell m at level l holds points (sorted finest-level keys)
-__device__ __forceinline__ bool cell_nonempty(const uint64_t *keys, int64_t n, int l, uint64_t m) {
-    const int shift = 3 * (kMortonBits - l);
-    const uint64_t lo = shift >= 64 ? 0ull : (m << shift);
+// whether cell m at level l of system sy holds points (sorted point keys with
+// kb bits per axis; sy < 2^(63 - 3 kb))
+__device__ __forceinline__ bool cell_nonempty(const uint64_t *keys, int64_t n, int kb, int l, uint64_t sy,
+                                              uint64_t m) {
+    const int shift = 3 * (kb - l);
+    const uint64_t pre = (sy << (3 * l)) | m;  // the cell's key prefix
+    const uint64_t lo = pre << shift;
     int64_t a = 0, b = n;
     while (a < b) {
         const int64_t mid = (a + b) >> 1;
         if (keys[mid] < lo) a = mid + 1; else b = mid;
     }
-    return a < n && (shift >= 64 ? true : (keys[a] >> shift) == m);
+    return a < n && (keys[a] >> shift) == pre;
 }
 
-__global__ void k_push_balance(const uint64_t *keys, int64_t n, int max_level, uint64_t *forced, uint32_t fcap,
-                               uint64_t *slist, int ns, int *count, int lcap, int *changed, int *overflow) {
+__global__ void k_push_balance(const uint64_t *keys, int64_t n, int max_level, int kb, uint64_t *forced,
+                               uint32_t fcap, uint64_t *slist, int ns, int *count, int lcap, int *changed,
+                               int *overflow) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
     const uint64_t sk = slist[i];
-    const int ls = (63 - __clzll((long long)sk)) / 3;
+    const uint64_t sys = sk >> (3 * kb), ck = sk & ((1ull << (3 * kb)) - 1ull);
+    const int ls = (63 - __clzll((long long)ck)) / 3;
     if (ls < 1 || ls >= max_level) return;  // a cell at the deepest level never splits
     int sx, sy, sz;
-    morton_decode(sk ^ (1ull << (3 * ls)), sx, sy, sz);
+    morton_decode(ck ^ (1ull << (3 * ls)), sx, sy, sz);
     const int l = ls - 1, lim = 1 << l;
     const int px = sx >> 1, py = sy >> 1, pz = sz >> 1;
     // level-l cells sharing a boundary point with s: 2 i - 1 <= s <= 2 i + 2 per axis
@@ -356,10 +453,10 @@ __global__ void k_push_balance(const uint64_t *keys, int64_t n, int max_level, u
                 if (iz < 0 || iz >= lim) continue;
                 if (ix == px && iy == py && iz == pz) continue;
                 const uint64_t m = morton_encode(ix, iy, iz);
-                const uint64_t key = cell_key(l, m);
+                const uint64_t key = forced_key(l, m, sys, kb);
                 if (hset_contains(forced, fcap, key)) continue;
-                if (l > 0 && !hset_contains(forced, fcap, cell_key(l - 1, m >> 3))) continue;
-                if (!cell_nonempty(keys, n, l, m)) continue;
+                if (l > 0 && !hset_contains(forced, fcap, forced_key(l - 1, m >> 3, sys, kb))) continue;
+                if (!cell_nonempty(keys, n, kb, l, sys, m)) continue;
                 if (hset_insert(forced, fcap, key, overflow)) {
                     const int k = atomicAdd(count, 1);
                     if (k < lcap) slist[k] = key; else atomicExch(overflow, 1);
@@ -374,7 +471,7 @@ __global__ void k_push_balance(const uint64_t *keys, int64_t n, int max_level, u
 __global__ void k_box_finish(int nb, const uint64_t *bkey, const int8_t *blevel, const int32_t *bstart,
                              const int32_t *bcount, const uint8_t *bcmask, const int32_t *psrc, const int32_t *ptgt,
                              LevelTable lt, int32_t *bnsrc, int32_t *bntgt, int32_t *bcol, uint8_t *bflags,
-                             int32_t *isleaf_i32, int32_t *isnonleaf_i32) {
+                             int32_t *isleaf_i32, int32_t *isnonleaf_i32, int *nleaf) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     int32_t s = bstart[b], e = s + bcount[b];
@@ -382,7 +479,8 @@ __global__ void k_box_finish(int nb, const uint64_t *bkey, const int8_t *blevel,
     bntgt[b] = ptgt ? ptgt[e] - ptgt[s] : e - s;
     int l = blevel[b];
     int ix, iy, iz;
-    morton_decode(bkey[b], ix, iy, iz);
+    morton_decode(key_cell(bkey[b], l), ix, iy, iz);
+    const uint64_t pre = key_sys(bkey[b], l) << (3 * l);
     int lim = 1 << l;
     int k = 0;
     for (int dx = -1; dx <= 1; ++dx)
@@ -392,13 +490,17 @@ __global__ void k_box_finish(int nb, const uint64_t *bkey, const int8_t *blevel,
                 int c = -1;
                 if (jx >= 0 && jy >= 0 && jz >= 0 && jx < lim && jy < lim && jz < lim)
                     c = (dx == 0 && dy == 0 && dz == 0) ? b
-                                                         : find_box(bkey, lt.start[l], lt.count[l], morton_encode(jx, jy, jz));
+                                                         : find_box(bkey, lt.start[l], lt.count[l],
+                                                                    pre | morton_encode(jx, jy, jz));
                 bcol[(int64_t)b * 27 + k] = c;
             }
     bool leaf = bcmask[b] == 0;
     bflags[b] = leaf ? BF_LEAF : 0;
     isleaf_i32[b] = leaf ? 1 : 0;
-    isnonleaf_i32[b] = leaf ? 0 : 1;
+    // expansion slots: every non-leaf box, and every root (a root that is a
+    // leaf anterpolates its own sources for the windowed term W_0)
+    isnonleaf_i32[b] = (leaf && l > 0) ? 0 : 1;
+    if (leaf) atomicAdd(nleaf, 1);
 }
 
 __global__ void k_box_flags(int nb, const int32_t *bnsrc, const int32_t *bntgt, const int32_t *bcol, uint8_t *bflags) {
@@ -423,11 +525,10 @@ __global__ void k_box_flags_in(int nb, const int32_t *bnsrc, const int32_t *bntg
     if (fin) bflags[b] |= BF_FIN;
 }
 
-__global__ void k_slots(int nb, const int32_t *isnonleaf, const int32_t *excl, int32_t *bslot, int root_leaf) {
+__global__ void k_slots(int nb, const int32_t *isslot, const int32_t *excl, int32_t *bslot) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    bslot[b] = isnonleaf[b] ? excl[b] : -1;
-    if (root_leaf && b == 0) bslot[0] = 0;
+    bslot[b] = isslot[b] ? excl[b] : -1;
 }
 
 __global__ void k_slot2box(int nb, const int32_t *bslot, int32_t *slot2box) {
@@ -449,7 +550,7 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
     if (b >= nb || !(bflags[b] & BF_LEAF)) return;
     int l = blevel[b];
     int ix, iy, iz;
-    morton_decode(bkey[b], ix, iy, iz);
+    morton_decode(key_cell(bkey[b], l), ix, iy, iz);
     double R = level_R(l);
     double cx = (ix + 0.5) * R, cy = (iy + 0.5) * R, cz = (iz + 0.5) * R;
     int32_t s = bstart[b], e = s + bcount[b];
@@ -500,7 +601,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
     int T = tleaves[i];
     int a = blevel[T];
     int tx, ty, tz;
-    morton_decode(bkey[T], tx, ty, tz);
+    morton_decode(key_cell(bkey[T], a), tx, ty, tz);
     int n = 0;
     int32_t *out = FILL ? list + off[i] : nullptr;
     long long np = 0;
@@ -511,7 +612,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
             int C = bcol[(int64_t)B * 27 + k];
             if (C < 0 || !(bflags[C] & BF_LEAF) || bnsrc[C] == 0) continue;
             int cx, cy, cz;
-            morton_decode(bkey[C], cx, cy, cz);
+            morton_decode(key_cell(bkey[C], b), cx, cy, cz);
             if (box_dist2(a, tx, ty, tz, b, cx, cy, cz) >= Rb * Rb) continue;
             if (FILL) out[n] = C;
             np += bnsrc[C];
@@ -532,7 +633,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
             int D = c0 + kk++;
             if (!(bflags[D] & BF_LEAF) || bnsrc[D] == 0) continue;
             int dx, dy, dz;
-            morton_decode(bkey[D], dx, dy, dz);
+            morton_decode(key_cell(bkey[D], a + 1), dx, dy, dz);
             if (box_dist2(a, tx, ty, tz, a + 1, dx, dy, dz) >= R1 * R1) continue;
             if (FILL) out[n] = D;
             np += bnsrc[D];
@@ -573,7 +674,7 @@ __global__ void k_leaf_export(int nb, const uint64_t *bkey, const int8_t *blevel
     for (int32_t k = s + threadIdx.x; k < e; k += blockDim.x) {
         uint32_t i = idx[k];
         lev_out[i] = blevel[b];
-        cell_out[i] = (int64_t)bkey[b];
+        cell_out[i] = (int64_t)key_cell(bkey[b], blevel[b]);
     }
 }
 
@@ -617,25 +718,45 @@ int TreeBuilder::grow_boxes(int64_t need, cudaStream_t st, std::string &err) {
     return 0;
 }
 
+int forest_key_bits(int nsys) {
+    int sb = 0;
+    while (sb < 40 && (1ll << sb) < (long long)nsys) ++sb;
+    return std::min(kMortonBits, (63 - sb) / 3);
+}
+
 int TreeBuilder::build(const double *src, int64_t ns, const double *charges, const double *tgt, int64_t nt, bool same,
-                       int leaf_cap, int max_level, int point_prec, cudaStream_t st, std::string &err) {
+                       int leaf_cap, int max_level, int point_prec, cudaStream_t st, std::string &err,
+                       int nsys_in, const int64_t *h_off) {
     n = same ? ns : ns + nt;
     this->same = same;
     const int64_t N = n;
-    // ---- 1. bounding box
+    const bool forest = h_off != nullptr;
+    if (forest && !same) { err = "a batch of systems needs targets equal to sources"; return DMK_ERR_INVALID_ARG_I; }
+    nsys = forest ? nsys_in : 1;
+    kb = forest ? forest_key_bits(nsys) : kMortonBits;
+    max_level = std::min(max_level, kb);
+    // ---- 1. bounding box (of every system)
     const int bb_blocks = 256;
-    if (ws.ensure(bbox_part, bb_blocks * 6 * sizeof(double)) || ws.ensure(frame, sizeof(Frame)) ||
-        ws.ensure(flags, 16 * sizeof(int))) {
+    if (ws.ensure(bbox_part, bb_blocks * 6 * sizeof(double)) || ws.ensure(frame, (int64_t)nsys * sizeof(Frame)) ||
+        ws.ensure(flags, 16 * sizeof(int)) || (forest && ws.ensure(sysoff, (int64_t)(nsys + 1) * 8)) ||
+        (forest && ws.ensure(psys, N * 4))) {
         err = "device allocation failed";
         return DMK_ERR_OOM_I;
     }
     int *d_flags = (int *)flags.p;  // [0] bad input, [1] changed, [2] overflow, [3] total
     CK(cudaMemsetAsync(d_flags, 0, 16 * sizeof(int), st));
-    ::dmk::launch_tick();
-    k_bbox_partial<<<bb_blocks, 256, 0, st>>>(src, ns, same ? nullptr : tgt, same ? 0 : nt, (double *)bbox_part.p,
-                                              d_flags);
-    ::dmk::launch_tick();
-    k_bbox_final<<<1, 32, 0, st>>>((double *)bbox_part.p, bb_blocks, (Frame *)frame.p);
+    const int64_t *d_off = forest ? (const int64_t *)sysoff.p : nullptr;
+    if (forest) {
+        CK(cudaMemcpyAsync(sysoff.p, h_off, (size_t)(nsys + 1) * 8, cudaMemcpyHostToDevice, st));
+        ::dmk::launch_tick();
+        k_bbox_sys<<<nsys, 256, 0, st>>>(src, d_off, (Frame *)frame.p, d_flags);
+    } else {
+        ::dmk::launch_tick();
+        k_bbox_partial<<<bb_blocks, 256, 0, st>>>(src, ns, same ? nullptr : tgt, same ? 0 : nt,
+                                                  (double *)bbox_part.p, d_flags);
+        ::dmk::launch_tick();
+        k_bbox_final<<<1, 32, 0, st>>>((double *)bbox_part.p, bb_blocks, (Frame *)frame.p);
+    }
     CK(cudaGetLastError());
     // ---- 2. keys and sort
     if (ws.ensure(keys, N * 8) || ws.ensure(keys2, N * 8) || ws.ensure(idx, N * 4) || ws.ensure(idx2, N * 4) ||
@@ -649,8 +770,8 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         return DMK_ERR_OOM_I;
     }
     ::dmk::launch_tick();
-    k_make_keys<<<nblk(N, 256), 256, 0, st>>>(src, ns, same ? nullptr : tgt, N, (const Frame *)frame.p,
-                                              (uint64_t *)keys.p, (uint32_t *)idx.p);
+    k_make_keys<<<nblk(N, 256), 256, 0, st>>>(src, ns, same ? nullptr : tgt, N, (const Frame *)frame.p, d_off,
+                                              nsys, kb, (uint64_t *)keys.p, (uint32_t *)idx.p);
     uint64_t *skeys;
     uint32_t *sidx;
     radix_sort_pairs((uint64_t *)keys.p, (uint32_t *)idx.p, (uint64_t *)keys2.p, (uint32_t *)idx2.p, N, 63,
@@ -659,8 +780,9 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     sorted_idx = sidx;
     ::dmk::launch_tick();
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(src, charges, ns, same ? nullptr : tgt, N, same ? 1 : 0,
-                                                  (const Frame *)frame.p, sidx, (double *)ux.p, (double *)uy.p,
-                                                  (double *)uz.p, (double *)q.p, (uint8_t *)pflag.p, (int32_t *)pout.p);
+                                                  (const Frame *)frame.p, skeys, kb, sidx, (double *)ux.p,
+                                                  (double *)uy.p, (double *)uz.p, (double *)q.p, (uint8_t *)pflag.p,
+                                                  (int32_t *)pout.p, forest ? (int32_t *)psys.p : nullptr);
     CK(cudaGetLastError());
     int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -675,25 +797,31 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     const uint32_t fcap = 1u << 20;
     if (ws.ensure(forced, fcap * sizeof(uint64_t))) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
     CK(cudaMemsetAsync(forced.p, 0, fcap * sizeof(uint64_t), st));
-    int64_t est = std::max<int64_t>(4096, 16 * (N / std::max(leaf_cap, 1) + 64));
+    int64_t est = std::max<int64_t>(4096, 16 * (N / std::max(leaf_cap, 1) + 64) + 2 * (int64_t)nsys);
     if (int rc = grow_boxes(est, st, err)) return rc;
     rounds = 0;
     bool pushed = false;  // the forced set has been completed on the cell sets
     for (int rebuilds = 0;; ++rebuilds) {
         if (rebuilds > 64) { err = "level restriction did not converge"; return DMK_ERR_INTERNAL_I; }
-        // root
-        uint64_t zero64 = 0;
-        int8_t zero8 = 0;
-        int32_t zero32 = 0, n32 = (int32_t)N, m1 = -1;
-        CK(cudaMemcpyAsync(bkey.p, &zero64, 8, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(blevel.p, &zero8, 1, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(bstart.p, &zero32, 4, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(bcount.p, &n32, 4, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(bparent.p, &m1, 4, cudaMemcpyHostToDevice, st));
+        // roots
+        if (forest) {
+            ::dmk::launch_tick();
+            k_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, d_off, (uint64_t *)bkey.p, (int8_t *)blevel.p,
+                                                      (int32_t *)bstart.p, (int32_t *)bcount.p, (int32_t *)bparent.p);
+        } else {
+            uint64_t zero64 = 0;
+            int8_t zero8 = 0;
+            int32_t zero32 = 0, n32 = (int32_t)N, m1 = -1;
+            CK(cudaMemcpyAsync(bkey.p, &zero64, 8, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(blevel.p, &zero8, 1, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(bstart.p, &zero32, 4, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(bcount.p, &n32, 4, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(bparent.p, &m1, 4, cudaMemcpyHostToDevice, st));
+        }
         lt_start[0] = 0;
-        lt_count[0] = 1;
+        lt_count[0] = nsys;
         nlev = 1;
-        int nbox = 1;
+        int nbox = nsys;
         for (int l = 0; l < max_level; ++l) {
             int lc = lt_count[l];
             if (ws.ensure(lvl_off9, (int64_t)lc * 9 * 4) || ws.ensure(lvl_cnt, (int64_t)lc * 4) ||
@@ -704,7 +832,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
             LevelArgs la{(const uint64_t *)skeys, (uint64_t *)bkey.p, (int8_t *)blevel.p, (int32_t *)bstart.p,
                          (int32_t *)bcount.p, (int32_t *)bparent.p, (int32_t *)bchild0.p, (uint8_t *)bcmask.p,
                          (int32_t *)lvl_off9.p, (int32_t *)lvl_cnt.p, (int32_t *)lvl_excl.p,
-                         (const uint64_t *)forced.p, fcap};
+                         (const uint64_t *)forced.p, fcap, kb};
             ::dmk::launch_tick();
             k_level_split<<<nblk(lc, 128), 128, 0, st>>>(la, l, lt_start[l], lc, leaf_cap, max_level);
             scan_exclusive_i32((int32_t *)lvl_cnt.p, (int32_t *)lvl_excl.p, lc, d_flags + 3, scan_tmp.p,
@@ -776,7 +904,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
             ::dmk::launch_tick();
             k_collect_nonleaf<<<nblk(nb, 128), 128, 0, st>>>((const uint64_t *)bkey.p, (const int8_t *)blevel.p,
                                                              (const uint8_t *)bcmask.p, nb, (uint64_t *)forced.p,
-                                                             fcap, (uint64_t *)slist.p, d_flags + 3, lcap,
+                                                             fcap, kb, (uint64_t *)slist.p, d_flags + 3, lcap,
                                                              d_flags + 2);
             int any = 0;
             for (int pr = 0;; ++pr) {
@@ -790,8 +918,8 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
                 ++rounds;
                 CK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
                 ::dmk::launch_tick();
-                k_push_balance<<<nblk(hc[2], 128), 128, 0, st>>>(skeys, N, max_level, (uint64_t *)forced.p, fcap,
-                                                                 (uint64_t *)slist.p, hc[2], d_flags + 3, lcap,
+                k_push_balance<<<nblk(hc[2], 128), 128, 0, st>>>(skeys, N, max_level, kb, (uint64_t *)forced.p,
+                                                                 fcap, (uint64_t *)slist.p, hc[2], d_flags + 3, lcap,
                                                                  d_flags + 1, d_flags + 2);
             }
             if (any) continue;  // rebuild with the completed forced set
@@ -799,7 +927,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         CK(cudaMemsetAsync(d_flags + 1, 0, 2 * sizeof(int), st));
         ::dmk::launch_tick();
         k_balance<<<nblk(nb, 128), 128, 0, st>>>((const uint64_t *)bkey.p, (const int8_t *)blevel.p,
-                                                 (const uint8_t *)bcmask.p, nb, lt, (uint64_t *)forced.p, fcap,
+                                                 (const uint8_t *)bcmask.p, nb, lt, (uint64_t *)forced.p, fcap, kb,
                                                  d_flags + 1, d_flags + 2);
         int hf[2];
         CK(cudaMemcpyAsync(hf, d_flags + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -830,29 +958,30 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         psrc = (const int32_t *)pscan0.p;
         ptgt = (const int32_t *)pscan1.p;
     }
-    int32_t *isleaf = (int32_t *)bscr0.p, *isnonleaf = (int32_t *)bscr1.p, *excl = (int32_t *)bscr2.p;
+    int32_t *isleaf = (int32_t *)bscr0.p, *isslot = (int32_t *)bscr1.p, *excl = (int32_t *)bscr2.p;
+    CK(cudaMemsetAsync(d_flags + 9, 0, sizeof(int), st));
     ::dmk::launch_tick();
     k_box_finish<<<nblk(nb, 128), 128, 0, st>>>(nb, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
                                                 (const int32_t *)bstart.p, (const int32_t *)bcount.p,
                                                 (const uint8_t *)bcmask.p, psrc, ptgt, lt, (int32_t *)bnsrc.p,
                                                 (int32_t *)bntgt.p, (int32_t *)bcol.p, (uint8_t *)bflags.p, isleaf,
-                                                isnonleaf);
+                                                isslot, d_flags + 9);
     ::dmk::launch_tick();
     k_box_flags<<<nblk(nb, 128), 128, 0, st>>>(nb, (const int32_t *)bnsrc.p, (const int32_t *)bntgt.p,
                                                (const int32_t *)bcol.p, (uint8_t *)bflags.p);
     ::dmk::launch_tick();
     k_box_flags_in<<<nblk(nb, 128), 128, 0, st>>>(nb, (const int32_t *)bnsrc.p, (const int32_t *)bntgt.p,
                                                   (const int32_t *)bcol.p, (uint8_t *)bflags.p);
-    scan_exclusive_i32(isnonleaf, excl, nb, d_flags + 6, scan_tmp.p, scan_tmp.bytes, st);
+    scan_exclusive_i32(isslot, excl, nb, d_flags + 6, scan_tmp.p, scan_tmp.bytes, st);
     root_leaf = (nlev == 1);
     ::dmk::launch_tick();
-    k_slots<<<nblk(nb, 128), 128, 0, st>>>(nb, isnonleaf, excl, (int32_t *)bslot.p, root_leaf ? 1 : 0);
+    k_slots<<<nblk(nb, 128), 128, 0, st>>>(nb, isslot, excl, (int32_t *)bslot.p);
     CK(cudaGetLastError());
-    int nonleaf = 0;
-    CK(cudaMemcpyAsync(&nonleaf, d_flags + 6, 4, cudaMemcpyDeviceToHost, st));
+    int hs[4] = {0, 0, 0, 0};  // slots, -, -, leaves
+    CK(cudaMemcpyAsync(hs, d_flags + 6, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    nslots = root_leaf ? 1 : nonleaf;
-    nleaves = nb - nonleaf;
+    nslots = hs[0];
+    nleaves = hs[3];
     if (ws.ensure(slot2box, (int64_t)std::max(nslots, 1) * 4)) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
     ::dmk::launch_tick();
     k_slot2box<<<nblk(nb, 128), 128, 0, st>>>(nb, (const int32_t *)bslot.p, (int32_t *)slot2box.p);

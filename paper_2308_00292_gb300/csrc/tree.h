@@ -68,13 +68,21 @@ template <> struct Vec4<double> { using type = double4_32a; };
 
 uint64_t host_morton_encode(uint32_t ix, uint32_t iy, uint32_t iz);
 
+// bits per axis of the point keys of a forest of nsys systems (the system
+// index takes the bits above them in a 63-bit key)
+int forest_key_bits(int nsys);
+
 class TreeBuilder {
 public:
     explicit TreeBuilder(Workspace &w) : ws(w) {}
     // Build the tree of the union of sources and targets (targets ignored
     // when same).  point_prec: 1 -> float4 leaf-local coordinates, 0 -> double4.
+    // A batch (h_off != NULL, host array of nsys + 1 ascending offsets into
+    // src, targets equal to sources) is built as a forest with one root per
+    // system, each system in its own unit box.
     int build(const double *src, int64_t ns, const double *charges, const double *tgt, int64_t nt, bool same,
-              int leaf_cap, int max_level, int point_prec, cudaStream_t st, std::string &err);
+              int leaf_cap, int max_level, int point_prec, cudaStream_t st, std::string &err, int nsys = 1,
+              const int64_t *h_off = nullptr);
     TreeView view() const;
     int export_leaves(int32_t *lev, int64_t *cell, cudaStream_t st, std::string &err);
 
@@ -82,6 +90,7 @@ public:
     int64_t n = 0;
     bool same = true;
     int nb = 0, nlev = 0, nslots = 0, nleaves = 0, ntleaves = 0, rounds = 0, near_list_len = 0;
+    int nsys = 1, kb = kMortonBits;  // systems (roots) and bits per axis of the point keys
     bool root_leaf = false;
     int64_t near_pairs = 0;
     int lt_start[kMaxLevel + 2] = {0}, lt_count[kMaxLevel + 2] = {0};
@@ -92,7 +101,7 @@ public:
     // points (sorted)
     DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, plocal_lo, pscan0, pscan1,
         scan_tmp;
-    DBuf bbox_part, frame, flags, forced, slist;
+    DBuf bbox_part, frame, flags, forced, slist, sysoff, psys;  // frame: one per system
     // boxes
     int64_t box_cap = 0;
     DBuf bkey, blevel, bstart, bcount, bparent, bchild0, bcmask, bflags, bnsrc, bntgt, bcol, bslot;

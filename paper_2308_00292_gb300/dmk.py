@@ -31,7 +31,8 @@ ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "D
 
 EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_grad", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
             "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree",
-            "dmk_direct_noalloc"]
+            "dmk_direct_noalloc", "dmk_tune_leaf_cap", "dmk_eval_batch",
+            "dmk_tune_leaf_cap_batch"]
 
 
 class Opts(ctypes.Structure):
@@ -81,6 +82,7 @@ def lib():
                                    ctypes.POINTER(vp)]
             L.dmk_eval.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
             L.dmk_eval_grad.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, vp]
+            L.dmk_eval_batch.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.c_int, vp, vp]
             L.dmk_eval_host.argtypes = [vp, dp, i64, dp, dp, i64, dp, vp]
             L.dmk_plan_destroy.argtypes = [vp]
             L.dmk_error_string.argtypes = [ctypes.c_int]
@@ -92,6 +94,12 @@ def lib():
             L.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.dmk_get_tree.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), i64]
             L.dmk_direct_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+            L.dmk_tune_leaf_cap.argtypes = [vp, vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_float), vp]
+            L.dmk_tune_leaf_cap_batch.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), vp]
             for name in EXPORTED:
                 getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
             _lib = L
@@ -165,6 +173,54 @@ class Plan:
         _check(lib().dmk_eval_grad(self._h, sources.data_ptr(), ns, charges.data_ptr(), tgt.data_ptr(), nt,
                                    out.data_ptr(), gout.data_ptr(), st))
         return out, gout
+
+    def eval_batch(self, points, charges, offsets, out=None, stream=None):
+        """Potentials of independent systems: system s is points[offsets[s]:offsets[s+1]]
+        (torch CUDA float64 tensors; offsets a host sequence of n_systems + 1 ints)."""
+        import torch
+        assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+        assert charges.is_cuda and charges.dtype == torch.float64 and charges.is_contiguous()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if out is None:
+            out = torch.empty(points.shape[0], dtype=torch.float64, device=points.device)
+        st = stream if stream is not None else torch.cuda.current_stream(points.device).cuda_stream
+        _check(lib().dmk_eval_batch(self._h, points.data_ptr(), charges.data_ptr(),
+                                    off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
+                                    out.data_ptr(), st))
+        return out
+
+    def tune_leaf_cap(self, sources, charges, targets=None, candidates=None, reps=0, stream=None):
+        """Time the given problem at each candidate leaf capacity and keep the
+        fastest in the plan; returns (best, {candidate: ms})."""
+        import torch
+        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
+        tgt = sources if targets is None else targets
+        cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
+        ncand = 0 if candidates is None else len(candidates)
+        times = (ctypes.c_float * (7 if candidates is None else max(ncand, 1)))()
+        best = ctypes.c_int()
+        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+        _check(lib().dmk_tune_leaf_cap(self._h, sources.data_ptr(), sources.shape[0], charges.data_ptr(),
+                                       tgt.data_ptr(), tgt.shape[0], cand, ncand, reps, ctypes.byref(best),
+                                       times, st))
+        tried = list(candidates) if candidates is not None else [64, 100, 140, 200, 280, 400, 560]
+        return best.value, dict(zip(tried, list(times)[:len(tried)]))
+
+    def tune_leaf_cap_batch(self, points, charges, offsets, candidates=None, reps=0, stream=None):
+        """tune_leaf_cap for a batch of systems (as in eval_batch)."""
+        import torch
+        assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
+        ncand = 0 if candidates is None else len(candidates)
+        tried = list(candidates) if candidates is not None else [64, 100, 140, 200, 280, 400, 560]
+        times = (ctypes.c_float * len(tried))()
+        best = ctypes.c_int()
+        st = stream if stream is not None else torch.cuda.current_stream(points.device).cuda_stream
+        _check(lib().dmk_tune_leaf_cap_batch(self._h, points.data_ptr(), charges.data_ptr(),
+                                             off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
+                                             cand, ncand, reps, ctypes.byref(best), times, st))
+        return best.value, dict(zip(tried, list(times)))
 
     def eval_host(self, sources, charges, targets=None, out=None, stream=0):
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)

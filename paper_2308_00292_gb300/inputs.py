@@ -12,6 +12,8 @@ Workloads:
                    charges                                       (C2 shape)
   sphere        -- points on a sphere of radius 0.45, charges U[-1,1]
                                                                  (Table 2 shape)
+  batch         -- many independent systems of log-uniform sizes, each
+                   uniform in the cube or one Gaussian cluster   (batched)
 """
 from __future__ import annotations
 
@@ -66,6 +68,40 @@ def sphere(n: int, seed: int = 5, radius: float = 0.45):
     return x, q
 
 
+def batch(nsys: int, seed: int = 6, n_lo: int = 500, n_hi: int = 50_000, sigma_lo: float = 1e-2,
+          sigma_hi: float = 1e-1):
+    """nsys independent systems, one after another.
+
+    System sizes are log-uniform integers in [n_lo, n_hi]; each system is, with
+    probability 1/2, uniform in [0,1)^3 or a single Gaussian cluster (centre
+    U[0.3, 0.7]^3, width log-uniform in [sigma_lo, sigma_hi], points outside
+    [0,1)^3 redrawn).  Charges are U[-1, 1].  Returns (points, charges,
+    offsets) with offsets[s] .. offsets[s + 1] the points of system s.
+    """
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi + 1), size=nsys))).astype(np.int64)
+    sizes = np.clip(sizes, n_lo, n_hi)
+    kinds = rng.integers(0, 2, size=nsys)
+    off = np.zeros(nsys + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    x = np.empty((int(off[-1]), 3))
+    for s in range(nsys):
+        m = int(sizes[s])
+        if kinds[s] == 0:
+            pts = rng.uniform(0.0, 1.0, size=(m, 3))
+        else:
+            c = rng.uniform(0.3, 0.7, size=3)
+            sig = float(np.exp(rng.uniform(np.log(sigma_lo), np.log(sigma_hi))))
+            pts = c + sig * rng.standard_normal((m, 3))
+            bad = np.any((pts < 0.0) | (pts >= 1.0), axis=1)
+            while bad.any():
+                pts[bad] = c + sig * rng.standard_normal((int(bad.sum()), 3))
+                bad = np.any((pts < 0.0) | (pts >= 1.0), axis=1)
+        x[off[s]:off[s + 1]] = pts
+    q = rng.uniform(-1.0, 1.0, size=int(off[-1]))
+    return x, q, off
+
+
 # The configurations the library is measured on (sizes, distributions, seeds).
 CONFIGS = {
     "laplace3d_uniform_n2e4": dict(gen="uniform_cube", n=20000, seed=1, eps=1e-6, leaf_cap=280),
@@ -76,6 +112,8 @@ CONFIGS = {
     "laplace3d_clustered_n2e6": dict(gen="clustered", n=2_000_000, seed=2, eps=1e-6, leaf_cap=200),
     # the differentiable workload: potentials plus gradients in charges and positions
     "laplace3d_uniform_n2e6": dict(gen="uniform_cube", n=2_000_000, seed=4, eps=1e-6, leaf_cap=200),
+    # 4096 independent systems of 500 .. 50 000 points (about 4.4e7 in all)
+    "laplace3d_batched_4096": dict(gen="batch", nsys=4096, seed=6, eps=1e-6, leaf_cap=0),
 }
 
 

@@ -105,3 +105,20 @@ def test_plan_tables_match_oracle(dmk, oracle_mod, eps):
     qv = np.polynomial.chebyshev.chebval(2 * t - 1, ch)
     ref_q = oracle_mod.kernel(oprm, oracle_mod.S_MOLLIFIED, 0, np.sqrt(t))
     assert np.max(np.abs(qv - ref_q)) < 2e-3 * eps * ref_q[0]
+
+
+def test_tuner_argument_validation_without_device(dmk):
+    L = dmk.lib()
+    best = ctypes.c_int(-1)
+    assert L.dmk_tune_leaf_cap(None, None, 0, None, None, 0, None, 0, 0, ctypes.byref(best), None, None) == 1
+    p = dmk.Plan(1e-6, flags=dmk.FLAG_HOST_ONLY)
+    assert L.dmk_tune_leaf_cap(p._h, None, 0, None, None, 0, None, 0, 0, ctypes.byref(best), None, None) == 1
+    assert best.value == -1
+
+
+def test_batch_argument_validation_without_device(dmk):
+    L = dmk.lib()
+    off = (ctypes.c_int64 * 3)(0, 5, 9)
+    assert L.dmk_eval_batch(None, None, None, off, 2, None, None) == 1
+    p = dmk.Plan(1e-6, flags=dmk.FLAG_HOST_ONLY)
+    assert L.dmk_eval_batch(p._h, None, None, off, 2, None, None) == 1
