@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("gauss_b", ctypes.c_double),
         ("max_level", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("lam", ctypes.c_double),
     ]
 
 
@@ -70,6 +71,8 @@ def _load():
             lib.oracle_default_params.restype = None
             lib.oracle_direct.argtypes = [dp, dp, i64, dp, i64, dp, ctypes.c_int]
             lib.oracle_direct.restype = None
+            lib.oracle_direct_yukawa.argtypes = [dp, dp, i64, dp, i64, ctypes.c_double, dp, ctypes.c_int]
+            lib.oracle_direct_yukawa.restype = None
             lib.oracle_dmk.argtypes = [ctypes.POINTER(Params), dp, dp, i64, dp, i64, dp, dp, dp]
             lib.oracle_dmk.restype = ctypes.c_int
             lib.oracle_direct_grad.argtypes = [dp, dp, i64, dp, i64, dp, ctypes.c_int]
@@ -118,13 +121,18 @@ def params(eps=1e-6, splitting=PSWF, leaf_cap=280, nthreads=0, **kw) -> Params:
     return prm
 
 
-def direct(src, rho, tgt=None, nthreads=0) -> np.ndarray:
-    """O1: u_i = sum_{j: y_j != x_i} rho_j / |x_i - y_j| (compensated sums)."""
+def direct(src, rho, tgt=None, nthreads=0, lam=0.0) -> np.ndarray:
+    """O1: u_i = sum_{j: y_j != x_i} rho_j K(|x_i - y_j|) (compensated sums),
+    K(r) = 1/r, or exp(-lam r)/r (Yukawa) when lam > 0."""
     src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
     rho = _c64(rho, src.shape[0])
     tgt = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 3)
     out = np.zeros(tgt.shape[0])
-    _load().oracle_direct(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], _dp(out), nthreads)
+    if lam > 0.0:
+        _load().oracle_direct_yukawa(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], lam, _dp(out),
+                                     nthreads)
+    else:
+        _load().oracle_direct(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], _dp(out), nthreads)
     return out
 
 

@@ -36,6 +36,22 @@
  *     one finest Morton cell (coincident points); otherwise duplicates would
  *     drive the tree to the depth cap, where their self terms rho S_L(0)
  *     grow like 2^L and the far field's eps-relative error no longer cancels.
+ *   - Yukawa kernel exp(-lambda r) / r (lambda > 0), split in Fourier space
+ *     (Sec. 3.7, eqs. yukawaPSWFkernels / yukawagaussiankernels, times the 4 pi
+ *     of the kernel without its 1/(4 pi)): the unit-box map turns lambda into
+ *     lambda S.  The PSWF mollified kernel has no closed form in physical
+ *     space; it is the radial inverse transform
+ *       S_l(r) = 2 / (pi psi(0) r) int_0^inf psi(sqrt(k^2 + lambda^2) R_l / c)
+ *                k sin(k r) / (k^2 + lambda^2) dk.
+ *     psi decays only like 1/x beyond x = 1, so the integral is taken as the
+ *     Laplace mollifier Phi(r/R_l)/r (its lambda = 0 value, in closed form) plus
+ *     the integral of the difference of the two integrands, which decays
+ *     faster by (lambda R_l / c)^2 / x^2; that one by Gauss-Legendre panels up
+ *     to x = sqrt(k^2 + lambda^2) R_l / c = 4.  The Gaussian one has the closed form
+ *     (e^{-lambda r} erfc(a - r/sigma) - e^{lambda r} erfc(a + r/sigma)) / (2 r),
+ *     a = lambda sigma / 2.  The windowed root kernel multiplies the mollifier by
+ *     the transform of the kernel truncated at R_t:
+ *       4 pi (k - e^{-lambda R_t} (lambda sin k R_t + k cos k R_t)) / (k (k^2 + lambda^2)).
  */
 #include "dmk_oracle.h"
 
@@ -287,6 +303,19 @@ static double pswf_eval(const pswf_t *s, double x)
     return acc / s->lambda0;
 }
 
+/* psi(x1) - psi(x2) without cancellation, from the eigen-relation:
+ * (1/lambda_0) int psi(t) (cos(c x1 t) - cos(c x2 t)) dt with the difference of
+ * cosines written as -2 sin(c (x1 + x2) t / 2) sin(c (x1 - x2) t / 2).  Needed
+ * where both arguments are small (the Yukawa Dhat_l near k = 0). */
+static double pswf_diff(const pswf_t *s, double x1, double x2)
+{
+    double acc = 0.0;
+    for (int i = 0; i < PSWF_NQ; ++i)
+        acc += s->wq[i] * s->psiq[i] * sin(0.5 * s->c * (x1 + x2) * s->xq[i]) *
+               sin(0.5 * s->c * (x1 - x2) * s->xq[i]);
+    return -2.0 * acc / s->lambda0;
+}
+
 /* Phi(s) = c_0^{-1} int_0^s psi(t) dt for s in [0, 1]; 1 beyond (Sec. 3.6).
  * Uses int_0^s P_k = (P_{k+1}(s) - P_{k-1}(s)) / (2k + 1) for even k >= 2. */
 static double pswf_Phi(const pswf_t *s, double x)
@@ -306,21 +335,57 @@ static double pswf_Phi(const pswf_t *s, double x)
 /* 3. Kernel splittings                                                    */
 /* ====================================================================== */
 
+#define YUK_LEVELS 22   /* levels 0 .. 21 */
+#define YUK_PANELS 8    /* regular panels up to the cutoff */
+#define YUK_NODES 24    /* Gauss-Legendre nodes per panel */
+#define YUK_MAXP 40     /* regular plus graded panels */
+#define YUK_NQ (YUK_MAXP * YUK_NODES)
+
 typedef struct {
     oracle_params prm;
     pswf_t *pswf;   /* PSWF splitting only */
     double Rt;      /* truncation radius of the windowed root kernel */
     double hW;      /* root Fourier spacing */
+    double lam;     /* Yukawa parameter in unit-box units (0: Laplace) */
+    /* PSWF Yukawa: per level, nodes k_j and weights g_j of
+     * S_l(r) = Phi(r / R_l) / r + sum_j g_j sin(k_j r) / r,
+     * S_l(0) = psi(0) / (c_0 R_l) + sum_j g_j k_j */
+    double (*yk)[YUK_NQ], (*yg)[YUK_NQ];
+    int yn[YUK_LEVELS];
 } split_t;
 
 static double level_R(int l) { return ldexp(1.0, -l); }
 
 static double gauss_sigma(const split_t *sp, int l) { return level_R(l) / sp->prm.delta; }
 
+/* Yukawa: the level-l mollified kernel, the Laplace one plus the radial
+ * quadrature of the difference */
+static double yuk_pswf_S(const split_t *sp, int l, double r)
+{
+    double acc = 0.0, R = level_R(l);
+    if (r == 0.0) {
+        for (int j = 0; j < sp->yn[l]; ++j) acc += sp->yg[l][j] * sp->yk[l][j];
+        return 1.0 / (sp->pswf->c0 * R) + acc;
+    }
+    for (int j = 0; j < sp->yn[l]; ++j) acc += sp->yg[l][j] * sin(sp->yk[l][j] * r);
+    return (pswf_Phi(sp->pswf, r / R) + acc) / r;
+}
+
+static double yuk_gauss_S(double lam, double sg, double r)
+{
+    double a = 0.5 * lam * sg;
+    if (r == 0.0) return 2.0 / (sqrt(M_PI) * sg) * exp(-a * a) - lam * erfc(a);
+    return (exp(-lam * r) * erfc(a - r / sg) - exp(lam * r) * erfc(a + r / sg)) / (2.0 * r);
+}
+
 /* mollified kernel S_l(r); r = 0 gives its finite limit */
 static double split_S(const split_t *sp, int l, double r)
 {
     double R = level_R(l);
+    if (sp->lam > 0.0) {
+        if (sp->prm.splitting == ORACLE_PSWF) return yuk_pswf_S(sp, l, r);
+        return yuk_gauss_S(sp->lam, gauss_sigma(sp, l), r);
+    }
     if (sp->prm.splitting == ORACLE_PSWF) {
         if (r == 0.0) return 1.0 / (sp->pswf->c0 * R); /* psi(0) = 1 */
         return pswf_Phi(sp->pswf, r / R) / r;
@@ -331,10 +396,16 @@ static double split_S(const split_t *sp, int l, double r)
     }
 }
 
-/* residual kernel R_l(r) = 1/r - S_l(r), r > 0 */
+/* residual kernel R_l(r) = K(r) - S_l(r), r > 0 */
 static double split_R(const split_t *sp, int l, double r)
 {
     double R = level_R(l);
+    if (sp->lam > 0.0) {
+        if (sp->prm.splitting == ORACLE_PSWF) return exp(-sp->lam * r) / r - yuk_pswf_S(sp, l, r);
+        /* the closed form, without the cancellation of K - S_l */
+        double sg = gauss_sigma(sp, l), a = 0.5 * sp->lam * sg;
+        return (exp(-sp->lam * r) * erfc(r / sg - a) + exp(sp->lam * r) * erfc(r / sg + a)) / (2.0 * r);
+    }
     if (sp->prm.splitting == ORACLE_PSWF) {
         return (1.0 - pswf_Phi(sp->pswf, r / R)) / r;
     } else {
@@ -362,6 +433,19 @@ static double split_dR(const split_t *sp, int l, double r)
 static double split_Dhat(const split_t *sp, int l, double k)
 {
     double R = level_R(l), R1 = level_R(l + 1);
+    if (sp->lam > 0.0) {
+        /* 4 pi [G_{l+1}(k) - G_l(k)] / (k^2 + lambda^2), G the mollifier in
+         * the variable sqrt(k^2 + lambda^2) */
+        double k2 = k * k + sp->lam * sp->lam, kk = sqrt(k2);
+        if (sp->prm.splitting == ORACLE_PSWF) {
+            const pswf_t *s = sp->pswf;
+            return 4.0 * M_PI * pswf_diff(s, kk * R1 / s->c, kk * R / s->c) / k2;
+        }
+        double s0 = gauss_sigma(sp, l), s1 = gauss_sigma(sp, l + 1);
+        /* e^{-a} - e^{-b} = e^{-a} (1 - e^{a - b}), without cancellation */
+        double a = k2 * s1 * s1 / 4.0, b = k2 * s0 * s0 / 4.0;
+        return 4.0 * M_PI * exp(-a) * (-expm1(a - b)) / k2;
+    }
     if (sp->prm.splitting == ORACLE_PSWF) {
         const pswf_t *s = sp->pswf;
         if (k == 0.0) return 2.0 * M_PI * s->c2 / s->c0 * (R * R - R1 * R1);
@@ -378,6 +462,37 @@ static double split_What(const split_t *sp, double k)
 {
     double Rt = sp->Rt;
     double win;
+    if (sp->lam > 0.0) {
+        double lam = sp->lam, k2 = k * k + lam * lam, kk = sqrt(k2);
+        if (sp->prm.splitting == ORACLE_PSWF) win = pswf_eval(sp->pswf, kk / sp->pswf->c);
+        else { double sg = gauss_sigma(sp, 0); win = exp(-k2 * sg * sg / 4.0); }
+        /* transform of exp(-lambda r)/r truncated at Rt */
+        double tr;
+        if (k == 0.0) {
+            /* 1 - e^{-x} (1 + x) = sum_{n >= 2} (-1)^n (n - 1) x^n / n!  (its
+             * series for small x; -expm1(-x) - x e^{-x} otherwise), x = lambda R_t */
+            double x = lam * Rt, v;
+            if (x < 0.1) {
+                double term = 0.5 * x * x;  /* x^n / n! at n = 2 */
+                v = 0.0;
+                for (int n = 2; n < 20; ++n) {
+                    v += ((n & 1) ? -1.0 : 1.0) * (n - 1) * term;
+                    term *= x / (n + 1);
+                }
+            } else {
+                v = -expm1(-x) - x * exp(-x);
+            }
+            tr = 4.0 * M_PI * v / (lam * lam);
+        }
+        else {
+            /* k - e^{-x} (lambda sin kR_t + k cos kR_t) as a sum without
+             * cancellation: -k expm1(-x) + 2 k e^{-x} sin^2(k R_t / 2) - e^{-x} lambda sin kR_t */
+            double x = lam * Rt, sn = sin(0.5 * k * Rt);
+            double num = -k * expm1(-x) + 2.0 * k * exp(-x) * sn * sn - exp(-x) * lam * sin(k * Rt);
+            tr = 4.0 * M_PI * num / (k * k2);
+        }
+        return tr * win;
+    }
     if (sp->prm.splitting == ORACLE_PSWF) win = pswf_eval(sp->pswf, k / sp->pswf->c);
     else { double sg = gauss_sigma(sp, 0); win = exp(-k * k * sg * sg / 4.0); }
     if (k == 0.0) return 2.0 * M_PI * Rt * Rt * win;
@@ -465,7 +580,57 @@ static int split_init(split_t *sp, const oracle_params *in)
     return 0;
 }
 
-static void split_free(split_t *sp) { free(sp->pswf); sp->pswf = NULL; }
+/* set the Yukawa parameter (unit-box units) and, for the PSWF splitting, the
+ * radial quadrature of every level's mollified kernel */
+static int split_set_lambda(split_t *sp, double lam)
+{
+    sp->lam = lam;
+    if (!(lam > 0.0) || sp->prm.splitting != ORACLE_PSWF) return 0;
+    sp->yk = malloc(sizeof(*sp->yk) * YUK_LEVELS);
+    sp->yg = malloc(sizeof(*sp->yg) * YUK_LEVELS);
+    if (!sp->yk || !sp->yg) return -1;
+    double xg[YUK_NODES], wg[YUK_NODES];
+    gauss_legendre(YUK_NODES, xg, wg);
+    const pswf_t *s = sp->pswf;
+    for (int l = 0; l < YUK_LEVELS; ++l) {
+        double R = level_R(l);
+        /* k from 0 to where sqrt(k^2 + lambda^2) R / c = 4, in panels: the
+         * factor k / (k^2 + lambda^2) varies on the scale lambda near k = 0
+         * (poles at +-i lambda), so the first panels grow geometrically from
+         * width lambda, then regular panels of width kmax / 8 follow */
+        double x4 = 4.0 * s->c / R;
+        double kmax = x4 > lam ? sqrt(x4 * x4 - lam * lam) : 0.0;
+        double pw = kmax / YUK_PANELS;
+        double br[YUK_MAXP + 1];
+        int nb = 0;
+        br[nb++] = 0.0;
+        for (double b = lam; b < pw && nb < YUK_MAXP - YUK_PANELS; b *= 3.0) br[nb++] = b;
+        double b0 = br[nb - 1];
+        for (int q = 1; q <= YUK_PANELS; ++q) br[nb++] = b0 + (kmax - b0) * q / YUK_PANELS;
+        int j = 0;
+        for (int q = 0; q + 1 < nb; ++q) {
+            double a = br[q], h = br[q + 1] - br[q];
+            for (int i = 0; i < YUK_NODES; ++i, ++j) {
+                double k = a + 0.5 * h * (xg[i] + 1.0), w = 0.5 * h * wg[i];
+                double k2 = k * k + lam * lam;
+                sp->yk[l][j] = k;
+                sp->yg[l][j] = 2.0 / M_PI * w *
+                               (pswf_eval(s, sqrt(k2) * R / s->c) * k / k2 - pswf_eval(s, k * R / s->c) / k);
+            }
+        }
+        sp->yn[l] = j;
+    }
+    return 0;
+}
+
+static void split_free(split_t *sp)
+{
+    free(sp->pswf);
+    free(sp->yk);
+    free(sp->yg);
+    sp->pswf = NULL;
+    sp->yk = sp->yg = NULL;
+}
 
 /* ====================================================================== */
 /* 4. O1: direct summation                                                 */
@@ -488,6 +653,34 @@ void oracle_direct(const double *src, const double *rho, int64_t ns,
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 == 0.0) continue;
             double term = rho[j] / sqrt(r2);
+            double t = sum + term;
+            if (fabs(sum) >= fabs(term)) comp += (sum - t) + term;
+            else comp += (term - t) + sum;
+            sum = t;
+        }
+        pot[i] = sum + comp;
+    }
+}
+
+/* O1 for the Yukawa kernel: u_i = sum_{j : y_j != x_i} rho_j exp(-lambda r) / r */
+void oracle_direct_yukawa(const double *src, const double *rho, int64_t ns,
+                          const double *tgt, int64_t nt, double lambda, double *pot, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < nt; ++i) {
+        double sum = 0.0, comp = 0.0;
+        double x = tgt[3 * i], y = tgt[3 * i + 1], z = tgt[3 * i + 2];
+        for (int64_t j = 0; j < ns; ++j) {
+            double dx = x - src[3 * j], dy = y - src[3 * j + 1], dz = z - src[3 * j + 2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            double term = rho[j] * exp(-lambda * r) / r;
             double t = sum + term;
             if (fabs(sum) >= fabs(term)) comp += (sum - t) + term;
             else comp += (term - t) + sum;
@@ -1399,6 +1592,8 @@ int oracle_dmk(const oracle_params *prm_in,
     otree t;
     memset(&t, 0, sizeof(t));
     int rc = points_init(&P, src, rho, ns, tgt, nt);
+    /* exp(-lambda |x - y|) = exp(-(lambda S) |u - v|) in the unit box */
+    if (rc == 0) rc = split_set_lambda(&sp, sp.prm.lambda * P.S);
     if (rc == 0) rc = tree_make(&t, &P, &sp.prm);
     double *ufar = NULL, *unear = NULL;
     if (rc == 0) {
@@ -1431,6 +1626,7 @@ int oracle_dmk_grad(const oracle_params *prm_in,
 {
     if (ns < 0 || nt < 0) return -1;
     if (nt == 0) return 0;
+    if (prm_in->lambda != 0.0) return -1; /* gradients: Laplace kernel only */
     split_t sp;
     if (split_init(&sp, prm_in) != 0) return -1;
 #ifdef _OPENMP
@@ -1537,6 +1733,7 @@ void oracle_kernel(const oracle_params *prm, int what, int level,
 {
     split_t sp;
     if (split_init(&sp, prm) != 0) return;
+    if (split_set_lambda(&sp, prm->lambda) != 0) { split_free(&sp); return; }
     for (int64_t i = 0; i < n; ++i) {
         double x = r[i];
         switch (what) {

@@ -10,6 +10,7 @@
  * (Sec. 3.4, Steps 0-5) with plain loops in double precision.
  *
  * Kernel: the 3D Laplace kernel 1/r without the 1/(4 pi) factor (eq. laplacesum),
+ * or the Yukawa kernel exp(-lambda r) / r (Sec. 3.7, oracle_params.lambda > 0);
  * coincident source/target pairs contribute zero (Sec. 3.1 self-interaction
  * remark).
  *
@@ -51,6 +52,8 @@ typedef struct {
     double gauss_b;    /* Gaussian: window parameter b of Lemma trunc_lemma */
     int max_level;     /* deepest level a box may have (<= 21) */
     int nthreads;      /* OpenMP threads (0 = runtime default) */
+    double lambda;     /* Yukawa kernel exp(-lambda r) / r when > 0 (input units;
+                          oracle_kernel takes it in unit-box units); 0: 1 / r */
 } oracle_params;
 
 /* Fill defaults from eps / splitting; fields already > 0 are kept. */
@@ -60,6 +63,10 @@ void oracle_default_params(oracle_params *prm);
  * (Neumaier) summation.  Coordinates row-major [n][3]. */
 void oracle_direct(const double *src, const double *rho, int64_t ns,
                    const double *tgt, int64_t nt, double *pot, int nthreads);
+
+/* O1 for the Yukawa kernel exp(-lambda r) / r (Sec. 3.7), same conventions. */
+void oracle_direct_yukawa(const double *src, const double *rho, int64_t ns,
+                          const double *tgt, int64_t nt, double lambda, double *pot, int nthreads);
 
 /* O2: the plain DMK pass.  tgt may be the same pointer as src (with nt == ns),
  * in which case every point is both a source and a target.  pot_far / pot_near
