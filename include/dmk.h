@@ -47,8 +47,10 @@ typedef enum {
 
 /* ---- kernels and precision ---------------------------------------------- */
 typedef enum {
-    DMK_LAPLACE = 0,       /* 1/r in 3D (Sec. 3); the only kernel implemented */
-    DMK_YUKAWA = 1,        /* reserved: exp(-lambda r)/r (Sec. 4) */
+    DMK_LAPLACE = 0,       /* 1/r in 3D (Sec. 3) */
+    DMK_YUKAWA = 1,        /* exp(-lambda r)/r in 3D, lambda = opts.kernel_param > 0,
+                              split in Fourier space (Sec. 3.7); no batches, no
+                              gradients */
     DMK_LOG2D = 2,         /* reserved: log r in 2D (Sec. 4) */
     DMK_SQRTLAPLACE = 3    /* reserved: 1/r^2 in 3D (Sec. 4) */
 } dmk_kernel;
@@ -75,7 +77,7 @@ typedef struct {
     int leaf_cap;        /* n_s: a box with more points is subdivided
                             (default 280 at eps >= 1e-6, 800 below, Sec. 5.1.1) */
     int precision;       /* dmk_precision (default DMK_FP64) */
-    double kernel_param; /* reserved (Yukawa lambda) */
+    double kernel_param; /* DMK_YUKAWA: lambda > 0, in the units of the points */
     int flags;           /* DMK_FLAG_* */
     int max_level;       /* deepest tree level, 1..20 (default 20) */
     int p;               /* override: Chebyshev order per dimension (Table 1) */
@@ -273,6 +275,18 @@ DMK_API int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out);
  *   3  residual polynomial: Chebyshev coefficients of q(t) = Phi(sqrt t)/sqrt t
  *      on t in [0, 1] */
 DMK_API int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len);
+
+/* Yukawa tables of a DMK_YUKAWA plan at a unit-box lambda (the library uses
+ * lambda S, S the largest extent of the points): which
+ *   0  translation weights w_l(s), s = |m|^2 = 0..3 nf^2, of the given level
+ *      (eqs. yukawaPSWFkernels, wlmdef: (h_l / 2 pi)^3 Dhat_l(h_l |m|))
+ *   1  root weights wW(s), s = 0..3 n0^2 (windowed kernel, eq. windowedkernelft2
+ *      with the transform of exp(-lambda r)/r truncated at R_t)
+ *   2  residual polynomial of the given level, monomials in 2 t - 1 with
+ *      t = r^2 / R_l^2 (degree <= 62): the mollified kernel is S_l(r) = q_l(t) / R_l
+ * Works on host-only plans (no device).  Arguments as in dmk_plan_get_table. */
+DMK_API int dmk_plan_get_yukawa_table(dmk_plan_t plan, double lambda_unit, int level, int which, double *out,
+                                      int64_t n, int64_t *len);
 
 /* Statistics of the last dmk_eval. */
 typedef struct {

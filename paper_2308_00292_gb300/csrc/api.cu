@@ -40,7 +40,10 @@ struct dmk_plan_s {
     int precision = 0;
     int leaf_cap = 280, max_level = 20;
     int qdeg = 0;
+    double lambda = 0.0;        // Yukawa parameter (input units), 0 for Laplace
+    dmk::YukawaTables yt;       // Yukawa tables at the last unit-box lambda
     dmk::Workspace ws;
+    dmk::DBuf ytab;             // their device copy (working precision)
     dmk::DBuf tab;  // device tables (working precision)
     dmk::DevTables<double> dt_d{};
     dmk::DevTables<float> dt_f{};
@@ -108,6 +111,35 @@ int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
     return DMK_OK;
 }
 
+// per-evaluation tables of the Yukawa kernel at the unit-box lambda S
+template <typename T>
+int upload_yukawa(dmk_plan_s *pl, dmk::DevTables<T> &dt, double lam_unit, int nlev) {
+    if (pl->yt.lam != lam_unit || pl->yt.nlev < nlev) {
+        std::string err;
+        if (dmk::build_yukawa_tables(pl->tb, lam_unit, nlev, pl->yt, err) != 0)
+            return fail(DMK_ERR_UNSUPPORTED, err);
+        std::vector<T> h;
+        auto push = [&](const std::vector<double> &v) {
+            size_t off = h.size();
+            for (double x : v) h.push_back((T)x);
+            while (h.size() % 32) h.push_back((T)0);
+            return off;
+        };
+        const size_t ow = push(pl->yt.wl), oW = push(pl->yt.wW), oq = push(pl->yt.qmono);
+        if (pl->ws.ensure(pl->ytab, (int64_t)h.size() * sizeof(T)))
+            return fail(DMK_ERR_OOM, "device allocation failed (Yukawa tables)");
+        if (cudaMemcpy(pl->ytab.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "copying the Yukawa tables to the device failed");
+        const T *base = (const T *)pl->ytab.p;
+        dt.wl = base + ow;
+        dt.wW = base + oW;
+        dt.ql = base + oq;
+        dt.lam = (T)lam_unit;
+        dt.qdeg = pl->yt.qdeg;
+    }
+    return DMK_OK;
+}
+
 bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 19 || p == 28 || p == 38; }
 
 int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
@@ -133,6 +165,15 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     int rc = pl->tree->build(src, ns, q, same ? nullptr : tgt, same ? 0 : nt, same, pl->leaf_cap, pl->max_level,
                              single ? 1 : 0, st, err, nsys, h_off);
     if (rc) return fail(rc, "tree: " + err);
+    if (pl->kernel == DMK_YUKAWA) {
+        if (nsys > 1) return fail(DMK_ERR_UNSUPPORTED, "Yukawa batches: every system has its own lambda S");
+        if (grad) return fail(DMK_ERR_UNSUPPORTED, "the Yukawa kernel has no gradient pass");
+        // exp(-lambda |x - y|) = exp(-(lambda S) |u - v|) in the unit box
+        const double lam_unit = pl->lambda * pl->tree->h_frame.S;
+        rc = single ? upload_yukawa<float>(pl, pl->dt_f, lam_unit, pl->tree->nlev)
+                    : upload_yukawa<double>(pl, pl->dt_d, lam_unit, pl->tree->nlev);
+        if (rc) return rc;
+    }
     dmk::PassCtx cx{};
     cx.tree = pl->tree.get();
     cx.bufs = &pl->bufs;
@@ -235,10 +276,13 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     if (!out) return fail(DMK_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!(eps >= 1e-12 && eps <= 1e-2)) return fail(DMK_ERR_INVALID_ARG, "eps must lie in [1e-12, 1e-2]");
-    if (kernel != DMK_LAPLACE) return fail(DMK_ERR_UNSUPPORTED, "only DMK_LAPLACE is implemented");
-    if (dim != 3) return fail(DMK_ERR_UNSUPPORTED, "DMK_LAPLACE is implemented in 3 dimensions");
+    if (kernel != DMK_LAPLACE && kernel != DMK_YUKAWA)
+        return fail(DMK_ERR_UNSUPPORTED, "only DMK_LAPLACE and DMK_YUKAWA are implemented");
+    if (dim != 3) return fail(DMK_ERR_UNSUPPORTED, "the kernels are implemented in 3 dimensions");
     dmk_opts o{};
     if (opts) o = *opts;
+    if (kernel == DMK_YUKAWA && !(o.kernel_param > 0.0 && std::isfinite(o.kernel_param)))
+        return fail(DMK_ERR_INVALID_ARG, "DMK_YUKAWA needs kernel_param = lambda > 0");
     if (o.leaf_cap < 0 || o.precision < 0 || o.precision > 1 || o.max_level < 0 || o.max_level > dmk::kMaxLevel ||
         o.nf < 0 || o.nf > dmk::kMaxNf || !valid_p(o.p) || (o.flags & ~7))
         return fail(DMK_ERR_INVALID_ARG, "option out of range");
@@ -247,6 +291,7 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     std::unique_ptr<dmk_plan_s> pl(new (std::nothrow) dmk_plan_s());
     if (!pl) return fail(DMK_ERR_OOM, "host allocation failed");
     pl->kernel = kernel;
+    pl->lambda = kernel == DMK_YUKAWA ? o.kernel_param : 0.0;
     pl->dim = dim;
     pl->eps = eps;
     pl->opts = o;
@@ -260,6 +305,9 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     if (o.precision == DMK_MIXED && eps < 1e-7) return fail(DMK_ERR_UNSUPPORTED, "DMK_MIXED needs eps >= 1e-7");
     int p_req = o.p;
     if (p_req == 0 && o.precision == DMK_MIXED && eps < 1e-3 * (1 - 1e-12)) p_req = 19;
+    // the Yukawa kernel at the 1e-6 row: p = 18 leaves its far field at ~1.0 eps
+    // (lambda S = 10, uniform points), p = 19 at ~0.8 eps
+    if (p_req == 0 && kernel == DMK_YUKAWA && eps < 1e-3 * (1 - 1e-12) && eps >= 1e-6 * (1 - 1e-12)) p_req = 19;
     if (dmk::build_tables(eps, p_req, o.nf, pl->tb, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
     pl->qdeg = (int)pl->tb.qmono.size() - 1;
     if (pl->qdeg >= 64) return fail(DMK_ERR_INTERNAL, "residual polynomial degree above 63");
@@ -493,6 +541,34 @@ int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64
         break;
     case 3: v = plan->tb.qcheb; break;
     default: return fail(DMK_ERR_INVALID_ARG, "unknown table");
+    }
+    *len = (int64_t)v.size();
+    if (out) {
+        if (n < (int64_t)v.size()) return fail(DMK_ERR_INVALID_ARG, "output too small");
+        std::memcpy(out, v.data(), v.size() * sizeof(double));
+    }
+    return DMK_OK;
+}
+
+int dmk_plan_get_yukawa_table(dmk_plan_t plan, double lambda_unit, int level, int which, double *out, int64_t n,
+                              int64_t *len) {
+    if (!plan || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (plan->kernel != DMK_YUKAWA) return fail(DMK_ERR_INVALID_ARG, "not a DMK_YUKAWA plan");
+    if (!(lambda_unit > 0.0) || level < 0 || level > dmk::kMaxLevel || which < 0 || which > 2)
+        return fail(DMK_ERR_INVALID_ARG, "argument out of range");
+    dmk::YukawaTables yt;
+    std::string err;
+    if (dmk::build_yukawa_tables(plan->tb, lambda_unit, level + 1, yt, err) != 0)
+        return fail(DMK_ERR_UNSUPPORTED, err);
+    const int ns = 3 * plan->tb.nf * plan->tb.nf + 1;
+    std::vector<double> v;
+    if (which == 0) v.assign(yt.wl.begin() + (size_t)level * ns, yt.wl.begin() + (size_t)(level + 1) * ns);
+    else if (which == 1) v = yt.wW;
+    else {
+        // the level's own degree, without its header
+        const size_t row = (size_t)level * (yt.qdeg + 2);
+        const int dg = (int)yt.qmono[row];
+        v.assign(yt.qmono.begin() + row + 1, yt.qmono.begin() + row + 2 + dg);
     }
     *len = (int64_t)v.size();
     if (out) {

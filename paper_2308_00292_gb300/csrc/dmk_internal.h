@@ -28,6 +28,7 @@ struct Pswf {
     double operator()(double x) const;   // psi_0^c(x), psi(0) = 1
     double Phi(double s) const;          // c_0^{-1} int_0^s psi (1 for s >= 1)
     double eval_inside(double x) const;  // Legendre series, |x| <= 1
+    double diff(double x1, double x2) const;  // psi(x1) - psi(x2) without cancellation
     double c, chi0 = 0, lambda0 = 0, c0 = 0, c2 = 0;
     std::vector<double> coef, qx, qw, qpsi;
 };
@@ -39,6 +40,19 @@ struct Tables {
 };
 
 int build_tables(double eps, int p_override, int nf_override, Tables &tb, std::string &err);
+
+// Yukawa kernel exp(-lambda r)/r (Sec. 3.7, Fourier-space splitting) at a
+// unit-box lambda: level-dependent translation weights w_l(|m|^2) (not scaled
+// by 1/R_l), root weights wW(|m|^2) and residual polynomials q_l, monomials in
+// 2 t - 1, t = r^2 / R_l^2, with S_l(r) = q_l(t) / R_l; row l of qmono is
+// [degree of level l, c_0 .. c_qdeg] (zero padded), qdeg the largest degree.
+constexpr int kMaxYukawaDegree = 62;
+struct YukawaTables {
+    double lam = -1.0;
+    int nlev = 0, qdeg = 0;
+    std::vector<double> wl, wW, qmono;  // [nlev][3 nf^2 + 1], [3 n0^2 + 1], [nlev][qdeg + 2]
+};
+int build_yukawa_tables(const Tables &tb, double lam, int nlev, YukawaTables &yt, std::string &err);
 
 // ---------------------------------------------------------------- device views
 // Plan tables on the device, in the working precision T.
@@ -53,6 +67,12 @@ struct DevTables {
     const T *w;              // [3 nf^2 + 1], at R = 1
     const T *wW;             // [3 n0^2 + 1]
     const T *qmono;          // [qdeg + 1], q(t) = sum qmono[k] (2t-1)^k
+    // Yukawa kernel (null / 0 for Laplace): per-level translation weights
+    // [nlev][3 nf^2 + 1] (already including 1/R_l), per-level residual
+    // polynomials [nlev][qdeg + 1], lambda in unit-box units
+    const T *wl;
+    const T *ql;
+    T lam;
 };
 
 // Box flags

@@ -82,6 +82,11 @@ __device__ __forceinline__ float inv_radius(float thr) {
 __device__ __forceinline__ double inv_radius(double thr) {
     return __longlong_as_double((long long)(1023 + (int)(__double_as_longlong(thr) & 31)) << 52);
 }
+__device__ __forceinline__ int packed_level(float thr) { return __float_as_int(thr) & 31; }
+__device__ __forceinline__ int packed_level(double thr) { return (int)(__double_as_longlong(thr) & 31); }
+template <typename T> __device__ __forceinline__ T exp_t(T x);
+template <> __device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 
 // screening of 32 staged sources k = u0 + sub + G i against this lane's
 // target: bit i set when |t - s|^2 < R_b^2 (1 + 2^-9), with the difference
@@ -110,12 +115,18 @@ __device__ __forceinline__ unsigned screen_g(const typename Vec4<T>::type *sh, i
                                : screen_unit<T, G, false>(sh, u0, sub, fill, t2x, t2y, t2z, ntt);
 }
 
-template <typename T, int QD, bool GRAD>
+// YUK: the Yukawa kernel exp(-lam r)/r, whose residual polynomial depends on
+// the level (the kernel is not scale invariant): the per-level rows
+// [degree, c_0 .. c_qdeg] (stride qdeg + 2) sit in shared memory after the
+// warps' areas, and the degrees are run-time values (one instantiation per
+// precision)
+template <typename T, int QD, bool GRAD, bool YUK>
 __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, const int32_t *tleaves,
                                                        const int32_t *nl_off, const int32_t *nl_src,
                                                        const typename Vec4<T>::type *__restrict__ plocal,
                                                        const float4 *__restrict__ plocal_lo, const T *qmono,
-                                                       int qdeg, double *unear, double *gnear, int *counter) {
+                                                       int qdeg, int nlev, T lam, double *unear, double *gnear,
+                                                       int *counter) {
     using V4 = typename Vec4<T>::type;
     constexpr bool kHiLo = sizeof(T) == 4;
     constexpr unsigned FULL = 0xffffffffu;
@@ -123,9 +134,15 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
     NearWarpT<T, GRAD> &W = reinterpret_cast<NearWarpT<T, GRAD> *>(nsm)[threadIdx.x >> 5];
     // residual polynomial coefficients in registers (degree QD known at compile time)
     T qc[QD + 1];
+    T *s_q = reinterpret_cast<T *>(nsm + (kNearThreads / 32) * sizeof(NearWarpT<T, GRAD>));
+    if constexpr (YUK) {
+        for (int i = threadIdx.x; i < nlev * (qdeg + 2); i += kNearThreads) s_q[i] = qmono[i];
+        __syncthreads();
+    } else {
 #pragma unroll
-    for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
-    (void)qdeg;
+        for (int d = 0; d <= QD; ++d) qc[d] = qmono[d];
+    }
+    (void)lam;
     const int lane = threadIdx.x & 31;
     const T kBig = (T)1e30;
     // pairs inside the support of the residual kernel (statistics); the
@@ -333,15 +350,25 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                             const T iR = inv_radius(y.w), iR2 = iR * iR;
                             const T r2 = dx * dx + dy * dy + dz * dz;
                             const T xx = (T)2 * r2 * iR2 - (T)1;  // r < R_b  <=>  xx < 1
-                            T qv = qc[QD], dq = 0;
+                            T qv, dq = 0;
+                            if constexpr (YUK) {
+                                const T *qr = s_q + packed_level(y.w) * (qdeg + 2);
+                                const int dg = (int)qr[0];
+                                qv = qr[1 + dg];
+                                for (int d = dg - 1; d >= 0; --d) qv = qv * xx + qr[1 + d];
+                            } else {
+                                qv = qc[QD];
 #pragma unroll
-                            for (int d = QD - 1; d >= 0; --d) {
-                                if constexpr (GRAD) dq = dq * xx + qv;
-                                qv = qv * xx + qc[d];
+                                for (int d = QD - 1; d >= 0; --d) {
+                                    if constexpr (GRAD) dq = dq * xx + qv;
+                                    qv = qv * xx + qc[d];
+                                }
                             }
                             const T rinv = r2 > (T)0 ? rsqrt_t<T>(r2) : (T)0;
                             const bool in = xx < (T)1;
-                            const T val = in ? qj * (rinv - qv * iR) : (T)0;
+                            T kern = rinv;
+                            if constexpr (YUK) kern = exp_t<T>(-lam * r2 * rinv) * rinv;
+                            const T val = in ? qj * (kern - qv * iR) : (T)0;
                             inside32 += in ? 1u : 0u;
                             part += val;
                             if constexpr (GRAD) {
@@ -403,16 +430,18 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
 }
 
 // launch k_near with the residual polynomial degree as a template argument;
-// returns 1 for a degree outside 2..30, 2 for a failed launch
-template <typename T, int QD, bool GRAD>
+// returns 1 for a degree outside 2..30, 2 for a failed launch, 3 for an
+// unsupported combination (the Yukawa kernel with gradients)
+template <typename T, int QD, bool GRAD, bool YUK>
 static cudaError_t launch_near_qd(int grid, cudaStream_t st, const NearArgs &a) {
-    constexpr size_t smem = (size_t)(kNearThreads / 32) * sizeof(NearWarpT<T, GRAD>);
+    const size_t smem = (size_t)(kNearThreads / 32) * sizeof(NearWarpT<T, GRAD>) +
+                        (YUK ? (size_t)a.nlev * (a.qdeg + 2) * sizeof(T) : 0);
     cudaError_t e =
-        cudaFuncSetAttribute(k_near<T, QD, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_near<T, QD, GRAD, YUK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_near<T, QD, GRAD><<<grid, kNearThreads, smem, st>>>(
+    k_near<T, QD, GRAD, YUK><<<grid, kNearThreads, smem, st>>>(
         a.tv, a.ntl, a.tleaves, a.nl_off, a.nl_src, (const typename Vec4<T>::type *)a.plocal, a.plocal_lo,
-        (const T *)a.qmono, QD, a.unear, a.gnear, a.counter);
+        (const T *)a.qmono, a.qdeg, a.nlev, (T)a.lam, a.unear, a.gnear, a.counter);
     return cudaGetLastError();
 }
 
@@ -421,7 +450,7 @@ static int launch_near_t(int grid, cudaStream_t st, const NearArgs &a) {
     switch (a.qdeg) {
 #define DMK_NEAR_CASE(d) \
     case d: \
-        return launch_near_qd<T, d, GRAD>(grid, st, a) == cudaSuccess ? 0 : 2;
+        return launch_near_qd<T, d, GRAD, false>(grid, st, a) == cudaSuccess ? 0 : 2;
         DMK_NEAR_CASE(2) DMK_NEAR_CASE(3) DMK_NEAR_CASE(4) DMK_NEAR_CASE(5) DMK_NEAR_CASE(6) DMK_NEAR_CASE(7)
         DMK_NEAR_CASE(8) DMK_NEAR_CASE(9) DMK_NEAR_CASE(10) DMK_NEAR_CASE(11) DMK_NEAR_CASE(12) DMK_NEAR_CASE(13)
         DMK_NEAR_CASE(14) DMK_NEAR_CASE(15) DMK_NEAR_CASE(16) DMK_NEAR_CASE(17) DMK_NEAR_CASE(18) DMK_NEAR_CASE(19)
@@ -441,6 +470,13 @@ int launch_near(bool single, const NearArgs &a, int num_sms, cudaStream_t st) {
     if (grid <= 0) return 0;
     ::dmk::launch_tick();
     const bool grad = a.gnear != nullptr;
+    if (a.yukawa) {
+        if (grad || a.nlev < 1 || a.nlev > kMaxLevel + 1) return 3;
+        if (a.qdeg < 2 || a.qdeg > kMaxYukawaDegree) return 1;
+        const cudaError_t e = single ? launch_near_qd<float, 2, false, true>(grid, st, a)
+                                     : launch_near_qd<double, 2, false, true>(grid, st, a);
+        return e == cudaSuccess ? 0 : 2;
+    }
     if (single) return grad ? launch_near_t<float, true>(grid, st, a) : launch_near_t<float, false>(grid, st, a);
     return grad ? launch_near_t<double, true>(grid, st, a) : launch_near_t<double, false>(grid, st, a);
 }

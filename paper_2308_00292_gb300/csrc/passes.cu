@@ -1275,7 +1275,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                         for (int h = 0; h < 2; ++h) {
                             const int mz = mz0 + h;
                             if (mz >= NH) continue;
-                            const T w = tb.w[mxp * mxp + myv * myv + mz * mz] * invR;
+                            const int sq = mxp * mxp + myv * myv + mz * mz;
+                            const T w = tb.wl ? tb.wl[(size_t)level * (3 * NF * NF + 1) + sq] : tb.w[sq] * invR;
                             // S0 + omega S1 + omega^2 S2 = T - 1.5 U + i (sqrt3/2) D
                             const C2 psp{w * (Tp[h].x - (T)1.5 * Up[h].x - kH * Dp[h].y),
                                          w * (Tp[h].y - (T)1.5 * Up[h].y + kH * Dp[h].x)};
@@ -1661,13 +1662,17 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                     (const int32_t *)cx.tree->nl_src.p,
                     cx.tree->plocal.p,
                     (const float4 *)cx.tree->plocal_lo.p,
-                    tb.qmono,
+                    tb.ql ? (const void *)tb.ql : (const void *)tb.qmono,
                     tb.qdeg,
                     unear,
                     gnear,
-                    (int *)cx.bufs->counter.p};
+                    (int *)cx.bufs->counter.p,
+                    tb.ql != nullptr,
+                    (double)tb.lam,
+                    tv.nlev};
         int rc_near = launch_near(sizeof(T) == 4, na, cx.num_sms, cx.side);
         if (rc_near == 1) { err = "residual polynomial degree outside 2..30"; return DMK_ERR_UNSUPPORTED; }
+        if (rc_near == 3) { err = "the Yukawa near field has no gradient pass"; return DMK_ERR_UNSUPPORTED; }
         if (rc_near) { err = "near-field launch failed"; return DMK_ERR_CUDA; }
         PCK(cudaGetLastError());
     }

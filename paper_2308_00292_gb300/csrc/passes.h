@@ -48,10 +48,14 @@ struct NearArgs {
     const int32_t *tleaves, *nl_off, *nl_src;
     const void *plocal;         // float4 or double4 leaf-local points
     const float4 *plocal_lo;    // single precision: lo parts
-    const void *qmono;          // residual polynomial, monomial coefficients (float or double)
+    const void *qmono;          // residual polynomial, monomial coefficients (float or double);
+                                // per level [nlev][qdeg + 1] for the Yukawa kernel
     int qdeg;
     double *unear, *gnear;
     int *counter;
+    bool yukawa;                // kernel exp(-lam r)/r with per-level polynomials
+    double lam;                 // unit-box lambda (Yukawa)
+    int nlev;                   // levels of the per-level table
 };
 int launch_near(bool single, const NearArgs &a, int num_sms, cudaStream_t st);
 

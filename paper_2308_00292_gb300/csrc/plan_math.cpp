@@ -176,6 +176,16 @@ double Pswf::operator()(double x) const {
     return acc / lambda0;
 }
 
+// psi(x1) - psi(x2) = lambda_0^{-1} int psi(t) (cos c x1 t - cos c x2 t) dt with
+// cos a - cos b = -2 sin((a + b)/2) sin((a - b)/2): no cancellation when both
+// arguments are small
+double Pswf::diff(double x1, double x2) const {
+    double acc = 0.0;
+    for (size_t i = 0; i < qx.size(); ++i)
+        acc += qw[i] * qpsi[i] * std::sin(0.5 * c * (x1 + x2) * qx[i]) * std::sin(0.5 * c * (x1 - x2) * qx[i]);
+    return -2.0 * acc / lambda0;
+}
+
 // Phi(s) = c_0^{-1} int_0^s psi, by Gauss-Legendre quadrature on [0, s].
 double Pswf::Phi(double s) const {
     if (s >= 1.0) return 1.0;
@@ -186,6 +196,46 @@ double Pswf::Phi(double s) const {
     for (size_t i = 0; i < gx.size(); ++i) acc += gw[i] * eval_inside(0.5 * s * (gx[i] + 1.0));
     return 0.5 * s * acc / c0;
 }
+
+// ---- Chebyshev fits -----------------------------------------------------------
+namespace {
+// Chebyshev coefficients of f on t in [0, 1] from its values at the 64 points
+// t_j = (1 + cos(pi (j + 1/2) / 64)) / 2, truncated where the tail falls below tol
+std::vector<double> cheb_fit(const std::vector<double> &vals, double tol) {
+    const int nc = (int)vals.size();
+    std::vector<double> ch(nc, 0.0);
+    for (int k = 0; k < nc; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < nc; ++j) acc += vals[j] * std::cos(M_PI * k * (j + 0.5) / nc);
+        ch[k] = acc * (k == 0 ? 1.0 : 2.0) / nc;
+    }
+    int deg = nc - 1;
+    double tail = 0.0;
+    while (deg > 2 && tail + std::fabs(ch[deg]) < tol) { tail += std::fabs(ch[deg]); --deg; }
+    ch.resize(deg + 1);
+    return ch;
+}
+
+// monomial coefficients in x = 2t - 1 of a Chebyshev series (for Horner)
+std::vector<double> cheb_to_mono(const std::vector<double> &ch) {
+    const int deg = (int)ch.size() - 1;
+    std::vector<double> mono(deg + 1, 0.0), Tm2(deg + 1, 0.0), Tm1(deg + 1, 0.0), Tc(deg + 1, 0.0);
+    Tm2[0] = 1.0;
+    mono[0] += ch[0];
+    if (deg >= 1) { Tm1[1] = 1.0; mono[1] += ch[1]; }
+    for (int k = 2; k <= deg; ++k) {
+        std::fill(Tc.begin(), Tc.end(), 0.0);
+        for (int i = 0; i < k; ++i) Tc[i + 1] += 2.0 * Tm1[i];
+        for (int i = 0; i <= k - 2; ++i) Tc[i] -= Tm2[i];
+        for (int i = 0; i <= k; ++i) mono[i] += ch[k] * Tc[i];
+        Tm2 = Tm1;
+        Tm1 = Tc;
+    }
+    return mono;
+}
+
+double cheb_node01(int j, int nc) { return 0.5 * (std::cos(M_PI * (j + 0.5) / nc) + 1.0); }
+}  // namespace
 
 // ---- plan tables ------------------------------------------------------------
 int build_tables(double eps, int p_override, int nf_override, Tables &tb, std::string &err) {
@@ -312,41 +362,175 @@ int build_tables(double eps, int p_override, int nf_override, Tables &tb, std::s
     // target accuracy
     {
         const int nc = 64;
-        std::vector<double> vals(nc), ch(nc, 0.0);
+        std::vector<double> vals(nc);
         for (int j = 0; j < nc; ++j) {
-            double x = std::cos(M_PI * (j + 0.5) / nc);
-            double t = 0.5 * (x + 1.0);
-            double s = std::sqrt(t);
+            double s = std::sqrt(cheb_node01(j, nc));
             vals[j] = (s == 0.0) ? tb.psi0_over_c0 : psi.Phi(s) / s;
-        }
-        for (int k = 0; k < nc; ++k) {
-            double acc = 0.0;
-            for (int j = 0; j < nc; ++j) acc += vals[j] * std::cos(M_PI * k * (j + 0.5) / nc);
-            ch[k] = acc * (k == 0 ? 1.0 : 2.0) / nc;
         }
         double tol = 1e-3 * eps * tb.psi0_over_c0;
         tol = std::max(tol, 1e-15 * tb.psi0_over_c0);
-        int deg = nc - 1;
-        double tail = 0.0;
-        while (deg > 2 && tail + std::fabs(ch[deg]) < tol) { tail += std::fabs(ch[deg]); --deg; }
-        tb.qcheb.assign(ch.begin(), ch.begin() + deg + 1);
-        // monomial form in x = 2t - 1 for Horner evaluation on the device
-        std::vector<double> mono(deg + 1, 0.0), Tm2(deg + 1, 0.0), Tm1(deg + 1, 0.0), Tc(deg + 1, 0.0);
-        Tm2[0] = 1.0;
-        mono[0] += tb.qcheb[0];
-        if (deg >= 1) { Tm1[1] = 1.0; mono[1] += tb.qcheb[1]; }
-        for (int k = 2; k <= deg; ++k) {
-            std::fill(Tc.begin(), Tc.end(), 0.0);
-            for (int i = 0; i < k; ++i) Tc[i + 1] += 2.0 * Tm1[i];
-            for (int i = 0; i <= k - 2; ++i) Tc[i] -= Tm2[i];
-            for (int i = 0; i <= k; ++i) mono[i] += tb.qcheb[k] * Tc[i];
-            Tm2 = Tm1;
-            Tm1 = Tc;
-        }
-        tb.qmono = mono;
+        tb.qcheb = cheb_fit(vals, tol);
+        tb.qmono = cheb_to_mono(tb.qcheb);
     }
     tb.psi_grid.resize(257);
     for (int k = 0; k <= 256; ++k) tb.psi_grid[k] = psi(k / 64.0);
+    return 0;
+}
+
+
+// ---- Yukawa kernel (Sec. 3.7) ------------------------------------------------
+// The Fourier-space splitting replaces k by sqrt(k^2 + lambda^2) in the
+// mollifier psi(k R_l / c) / psi(0) and divides by k^2 + lambda^2:
+//   Dhat_l(k) = 4 pi [psi(kk R_{l+1} / c) - psi(kk R_l / c)] / kk^2,  kk^2 = k^2 + lambda^2,
+//   What_0(k) = psi(kk / c) That(k),  That the transform of exp(-lambda r)/r cut at R_t,
+//   S_l(r)    = 2 / (pi r) int_0^inf psi(kk R_l / c) k sin(k r) / kk^2 dk.
+// S_l is evaluated as the Laplace mollifier Phi(r / R_l) / r (its lambda = 0
+// value) plus the radial transform of the difference of the integrands, which
+// decays fast; the residual is R_l(r) = exp(-lambda r) / r - S_l(r).
+namespace {
+// psi on [0, X] as a Chebyshev interpolant (psi itself beyond X)
+struct PsiProxy {
+    const Pswf &psi;
+    double X;
+    std::vector<double> a;
+    PsiProxy(const Pswf &p, double xmax) : psi(p), X(xmax) {
+        const int n = std::min(1024, (int)(0.6 * p.c * X) + 100);
+        std::vector<double> f(n);
+        for (int j = 0; j < n; ++j) f[j] = psi(0.5 * X * (std::cos(M_PI * (j + 0.5) / n) + 1.0));
+        a.assign(n, 0.0);
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += f[j] * std::cos(M_PI * k * (j + 0.5) / n);
+            a[k] = acc * (k == 0 ? 1.0 : 2.0) / n;
+        }
+    }
+    double operator()(double x) const {
+        x = std::fabs(x);
+        if (x > X) return psi(x);
+        const double u = 2.0 * x / X - 1.0;
+        double b1 = 0.0, b2 = 0.0;  // Clenshaw
+        for (int k = (int)a.size() - 1; k >= 1; --k) {
+            const double b0 = 2.0 * u * b1 - b2 + a[k];
+            b2 = b1;
+            b1 = b0;
+        }
+        return u * b1 - b2 + a[0];
+    }
+    // psi(x1) - psi(x2); the eigen-relation form where both are small
+    double diff(double x1, double x2) const {
+        if (std::max(std::fabs(x1), std::fabs(x2)) < 0.25) return psi.diff(x1, x2);
+        return (*this)(x1) - (*this)(x2);
+    }
+};
+
+// 1 - e^{-x} (1 + x) without cancellation
+double one_minus_exp_1px(double x) {
+    if (x < 0.1) {
+        double term = 0.5 * x * x, v = 0.0;
+        for (int n = 2; n < 20; ++n) {
+            v += ((n & 1) ? -1.0 : 1.0) * (n - 1) * term;
+            term *= x / (n + 1);
+        }
+        return v;
+    }
+    return -std::expm1(-x) - x * std::exp(-x);
+}
+}  // namespace
+
+int build_yukawa_tables(const Tables &tb, double lam, int nlev, YukawaTables &yt, std::string &err) {
+    if (!(lam > 0.0) || nlev < 1 || nlev > kMaxLevel + 1) { err = "Yukawa tables: bad lambda or level count"; return -1; }
+    Pswf psi(tb.c);
+    const double c = tb.c;
+    const int nf = tb.nf, ns = 3 * nf * nf + 1, n0 = tb.n0, nsW = 3 * n0 * n0 + 1;
+    // largest psi argument: translation weights, root weights, quadrature
+    double X = 4.5;
+    X = std::max(X, std::sqrt((4.0 * M_PI * M_PI / 9.0) * (ns - 1) + lam * lam) / c);
+    X = std::max(X, std::sqrt(tb.hW * tb.hW * (nsW - 1) + lam * lam) / c);
+    X = std::min(X, 40.0);
+    PsiProxy ps(psi, X);
+
+    yt.lam = lam;
+    yt.nlev = nlev;
+    // translation weights (h_l / 2 pi)^3 Dhat_l(h_l |m|), h_l = 2 pi / (3 R_l)
+    yt.wl.assign((size_t)nlev * ns, 0.0);
+    for (int l = 0; l < nlev; ++l) {
+        const double R = std::ldexp(1.0, -l);
+        const double h = 2.0 * M_PI / (3.0 * R), sc = std::pow(1.0 / (3.0 * R), 3);
+        for (int s = 0; s < ns; ++s) {
+            const double k2 = h * h * s + lam * lam, kk = std::sqrt(k2);
+            yt.wl[(size_t)l * ns + s] = sc * 4.0 * M_PI * ps.diff(0.5 * kk * R / c, kk * R / c) / k2;
+        }
+    }
+    // root weights
+    const double Rt = 1.0 + std::sqrt(3.0), scW = std::pow(tb.hW / (2.0 * M_PI), 3);
+    yt.wW.assign(nsW, 0.0);
+    for (int s = 0; s < nsW; ++s) {
+        const double k = tb.hW * std::sqrt((double)s), k2 = k * k + lam * lam;
+        const double xt = lam * Rt;
+        double tr;
+        if (s == 0) {
+            tr = 4.0 * M_PI * one_minus_exp_1px(xt) / (lam * lam);
+        } else {
+            const double sn = std::sin(0.5 * k * Rt);
+            const double num = -k * std::expm1(-xt) + 2.0 * k * std::exp(-xt) * sn * sn - std::exp(-xt) * lam * std::sin(k * Rt);
+            tr = 4.0 * M_PI * num / (k * k2);
+        }
+        yt.wW[s] = scW * ps(std::sqrt(k2) / c) * tr;
+    }
+    // residual polynomials: q_l(t) = R_l S_l(R_l sqrt t)
+    std::vector<double> gx, gw;
+    gl_rule(24, gx, gw);
+    const int nc = 64;
+    std::vector<std::vector<double>> monos(nlev);
+    int qdeg = 2;
+    for (int l = 0; l < nlev; ++l) {
+        const double R = std::ldexp(1.0, -l);
+        // panels in k: graded from width lambda near 0 (poles at +-i lambda),
+        // then 8 regular panels up to sqrt(k^2 + lambda^2) R / c = 4
+        const double x4 = 4.0 * c / R, kmax = x4 > lam ? std::sqrt(x4 * x4 - lam * lam) : 0.0, pw = kmax / 8.0;
+        std::vector<double> br{0.0};
+        for (double b = lam; b < pw && br.size() < 32; b *= 3.0) br.push_back(b);
+        const double b0 = br.back();
+        for (int q = 1; q <= 8; ++q) br.push_back(b0 + (kmax - b0) * q / 8.0);
+        std::vector<double> kn, gn;  // nodes, weights x integrand without sin(k r)
+        for (size_t q = 0; q + 1 < br.size(); ++q) {
+            const double a = br[q], hq = br[q + 1] - br[q];
+            for (int i = 0; i < 24; ++i) {
+                const double k = a + 0.5 * hq * (gx[i] + 1.0), k2 = k * k + lam * lam;
+                kn.push_back(k);
+                gn.push_back(2.0 / M_PI * 0.5 * hq * gw[i] * (ps(std::sqrt(k2) * R / c) * k / k2 - ps(k * R / c) / k));
+            }
+        }
+        std::vector<double> vals(nc);
+        for (int j = 0; j < nc; ++j) {
+            const double t = cheb_node01(j, nc), st = std::sqrt(t), r = R * st;
+            double acc = 0.0;
+            if (st == 0.0) {
+                for (size_t i = 0; i < kn.size(); ++i) acc += gn[i] * kn[i];
+                vals[j] = tb.psi0_over_c0 + R * acc;
+            } else {
+                for (size_t i = 0; i < kn.size(); ++i) acc += gn[i] * std::sin(kn[i] * r);
+                vals[j] = psi.Phi(st) / st + acc / st;
+            }
+        }
+        // the mollifier carries the transform of psi beyond x = 1 (where psi is
+        // below eps but not zero): high Chebyshev modes of size ~1e-3 eps,
+        // dropped up to 2e-2 eps S_l(0) in all
+        double vmax = 0.0;  // q_l(0), the largest value
+        for (double v : vals) vmax = std::max(vmax, std::fabs(v));
+        const double tol = std::max(2e-2 * tb.eps * vmax, 1e-15 * tb.psi0_over_c0);
+        monos[l] = cheb_to_mono(cheb_fit(vals, tol));
+        qdeg = std::max(qdeg, (int)monos[l].size() - 1);
+    }
+    if (qdeg > kMaxYukawaDegree) { err = "Yukawa residual polynomial degree above 62"; return -1; }
+    // rows [degree, c_0 .. c_qdeg]: each level is evaluated at its own degree
+    // (large lambda R_l needs high degrees at the coarse levels only)
+    yt.qdeg = qdeg;
+    yt.qmono.assign((size_t)nlev * (qdeg + 2), 0.0);
+    for (int l = 0; l < nlev; ++l) {
+        yt.qmono[(size_t)l * (qdeg + 2)] = (double)(monos[l].size() - 1);
+        for (size_t d = 0; d < monos[l].size(); ++d) yt.qmono[(size_t)l * (qdeg + 2) + 1 + d] = monos[l][d];
+    }
     return 0;
 }
 

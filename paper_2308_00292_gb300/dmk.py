@@ -20,6 +20,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdmk.so")
 
 DMK_LAPLACE = 0
+DMK_YUKAWA = 1
 DMK_FP64 = 0
 DMK_MIXED = 1
 FLAG_FAR_ONLY = 1
@@ -32,7 +33,7 @@ ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "D
 EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_grad", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
             "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree",
             "dmk_direct_noalloc", "dmk_tune_leaf_cap", "dmk_eval_batch",
-            "dmk_tune_leaf_cap_batch"]
+            "dmk_tune_leaf_cap_batch", "dmk_plan_get_yukawa_table"]
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +84,8 @@ def lib():
             L.dmk_eval.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp]
             L.dmk_eval_grad.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, vp]
             L.dmk_eval_batch.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.c_int, vp, vp]
+            L.dmk_plan_get_yukawa_table.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, i64,
+                                                    ctypes.POINTER(i64)]
             L.dmk_eval_host.argtypes = [vp, dp, i64, dp, dp, i64, dp, vp]
             L.dmk_plan_destroy.argtypes = [vp]
             L.dmk_error_string.argtypes = [ctypes.c_int]
@@ -116,9 +119,10 @@ class Plan:
     """A DMK plan: ``Plan(eps, precision=DMK_MIXED, leaf_cap=200)``."""
 
     def __init__(self, eps=1e-6, precision=DMK_FP64, leaf_cap=0, flags=0, max_level=0, p=0, nf=0, kernel=DMK_LAPLACE,
-                 dim=3):
+                 dim=3, lam=0.0):
+        """lam: the Yukawa parameter (kernel DMK_YUKAWA, exp(-lam r)/r)."""
         self._h = ctypes.c_void_p()
-        o = Opts(leaf_cap, precision, 0.0, flags, max_level, p, nf)
+        o = Opts(leaf_cap, precision, float(lam), flags, max_level, p, nf)
         _check(lib().dmk_plan(kernel, dim, eps, ctypes.byref(o), ctypes.byref(self._h)))
 
     def close(self):
@@ -238,6 +242,15 @@ class Plan:
         p = PlanParams()
         _check(lib().dmk_plan_get_params(self._h, ctypes.byref(p)))
         return {k: getattr(p, k) for k, _ in p._fields_}
+
+    def yukawa_table(self, lambda_unit: float, level: int, which: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().dmk_plan_get_yukawa_table(self._h, lambda_unit, level, which, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().dmk_plan_get_yukawa_table(self._h, lambda_unit, level, which,
+                                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                                               ctypes.byref(n)))
+        return out
 
     def table(self, which: int) -> np.ndarray:
         n = ctypes.c_int64()

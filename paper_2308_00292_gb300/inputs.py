@@ -114,6 +114,8 @@ CONFIGS = {
     "laplace3d_uniform_n2e6": dict(gen="uniform_cube", n=2_000_000, seed=4, eps=1e-6, leaf_cap=200),
     # 4096 independent systems of 500 .. 50 000 points (about 4.4e7 in all)
     "laplace3d_batched_4096": dict(gen="batch", nsys=4096, seed=6, eps=1e-6, leaf_cap=0),
+    # the Yukawa kernel exp(-10 r)/r on 4e6 uniform points at eps 1e-8
+    "yukawa3d_uniform_n4e6": dict(gen="uniform_cube", n=4_000_000, seed=7, eps=1e-8, lam=10.0, leaf_cap=0),
 }
 
 

@@ -50,7 +50,8 @@ def test_argument_validation_without_device(dmk):
     o = dmk.Opts()
     assert L.dmk_plan(0, 3, 1.0, ctypes.byref(o), ctypes.byref(h)) == 1      # eps out of range
     assert L.dmk_plan(0, 3, float("nan"), ctypes.byref(o), ctypes.byref(h)) == 1
-    assert L.dmk_plan(1, 3, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # kernel not implemented
+    assert L.dmk_plan(1, 3, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 1      # Yukawa without lambda
+    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # kernel not implemented
     assert L.dmk_plan(0, 2, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # dimension
     assert L.dmk_plan(0, 3, 1e-6, ctypes.byref(o), None) == 1
     bad = dmk.Opts(p=17)
