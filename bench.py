@@ -110,23 +110,32 @@ NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares,
 
 # DRAM bytes per algorithmic unit, from one ncu capture of every k_local and
 # k_near launch of an evaluation of the 2e6-point clustered workload (profiles/
-# dram_traffic_laplace3d_clustered_n2e6.md), valid only for the kernel source
-# it was taken on.
-TRAFFIC_SOURCE = "paper_2308_00292_gb300/csrc/passes.cu"
-TRAFFIC_SHA256 = "2be5f3a5c84a7a6a9f8edc72e4f7d2d4bd09f5c432dfb6c170e79f6b56896e4c"
-TRAFFIC_PER_UNIT = {"k_local": (847.0e6 + 146.7e6) / 7.106e10,  # bytes per algorithmic flop
-                    "k_near": (74.7e6 + 7.5e6) / 4.693e9}         # bytes per candidate pair
+# dram_traffic_laplace3d_clustered_n2e6.md), each valid only for the kernel
+# source it was taken on: kernel -> (source file, its sha256, bytes per unit)
+TRAFFIC = {
+    # bytes per algorithmic flop
+    "k_local": ("paper_2308_00292_gb300/csrc/passes.cu",
+                "59efc955d43dbbe26c4933eb9bca3d6756a7782b2e809ada8d3574574278cb6f",
+                (846.5e6 + 152.6e6) / 7.106e10),
+    # bytes per candidate pair
+    "k_near": ("paper_2308_00292_gb300/csrc/near.cu",
+               "46cf5ecdd7047ff4c9db9c5a4801cf03ea825c4cc5c499e6bc2b9ad83061485d",
+               (74.25e6 + 7.2e6) / 4.693e9),
+}
 
 
 def traffic_per_unit(kernel: str):
     """DRAM bytes per unit of work of a kernel, or None if its source changed since the capture."""
     import hashlib
+    if kernel not in TRAFFIC:
+        return None
+    src, sha_want, per_unit = TRAFFIC[kernel]
     try:
-        with open(os.path.join(ROOT, TRAFFIC_SOURCE), "rb") as f:
+        with open(os.path.join(ROOT, src), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
-    return TRAFFIC_PER_UNIT.get(kernel) if sha == TRAFFIC_SHA256 else None
+    return per_unit if sha == sha_want else None
 
 
 def near_flops_per_pair(qdeg: int) -> int:

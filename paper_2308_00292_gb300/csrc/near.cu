@@ -13,8 +13,8 @@ namespace dmk {
 // Residual near field (Steps 4 and 5)
 // ---------------------------------------------------------------------------
 // One warp per target leaf, taken from an atomic work counter.  The leaf's
-// points are taken in groups of up to 32 targets; when the leaf holds fewer
-// than 32 points, G adjacent lanes share a target and split its candidates.
+// points are taken in groups of up to 32 targets; when fewer than 32 targets
+// remain, G adjacent lanes share a target and split its candidates.
 // For each group:
 //   1. the source leaves of the interaction list are read 32 at a time, one
 //      per lane, and a leaf whose box lies farther than R_b from the group's
@@ -167,11 +167,15 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
         // (at most ~22 significant bits for the level gaps of a balanced tree)
         const T cTx = dyadic_centre<T>(tx, a), cTy = dyadic_centre<T>(ty, a), cTz = dyadic_centre<T>(tz, a);
         const int ts = tv.bstart[Tb], nt = tv.bcount[Tb];
-        const int G = nt >= 32 ? 1 : (nt >= 16 ? 2 : (nt >= 8 ? 4 : 8));
-        const int per = 32 / G, t = lane / G, sub = lane % G;
         const int l0 = nl_off[it], l1 = nl_off[it + 1];
-        for (int j0 = 0; j0 < nt; j0 += per) {
-            const int ng = min(per, nt - j0);
+        for (int j0 = 0, per = 32; j0 < nt; j0 += per) {
+            // lanes per target from the targets still to do: the last group of a
+            // leaf shares lanes instead of leaving them idle
+            const int rem = nt - j0;
+            const int G = rem >= 32 ? 1 : (rem >= 16 ? 2 : (rem >= 8 ? 4 : 8));
+            per = 32 / G;
+            const int t = lane / G, sub = lane % G;
+            const int ng = min(per, rem);
             // the group's targets and their bounding box
             T bl[3] = {kBig, kBig, kBig}, bh[3] = {-kBig, -kBig, -kBig};
             if (lane < ng) {
@@ -241,40 +245,60 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                 if (lane == 0) W.loff[0] = 0;
                 const int stream = __shfl_sync(FULL, cum, 31);
                 __syncwarp();
-                int lf = 0;  // leaf of this lane's next staged position (positions only grow)
-                for (int c0 = 0; c0 < stream; c0 += kNC) {
-                    // 2. stage kNC sources of the stream in the target leaf's frame
-                    const int fill = min(kNC, stream - c0);
-                    for (int k = lane; k < fill; k += 32) {
-                        const int pos = c0 + k;
-                        while (W.loff[lf + 1] <= pos) ++lf;
-                        const int src = W.lss[lf] + pos - W.loff[lf];
-                        const V4 y = plocal[src];
-                        const T ax = W.lox[lf], ay = W.loy[lf], az = W.loz[lf];
-                        const int lev = W.lb_[lf];
+                int lf = 0;  // leaf of this lane's next stream position (positions only grow)
+                const unsigned lt_mask = (1u << lane) - 1u;
+                for (int cur = 0; cur < stream;) {
+                    // 2. stage up to kNC sources of the stream in the target leaf's
+                    // frame, 32 positions at a time, keeping only sources closer than
+                    // R_b (1 + 2^-10) to the group's bounding box: the others cannot
+                    // reach any of its targets
+                    int fill = 0;
+                    while (fill <= kNC - 32 && cur < stream) {
+                        const int pos = cur + lane;
+                        bool keep = false;
                         V4 hv;
-                        hv.x = y.x + ax;
-                        hv.y = y.y + ay;
-                        hv.z = y.z + az;
-                        const T Rb2 = ldexp_t<T>((T)1.001953125, -2 * lev);  // R_b^2 (1 + 2^-9)
-                        hv.w = pack_level(hv.x * hv.x + hv.y * hv.y + hv.z * hv.z - Rb2, lev);
-                        W.sh[k] = hv;
-                        if (kHiLo) {  // TwoSum error terms plus the lo parts
-                            const float4 yl = plocal_lo[src];
-                            float4 lv;
-                            T bb = hv.x - y.x;
-                            lv.x = (float)(((y.x - (hv.x - bb)) + (ax - bb)) + (T)yl.x);
-                            bb = hv.y - y.y;
-                            lv.y = (float)(((y.y - (hv.y - bb)) + (ay - bb)) + (T)yl.y);
-                            bb = hv.z - y.z;
-                            lv.z = (float)(((y.z - (hv.z - bb)) + (az - bb)) + (T)yl.z);
-                            lv.w = (float)y.w;
-                            W.sl[k] = lv;
-                        } else {
-                            W.sq[k] = y.w;
+                        float4 lv = make_float4(0.f, 0.f, 0.f, 0.f);
+                        T qsrc = 0;
+                        if (pos < stream) {
+                            while (W.loff[lf + 1] <= pos) ++lf;
+                            const int src = W.lss[lf] + pos - W.loff[lf];
+                            const V4 y = plocal[src];
+                            const T ax = W.lox[lf], ay = W.loy[lf], az = W.loz[lf];
+                            const int lev = W.lb_[lf];
+                            hv.x = y.x + ax;
+                            hv.y = y.y + ay;
+                            hv.z = y.z + az;
+                            const T Rb2 = ldexp_t<T>((T)1.001953125, -2 * lev);  // R_b^2 (1 + 2^-9)
+                            const T gx = max((T)0, max(bl[0] - hv.x, hv.x - bh[0]));
+                            const T gy = max((T)0, max(bl[1] - hv.y, hv.y - bh[1]));
+                            const T gz = max((T)0, max(bl[2] - hv.z, hv.z - bh[2]));
+                            keep = gx * gx + gy * gy + gz * gz < Rb2;
+                            hv.w = pack_level(hv.x * hv.x + hv.y * hv.y + hv.z * hv.z - Rb2, lev);
+                            if (kHiLo) {  // TwoSum error terms plus the lo parts
+                                const float4 yl = plocal_lo[src];
+                                T bb = hv.x - y.x;
+                                lv.x = (float)(((y.x - (hv.x - bb)) + (ax - bb)) + (T)yl.x);
+                                bb = hv.y - y.y;
+                                lv.y = (float)(((y.y - (hv.y - bb)) + (ay - bb)) + (T)yl.y);
+                                bb = hv.z - y.z;
+                                lv.z = (float)(((y.z - (hv.z - bb)) + (az - bb)) + (T)yl.z);
+                                lv.w = (float)y.w;
+                            } else {
+                                qsrc = y.w;
+                            }
                         }
+                        const unsigned km = __ballot_sync(FULL, keep);
+                        if (keep) {
+                            const int k = fill + __popc(km & lt_mask);
+                            W.sh[k] = hv;
+                            if (kHiLo) W.sl[k] = lv;
+                            else W.sq[k] = qsrc;
+                        }
+                        fill += __popc(km);
+                        cur += 32;
                     }
                     __syncwarp();
+                    if (fill == 0) continue;
                     // 3. screening, 32 candidates per lane: k = u0 + sub + G i
                     for (int u0 = 0; u0 < fill; u0 += 32 * G) {
                         unsigned mask = 0;
