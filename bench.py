@@ -115,12 +115,12 @@ NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares,
 TRAFFIC = {
     # bytes per algorithmic flop
     "k_local": ("paper_2308_00292_gb300/csrc/passes.cu",
-                "59efc955d43dbbe26c4933eb9bca3d6756a7782b2e809ada8d3574574278cb6f",
-                (846.5e6 + 152.6e6) / 7.106e10),
+                "fc4b9af9ddfcc3557a2b4d4fb90c87cb43efb9dbbdaa9a513494f3772602d6f2",
+                (844.3e6 + 146.6e6) / 7.106e10),
     # bytes per candidate pair
     "k_near": ("paper_2308_00292_gb300/csrc/near.cu",
-               "46cf5ecdd7047ff4c9db9c5a4801cf03ea825c4cc5c499e6bc2b9ad83061485d",
-               (74.25e6 + 7.2e6) / 4.693e9),
+               "da5054e095dbfb3012a473a0d690619f48e9e42b21dd55c41fc453b0aadca925",
+               (74.25e6 + 7.45e6) / 4.693e9),
 }
 
 

@@ -717,11 +717,30 @@ __device__ __forceinline__ void shift_pass(const T *__restrict__ A, const T *in,
     }
 }
 
+// Work split of a contraction with `base` independent outputs per coefficient
+// index (P of them) over `threads` threads: the index is cut into G groups of
+// ceil(P / G) per thread item, and base * G items run in ceil(base G / threads)
+// rounds between barriers.  Per inner step an item loads its inputs (~2
+// instructions) and updates its accumulators (~3 each), so G minimises
+// rounds x (2 + 3 ceil(P / G)), the time to the barrier, with at most max_per
+// accumulators per item (registers); ties go to fewer groups.
+constexpr int best_groups(int base, int P, int threads, int max_per) {
+    int best = P, cost = 1 << 30;
+    for (int G = 1; G <= P; ++G) {
+        const int per = (P + G - 1) / G;
+        if (per > max_per) continue;
+        const int c = ((base * G + threads - 1) / threads) * (2 + 3 * per);
+        if (c < cost) { cost = c; best = G; }
+    }
+    return best;
+}
+
 template <int P, int NF> struct LocalShape {
     static constexpr int NH = NF + 1, N1 = 2 * NF + 1;
-    static constexpr int AG = (P + 6) / 7, AC = (P + AG - 1) / AG;  // phase B: a-groups, a per group
-    static constexpr int BG = (P + 7) / 8, BC = (P + BG - 1) / BG;  // phase C
-    static constexpr int CG = (P + 8) / 9, CC = (P + CG - 1) / CG;  // phase D
+    // phase B: a-groups, a per group (two complex accumulators per a)
+    static constexpr int AG = best_groups(NH * NH, P, 512, 8), AC = (P + AG - 1) / AG;
+    static constexpr int BG = best_groups(P * NH, P, 512, 10), BC = (P + BG - 1) / BG;  // phase C
+    static constexpr int CG = best_groups(P * P, P, 512, 20), CC = (P + CG - 1) / CG;   // phase D
     // tensor-core leaf evaluation D[j][ab] = sum_c T_c(z_j) Lambda[ab][c]:
     // 128 targets per tile (M), ab padded to NP (N, multiple of 16, split into
     // at most two MMAs of <= 256 columns), c padded to KP (K, multiple of 8)

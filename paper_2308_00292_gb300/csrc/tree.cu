@@ -546,7 +546,8 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
                               const int32_t *bcount, const uint8_t *bflags, const double *ux, const double *uy,
                               const double *uz, const double *q, const uint8_t *pflag, int32_t *pleaf,
                               typename Vec4<T>::type *plocal, float4 *plocal_lo) {
-    int b = blockIdx.x;
+    // one warp per box (leaves hold tens of points)
+    int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= nb || !(bflags[b] & BF_LEAF)) return;
     int l = blevel[b];
     int ix, iy, iz;
@@ -554,7 +555,7 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
     double R = level_R(l);
     double cx = (ix + 0.5) * R, cy = (iy + 0.5) * R, cz = (iz + 0.5) * R;
     int32_t s = bstart[b], e = s + bcount[b];
-    for (int32_t k = s + threadIdx.x; k < e; k += blockDim.x) {
+    for (int32_t k = s + (threadIdx.x & 31); k < e; k += 32) {
         pleaf[k] = b;
         typename Vec4<T>::type v;
         const double dx = ux[k] - cx, dy = uy[k] - cy, dz = uz[k] - cz;
@@ -989,7 +990,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     // leaf index and local coordinates of every point
     if (point_prec)
         { ::dmk::launch_tick();
-        k_point_local<float><<<nb, 128, 0, st>>>(nb, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
+        k_point_local<float><<<nblk(nb, 4), 128, 0, st>>>(nb, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
                                                  (const int32_t *)bstart.p, (const int32_t *)bcount.p,
                                                  (const uint8_t *)bflags.p, (const double *)ux.p,
                                                  (const double *)uy.p, (const double *)uz.p, (const double *)q.p,
@@ -998,7 +999,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         }
     else
         { ::dmk::launch_tick();
-        k_point_local<double><<<nb, 128, 0, st>>>(nb, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
+        k_point_local<double><<<nblk(nb, 4), 128, 0, st>>>(nb, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
                                                   (const int32_t *)bstart.p, (const int32_t *)bcount.p,
                                                   (const uint8_t *)bflags.p, (const double *)ux.p,
                                                   (const double *)uy.p, (const double *)uz.p, (const double *)q.p,
