@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
                                                         const T *LamW, double *ufar, BufLayout lay, char *slab,
                                                         unsigned long long *flops, int *tc_err, int *run_ctr,
-                                                        double *gfar) {
+                                                        double *gfar, typename Cplx<T>::type *psig) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
     constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P, NHP = nz_pad<NF>();
@@ -1085,6 +1085,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
+    __shared__ int s_blk[64];  // slots of the F_out boxes of a sibling group's 4 x 4 x 4 block
+    __shared__ int s_gtr;
     __shared__ __align__(8) uint64_t s_bar;  // MMA completion
     __shared__ uint32_t s_tmem;              // TMEM accumulator base
     __shared__ int s_pending;                // an MMA batch outlived its wait
@@ -1176,6 +1178,138 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                 gnr = s_gnr;
                 if (gnr > 0) fetch_xyz(tv, s_grs, s_gro, gnr, s_gxyz);
             }
+            // ---- incoming expansions of the whole sibling group at once: the
+            // colleagues of the 8 children of a parent lie in the 4 x 4 x 4 block of
+            // the children of the parent's colleagues, and the phase omega^(m . delta)
+            // factorises over the axes, so three 3-tap passes over the block (z, then
+            // y, then x) form all siblings' Psi = w_l sum_S omega^(m . delta) Phi_S
+            // while reading each colleague's Phi once instead of once per sibling.
+            // The results go to this block's scratch, one plane-wave array per octant.
+            bool gtr = false;
+            if (level > 0) {
+                __syncthreads();
+                if (tid < 32) {
+                    // warp 0: the block's F_out slots (lane k: the parent's colleague k),
+                    // and the Phi reads of both ways: the group pass reads every F_out
+                    // box of the block once, writes and re-reads 8 + n_fin arrays; the
+                    // per-box pass reads each F_in sibling's F_out colleagues
+                    const int lane = tid;
+                    for (int q = lane; q < 64; q += 32) s_blk[q] = -1;
+                    __syncwarp();
+                    int present = 0, sumcol = 0, nfin = 0;
+                    const int Pg = parent_of(g0);
+                    if (lane < 27) {
+                        const int C = tv.bcol[(size_t)Pg * 27 + lane];
+                        if (C >= 0 && !(tv.bflags[C] & BF_LEAF)) {
+                            const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+                            const unsigned cm = tv.bcmask[C];
+                            int D = tv.bchild0[C];
+                            for (int oc = 0; oc < 8; ++oc) {
+                                if (!(cm & (1u << oc))) continue;
+                                const int Dc = D++;
+                                // block position of the child (octant bit 0 = x, 1 = y, 2 = z)
+                                const int X = 2 * dx + (oc & 1) + 1, Y = 2 * dy + ((oc >> 1) & 1) + 1,
+                                          Z = 2 * dz + ((oc >> 2) & 1) + 1;
+                                if (X < 0 || X > 3 || Y < 0 || Y > 3 || Z < 0 || Z > 3) continue;
+                                if (tv.bflags[Dc] & BF_FOUT) {
+                                    s_blk[(X * 4 + Y) * 4 + Z] = tv.bslot[Dc];
+                                    ++present;
+                                }
+                            }
+                        }
+                    }
+                    for (int t = lane; t < (g1 - g0) * 27; t += 32) {
+                        const int b = lstart + g0 + t / 27, k = t % 27;
+                        if (!(tv.bflags[b] & BF_FIN) || tv.bntgt[b] == 0) continue;
+                        const int Sb = tv.bcol[(size_t)b * 27 + k];
+                        if (Sb >= 0 && (tv.bflags[Sb] & BF_FOUT)) ++sumcol;
+                        if (k == 0) ++nfin;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        present += __shfl_xor_sync(0xffffffffu, present, o);
+                        sumcol += __shfl_xor_sync(0xffffffffu, sumcol, o);
+                        nfin += __shfl_xor_sync(0xffffffffu, nfin, o);
+                    }
+                    if (lane == 0) s_gtr = nfin >= 2 && present + 8 + nfin < sumcol;
+                }
+                __syncthreads();
+                gtr = s_gtr != 0;
+            }
+            if (gtr) {
+                C2 *gout = psig + (size_t)blockIdx.x * 8 * pstride;
+                const T kc = (T)-0.5;
+                for (int i = tid; i < N1 * N1 * NH; i += kLThreads) {
+                    const int mz = i % NH, mx = (i / NH) % N1, my = i / (NH * N1);
+                    const int mxv = mx - NF, myv = my - NF;
+                    // omega^(m r) for r = 1 per axis: (cos, sin) of 2 pi (m mod 3) / 3;
+                    // r = -1 is its conjugate
+                    const int rx = (mxv % 3 + 3) % 3, ry = (myv % 3 + 3) % 3, rz = mz % 3;
+                    const T cx = rx ? kc : (T)1, sx = rx == 0 ? (T)0 : (rx == 1 ? kH : -kH);
+                    const T cy = ry ? kc : (T)1, sy = ry == 0 ? (T)0 : (ry == 1 ? kH : -kH);
+                    const T cz = rz ? kc : (T)1, sz = rz == 0 ? (T)0 : (rz == 1 ? kH : -kH);
+                    // v + w * omega^(+m) and * omega^(-m)
+                    auto rp = [](C2 v, T c, T sn) { return C2{c * v.x - sn * v.y, c * v.y + sn * v.x}; };
+                    auto rm = [](C2 v, T c, T sn) { return C2{c * v.x + sn * v.y, c * v.y - sn * v.x}; };
+                    auto add = [](C2 &a, C2 b) { a.x += b.x; a.y += b.y; };
+                    const size_t off = (size_t)(my * N1 + mx) * NHP + mz;
+                    C2 out[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) out[q] = C2{0, 0};
+#pragma unroll
+                    for (int X = 0; X < 4; ++X) {
+                        C2 yy[4] = {C2{0, 0}, C2{0, 0}, C2{0, 0}, C2{0, 0}};  // [oy][oz]
+                        bool anyx = false;
+#pragma unroll
+                        for (int Y = 0; Y < 4; ++Y) {
+                            const int *bl = s_blk + (X * 4 + Y) * 4;
+                            if (bl[0] < 0 && bl[1] < 0 && bl[2] < 0 && bl[3] < 0) continue;
+                            anyx = true;
+                            C2 v[4];
+#pragma unroll
+                            for (int Z = 0; Z < 4; ++Z) v[Z] = bl[Z] >= 0 ? Phi[(size_t)bl[Z] * pstride + off] : C2{0, 0};
+                            // z: sibling oz at 1 + oz takes Z = oz, oz + 1, oz + 2 (delta 1, 0, -1)
+                            C2 z0 = rp(v[0], cz, sz), z1 = rp(v[1], cz, sz);
+                            add(z0, v[1]);
+                            add(z1, v[2]);
+                            add(z0, rm(v[2], cz, sz));
+                            add(z1, rm(v[3], cz, sz));
+                            // y: sibling oy takes Y = oy (delta 1), oy + 1 (0), oy + 2 (-1)
+                            if (Y <= 1) {  // oy = Y: delta 1;  Y = 1 also oy = 0 with delta 0
+                                const int oy = Y;
+                                add(yy[oy * 2 + 0], rp(z0, cy, sy));
+                                add(yy[oy * 2 + 1], rp(z1, cy, sy));
+                            }
+                            if (Y >= 1 && Y <= 2) {  // delta 0 for oy = Y - 1
+                                add(yy[(Y - 1) * 2 + 0], z0);
+                                add(yy[(Y - 1) * 2 + 1], z1);
+                            }
+                            if (Y >= 2) {  // delta -1 for oy = Y - 2
+                                add(yy[(Y - 2) * 2 + 0], rm(z0, cy, sy));
+                                add(yy[(Y - 2) * 2 + 1], rm(z1, cy, sy));
+                            }
+                        }
+                        if (!anyx) continue;
+                        // x: sibling ox takes X = ox (delta 1), ox + 1 (0), ox + 2 (-1)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (X <= 1) add(out[q * 2 + X], rp(yy[q], cx, sx));
+                            if (X >= 1 && X <= 2) add(out[q * 2 + (X - 1)], yy[q]);
+                            if (X >= 2) add(out[q * 2 + (X - 2)], rm(yy[q], cx, sx));
+                        }
+                    }
+                    const int sq = mxv * mxv + myv * myv + mz * mz;
+                    const T w = tb.wl ? tb.wl[(size_t)level * (3 * NF * NF + 1) + sq] : tb.w[sq] * invR;
+                    // out[(oy * 2 + oz) * 2 + ox] belongs to octant ox | oy << 1 | oz << 2
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int ox = q & 1, oz = (q >> 1) & 1, oy = q >> 2;
+                        const int oc = ox | (oy << 1) | (oz << 2);
+                        gout[(size_t)oc * pstride + off] = C2{w * out[q].x, w * out[q].y};
+                    }
+                }
+                __syncthreads();
+            }
             for (int it = g0; it < g1; ++it) {
                 const int B = lstart + it;
                 if (tv.bntgt[B] == 0) continue;
@@ -1237,7 +1371,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     // phase of colleague j for modes of residue class r = (m_x, m_y, m_z) mod 3
                     // (r = r_x + 3 r_y + 9 r_z): omega^k with k = r . delta_j mod 3, kept as
                     // (k != 0, +1 / -1 / 0 for k = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3/2) D
-                    for (int t = tid; t < 27 * ncol; t += kLThreads) {
+                    for (int t = tid; t < (gtr ? 0 : 27 * ncol); t += kLThreads) {
                         const int j = t / 27, r = t % 27;
                         const int k = ((r % 3) * s_cd[j][0] + ((r / 3) % 3) * s_cd[j][1] + (r / 9) * s_cd[j][2]) % 3;
                         s_ud[t] = make_float2(k ? 1.f : 0.f, k == 1 ? 1.f : (k == 2 ? -1.f : 0.f));
@@ -1246,7 +1380,24 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     // phase A: Psi = w_l * sum_S omega^(m.delta) Phi_S, folded into even/odd in m_x;
                     // a thread takes two adjacent m_z (one 16-byte load per colleague and sign
                     // of m_x), four colleagues per step for memory-level parallelism
-                    for (int i = tid; i < N1 * NH * (NHP / 2); i += kLThreads) {
+                    if (gtr) {
+                        // the group pass formed this box's Psi: fold it into even/odd in m_x
+                        const C2 *g = psig + ((size_t)blockIdx.x * 8 + (size_t)(tv.bkey[B] & 7ull)) * pstride;
+                        for (int i = tid; i < N1 * NH * NH; i += kLThreads) {
+                            const int mz = i % NH, mxp = (i / NH) % NH, my = i / (NH * NH);
+                            const C2 psp = g[(size_t)(my * N1 + NF + mxp) * NHP + mz];
+                            const size_t o = (size_t)(my * NH + mxp) * NHP + mz;
+                            if (mxp > 0) {
+                                const C2 psm = g[(size_t)(my * N1 + NF - mxp) * NHP + mz];
+                                PsE[o] = C2{psp.x + psm.x, psp.y + psm.y};
+                                PsO[o] = C2{psp.x - psm.x, psp.y - psm.y};
+                            } else {
+                                PsE[o] = psp;
+                                PsO[o] = C2{0, 0};
+                            }
+                        }
+                    }
+                    for (int i = tid; i < (gtr ? 0 : N1 * NH * (NHP / 2)); i += kLThreads) {
                         const int my = i / (NH * (NHP / 2)), r = i % (NH * (NHP / 2)), mxp = r / (NHP / 2);
                         const int mz0 = 2 * (r % (NHP / 2));
                         const int myv = my - NF;
@@ -1772,6 +1923,11 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             return DMK_ERR_INTERNAL;
         }
         PCK(cudaFuncSetAttribute(k_local<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
+        // per block: the plane-wave arrays of one sibling group (8 octants)
+        if (ws.ensure(cx.bufs->psig, (int64_t)cx.num_sms * 8 * N1 * N1 * nz_pad<NF>() * sizeof(C2))) {
+            err = "device allocation failed (group translation)";
+            return DMK_ERR_OOM;
+        }
         for (int l = 0; l < tv.nlev; ++l) {
             int lc = tv.lev_count[l];
             int grid = std::min((lc + 7) / 8, cx.num_sms);
@@ -1782,7 +1938,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                                                        LamW, ufar, lay, (char *)cx.bufs->slab.p,
                                                                        (unsigned long long *)cx.bufs->counter.p + 2,
                                                                        (int *)cx.bufs->counter.p + 6,
-                                                                       (int *)cx.bufs->counter.p + 32 + l, gfar);
+                                                                       (int *)cx.bufs->counter.p + 32 + l, gfar,
+                                                                       (C2 *)cx.bufs->psig.p);
         }
         PCK(cudaGetLastError());
     }

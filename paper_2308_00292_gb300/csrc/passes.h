@@ -15,7 +15,7 @@ struct BufLayout {
 };
 
 struct PassBufs {
-    DBuf M, Lam, LamW, Phi, ufar, unear, gfar, gnear, slab, rootscr, counter;
+    DBuf M, Lam, LamW, Phi, ufar, unear, gfar, gnear, slab, rootscr, counter, psig;
 };
 
 struct PassCtx {
