@@ -1086,7 +1086,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
     __shared__ int s_blk[64];  // slots of the F_out boxes of a sibling group's 4 x 4 x 4 block
-    __shared__ int s_gtr;
+    __shared__ int s_gtr;      // the group pass runs: bit 8, and the octants it keeps (F_in siblings)
     __shared__ __align__(8) uint64_t s_bar;  // MMA completion
     __shared__ uint32_t s_tmem;              // TMEM accumulator base
     __shared__ int s_pending;                // an MMA batch outlived its wait
@@ -1197,6 +1197,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     for (int q = lane; q < 64; q += 32) s_blk[q] = -1;
                     __syncwarp();
                     int present = 0, sumcol = 0, nfin = 0;
+                    unsigned keep = 0;  // octants of the incoming siblings
                     const int Pg = parent_of(g0);
                     if (lane < 27) {
                         const int C = tv.bcol[(size_t)Pg * 27 + lane];
@@ -1223,20 +1224,27 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                         if (!(tv.bflags[b] & BF_FIN) || tv.bntgt[b] == 0) continue;
                         const int Sb = tv.bcol[(size_t)b * 27 + k];
                         if (Sb >= 0 && (tv.bflags[Sb] & BF_FOUT)) ++sumcol;
-                        if (k == 0) ++nfin;
+                        if (k == 0) {
+                            ++nfin;
+                            keep |= 1u << (unsigned)(tv.bkey[b] & 7ull);
+                        }
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         present += __shfl_xor_sync(0xffffffffu, present, o);
                         sumcol += __shfl_xor_sync(0xffffffffu, sumcol, o);
                         nfin += __shfl_xor_sync(0xffffffffu, nfin, o);
+                        keep |= __shfl_xor_sync(0xffffffffu, keep, o);
                     }
-                    if (lane == 0) s_gtr = nfin >= 2 && present + 8 + nfin < sumcol;
+                    // reads of the group pass: the block's F_out boxes once, and its
+                    // result written and re-read once per incoming sibling
+                    if (lane == 0) s_gtr = (nfin >= 2 && present + 2 * nfin < sumcol) ? (int)(256u | keep) : 0;
                 }
                 __syncthreads();
                 gtr = s_gtr != 0;
             }
             if (gtr) {
+                const unsigned gkeep = (unsigned)s_gtr & 255u;
                 C2 *gout = psig + (size_t)blockIdx.x * 8 * pstride;
                 const T kc = (T)-0.5;
                 for (int i = tid; i < N1 * N1 * NH; i += kLThreads) {
@@ -1305,7 +1313,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     for (int q = 0; q < 8; ++q) {
                         const int ox = q & 1, oz = (q >> 1) & 1, oy = q >> 2;
                         const int oc = ox | (oy << 1) | (oz << 2);
-                        gout[(size_t)oc * pstride + off] = C2{w * out[q].x, w * out[q].y};
+                        if (gkeep & (1u << oc)) gout[(size_t)oc * pstride + off] = C2{w * out[q].x, w * out[q].y};
                     }
                 }
                 __syncthreads();
