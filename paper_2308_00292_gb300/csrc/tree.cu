@@ -217,34 +217,37 @@ __device__ __forceinline__ int point_sys(const int64_t *off, int nsys, int64_t i
     return lo;
 }
 
+// unit-box coordinates of every point (kept in input order for the gather:
+// the map costs three FP64 divisions, done once) and its key
 __global__ void k_make_keys(const double *src, int64_t ns, const double *tgt, int64_t n, const Frame *frame,
-                            const int64_t *off, int nsys, int kb, uint64_t *keys, uint32_t *idx) {
+                            const int64_t *off, int nsys, int kb, uint64_t *keys, uint32_t *idx, double *u) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *x = i < ns ? src + 3 * i : tgt + 3 * (i - ns);
     const int sy = point_sys(off, nsys, i);
     const Frame f = frame[sy];
-    uint32_t c0 = fine_cell(unit_coord(x[0], f.lo[0], f.S), kb);
-    uint32_t c1 = fine_cell(unit_coord(x[1], f.lo[1], f.S), kb);
-    uint32_t c2 = fine_cell(unit_coord(x[2], f.lo[2], f.S), kb);
+    const double u0 = unit_coord(x[0], f.lo[0], f.S), u1 = unit_coord(x[1], f.lo[1], f.S),
+                 u2 = unit_coord(x[2], f.lo[2], f.S);
+    u[3 * i] = u0;
+    u[3 * i + 1] = u1;
+    u[3 * i + 2] = u2;
+    uint32_t c0 = fine_cell(u0, kb);
+    uint32_t c1 = fine_cell(u1, kb);
+    uint32_t c2 = fine_cell(u2, kb);
     keys[i] = morton_encode(c0, c1, c2) | ((uint64_t)sy << (3 * kb));
     idx[i] = (uint32_t)i;
 }
 
-__global__ void k_gather_points(const double *src, const double *charges, int64_t ns, const double *tgt, int64_t n,
-                                int same, const Frame *frame, const uint64_t *skeys, int kb, const uint32_t *idx,
-                                double *ux, double *uy, double *uz, double *q, uint8_t *pflag, int32_t *pout,
-                                int32_t *psys) {
+__global__ void k_gather_points(const double *u, const double *charges, int64_t ns, int64_t n, int same,
+                                const uint64_t *skeys, int kb, const uint32_t *idx, double *ux, double *uy,
+                                double *uz, double *q, uint8_t *pflag, int32_t *pout, int32_t *psys) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int64_t i = idx[k];
-    const double *x = i < ns ? src + 3 * i : tgt + 3 * (i - ns);
-    const int sy = (int)(skeys[k] >> (3 * kb));
-    if (psys) psys[k] = sy;
-    const Frame f = frame[sy];
-    ux[k] = unit_coord(x[0], f.lo[0], f.S);
-    uy[k] = unit_coord(x[1], f.lo[1], f.S);
-    uz[k] = unit_coord(x[2], f.lo[2], f.S);
+    if (psys) psys[k] = (int)(skeys[k] >> (3 * kb));
+    ux[k] = u[3 * i];
+    uy[k] = u[3 * i + 1];
+    uz[k] = u[3 * i + 2];
     if (same) {
         q[k] = charges[i];
         pflag[k] = 3;
@@ -592,11 +595,16 @@ __device__ __forceinline__ double box_dist2(int la, int ax, int ay, int az, int 
     return d2;
 }
 
+// FILL = false: count every list (cnt, pairs) and write it to tmp, kNearCap
+// entries per target leaf (cap_over is set if a list is longer); FILL = true:
+// write the lists at their offsets
+constexpr int kNearCap = 128;
 template <bool FILL>
 __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bkey, const int8_t *blevel,
                              const int32_t *bparent, const int32_t *bchild0, const uint8_t *bcmask,
                              const uint8_t *bflags, const int32_t *bnsrc, const int32_t *bntgt, const int32_t *bcol,
-                             int32_t *cnt, const int32_t *off, int32_t *list, unsigned long long *pairs) {
+                             int32_t *cnt, const int32_t *off, int32_t *list, unsigned long long *pairs,
+                             int32_t *tmp, int *cap_over) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntl) return;
     int T = tleaves[i];
@@ -604,7 +612,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
     int tx, ty, tz;
     morton_decode(key_cell(bkey[T], a), tx, ty, tz);
     int n = 0;
-    int32_t *out = FILL ? list + off[i] : nullptr;
+    int32_t *out = FILL ? list + off[i] : tmp + (size_t)i * kNearCap;
     long long np = 0;
     int B = T;
     for (int b = a; b >= 0; --b) {
@@ -615,7 +623,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
             int cx, cy, cz;
             morton_decode(key_cell(bkey[C], b), cx, cy, cz);
             if (box_dist2(a, tx, ty, tz, b, cx, cy, cz) >= Rb * Rb) continue;
-            if (FILL) out[n] = C;
+            if (FILL || n < kNearCap) out[n] = C;
             np += bnsrc[C];
             ++n;
         }
@@ -636,15 +644,24 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
             int dx, dy, dz;
             morton_decode(key_cell(bkey[D], a + 1), dx, dy, dz);
             if (box_dist2(a, tx, ty, tz, a + 1, dx, dy, dz) >= R1 * R1) continue;
-            if (FILL) out[n] = D;
+            if (FILL || n < kNearCap) out[n] = D;
             np += bnsrc[D];
             ++n;
         }
     }
     if (!FILL) {
         cnt[i] = n;
+        if (n > kNearCap) atomicExch(cap_over, 1);
         atomicAdd(pairs, (unsigned long long)(np * (long long)bntgt[T]));
     }
+}
+
+// the counted lists, copied from the fixed-capacity scratch to their offsets
+__global__ void k_compact_lists(int ntl, const int32_t *tmp, const int32_t *off, int32_t *list) {
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= ntl) return;
+    const int o = off[i], n = off[i + 1] - o;
+    for (int k = threadIdx.x & 31; k < n; k += 32) list[o + k] = tmp[(size_t)i * kNearCap + k];
 }
 
 __global__ void k_list_target_leaves(int nb, const uint8_t *bflags, const int32_t *bntgt, const int32_t *excl,
@@ -762,7 +779,8 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     // ---- 2. keys and sort
     if (ws.ensure(keys, N * 8) || ws.ensure(keys2, N * 8) || ws.ensure(idx, N * 4) || ws.ensure(idx2, N * 4) ||
         ws.ensure(sort_tmp, radix_tmp_bytes(N)) || ws.ensure(ux, N * 8) || ws.ensure(uy, N * 8) ||
-        ws.ensure(uz, N * 8) || ws.ensure(q, N * 8) || ws.ensure(pflag, N) || ws.ensure(pout, N * 4) ||
+        ws.ensure(uz, N * 8) || ws.ensure(utmp, N * 24) || ws.ensure(q, N * 8) || ws.ensure(pflag, N) ||
+        ws.ensure(pout, N * 4) ||
         ws.ensure(pleaf, N * 4) || ws.ensure(plocal, N * (point_prec ? 16 : 32)) ||
         ws.ensure(plocal_lo, point_prec ? N * 16 : 16) ||
         ws.ensure(pscan0, (N + 1) * 4) || ws.ensure(pscan1, (N + 1) * 4) ||
@@ -772,7 +790,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     }
     ::dmk::launch_tick();
     k_make_keys<<<nblk(N, 256), 256, 0, st>>>(src, ns, same ? nullptr : tgt, N, (const Frame *)frame.p, d_off,
-                                              nsys, kb, (uint64_t *)keys.p, (uint32_t *)idx.p);
+                                              nsys, kb, (uint64_t *)keys.p, (uint32_t *)idx.p, (double *)utmp.p);
     uint64_t *skeys;
     uint32_t *sidx;
     radix_sort_pairs((uint64_t *)keys.p, (uint32_t *)idx.p, (uint64_t *)keys2.p, (uint32_t *)idx2.p, N, 63,
@@ -780,10 +798,10 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     sorted_keys = skeys;
     sorted_idx = sidx;
     ::dmk::launch_tick();
-    k_gather_points<<<nblk(N, 256), 256, 0, st>>>(src, charges, ns, same ? nullptr : tgt, N, same ? 1 : 0,
-                                                  (const Frame *)frame.p, skeys, kb, sidx, (double *)ux.p,
-                                                  (double *)uy.p, (double *)uz.p, (double *)q.p, (uint8_t *)pflag.p,
-                                                  (int32_t *)pout.p, forest ? (int32_t *)psys.p : nullptr);
+    k_gather_points<<<nblk(N, 256), 256, 0, st>>>((const double *)utmp.p, charges, ns, N, same ? 1 : 0, skeys, kb,
+                                                  sidx, (double *)ux.p, (double *)uy.p, (double *)uz.p,
+                                                  (double *)q.p, (uint8_t *)pflag.p, (int32_t *)pout.p,
+                                                  forest ? (int32_t *)psys.p : nullptr);
     CK(cudaGetLastError());
     int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1016,7 +1034,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     CK(cudaStreamSynchronize(st));
     if (ws.ensure(tleaves, (int64_t)std::max(ntleaves, 1) * 4) ||
         ws.ensure(nl_cnt, (int64_t)(ntleaves + 1) * 4) || ws.ensure(nl_off, (int64_t)(ntleaves + 1) * 4) ||
-        ws.ensure(pairs, 8)) {
+        ws.ensure(pairs, 8) || ws.ensure(nl_tmp, (int64_t)std::max(ntleaves, 1) * kNearCap * 4)) {
         err = "device allocation failed";
         return DMK_ERR_OOM_I;
     }
@@ -1024,34 +1042,43 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     k_list_target_leaves<<<nblk(nb, 128), 128, 0, st>>>(nb, (const uint8_t *)bflags.p, (const int32_t *)bntgt.p,
                                                          excl, istl, (int32_t *)tleaves.p);
     CK(cudaMemsetAsync(pairs.p, 0, 8, st));
+    CK(cudaMemsetAsync(d_flags + 9, 0, sizeof(int), st));  // a list longer than the scratch capacity
     if (ntleaves > 0) {
         ::dmk::launch_tick();
         k_near_lists<false><<<nblk(ntleaves, 128), 128, 0, st>>>(
             ntleaves, (const int32_t *)tleaves.p, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
             (const int32_t *)bparent.p, (const int32_t *)bchild0.p, (const uint8_t *)bcmask.p,
             (const uint8_t *)bflags.p, (const int32_t *)bnsrc.p, (const int32_t *)bntgt.p, (const int32_t *)bcol.p,
-            (int32_t *)nl_cnt.p, nullptr, nullptr, (unsigned long long *)pairs.p);
+            (int32_t *)nl_cnt.p, nullptr, nullptr, (unsigned long long *)pairs.p, (int32_t *)nl_tmp.p,
+            d_flags + 9);
         scan_exclusive_i32((int32_t *)nl_cnt.p, (int32_t *)nl_off.p, ntleaves, d_flags + 8, scan_tmp.p,
                            scan_tmp.bytes, st);
         ::dmk::launch_tick();
         k_set_last<<<1, 1, 0, st>>>((int32_t *)nl_off.p, ntleaves, d_flags + 8);
     }
-    int ntot = 0;
+    int ntot = 0, over = 0;
     CK(cudaMemcpyAsync(&ntot, d_flags + 8, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&over, d_flags + 9, 4, cudaMemcpyDeviceToHost, st));
     unsigned long long hp = 0;
     CK(cudaMemcpyAsync(&hp, pairs.p, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ntleaves == 0) ntot = 0;
     near_pairs = (int64_t)hp;
     if (ws.ensure(nl_src, (int64_t)std::max(ntot, 1) * 4)) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
-    if (ntleaves > 0)
-        { ::dmk::launch_tick();
+    if (ntleaves > 0 && !over) {
+        // every list fitted the scratch: copy them to their offsets
+        ::dmk::launch_tick();
+        k_compact_lists<<<nblk(ntleaves, 4), 128, 0, st>>>(ntleaves, (const int32_t *)nl_tmp.p,
+                                                           (const int32_t *)nl_off.p, (int32_t *)nl_src.p);
+    } else if (ntleaves > 0) {
+        // some list is longer than the scratch: traverse again, writing at the offsets
+        ::dmk::launch_tick();
         k_near_lists<true><<<nblk(ntleaves, 128), 128, 0, st>>>(
             ntleaves, (const int32_t *)tleaves.p, (const uint64_t *)bkey.p, (const int8_t *)blevel.p,
             (const int32_t *)bparent.p, (const int32_t *)bchild0.p, (const uint8_t *)bcmask.p,
             (const uint8_t *)bflags.p, (const int32_t *)bnsrc.p, (const int32_t *)bntgt.p, (const int32_t *)bcol.p,
-            nullptr, (const int32_t *)nl_off.p, (int32_t *)nl_src.p, nullptr);
-        }
+            nullptr, (const int32_t *)nl_off.p, (int32_t *)nl_src.p, nullptr, nullptr, nullptr);
+    }
     CK(cudaGetLastError());
     near_list_len = ntot;
     return 0;

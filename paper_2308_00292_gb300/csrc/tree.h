@@ -99,8 +99,8 @@ public:
     const uint32_t *sorted_idx = nullptr;
 
     // points (sorted)
-    DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, q, pflag, pout, pleaf, plocal, plocal_lo, pscan0, pscan1,
-        scan_tmp;
+    DBuf keys, keys2, idx, idx2, sort_tmp, ux, uy, uz, utmp, q, pflag, pout, pleaf, plocal, plocal_lo, pscan0,
+        pscan1, scan_tmp;
     DBuf bbox_part, frame, flags, forced, slist, sysoff, psys;  // frame: one per system
     // boxes
     int64_t box_cap = 0;
@@ -108,7 +108,7 @@ public:
     DBuf bscr0, bscr1, bscr2, slot2box;
     DBuf lvl_off9, lvl_cnt, lvl_excl;
     // near-field lists
-    DBuf tleaves, nl_cnt, nl_off, nl_src, pairs;
+    DBuf tleaves, nl_cnt, nl_off, nl_src, nl_tmp, pairs;
 
 private:
     int grow_boxes(int64_t need, cudaStream_t st, std::string &err);
