@@ -220,3 +220,19 @@ def test_full_size_clustered_sampled(dmk, oracle_mod):
             u = plan.eval(xd, qd).cpu().numpy()
         assert np.all(np.isfinite(u))
         assert rel(u[idx], ref) < 1e-6, (prec, rel(u[idx], ref))
+
+
+def test_full_size_clustered_sampled_eps1e9(dmk, oracle_mod):
+    """The same 1e7-point clustered cloud at eps = 1e-9 (the workload's second
+    precision; the FP64 path, since single precision cannot reach it): rel-L2
+    over 128 sampled targets against the direct sum <= 1e-9."""
+    cfg = inputs.CONFIGS["laplace3d_clustered_n1e7_eps1e-9"]
+    x, q = inputs.make(**cfg)
+    rng = np.random.default_rng(4)
+    idx = rng.choice(x.shape[0], 128, replace=False)
+    ref = oracle_mod.direct(x, q, x[idx])
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    with dmk.Plan(cfg["eps"], precision=dmk.DMK_FP64, leaf_cap=cfg["leaf_cap"]) as plan:
+        u = plan.eval(xd, qd).cpu().numpy()
+    assert np.all(np.isfinite(u))
+    assert rel(u[idx], ref) < 1e-9, rel(u[idx], ref)
