@@ -64,9 +64,11 @@ typedef enum {
 /* Flags for dmk_opts.flags. */
 enum {
     DMK_FLAG_FAR_ONLY = 1,    /* return only the far part (windowed + difference
-                                 kernels, eqs. farpotential): a diagnostic */
+                                 kernels, eqs. farpotential): a diagnostic; the
+                                 near-field pass is skipped */
     DMK_FLAG_NEAR_ONLY = 2,   /* return only the residual-kernel part and the
-                                 self corrections (eq. nearpotential, Step 5) */
+                                 self corrections (eq. nearpotential, Step 5); the
+                                 far-field passes are skipped */
     DMK_FLAG_HOST_ONLY = 4    /* dmk_plan: build the host-side tables only and
                                  touch no device (for inspecting the plan); such
                                  a plan cannot be evaluated */

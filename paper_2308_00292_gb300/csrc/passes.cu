@@ -1832,7 +1832,10 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
     PCK(cudaEventRecord(cx.fork, st));
     PCK(cudaStreamWaitEvent(cx.side, cx.fork, 0));
     cudaEventRecord(cx.nev[0], cx.side);
-    if (cx.tree->ntleaves > 0) {
+    // the diagnostic modes skip the half they do not return: far part only (1),
+    // near part only (2)
+    const bool do_far = cx.mode != 2, do_near = cx.mode != 1;
+    if (cx.tree->ntleaves > 0 && do_near) {
         NearArgs na{tv,
                     cx.tree->ntleaves,
                     (const int32_t *)cx.tree->tleaves.p,
@@ -1868,7 +1871,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         }
         PCK(cudaFuncSetAttribute(k_upward<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         const int lmax = tv.nlev - 1;
-        for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0; --l) {
+        for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0 && do_far; --l) {
             int lc = tv.lev_count[l];
             int grid = std::min(lc, maxgrid);
             if (grid <= 0) continue;
@@ -1887,7 +1890,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         return DMK_ERR_OOM;
     }
     C2 *Phi = (C2 *)cx.bufs->Phi.p;
-    if (!cx.tree->root_leaf && nslots > 0) {
+    if (do_far && !cx.tree->root_leaf && nslots > 0) {
         BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * P * NH * sizeof(C2), (size_t)P * N1 * NH * sizeof(C2),
                                      (size_t)P * NH * sizeof(T)},
                                     smem_limit);
@@ -1906,9 +1909,11 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         const size_t scr = (size_t)(2 * P * P * nhW + 2 * P * NW * nhW + NW * NW * nhW);
         const int grid = std::min(nroots, maxgrid);
         if (ws.ensure(cx.bufs->rootscr, (int64_t)grid * scr * sizeof(C2))) { err = "oom root"; return DMK_ERR_OOM; }
-        ::dmk::launch_tick();
-        k_root<T, P><<<grid, kThreads, 0, st>>>(tv, tb, M, nroots, LamW, (C2 *)cx.bufs->rootscr.p, scr);
-        PCK(cudaGetLastError());
+        if (do_far) {
+            ::dmk::launch_tick();
+            k_root<T, P><<<grid, kThreads, 0, st>>>(tv, tb, M, nroots, LamW, (C2 *)cx.bufs->rootscr.p, scr);
+            PCK(cudaGetLastError());
+        }
     }
     // ---- local expansions, coarsest level first; leaves evaluate
     {
@@ -1936,7 +1941,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             err = "device allocation failed (group translation)";
             return DMK_ERR_OOM;
         }
-        for (int l = 0; l < tv.nlev; ++l) {
+        for (int l = 0; l < tv.nlev && do_far; ++l) {
             int lc = tv.lev_count[l];
             int grid = std::min((lc + 7) / 8, cx.num_sms);
             if (grid <= 0) continue;
