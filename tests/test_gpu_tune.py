@@ -77,3 +77,17 @@ def test_invalid_candidates_leave_the_plan_unchanged(dmk):
         with pytest.raises(dmk.DMKError):
             plan.tune_leaf_cap(dev(x), dev(q), candidates=[100], reps=1000)
         assert plan.params()["leaf_cap"] == 90
+
+
+def test_batch_tuner(dmk, oracle_mod):
+    x, q, off = inputs.batch(12, seed=616, n_lo=300, n_hi=4000)
+    xd, qd = dev(x), dev(q)
+    with dmk.Plan(eps=1e-6, precision=1) as plan:
+        best, times = plan.tune_leaf_cap_batch(xd, qd, off, candidates=[30, 90, 250], reps=1)
+        assert best in (30, 90, 250)
+        assert times[best] == min(times.values())
+        assert plan.params()["leaf_cap"] == best
+        u = plan.eval_batch(xd, qd, off).cpu().numpy()
+    for s in range(len(off) - 1):
+        a, b = off[s], off[s + 1]
+        assert rel(u[a:b], oracle_mod.direct(x[a:b], q[a:b])) < 1e-6, s

@@ -112,3 +112,12 @@ def test_unsupported_combinations(dmk):
         # a single-system batch is the plain evaluation
         u = plan.eval_batch(dev(x), dev(q), [0, 500]).cpu().numpy()
         assert np.all(np.isfinite(u))
+
+
+def test_fp64_separate_targets_match_oracle(dmk, oracle_mod):
+    x, q = inputs.clustered(4000, seed=908, nclusters=3)
+    y = np.random.default_rng(909).random((1200, 3))
+    u = run(dmk, x, q, y, eps=1e-9, leaf_cap=60, precision=0, lam=7.0)
+    ref = oracle_mod.dmk(x, q, y, eps=1e-9, leaf_cap=60, lam=7.0)
+    assert rel(u, ref) < 2e-1 * 1e-9
+    assert rel(u, oracle_mod.direct(x, q, y, lam=7.0)) < 1e-9
