@@ -115,8 +115,8 @@ NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares,
 TRAFFIC = {
     # bytes per algorithmic flop
     "k_local": ("paper_2308_00292_gb300/csrc/passes.cu",
-                "4535c7a894c11b156b3a3b4c1a2a925d0d5758ae4d048b071dfabaa630272870",
-                (1389.2e6 + 1111.2e6) / 7.106e10),
+                "6c5879d89bc324243013b044981eebeadc2bbadc368f8c5b0c170913fc313ed5",
+                (1413.1e6 + 1110.7e6) / 7.106e10),
     # bytes per candidate pair
     "k_near": ("paper_2308_00292_gb300/csrc/near.cu",
                "da5054e095dbfb3012a473a0d690619f48e9e42b21dd55c41fc453b0aadca925",

@@ -235,8 +235,11 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
         // the previous batch's MMAs read the operands: they must be done
         if (pending && tid == 0) ok = tc::mbar_wait(bar, pend_par, 2000000000ll) && ok;
         __syncthreads();
-        // A operand: row bc, column j (K-major core matrices), 4 points per float4
-        for (int t = tid; t < U::A_FL / 4; t += blockDim.x) {
+        // A operand: row bc, column j (K-major core matrices), 4 points per float4;
+        // a fixed trip count, unrolled, so that the loads of all of a thread's
+        // elements are in flight together
+#pragma unroll
+        for (int t = tid; t < U::A_FL / 4; t += kThreads) {
             const int r8 = t & 7, k4 = (t >> 3) % (KC / 4), bc = ((t >> 3) / (KC / 4)) * 8 + r8;
             float h[4], l[4];
 #pragma unroll
@@ -249,7 +252,8 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
             reinterpret_cast<float4 *>(Al)[t] = make_float4(l[0], l[1], l[2], l[3]);
         }
         // B operand: row a, column j
-        for (int t = tid; t < U::B_FL / 4; t += blockDim.x) {
+#pragma unroll
+        for (int t = tid; t < U::B_FL / 4; t += kThreads) {
             const int r8 = t & 7, k4 = (t >> 3) % (KC / 4), a = ((t >> 3) / (KC / 4)) * 8 + r8;
             float h[4], l[4];
 #pragma unroll
@@ -297,7 +301,8 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
         const bool wok = __all_sync(0xffffffffu, ok);
         tc::fence_after_sync();
         if (wok) {
-            const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+            const int warp = tid >> 5, lane = tid & 31, nw = kThreads >> 5;
+#pragma unroll
             for (int mt = warp >> 2; mt < U::MT; mt += nw >> 2) {
                 const int bc = mt * 128 + (warp & 3) * 32 + lane;
                 const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * U::NA);
@@ -894,6 +899,8 @@ __device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ntot = ro[nr];
     // B operand: row ab, column c of Lev; one float4 (4 columns) per step
+    // (unrolled: a fixed trip count, all loads of a thread in flight together)
+#pragma unroll
     for (int t = tid; t < S::NP * S::KP / 4; t += kLThreads) {
         const int r = t & 7, k4 = (t >> 3) % (S::KP / 4), n = ((t >> 3) / (S::KP / 4)) * 8 + r;
         float h[4], l[4];
