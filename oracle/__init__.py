@@ -94,6 +94,16 @@ def _load():
             lib.oracle_h.restype = ctypes.c_double
             lib.oracle_hW.argtypes = [ctypes.POINTER(Params)]
             lib.oracle_hW.restype = ctypes.c_double
+            lib.oracle_direct_log2d.argtypes = [dp, dp, i64, dp, i64, dp, ctypes.c_int]
+            lib.oracle_direct_log2d.restype = None
+            lib.oracle_dmk_log2d.argtypes = [ctypes.POINTER(Params), dp, dp, i64, dp, i64, dp, dp, dp]
+            lib.oracle_dmk_log2d.restype = ctypes.c_int
+            lib.oracle_kernel_log2d.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, dp, i64, dp]
+            lib.oracle_kernel_log2d.restype = None
+            lib.oracle_hW_log2d.argtypes = [ctypes.POINTER(Params)]
+            lib.oracle_hW_log2d.restype = ctypes.c_double
+            lib.oracle_n0_log2d.argtypes = [ctypes.POINTER(Params)]
+            lib.oracle_n0_log2d.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -249,3 +259,61 @@ def h(prm: Params, level: int) -> float:
 
 def hW(prm: Params) -> float:
     return _load().oracle_hW(ctypes.byref(prm))
+
+
+# ---- the 2D Laplace kernel log r (Sec. 3.7 at lambda = 0, in the plane) ----
+
+def params_log2d(eps=1e-6, leaf_cap=120, nthreads=0, **kw) -> Params:
+    """Parameters of the 2D pass; fields left at 0 are filled by the library
+    (c, p, nf from Table 1, n0 from the 2D root window)."""
+    prm = Params()
+    prm.splitting = PSWF
+    prm.eps = eps
+    prm.leaf_cap = leaf_cap
+    prm.nthreads = nthreads
+    for k, v in kw.items():
+        setattr(prm, k, v)
+    return prm
+
+
+def direct_log2d(src, rho, tgt=None, nthreads=0) -> np.ndarray:
+    """O1 in the plane: u_i = sum_{j: y_j != x_i} rho_j log |x_i - y_j|."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    rho = _c64(rho, src.shape[0])
+    tgt = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros(tgt.shape[0])
+    _load().oracle_direct_log2d(_dp(src), _dp(rho), src.shape[0], _dp(tgt), tgt.shape[0], _dp(out), nthreads)
+    return out
+
+
+def dmk_log2d(src, rho, tgt=None, prm: Params | None = None, parts: bool = False, **kw):
+    """O2 in the plane for log r.  Returns the potentials (input units), or
+    (pot, far, near) with the unit-box far and near parts if parts is True."""
+    prm = prm if prm is not None else params_log2d(**kw)
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    rho = _c64(rho, src.shape[0])
+    tgt_a = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 2)
+    nt = tgt_a.shape[0]
+    pot, far, near = np.zeros(nt), np.zeros(nt), np.zeros(nt)
+    rc = _load().oracle_dmk_log2d(ctypes.byref(prm), _dp(src), _dp(rho), src.shape[0], _dp(tgt_a), nt,
+                                  _dp(pot), _dp(far), _dp(near))
+    if rc != 0:
+        raise RuntimeError("oracle_dmk_log2d failed with code %d" % rc)
+    return (pot, far, near) if parts else pot
+
+
+def kernel_log2d(prm: Params, what: int, level: int, r) -> np.ndarray:
+    """2D pieces: S_MOLLIFIED gives S_l(0) (r ignored), R_RESIDUAL R_l(r),
+    DHAT Dhat_l(k), WHAT What_0(k)."""
+    r = np.ascontiguousarray(np.atleast_1d(r), dtype=np.float64)
+    out = np.zeros_like(r)
+    _load().oracle_kernel_log2d(ctypes.byref(prm), what, level, _dp(r), r.size, _dp(out))
+    return out
+
+
+def hW_log2d(prm: Params) -> float:
+    return _load().oracle_hW_log2d(ctypes.byref(prm))
+
+
+def n0_log2d(prm: Params) -> int:
+    return _load().oracle_n0_log2d(ctypes.byref(prm))

@@ -15,6 +15,8 @@
  *   4. O1: the direct sum (eq. discretesum with zero self-interaction)
  *   5. the level-restricted adaptive tree (Sec. 3.2, Step 0)
  *   6. the DMK algorithm, Steps 0-5 of Sec. 3.4
+ *   7. the 2D Laplace kernel log r: the Fourier-space splitting of Sec. 3.7
+ *      at lambda = 0 in the plane, a quad-tree, and Steps 0-5 in 2D
  *
  * Readings of the paper taken here:
  *   - Fourier spacing h_l = 2 pi / (3 R_l): the difference kernel D_l has
@@ -1757,4 +1759,815 @@ double oracle_hW(const oracle_params *prm)
     double h = sp.hW;
     split_free(&sp);
     return h;
+}
+
+/* ====================================================================== */
+/* 7. The 2D Laplace kernel log r (Sec. 3.7 at lambda = 0, in the plane)   */
+/* ====================================================================== */
+/*
+ * u_i = sum_{j : y_j != x_i} rho_j log |x_i - y_j| for points in the plane.
+ *
+ * In two dimensions the transform of log r is -2 pi / k^2 (a finite part;
+ * the delta term it leaves undetermined drops out of every piece below,
+ * since each piece carries a factor that vanishes at k = 0).  The splitting
+ * of Sec. 3.7 (eq. yukawaPSWFkernels at lambda = 0, psi(0) = 1) gives
+ *   Dhat_l(k) = -2 pi (psi(k R_{l+1} / c) - psi(k R_l / c)) / k^2,
+ *     Dhat_l(0) = -pi (c_2 / c_0) (R_l^2 - R_{l+1}^2),
+ *   Rhat_L(k) = -2 pi (1 - psi(k R_L / c)) / k^2,
+ * and the radial inverse transform of Rhat_L is the residual kernel
+ *   R_L(r) = F(r / R_L),  F(rho) = -int_0^inf (1 - psi(k / c)) J_0(k rho) / k dk.
+ * With int_0^inf (J_0(t) - [t < 1]) / t dt = log 2 - gamma (Euler's constant)
+ * the tail of the slowly decaying part is summed in closed form:
+ *   F(rho) = log(rho K / 2) + gamma - int_0^K (1 - psi(k / c) J_0(k rho)) / k dk,
+ * exact up to the part of psi beyond k = K, taken as K = 4 c (psi(x) is below
+ * psi(1) / (c x) there).  The integrand is smooth (O(k) at 0) and is summed
+ * with Gauss-Legendre panels.  F(rho) - log rho is smooth, so the mollified
+ * kernel log r - R_L(r) has the finite value at r = 0
+ *   S_L(0) = log R_L - log(K / 2) - gamma + int_0^K (1 - psi(k / c)) / k dk,
+ * which a coincident source adds through the far field (Step 5 removes it).
+ * The windowed root kernel is the kernel truncated at R_t = 1 + sqrt 2 (the
+ * diameter of the unit square plus the mollifier's radius R_0 = 1), times
+ * the mollifier:
+ *   What_0(k) = psi(k / c) 2 pi (R_t log R_t J_1(k R_t) / k - (1 - J_0(k R_t)) / k^2),
+ *   What_0(0) = pi R_t^2 (log R_t - 1/2),
+ * sampled with spacing h_W = 2 pi / (2 + R_t) (separations are at most 1 per
+ * coordinate).  The difference kernels use the spacing h_l = 2 pi / (3 R_l)
+ * of the 3D pass and weights (h / 2 pi)^2.  The Table 1 parameters (c, p,
+ * nf) carry over: the transforms decay through psi in the same way, and the
+ * 1/k^2 factor is the same as for 1/r in 3D.
+ * The unit-box map (the 3D one restricted to two coordinates) turns
+ * log |x - y| into log S + log |u - v|: the potential in input units adds
+ * log S times the charge of the sources not coincident with the target.
+ */
+
+#define L2_PANELS 10
+#define L2_NODES 20
+#define L2_NQ (L2_PANELS * L2_NODES)
+#define L2_EULER_GAMMA 0.57721566490153286061
+
+typedef struct {
+    oracle_params prm;
+    pswf_t *pswf;
+    double Rt, hW, K;
+    double qk[L2_NQ], qw[L2_NQ], qpsi[L2_NQ]; /* nodes, weights / k, psi(k / c) */
+    double G0;                                /* F(rho) - log rho at rho = 0 */
+} split2_t;
+
+static int split2_init(split2_t *sp, const oracle_params *in)
+{
+    memset(sp, 0, sizeof(*sp));
+    sp->prm = *in;
+    if (sp->prm.splitting != ORACLE_PSWF) return -1;
+    sp->Rt = 1.0 + sqrt(2.0);
+    sp->hW = 2.0 * M_PI / (2.0 + sp->Rt);
+    /* the 3D defaults, with the root modes for the 2D window */
+    oracle_params tmp = sp->prm;
+    tmp.n0 = 1;
+    oracle_default_params(&tmp);
+    if (sp->prm.n0 <= 0) sp->prm.n0 = (int)ceil(tmp.c / sp->hW) + 1;
+    tmp.n0 = sp->prm.n0;
+    sp->prm = tmp;
+    sp->pswf = (pswf_t *)malloc(sizeof(pswf_t));
+    if (!sp->pswf) return -1;
+    pswf_init(sp->pswf, sp->prm.c);
+    sp->K = 4.0 * sp->prm.c;
+    double xg[L2_NODES], wg[L2_NODES];
+    gauss_legendre(L2_NODES, xg, wg);
+    double acc = 0.0, pw = sp->K / L2_PANELS;
+    for (int q = 0, j = 0; q < L2_PANELS; ++q)
+        for (int i = 0; i < L2_NODES; ++i, ++j) {
+            double k = pw * (q + 0.5 * (xg[i] + 1.0));
+            sp->qk[j] = k;
+            sp->qw[j] = 0.5 * pw * wg[i] / k;
+            sp->qpsi[j] = pswf_eval(sp->pswf, k / sp->prm.c);
+            acc += sp->qw[j] * (1.0 - sp->qpsi[j]);
+        }
+    sp->G0 = log(0.5 * sp->K) + L2_EULER_GAMMA - acc;
+    return 0;
+}
+
+static void split2_free(split2_t *sp)
+{
+    free(sp->pswf);
+    sp->pswf = NULL;
+}
+
+/* residual kernel R_l(r) = F(r / R_l), r > 0 */
+static double split2_R(const split2_t *sp, int l, double r)
+{
+    double rho = r / level_R(l), acc = 0.0;
+    for (int j = 0; j < L2_NQ; ++j) acc += sp->qw[j] * (1.0 - sp->qpsi[j] * j0(sp->qk[j] * rho));
+    return log(rho * 0.5 * sp->K) + L2_EULER_GAMMA - acc;
+}
+
+/* mollified kernel at r = 0: lim (log r - R_l(r)) */
+static double split2_S0(const split2_t *sp, int l) { return log(level_R(l)) - sp->G0; }
+
+static double split2_Dhat(const split2_t *sp, int l, double k)
+{
+    double R = level_R(l), R1 = level_R(l + 1);
+    const pswf_t *s = sp->pswf;
+    if (k == 0.0) return -M_PI * s->c2 / s->c0 * (R * R - R1 * R1);
+    return -2.0 * M_PI * pswf_diff(s, k * R1 / s->c, k * R / s->c) / (k * k);
+}
+
+static double split2_What(const split2_t *sp, double k)
+{
+    double Rt = sp->Rt, win = pswf_eval(sp->pswf, k / sp->pswf->c);
+    if (k == 0.0) return M_PI * Rt * Rt * (log(Rt) - 0.5) * win;
+    return 2.0 * M_PI * (Rt * log(Rt) * j1(k * Rt) / k - (1.0 - j0(k * Rt)) / (k * k)) * win;
+}
+
+void oracle_direct_log2d(const double *src, const double *rho, int64_t ns,
+                         const double *tgt, int64_t nt, double *pot, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nt; ++i) {
+        double sum = 0.0, comp = 0.0;
+        for (int64_t j = 0; j < ns; ++j) {
+            double dx = tgt[2 * i] - src[2 * j], dy = tgt[2 * i + 1] - src[2 * j + 1];
+            if (dx == 0.0 && dy == 0.0) continue;
+            double v = rho[j] * 0.5 * log(dx * dx + dy * dy);
+            double t = sum + v; /* Neumaier */
+            if (fabs(sum) >= fabs(v)) comp += (sum - t) + v; else comp += (v - t) + sum;
+            sum = t;
+        }
+        pot[i] = sum + comp;
+    }
+}
+
+/* ---- quad-tree (the 3D rules of Sec. 3.2 Step 0 in two dimensions) ---- */
+
+typedef struct {
+    int level;
+    int64_t ix, iy;
+    int parent;
+    int child[4];
+    int64_t start, count;
+    int leaf;
+    int64_t nsrc, ntgt;
+    int col[9];
+    int ncol;
+    int fout, fin, has_local;
+    double *proxy;
+    cplx *Phi;
+    double *local;
+} obox2;
+
+typedef struct {
+    int64_t n;
+    double *u;          /* unit-box coordinates [n][2] */
+    int64_t *cell;      /* finest (level 21) cell [n][2] */
+    double *q;
+    char *is_src, *is_tgt;
+    int64_t *out_index;
+    double S;
+} opoints2;
+
+typedef struct {
+    obox2 *b;
+    int nb, cap;
+    int64_t *ord;
+    int lev_start[23], lev_count[23];
+    int nlev;
+} otree2;
+
+static uint64_t morton2(int64_t ix, int64_t iy, int level)
+{
+    uint64_t m = 0;
+    for (int b = 0; b < level; ++b) {
+        m |= (uint64_t)((ix >> b) & 1) << (2 * b);
+        m |= (uint64_t)((iy >> b) & 1) << (2 * b + 1);
+    }
+    return m;
+}
+
+static uint64_t cell_key2(int level, int64_t ix, int64_t iy)
+{
+    return morton2(ix, iy, level) | ((uint64_t)1 << (2 * level));
+}
+
+static int tree2_push(otree2 *t, const obox2 *b)
+{
+    if (t->nb == t->cap) {
+        int nc = t->cap ? 2 * t->cap : 1024;
+        obox2 *nbp = (obox2 *)realloc(t->b, (size_t)nc * sizeof(obox2));
+        if (!nbp) return -1;
+        t->b = nbp;
+        t->cap = nc;
+    }
+    t->b[t->nb++] = *b;
+    return t->nb - 1;
+}
+
+static int tree2_find(const otree2 *t, int level, int64_t ix, int64_t iy)
+{
+    if (level >= t->nlev) return -1;
+    int64_t lim = (int64_t)1 << level;
+    if (ix < 0 || iy < 0 || ix >= lim || iy >= lim) return -1;
+    uint64_t key = morton2(ix, iy, level);
+    int lo = t->lev_start[level], hi = lo + t->lev_count[level] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        uint64_t mk = morton2(t->b[mid].ix, t->b[mid].iy, level);
+        if (mk == key) return mid;
+        if (mk < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+static int tree2_build(otree2 *t, const opoints2 *P, const oracle_params *prm,
+                       const uint64_t *forced, int nforced)
+{
+    t->nb = 0;
+    for (int64_t i = 0; i < P->n; ++i) t->ord[i] = i;
+    int64_t *tmp = (int64_t *)malloc((size_t)(P->n > 0 ? P->n : 1) * sizeof(int64_t));
+    if (!tmp) return -1;
+    obox2 root;
+    memset(&root, 0, sizeof(root));
+    root.parent = -1;
+    for (int c = 0; c < 4; ++c) root.child[c] = -1;
+    root.count = P->n;
+    if (tree2_push(t, &root) < 0) { free(tmp); return -1; }
+    t->nlev = 1;
+    t->lev_start[0] = 0;
+    t->lev_count[0] = 1;
+    for (int l = 0; l < prm->max_level; ++l) {
+        int s = t->lev_start[l], e = s + t->lev_count[l];
+        int next_start = t->nb;
+        for (int bi = s; bi < e; ++bi) {
+            obox2 *b = &t->b[bi];
+            int same_cell = 1;
+            if (b->count > prm->leaf_cap) {
+                int64_t p0 = t->ord[b->start];
+                for (int64_t k = b->start + 1; k < b->start + b->count && same_cell; ++k) {
+                    int64_t pk = t->ord[k];
+                    if (P->cell[2 * pk] != P->cell[2 * p0] || P->cell[2 * pk + 1] != P->cell[2 * p0 + 1])
+                        same_cell = 0;
+                }
+            }
+            int split = (b->count > prm->leaf_cap && !same_cell) ||
+                        key_in(forced, nforced, cell_key2(l, b->ix, b->iy));
+            if (!split) continue;
+            int64_t cnt[4] = {0}, off[4], o2[4];
+            int shift = 20 - l;
+            for (int64_t k = b->start; k < b->start + b->count; ++k) {
+                int64_t pi = t->ord[k];
+                cnt[((P->cell[2 * pi] >> shift) & 1) | (((P->cell[2 * pi + 1] >> shift) & 1) << 1)]++;
+            }
+            off[0] = b->start;
+            for (int c = 1; c < 4; ++c) off[c] = off[c - 1] + cnt[c - 1];
+            memcpy(o2, off, sizeof(off));
+            for (int64_t k = b->start; k < b->start + b->count; ++k) {
+                int64_t pi = t->ord[k];
+                tmp[o2[((P->cell[2 * pi] >> shift) & 1) | (((P->cell[2 * pi + 1] >> shift) & 1) << 1)]++] = pi;
+            }
+            memcpy(t->ord + b->start, tmp + b->start, (size_t)b->count * sizeof(int64_t));
+            int64_t bix = b->ix, biy = b->iy;
+            for (int c = 0; c < 4; ++c) {
+                if (cnt[c] == 0) continue;
+                obox2 ch;
+                memset(&ch, 0, sizeof(ch));
+                ch.level = l + 1;
+                ch.ix = 2 * bix + (c & 1);
+                ch.iy = 2 * biy + ((c >> 1) & 1);
+                ch.parent = bi;
+                for (int q = 0; q < 4; ++q) ch.child[q] = -1;
+                ch.start = off[c];
+                ch.count = cnt[c];
+                int id = tree2_push(t, &ch);
+                if (id < 0) { free(tmp); return -1; }
+                t->b[bi].child[c] = id;
+            }
+        }
+        if (t->nb == next_start) break;
+        t->lev_start[l + 1] = next_start;
+        t->lev_count[l + 1] = t->nb - next_start;
+        t->nlev = l + 2;
+    }
+    free(tmp);
+    for (int i = 0; i < t->nb; ++i) {
+        obox2 *b = &t->b[i];
+        b->leaf = 1;
+        for (int c = 0; c < 4; ++c) if (b->child[c] >= 0) b->leaf = 0;
+    }
+    return 0;
+}
+
+/* level restriction, as in 3D: rebuild with violating leaves forced to split */
+static int tree2_build_balanced(otree2 *t, const opoints2 *P, const oracle_params *prm)
+{
+    uint64_t *forced = NULL;
+    int nforced = 0, capf = 0;
+    for (int iter = 0; iter < 64; ++iter) {
+        if (tree2_build(t, P, prm, forced, nforced) < 0) { free(forced); return -1; }
+        int added = 0;
+        for (int i = 0; i < t->nb; ++i) {
+            obox2 *T = &t->b[i];
+            if (!T->leaf || T->level + 1 >= t->nlev) continue;
+            int viol = 0;
+            for (int64_t jx = 2 * T->ix - 1; jx <= 2 * T->ix + 2 && !viol; ++jx)
+                for (int64_t jy = 2 * T->iy - 1; jy <= 2 * T->iy + 2 && !viol; ++jy) {
+                    int A = tree2_find(t, T->level + 1, jx, jy);
+                    if (A >= 0 && !t->b[A].leaf) viol = 1;
+                }
+            if (viol) {
+                if (nforced == capf) {
+                    capf = capf ? 2 * capf : 256;
+                    uint64_t *nfp = (uint64_t *)realloc(forced, (size_t)capf * sizeof(uint64_t));
+                    if (!nfp) { free(forced); return -1; }
+                    forced = nfp;
+                }
+                forced[nforced++] = cell_key2(T->level, T->ix, T->iy);
+                added = 1;
+            }
+        }
+        if (!added) { free(forced); return 0; }
+        qsort(forced, (size_t)nforced, sizeof(uint64_t), cmp_u64);
+    }
+    free(forced);
+    return -2;
+}
+
+static void tree2_free(otree2 *t)
+{
+    for (int i = 0; i < t->nb; ++i) {
+        free(t->b[i].proxy);
+        free(t->b[i].Phi);
+        free(t->b[i].local);
+    }
+    free(t->b);
+    free(t->ord);
+    memset(t, 0, sizeof(*t));
+}
+
+static int points2_init(opoints2 *P, const double *src, const double *rho, int64_t ns,
+                        const double *tgt, int64_t nt)
+{
+    memset(P, 0, sizeof(*P));
+    int same = (tgt == src && nt == ns);
+    int64_t n = same ? ns : ns + nt;
+    P->n = n;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    P->u = (double *)malloc(nn * 2 * sizeof(double));
+    P->cell = (int64_t *)malloc(nn * 2 * sizeof(int64_t));
+    P->q = (double *)malloc(nn * sizeof(double));
+    P->is_src = (char *)malloc(nn);
+    P->is_tgt = (char *)malloc(nn);
+    P->out_index = (int64_t *)malloc(nn * sizeof(int64_t));
+    if (!P->u || !P->cell || !P->q || !P->is_src || !P->is_tgt || !P->out_index) return -1;
+    double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = (i < ns) ? &src[2 * i] : &tgt[2 * (i - ns)];
+        for (int d = 0; d < 2; ++d) {
+            if (x[d] < lo[d]) lo[d] = x[d];
+            if (x[d] > hi[d]) hi[d] = x[d];
+        }
+    }
+    double S = 0.0;
+    for (int d = 0; d < 2; ++d) if (n > 0 && hi[d] - lo[d] > S) S = hi[d] - lo[d];
+    if (S == 0.0) S = 1.0;
+    P->S = S;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = (i < ns) ? &src[2 * i] : &tgt[2 * (i - ns)];
+        for (int d = 0; d < 2; ++d) {
+            volatile double diff = x[d] - lo[d];
+            double u = diff / S;
+            P->u[2 * i + d] = u;
+            int64_t c = (int64_t)floor(u * 2097152.0);
+            if (c > 2097151) c = 2097151;
+            if (c < 0) c = 0;
+            P->cell[2 * i + d] = c;
+        }
+        P->is_src[i] = same || i < ns;
+        P->is_tgt[i] = same || i >= ns;
+        P->q[i] = P->is_src[i] ? rho[i] : 0.0;
+        P->out_index[i] = same ? i : (i < ns ? -1 : i - ns);
+    }
+    return 0;
+}
+
+static void points2_free(opoints2 *P)
+{
+    free(P->u); free(P->cell); free(P->q); free(P->is_src); free(P->is_tgt); free(P->out_index);
+    memset(P, 0, sizeof(*P));
+}
+
+static int tree2_make(otree2 *t, const opoints2 *P, const oracle_params *prm)
+{
+    memset(t, 0, sizeof(*t));
+    t->ord = (int64_t *)malloc((size_t)(P->n > 0 ? P->n : 1) * sizeof(int64_t));
+    if (!t->ord) return -1;
+    int rc = tree2_build_balanced(t, P, prm);
+    if (rc < 0) return rc;
+    for (int i = 0; i < t->nb; ++i) {
+        obox2 *b = &t->b[i];
+        b->nsrc = b->ntgt = 0;
+        for (int64_t k = b->start; k < b->start + b->count; ++k) {
+            b->nsrc += P->is_src[t->ord[k]];
+            b->ntgt += P->is_tgt[t->ord[k]];
+        }
+        b->ncol = 0;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy) {
+                int c = tree2_find(t, b->level, b->ix + dx, b->iy + dy);
+                if (c >= 0) b->col[b->ncol++] = c;
+            }
+    }
+    for (int i = 0; i < t->nb; ++i) t->b[i].fout = !t->b[i].leaf && t->b[i].nsrc > 0;
+    for (int i = 0; i < t->nb; ++i) {
+        obox2 *b = &t->b[i];
+        b->fin = 0;
+        if (b->ntgt == 0) continue;
+        for (int k = 0; k < b->ncol; ++k) if (t->b[b->col[k]].fout) b->fin = 1;
+    }
+    return 0;
+}
+
+/* ---- the 2D transforms: the 3D ones with one axis fewer ---------------- */
+
+/* Y = (Mx (x) My) X for a real p^2 array */
+static void tensor2_real(const double *Mx, const double *My, int p, const double *X, double *Y)
+{
+    double *w = (double *)malloc((size_t)p * p * sizeof(double));
+    for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < p; ++k) acc += My[b * p + k] * X[a * p + k];
+            w[a * p + b] = acc;
+        }
+    for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < p; ++k) acc += Mx[a * p + k] * w[k * p + b];
+            Y[a * p + b] = acc;
+        }
+    free(w);
+}
+
+static void form_proxy2(const ops_t *o, const opoints2 *P, const otree2 *t, const obox2 *b, double *proxy)
+{
+    int p = o->p;
+    double R = level_R(b->level);
+    double cx = (b->ix + 0.5) * R, cy = (b->iy + 0.5) * R;
+    double ax[64], ay[64];
+    memset(proxy, 0, (size_t)p * p * sizeof(double));
+    for (int64_t k = b->start; k < b->start + b->count; ++k) {
+        int64_t pi = t->ord[k];
+        if (!P->is_src[pi]) continue;
+        anterp_weights(o, 2.0 * (P->u[2 * pi] - cx) / R, ax);
+        anterp_weights(o, 2.0 * (P->u[2 * pi + 1] - cy) / R, ay);
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) proxy[i * p + j] += P->q[pi] * ax[i] * ay[j];
+    }
+}
+
+static void prox2pw2(const ops_t *o, double h, double R, int nh, const double *proxy, cplx *Phi)
+{
+    int p = o->p, N = 2 * nh + 1;
+    cplx *E = (cplx *)malloc((size_t)N * p * sizeof(cplx));
+    cplx *X = (cplx *)malloc((size_t)p * p * sizeof(cplx));
+    cplx *Y1 = (cplx *)malloc((size_t)N * p * sizeof(cplx));
+    for (int m = -nh; m <= nh; ++m)
+        for (int j = 0; j < p; ++j) E[(m + nh) * p + j] = cexp(-I * h * m * 0.5 * R * o->t[j]);
+    for (int i = 0; i < p * p; ++i) X[i] = proxy[i];
+    int d0[3] = {p, p, 1}, d1[3] = {N, p, 1};
+    mode_apply_c(E, N, p, X, d0, 0, Y1);
+    mode_apply_c(E, N, p, Y1, d1, 1, Phi);
+    free(E); free(X); free(Y1);
+}
+
+static void pw2poly2(const ops_t *o, double h, double R, int nh, const cplx *Psi, double *coef)
+{
+    int p = o->p, N = 2 * nh + 1;
+    cplx *F = (cplx *)malloc((size_t)p * N * sizeof(cplx));
+    cplx *Y1 = (cplx *)malloc((size_t)p * N * sizeof(cplx));
+    cplx *Y2 = (cplx *)malloc((size_t)p * p * sizeof(cplx));
+    double *vals = (double *)malloc((size_t)p * p * sizeof(double));
+    for (int n = 0; n < p; ++n)
+        for (int m = -nh; m <= nh; ++m) F[n * N + (m + nh)] = cexp(I * h * m * 0.5 * R * o->t[n]);
+    int d0[3] = {N, N, 1}, d1[3] = {p, N, 1};
+    mode_apply_c(F, p, N, Psi, d0, 0, Y1);
+    mode_apply_c(F, p, N, Y1, d1, 1, Y2);
+    for (int i = 0; i < p * p; ++i) vals[i] = creal(Y2[i]);
+    tensor2_real(o->Vinv, o->Vinv, p, vals, coef);
+    free(F); free(Y1); free(Y2); free(vals);
+}
+
+static double eval_local2(const ops_t *o, const obox2 *b, const double *coef, const double *u)
+{
+    int p = o->p;
+    double R = level_R(b->level);
+    double tx[64], ty[64];
+    double xi = 2.0 * (u[0] - (b->ix + 0.5) * R) / R, yi = 2.0 * (u[1] - (b->iy + 0.5) * R) / R;
+    for (int n = 0; n < p; ++n) {
+        tx[n] = cheb_t(n, xi);
+        ty[n] = cheb_t(n, yi);
+    }
+    double acc = 0.0;
+    for (int a = 0; a < p; ++a) {
+        double s = 0.0;
+        for (int b2 = 0; b2 < p; ++b2) s += coef[a * p + b2] * ty[b2];
+        acc += tx[a] * s;
+    }
+    return acc;
+}
+
+static int add_subtree_leaves2(const otree2 *t, int X, int S, ilist *lists)
+{
+    const obox2 *b = &t->b[X];
+    if (b->leaf) return ilist_push(&lists[X], S);
+    for (int c = 0; c < 4; ++c)
+        if (b->child[c] >= 0 && add_subtree_leaves2(t, b->child[c], S, lists) < 0) return -1;
+    return 0;
+}
+
+/* Steps 2-5 of Sec. 3.4 in the plane (unit-box potentials) */
+static int run_dmk2(const split2_t *sp, const opoints2 *P, otree2 *t, double *ufar, double *unear)
+{
+    const oracle_params *prm = &sp->prm;
+    ops_t o;
+    if (ops_init(&o, prm->p, prm->nf, prm->n0) != 0) { ops_free(&o); return -1; }
+    int p = o.p, p2 = p * p, N1 = o.N1, NF = N1 * N1, nf = o.nf;
+    int Lmax = t->nlev - 1, rc = 0;
+    for (int64_t i = 0; i < P->n; ++i) { ufar[i] = 0.0; unear[i] = 0.0; }
+
+    /* Step 2: proxy charges on source leaves, merged upward (T_c2p) */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < t->nb; ++i) {
+        obox2 *b = &t->b[i];
+        if (!b->leaf || b->nsrc == 0) continue;
+        b->proxy = (double *)malloc((size_t)p2 * sizeof(double));
+        form_proxy2(&o, P, t, b, b->proxy);
+    }
+    for (int l = Lmax - 1; l >= 0; --l) {
+        int s = t->lev_start[l], e = s + t->lev_count[l];
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = s; i < e; ++i) {
+            obox2 *b = &t->b[i];
+            if (b->leaf || b->nsrc == 0) continue;
+            b->proxy = (double *)calloc((size_t)p2, sizeof(double));
+            double *tmp = (double *)malloc((size_t)p2 * sizeof(double));
+            for (int c = 0; c < 4; ++c) {
+                int ci = b->child[c];
+                if (ci < 0 || !t->b[ci].proxy) continue;
+                tensor2_real(o.c2p[c & 1], o.c2p[(c >> 1) & 1], p, t->b[ci].proxy, tmp);
+                for (int k = 0; k < p2; ++k) b->proxy[k] += tmp[k];
+            }
+            free(tmp);
+        }
+    }
+
+    /* Step 3: downward pass */
+    cplx *wl = (cplx *)malloc((size_t)NF * sizeof(cplx));
+    for (int l = 0; l <= Lmax; ++l) {
+        int s = t->lev_start[l], e = s + t->lev_count[l];
+        double R = level_R(l), h = split_h(l), ws = (h / (2.0 * M_PI)) * (h / (2.0 * M_PI));
+        for (int mx = -nf; mx <= nf; ++mx)
+            for (int my = -nf; my <= nf; ++my)
+                wl[(mx + nf) * N1 + (my + nf)] = ws * split2_Dhat(sp, l, h * sqrt((double)(mx * mx + my * my)));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = s; i < e; ++i) {
+            obox2 *b = &t->b[i];
+            if (!b->fout) continue;
+            b->Phi = (cplx *)malloc((size_t)NF * sizeof(cplx));
+            prox2pw2(&o, h, R, nf, b->proxy, b->Phi);
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = s; i < e; ++i) {
+            obox2 *b = &t->b[i];
+            if (!b->fin) continue;
+            cplx *Psi = (cplx *)calloc((size_t)NF, sizeof(cplx));
+            double *coef = (double *)malloc((size_t)p2 * sizeof(double));
+            double cB[2] = {(b->ix + 0.5) * R, (b->iy + 0.5) * R};
+            for (int k = 0; k < b->ncol; ++k) {
+                const obox2 *S = &t->b[b->col[k]];
+                if (!S->fout) continue;
+                double d[2] = {cB[0] - (S->ix + 0.5) * R, cB[1] - (S->iy + 0.5) * R};
+                for (int mx = -nf; mx <= nf; ++mx)
+                    for (int my = -nf; my <= nf; ++my) {
+                        int idx = (mx + nf) * N1 + (my + nf);
+                        Psi[idx] += wl[idx] * cexp(I * h * (mx * d[0] + my * d[1])) * S->Phi[idx];
+                    }
+            }
+            pw2poly2(&o, h, R, nf, Psi, coef);
+            if (!b->local) b->local = (double *)calloc((size_t)p2, sizeof(double));
+            for (int k = 0; k < p2; ++k) b->local[k] += coef[k];
+            b->has_local = 1;
+            free(Psi); free(coef);
+        }
+        if (l == 0) {
+            /* the windowed root kernel over the unit square */
+            obox2 *b = &t->b[0];
+            int n0 = o.n0, NW = o.NW;
+            if (!b->local) b->local = (double *)calloc((size_t)p2, sizeof(double));
+            if (b->proxy) {
+                cplx *PhiW = (cplx *)malloc((size_t)NW * NW * sizeof(cplx));
+                double *coef = (double *)malloc((size_t)p2 * sizeof(double));
+                prox2pw2(&o, sp->hW, 1.0, n0, b->proxy, PhiW);
+                double wsw = (sp->hW / (2.0 * M_PI)) * (sp->hW / (2.0 * M_PI));
+                for (int mx = -n0; mx <= n0; ++mx)
+                    for (int my = -n0; my <= n0; ++my)
+                        PhiW[(mx + n0) * NW + (my + n0)] *=
+                            wsw * split2_What(sp, sp->hW * sqrt((double)(mx * mx + my * my)));
+                pw2poly2(&o, sp->hW, 1.0, n0, PhiW, coef);
+                for (int k = 0; k < p2; ++k) b->local[k] += coef[k];
+                free(PhiW); free(coef);
+            }
+            b->has_local = 1;
+        }
+        /* local expansions to the children (T_p2c) */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = s; i < e; ++i) {
+            obox2 *b = &t->b[i];
+            if (b->leaf || !b->has_local) continue;
+            double *tmp = (double *)malloc((size_t)p2 * sizeof(double));
+            for (int c = 0; c < 4; ++c) {
+                int ci = b->child[c];
+                if (ci < 0) continue;
+                obox2 *ch = &t->b[ci];
+                tensor2_real(o.p2c[c & 1], o.p2c[(c >> 1) & 1], p, b->local, tmp);
+                if (!ch->local) ch->local = (double *)calloc((size_t)p2, sizeof(double));
+                for (int k = 0; k < p2; ++k) ch->local[k] += tmp[k];
+                ch->has_local = 1;
+            }
+            free(tmp);
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = s; i < e; ++i) {
+            obox2 *b = &t->b[i];
+            if (!b->leaf || !b->has_local) continue;
+            for (int64_t k = b->start; k < b->start + b->count; ++k) {
+                int64_t pi = t->ord[k];
+                if (P->is_tgt[pi]) ufar[pi] += eval_local2(&o, b, b->local, &P->u[2 * pi]);
+            }
+        }
+        for (int i = s; i < e; ++i) {
+            free(t->b[i].Phi);
+            t->b[i].Phi = NULL;
+        }
+    }
+    free(wl);
+
+    /* Step 4: residual kernels over the same lists as in 3D */
+    ilist *lists = (ilist *)calloc((size_t)t->nb, sizeof(ilist));
+    for (int S = 0; S < t->nb && rc == 0; ++S) {
+        const obox2 *b = &t->b[S];
+        if (!b->leaf || b->nsrc == 0) continue;
+        for (int k = 0; k < b->ncol; ++k)
+            if (add_subtree_leaves2(t, b->col[k], S, lists) < 0) rc = -1;
+        if (b->level > 0) {
+            int lp = b->level - 1;
+            int64_t px = b->ix >> 1, py = b->iy >> 1;
+            for (int64_t qx = px - 1; qx <= px + 1; ++qx)
+                for (int64_t qy = py - 1; qy <= py + 1; ++qy) {
+                    int X = tree2_find(t, lp, qx, qy);
+                    if (X < 0 || !t->b[X].leaf) continue;
+                    int adj = 2 * qx <= b->ix + 1 && 2 * qx + 2 >= b->ix && 2 * qy <= b->iy + 1 && 2 * qy + 2 >= b->iy;
+                    if (adj && ilist_push(&lists[X], S) < 0) rc = -1;
+                }
+        }
+    }
+    if (rc == 0) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int T = 0; T < t->nb; ++T) {
+            const obox2 *bt = &t->b[T];
+            if (!bt->leaf || bt->ntgt == 0) continue;
+            for (int64_t k = bt->start; k < bt->start + bt->count; ++k) {
+                int64_t ti = t->ord[k];
+                if (!P->is_tgt[ti]) continue;
+                const double *x = &P->u[2 * ti];
+                double acc = 0.0;
+                for (int li = 0; li < lists[T].n; ++li) {
+                    const obox2 *bs = &t->b[lists[T].s[li]];
+                    double Rb = level_R(bs->level);
+                    for (int64_t kk = bs->start; kk < bs->start + bs->count; ++kk) {
+                        int64_t sj = t->ord[kk];
+                        if (!P->is_src[sj]) continue;
+                        double dx = x[0] - P->u[2 * sj], dy = x[1] - P->u[2 * sj + 1];
+                        double r = sqrt(dx * dx + dy * dy);
+                        if (r == 0.0 || r >= Rb) continue;
+                        acc += P->q[sj] * split2_R(sp, bs->level, r);
+                    }
+                }
+                unear[ti] += acc;
+            }
+        }
+    }
+    for (int i = 0; i < t->nb; ++i) free(lists[i].s);
+    free(lists);
+
+    /* Step 5: a coincident source added rho S_L(0) through the far field */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int T = 0; T < t->nb; ++T) {
+        const obox2 *b = &t->b[T];
+        if (!b->leaf || b->ntgt == 0 || b->nsrc == 0) continue;
+        double S0 = split2_S0(sp, b->level);
+        for (int64_t k = b->start; k < b->start + b->count; ++k) {
+            int64_t ti = t->ord[k];
+            if (!P->is_tgt[ti]) continue;
+            for (int64_t kk = b->start; kk < b->start + b->count; ++kk) {
+                int64_t sj = t->ord[kk];
+                if (P->is_src[sj] && P->u[2 * ti] == P->u[2 * sj] && P->u[2 * ti + 1] == P->u[2 * sj + 1])
+                    unear[ti] -= P->q[sj] * S0;
+            }
+        }
+    }
+    ops_free(&o);
+    return rc;
+}
+
+int oracle_dmk_log2d(const oracle_params *prm_in,
+                     const double *src, const double *rho, int64_t ns,
+                     const double *tgt, int64_t nt,
+                     double *pot, double *pot_far, double *pot_near)
+{
+    if (ns < 0 || nt < 0) return -1;
+    if (nt == 0) return 0;
+    split2_t sp;
+    if (split2_init(&sp, prm_in) != 0) { split2_free(&sp); return -1; }
+#ifdef _OPENMP
+    if (sp.prm.nthreads > 0) omp_set_num_threads(sp.prm.nthreads);
+#endif
+    opoints2 P;
+    otree2 t;
+    memset(&t, 0, sizeof(t));
+    int rc = points2_init(&P, src, rho, ns, tgt, nt);
+    if (rc == 0) rc = tree2_make(&t, &P, &sp.prm);
+    double *ufar = NULL, *unear = NULL;
+    if (rc == 0) {
+        ufar = (double *)malloc((size_t)P.n * sizeof(double));
+        unear = (double *)malloc((size_t)P.n * sizeof(double));
+        if (!ufar || !unear) rc = -1;
+    }
+    if (rc == 0) rc = run_dmk2(&sp, &P, &t, ufar, unear);
+    if (rc == 0) {
+        /* log S times the charge of the sources not coincident with the target */
+        double qtot = 0.0, logS = log(P.S);
+        for (int64_t j = 0; j < P.n; ++j) if (P.is_src[j]) qtot += P.q[j];
+        for (int T = 0; T < t.nb; ++T) {
+            const obox2 *b = &t.b[T];
+            if (!b->leaf) continue;
+            for (int64_t k = b->start; k < b->start + b->count; ++k) {
+                int64_t ti = t.ord[k], o = P.out_index[ti];
+                if (o < 0) continue;
+                double qc = 0.0;
+                for (int64_t kk = b->start; kk < b->start + b->count; ++kk) {
+                    int64_t sj = t.ord[kk];
+                    if (P.is_src[sj] && P.u[2 * ti] == P.u[2 * sj] && P.u[2 * ti + 1] == P.u[2 * sj + 1])
+                        qc += P.q[sj];
+                }
+                pot[o] = ufar[ti] + unear[ti] + logS * (qtot - qc);
+                if (pot_far) pot_far[o] = ufar[ti];
+                if (pot_near) pot_near[o] = unear[ti];
+            }
+        }
+    }
+    free(ufar);
+    free(unear);
+    tree2_free(&t);
+    points2_free(&P);
+    split2_free(&sp);
+    return rc;
+}
+
+void oracle_kernel_log2d(const oracle_params *prm, int what, int level,
+                         const double *r, int64_t n, double *out)
+{
+    split2_t sp;
+    if (split2_init(&sp, prm) != 0) { split2_free(&sp); return; }
+    for (int64_t i = 0; i < n; ++i) {
+        double x = r[i];
+        switch (what) {
+        case 0: out[i] = split2_S0(&sp, level); break;
+        case 1: out[i] = split2_R(&sp, level, x); break;
+        case 3: out[i] = split2_Dhat(&sp, level, x); break;
+        case 4: out[i] = split2_What(&sp, x); break;
+        default: out[i] = NAN;
+        }
+    }
+    split2_free(&sp);
+}
+
+double oracle_hW_log2d(const oracle_params *prm)
+{
+    split2_t sp;
+    if (split2_init(&sp, prm) != 0) { split2_free(&sp); return NAN; }
+    double h = sp.hW;
+    split2_free(&sp);
+    return h;
+}
+
+int oracle_n0_log2d(const oracle_params *prm)
+{
+    split2_t sp;
+    if (split2_init(&sp, prm) != 0) { split2_free(&sp); return -1; }
+    int n0 = sp.prm.n0;
+    split2_free(&sp);
+    return n0;
 }

@@ -118,6 +118,29 @@ void oracle_kernel(const oracle_params *prm, int what, int level,
 double oracle_h(const oracle_params *prm, int level);
 double oracle_hW(const oracle_params *prm);
 
+
+/* ---- the 2D Laplace kernel log r (Sec. 3.7 at lambda = 0, in the plane) ----
+ * u_i = sum_{j : y_j != x_i} rho_j log |x_i - y_j|; coordinates row-major
+ * [n][2]; the PSWF splitting only (prm->splitting must be ORACLE_PSWF; c, p,
+ * nf from Table 1 as in 3D, n0 from the 2D root window).  The unit-box map
+ * is the 3D one on two coordinates; pot is in input units (it includes
+ * log S times the charge of the sources not coincident with the target),
+ * pot_far / pot_near (may be NULL) are the unit-box far and near parts. */
+void oracle_direct_log2d(const double *src, const double *rho, int64_t ns,
+                         const double *tgt, int64_t nt, double *pot, int nthreads);
+int oracle_dmk_log2d(const oracle_params *prm,
+                     const double *src, const double *rho, int64_t ns,
+                     const double *tgt, int64_t nt,
+                     double *pot, double *pot_far, double *pot_near);
+/* Kernel pieces in the unit box at level l: what 0 = S_l(0), the mollified
+ * kernel at r = 0 (r ignored); 1 = residual R_l(r); 3 = Dhat_l(k);
+ * 4 = What_0(k). */
+void oracle_kernel_log2d(const oracle_params *prm, int what, int level,
+                         const double *r, int64_t n, double *out);
+/* Root spacing h_W and mode count n0 of the 2D window. */
+double oracle_hW_log2d(const oracle_params *prm);
+int oracle_n0_log2d(const oracle_params *prm);
+
 #ifdef __cplusplus
 }
 #endif

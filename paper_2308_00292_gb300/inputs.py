@@ -14,6 +14,8 @@ Workloads:
                                                                  (Table 2 shape)
   batch         -- many independent systems of log-uniform sizes, each
                    uniform in the cube or one Gaussian cluster   (batched)
+  disk2d        -- points uniform in the unit disk, charges U[-1,1]  (2D log)
+  circle2d      -- points on the unit circle, charges U[-1,1]    (2D log, Table 3 shape)
 """
 from __future__ import annotations
 
@@ -103,6 +105,25 @@ def batch(nsys: int, seed: int = 6, n_lo: int = 500, n_hi: int = 50_000, sigma_l
 
 
 # The configurations the library is measured on (sizes, distributions, seeds).
+def disk2d(n: int, seed: int = 8):
+    """n points uniform in the unit disk (radius sqrt(U), angle U[0, 2 pi)),
+    charges uniform in [-1, 1]; coordinates (n, 2)."""
+    rng = np.random.default_rng(seed)
+    r = np.sqrt(rng.random(n))
+    th = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return np.stack([r * np.cos(th), r * np.sin(th)], axis=1), q
+
+
+def circle2d(n: int, seed: int = 9):
+    """n points on the unit circle (angle U[0, 2 pi)), charges uniform in
+    [-1, 1]; coordinates (n, 2)."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return np.stack([np.cos(th), np.sin(th)], axis=1), q
+
+
 CONFIGS = {
     "laplace3d_uniform_n2e4": dict(gen="uniform_cube", n=20000, seed=1, eps=1e-6, leaf_cap=280),
     "laplace3d_clustered_n1e7": dict(gen="clustered", n=10_000_000, seed=2, eps=1e-6, leaf_cap=200),

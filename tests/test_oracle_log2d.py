@@ -1,0 +1,168 @@
+"""Pins of the oracle's 2D Laplace kernel log r (Sec. 3.7 at lambda = 0 in the
+plane: the PSWF splitting done in Fourier space, where the transform of log r
+is -2 pi / k^2), against the mathematics: the two-point closed form, the
+Laplacian of the residual kernel (a general-purpose quadrature of the
+mollifier's Hankel transform), the residual's support and its log r
+singularity, the difference kernels as the difference of two residuals
+(numerical Hankel inversion of Dhat_l), the truncated-kernel transform of the
+root window (numerical integration), the direct sum within eps, and the
+log S term of the unit-box map.
+"""
+import numpy as np
+import pytest
+
+from paper_2308_00292_gb300 import inputs
+
+special = pytest.importorskip("scipy.special")
+integrate = pytest.importorskip("scipy.integrate")
+
+R_RESIDUAL, S_ZERO, DHAT, WHAT = 1, 0, 3, 4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gl(a, b, panels, nodes=32):
+    """Gauss-Legendre nodes and weights on [a, b] in equal panels."""
+    x, w = special.roots_legendre(nodes)
+    e = np.linspace(a, b, panels + 1)
+    h = np.diff(e)[:, None]
+    return ((e[:-1, None] + 0.5 * h * (x + 1)).ravel(), (0.5 * h * w).ravel())
+
+
+def test_direct_two_points(oracle_mod):
+    src = np.array([[0.1, 0.2], [0.4, 0.6]])
+    rho = np.array([2.0, -3.0])
+    u = oracle_mod.direct_log2d(src, rho)
+    assert u == pytest.approx([-3.0 * np.log(0.5), 2.0 * np.log(0.5)], rel=1e-15)
+    # coincident points do not interact
+    u = oracle_mod.direct_log2d(np.array([[0.3, 0.3], [0.3, 0.3]]), np.array([1.0, 1.0]))
+    assert np.all(u == 0.0)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_residual_laplacian(oracle_mod, eps):
+    """R_0 = F has transform -2 pi (1 - psi(k / c)) / k^2, so away from 0 its
+    radial Laplacian F'' + F' / r is -int_0^inf psi(k / c) J_0(k r) k dk."""
+    prm = oracle_mod.params_log2d(eps=eps)
+    c = oracle_mod.params(eps=eps).c
+    k, w = gl(0.0, 4 * c, 64)
+    psi = oracle_mod.pswf(c, k / c)
+    hh = 1e-3
+    for r in (0.1, 0.3, 0.55, 0.8):
+        f = oracle_mod.kernel_log2d(prm, R_RESIDUAL, 0, r + hh * np.arange(-2, 3))
+        d1 = (f[0] - 8 * f[1] + 8 * f[3] - f[4]) / (12 * hh)
+        d2 = (-f[0] + 16 * f[1] - 30 * f[2] + 16 * f[3] - f[4]) / (12 * hh * hh)
+        lap = -np.sum(w * psi * special.j0(k * r) * k)
+        assert d2 + d1 / r == pytest.approx(lap, rel=1e-6, abs=1e-6 * abs(lap) + 1e-7)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9, 1e-12])
+def test_residual_support_and_singularity(oracle_mod, eps):
+    """R_l vanishes (to eps) beyond R_l; R_l(r) - log r tends to -S_l(0), and
+    R_l(r) = R_0(r / R_l)."""
+    prm = oracle_mod.params_log2d(eps=eps)
+    out = oracle_mod.kernel_log2d(prm, R_RESIDUAL, 0, np.array([1.0, 1.1, 1.5, 2.5]))
+    assert np.all(np.abs(out) < 10 * eps)
+    inside = oracle_mod.kernel_log2d(prm, R_RESIDUAL, 0, np.array([0.5]))[0]
+    assert abs(inside) > 1e-3
+    for level in (0, 3):
+        R = 2.0 ** -level
+        s0 = oracle_mod.kernel_log2d(prm, S_ZERO, level, np.zeros(1))[0]
+        for r in (1e-9 * R, 1e-7 * R):
+            v = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, np.array([r]))[0]
+            assert np.log(r) - v == pytest.approx(s0, abs=1e-11)
+        r = np.array([0.05, 0.2, 0.7]) * R
+        assert oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, r) == pytest.approx(
+            oracle_mod.kernel_log2d(prm, R_RESIDUAL, 0, r / R), rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_difference_kernel_is_difference_of_residuals(oracle_mod, level):
+    """D_l = R_l - R_{l+1}: the Hankel inversion (1 / 2 pi) int Dhat_l(k) J_0(k r) k dk
+    of the oracle's Dhat_l, by Gauss-Legendre panels, against its residuals."""
+    prm = oracle_mod.params_log2d(eps=1e-9)
+    c = oracle_mod.params(eps=1e-9).c
+    R1 = 2.0 ** -(level + 1)
+    k, w = gl(0.0, 4.5 * c / R1, 160)
+    dh = oracle_mod.kernel_log2d(prm, DHAT, level, k)
+    for r in np.array([0.0, 0.1, 0.4, 0.9, 1.3]) * 2.0 ** -level:
+        d = np.sum(w * dh * special.j0(k * r) * k) / (2 * np.pi)
+        if r == 0.0:
+            ref = (oracle_mod.kernel_log2d(prm, S_ZERO, level + 1, np.zeros(1))[0]
+                   - oracle_mod.kernel_log2d(prm, S_ZERO, level, np.zeros(1))[0])
+        else:
+            ref = (oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, np.array([r]))[0]
+                   - oracle_mod.kernel_log2d(prm, R_RESIDUAL, level + 1, np.array([r]))[0])
+        assert d == pytest.approx(ref, abs=1e-8)
+    # the k = 0 value is the limit
+    d0, d1 = oracle_mod.kernel_log2d(prm, DHAT, level, np.array([0.0, 1e-4]))
+    assert d0 == pytest.approx(d1, rel=1e-7)
+
+
+def test_root_window_transform(oracle_mod):
+    """What_0(k) / psi(k / c) = 2 pi int_0^{R_t} log(r) J_0(k r) r dr, R_t = 1 + sqrt 2."""
+    prm = oracle_mod.params_log2d(eps=1e-6)
+    c = oracle_mod.params(eps=1e-6).c
+    Rt = 1.0 + np.sqrt(2.0)
+    for k in (0.0, 0.7, 3.3, 2 * np.pi / Rt, 11.0):
+        got = oracle_mod.kernel_log2d(prm, WHAT, 0, np.array([k]))[0] / oracle_mod.pswf(c, k / c)[0]
+        ref = 2 * np.pi * integrate.quad(lambda r: np.log(r) * special.j0(k * r) * r, 0, Rt,
+                                         epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+        assert got == pytest.approx(ref, rel=1e-11, abs=1e-12)
+
+
+CASES = {
+    "disk": lambda: inputs.disk2d(3000, seed=811),
+    "circle": lambda: inputs.circle2d(4000, seed=812),
+}
+
+
+def direct_in_unit_box(oracle_mod, x, q):
+    """The direct sum on the unit-box coordinates u = (x - lo) / S the pass
+    works on, plus log S times the other charges.  Rounding u moves a pair d
+    apart by about 1e-16 / d relative, so a pair 6e-8 apart (there is one in
+    the 4000-point circle) changes log d by 2e-9: below 1e-9 the pass is
+    compared with the sum on its own coordinates."""
+    lo = x.min(axis=0)
+    S = (x.max(axis=0) - lo).max()
+    u = (x - lo) / S
+    return oracle_mod.direct_log2d(u, q) + np.log(S) * (q.sum() - q)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("eps,leaf_cap", [(1e-6, 120), (1e-9, 160), (1e-12, 160)])
+def test_dmk_matches_direct(oracle_mod, case, eps, leaf_cap):
+    x, q = CASES[case]()
+    u = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=leaf_cap)
+    ref = oracle_mod.direct_log2d(x, q) if eps > 1e-10 else direct_in_unit_box(oracle_mod, x, q)
+    assert rel(u, ref) < eps
+
+
+def test_separate_targets_and_duplicates(oracle_mod):
+    x, q = inputs.circle2d(3000, seed=813)
+    y = np.random.default_rng(814).uniform(-1, 1, size=(1200, 2))
+    u = oracle_mod.dmk_log2d(x, q, y, eps=1e-9, leaf_cap=100)
+    assert rel(u, oracle_mod.direct_log2d(x, q, y)) < 1e-9
+    xd = np.r_[x[:2000], x[:400]]
+    qd = np.r_[q[:2000], q[:400]]
+    u = oracle_mod.dmk_log2d(xd, qd, eps=1e-9, leaf_cap=100)
+    assert rel(u, oracle_mod.direct_log2d(xd, qd)) < 1e-9
+
+
+def test_log_of_the_scale(oracle_mod):
+    """log |s x - s y| = log s + log |x - y|: a cloud scaled by s (and shifted)
+    has the potentials of the original plus log s times the charge of the
+    other sources."""
+    x, q = inputs.disk2d(2500, seed=815)
+    s = 37.0
+    u1 = oracle_mod.dmk_log2d(x, q, eps=1e-9, leaf_cap=100)
+    u2 = oracle_mod.dmk_log2d(s * x + 5.0, q, eps=1e-9, leaf_cap=100)
+    assert rel(u2 - np.log(s) * (q.sum() - q), u1) < 1e-12
+
+
+def test_gaussian_splitting_is_refused(oracle_mod):
+    x, q = inputs.disk2d(100, seed=816)
+    with pytest.raises(RuntimeError):
+        oracle_mod.dmk_log2d(x, q, splitting=oracle_mod.GAUSSIAN)
