@@ -51,7 +51,11 @@ typedef enum {
     DMK_YUKAWA = 1,        /* exp(-lambda r)/r in 3D, lambda = opts.kernel_param > 0,
                               split in Fourier space (Sec. 3.7); no batches, no
                               gradients */
-    DMK_LOG2D = 2,         /* reserved: log r in 2D (Sec. 4) */
+    DMK_LOG2D = 2,         /* log r in 2D (dim 2), the Fourier-space splitting of
+                              Sec. 3.7 at lambda = 0; DMK_FP64 only, both parts
+                              (no FAR_ONLY / NEAR_ONLY), no batches, no gradients;
+                              dmk_eval and dmk_eval_host take n x 2 coordinates;
+                              potentials sum rho_j log |x_i - y_j| over y_j != x_i */
     DMK_SQRTLAPLACE = 3    /* reserved: 1/r^2 in 3D (Sec. 4) */
 } dmk_kernel;
 
@@ -106,7 +110,8 @@ DMK_API int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opt
 /*
  * dmk_eval -- one evaluation pass (Steps 0, 2-5 of Sec. 3.4) on device data.
  *
- *   sources     device pointer, n_src x 3 doubles, row-major (x, y, z per point)
+ *   sources     device pointer, n_src x 3 doubles, row-major (x, y, z per point);
+ *               n_src x 2 (x, y) for a DMK_LOG2D plan
  *   n_src       number of sources (>= 0)
  *   charges     device pointer, n_src doubles
  *   targets     device pointer, n_tgt x 3 doubles; may be the same pointer as
@@ -275,7 +280,11 @@ DMK_API int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out);
  *   1  translation weights w(s), s = |m|^2 = 0..3 nf^2, at box side R = 1
  *   2  root weights wW(s), s = 0..3 n0^2, and (first) the root spacing hW
  *   3  residual polynomial: Chebyshev coefficients of q(t) = Phi(sqrt t)/sqrt t
- *      on t in [0, 1] */
+ *      on t in [0, 1]
+ * A DMK_LOG2D plan answers 1-3 with its 2D tables: 1 the weights w(s),
+ * s = 0..2 nf^2 (the same at every level), 2 hW and wW(s), s = 0..2 n0^2,
+ * 3 the Chebyshev coefficients (in 2 t - 1) of G with the residual
+ * R_l(r) = log(r / R_l) + G(r^2 / R_l^2); and 4: G(0). */
 DMK_API int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len);
 
 /* Yukawa tables of a DMK_YUKAWA plan at a unit-box lambda (the library uses

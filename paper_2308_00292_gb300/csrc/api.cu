@@ -7,6 +7,7 @@
 #include <string>
 
 #include "dmk.h"
+#include "log2d.h"
 #include "passes.h"
 
 namespace dmk {
@@ -47,6 +48,11 @@ struct dmk_plan_s {
     dmk::DBuf tab;  // device tables (working precision)
     dmk::DevTables<double> dt_d{};
     dmk::DevTables<float> dt_f{};
+    // the 2D Laplace kernel log r
+    dmk::Log2dTables t2;
+    dmk::DBuf tab2;
+    dmk::Log2dDev d2{};
+    dmk::Log2dBufs b2;
     std::unique_ptr<dmk::TreeBuilder> tree;
     dmk::PassBufs bufs;
     dmk::DBuf h_src, h_q, h_tgt, h_pot;  // device copies for dmk_eval_host
@@ -140,6 +146,73 @@ int upload_yukawa(dmk_plan_s *pl, dmk::DevTables<T> &dt, double lam_unit, int nl
     return DMK_OK;
 }
 
+int upload_log2d(dmk_plan_s *pl) {
+    const dmk::Tables &tb = pl->tb;
+    std::vector<double> h;
+    auto push = [&](const std::vector<double> &v) {
+        size_t off = h.size();
+        h.insert(h.end(), v.begin(), v.end());
+        while (h.size() % 32) h.push_back(0.0);
+        return off;
+    };
+    std::vector<double> A2(tb.A[0]);
+    A2.insert(A2.end(), tb.A[1].begin(), tb.A[1].end());
+    const size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(pl->t2.FWr),
+                 oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW), og = push(pl->t2.g);
+    if (pl->ws.ensure(pl->tab2, (int64_t)h.size() * 8)) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
+    if (cudaMemcpy(pl->tab2.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(DMK_ERR_CUDA, "copying the plan tables to the device failed");
+    const double *base = (const double *)pl->tab2.p;
+    dmk::Log2dDev &d = pl->d2;
+    d.p = tb.p;
+    d.nf = tb.nf;
+    d.N1 = 2 * tb.nf + 1;
+    d.n0 = pl->t2.n0;
+    d.NW = 2 * pl->t2.n0 + 1;
+    d.gdeg = (int)pl->t2.g.size() - 1;
+    d.A = base + oA;
+    d.Fr = base + oFr;
+    d.Fi = base + oFi;
+    d.FWr = base + oFWr;
+    d.FWi = base + oFWi;
+    d.w = base + ow;
+    d.wW = base + owW;
+    d.g = base + og;
+    d.G0 = pl->t2.G0;
+    return DMK_OK;
+}
+
+// one evaluation of the 2D pass (after the empty cases and cudaSetDevice)
+int eval_log2d(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
+               double *pot, cudaStream_t st) {
+    if (!pl->tree) pl->tree.reset(new dmk::TreeBuilder(pl->ws));
+    std::string err;
+    const long long launches0 = dmk::g_launches.load();
+    cudaEventRecord(pl->ev[0], st);
+    int rc = dmk::run_log2d(pl->d2, *pl->tree, pl->ws, pl->b2, src, ns, q, tgt, nt, pl->leaf_cap, pl->max_level,
+                            pot, st, err);
+    if (rc) return fail(rc, "2D pass: " + err);
+    cudaEventRecord(pl->ev[5], st);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("device execution failed: ") + cudaGetErrorString(ce));
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(ce));
+    dmk_eval_stats &s = pl->stats;
+    s = dmk_eval_stats{};
+    s.n_points = pl->tree->n;
+    s.n_levels = pl->tree->nlev;
+    s.n_boxes = pl->tree->nb;
+    s.n_leaves = pl->tree->nleaves;
+    s.near_pairs = pl->tree->near_pairs;
+    s.balance_rounds = pl->tree->rounds;
+    s.n_fin = pl->tree->ntleaves;
+    float t05 = 0;
+    cudaEventElapsedTime(&t05, pl->ev[0], pl->ev[5]);
+    s.t_total_ms = t05;
+    s.n_launches = dmk::g_launches.load() - launches0;
+    return DMK_OK;
+}
+
 bool valid_p(int p) { return p == 0 || p == 9 || p == 18 || p == 19 || p == 28 || p == 38; }
 
 int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, const double *tgt, int64_t nt,
@@ -157,6 +230,11 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     const bool same = (tgt == src && nt == ns);
     const int64_t n = same ? ns : ns + nt;
     if (n >= (int64_t)INT32_MAX / 2) return fail(DMK_ERR_UNSUPPORTED, "more than 2^30 points");
+    if (pl->kernel == DMK_LOG2D) {
+        if (grad) return fail(DMK_ERR_UNSUPPORTED, "the 2D kernel has no gradient pass");
+        if (nsys > 1) return fail(DMK_ERR_UNSUPPORTED, "the 2D kernel has no batched pass");
+        return eval_log2d(pl, src, ns, q, tgt, nt, pot, st);
+    }
     if (!pl->tree) pl->tree.reset(new dmk::TreeBuilder(pl->ws));
     std::string err;
     const bool single = pl->precision == DMK_MIXED;
@@ -276,9 +354,10 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     if (!out) return fail(DMK_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!(eps >= 1e-12 && eps <= 1e-2)) return fail(DMK_ERR_INVALID_ARG, "eps must lie in [1e-12, 1e-2]");
-    if (kernel != DMK_LAPLACE && kernel != DMK_YUKAWA)
-        return fail(DMK_ERR_UNSUPPORTED, "only DMK_LAPLACE and DMK_YUKAWA are implemented");
-    if (dim != 3) return fail(DMK_ERR_UNSUPPORTED, "the kernels are implemented in 3 dimensions");
+    if (kernel != DMK_LAPLACE && kernel != DMK_YUKAWA && kernel != DMK_LOG2D)
+        return fail(DMK_ERR_UNSUPPORTED, "only DMK_LAPLACE, DMK_YUKAWA (3D) and DMK_LOG2D (2D) are implemented");
+    if (dim != (kernel == DMK_LOG2D ? 2 : 3))
+        return fail(DMK_ERR_UNSUPPORTED, "DMK_LAPLACE and DMK_YUKAWA are 3D kernels, DMK_LOG2D a 2D one");
     dmk_opts o{};
     if (opts) o = *opts;
     if (kernel == DMK_YUKAWA && !(o.kernel_param > 0.0 && std::isfinite(o.kernel_param)))
@@ -288,6 +367,8 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
         return fail(DMK_ERR_INVALID_ARG, "option out of range");
     if ((o.flags & DMK_FLAG_FAR_ONLY) && (o.flags & DMK_FLAG_NEAR_ONLY))
         return fail(DMK_ERR_INVALID_ARG, "DMK_FLAG_FAR_ONLY and DMK_FLAG_NEAR_ONLY are exclusive");
+    if (kernel == DMK_LOG2D && (o.precision == DMK_MIXED || (o.flags & (DMK_FLAG_FAR_ONLY | DMK_FLAG_NEAR_ONLY))))
+        return fail(DMK_ERR_UNSUPPORTED, "the 2D pass runs in FP64 and evaluates both parts");
     std::unique_ptr<dmk_plan_s> pl(new (std::nothrow) dmk_plan_s());
     if (!pl) return fail(DMK_ERR_OOM, "host allocation failed");
     pl->kernel = kernel;
@@ -296,7 +377,11 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     pl->eps = eps;
     pl->opts = o;
     pl->precision = o.precision;
-    pl->leaf_cap = o.leaf_cap > 0 ? o.leaf_cap : (eps >= 1e-6 * (1 - 1e-12) ? 280 : 800);
+    // the paper's leaf capacities: 280 / 800 in 3D, 120 / 160 in 2D (Sec. 5.1)
+    if (kernel == DMK_LOG2D)
+        pl->leaf_cap = o.leaf_cap > 0 ? o.leaf_cap : (eps >= 1e-6 * (1 - 1e-12) ? 120 : 160);
+    else
+        pl->leaf_cap = o.leaf_cap > 0 ? o.leaf_cap : (eps >= 1e-6 * (1 - 1e-12) ? 280 : 800);
     pl->max_level = o.max_level > 0 ? o.max_level : dmk::kMaxLevel;
     std::string err;
     // Single precision cannot deliver eps below ~1e-7.  At the 1e-6 row of
@@ -310,6 +395,10 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     if (p_req == 0 && kernel == DMK_YUKAWA && eps < 1e-3 * (1 - 1e-12) && eps >= 1e-6 * (1 - 1e-12)) p_req = 19;
     if (dmk::build_tables(eps, p_req, o.nf, pl->tb, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
     pl->qdeg = (int)pl->tb.qmono.size() - 1;
+    if (kernel == DMK_LOG2D) {
+        if (dmk::build_log2d_tables(pl->tb, pl->t2, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
+        if (pl->t2.g.size() > 64) return fail(DMK_ERR_INTERNAL, "2D residual polynomial degree above 63");
+    }
     if (pl->qdeg >= 64) return fail(DMK_ERR_INTERNAL, "residual polynomial degree above 63");
     pl->host_only = (o.flags & DMK_FLAG_HOST_ONLY) != 0;
     if (!pl->host_only) {
@@ -340,8 +429,9 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
         }
         if (cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, least) != cudaSuccess)
             return fail(DMK_ERR_CUDA, "cudaStreamCreate failed");
-        int rc = pl->precision == DMK_MIXED ? upload_tables<float>(pl.get(), pl->dt_f)
-                                            : upload_tables<double>(pl.get(), pl->dt_d);
+        int rc = kernel == DMK_LOG2D           ? upload_log2d(pl.get())
+                 : pl->precision == DMK_MIXED ? upload_tables<float>(pl.get(), pl->dt_f)
+                                              : upload_tables<double>(pl.get(), pl->dt_d);
         if (rc) return rc;
     }
     *out = pl.release();
@@ -407,14 +497,15 @@ int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const d
     if (cudaSetDevice(plan->device) != cudaSuccess) return fail(DMK_ERR_CUDA, "cudaSetDevice failed");
     const bool same = (targets == sources && n_tgt == n_src);
     dmk::Workspace &ws = plan->ws;
-    if (ws.ensure(plan->h_src, std::max<int64_t>(n_src, 1) * 24) || ws.ensure(plan->h_q, std::max<int64_t>(n_src, 1) * 8) ||
-        ws.ensure(plan->h_pot, n_tgt * 8) || (!same && ws.ensure(plan->h_tgt, n_tgt * 24)))
+    const int64_t bpp = 8 * plan->dim;  // bytes per point
+    if (ws.ensure(plan->h_src, std::max<int64_t>(n_src, 1) * bpp) || ws.ensure(plan->h_q, std::max<int64_t>(n_src, 1) * 8) ||
+        ws.ensure(plan->h_pot, n_tgt * 8) || (!same && ws.ensure(plan->h_tgt, n_tgt * bpp)))
         return fail(DMK_ERR_OOM, "device allocation failed (host-call buffers)");
     if (n_src > 0 &&
-        (cudaMemcpyAsync(plan->h_src.p, sources, (size_t)n_src * 24, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (cudaMemcpyAsync(plan->h_src.p, sources, (size_t)(n_src * bpp), cudaMemcpyHostToDevice, st) != cudaSuccess ||
          cudaMemcpyAsync(plan->h_q.p, charges, (size_t)n_src * 8, cudaMemcpyHostToDevice, st) != cudaSuccess))
         return fail(DMK_ERR_CUDA, "host-to-device copy failed");
-    if (!same && cudaMemcpyAsync(plan->h_tgt.p, targets, (size_t)n_tgt * 24, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (!same && cudaMemcpyAsync(plan->h_tgt.p, targets, (size_t)(n_tgt * bpp), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail(DMK_ERR_CUDA, "host-to-device copy failed");
     const double *dsrc = (const double *)plan->h_src.p;
     const double *dtgt = same ? dsrc : (const double *)plan->h_tgt.p;
@@ -520,7 +611,7 @@ int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
     out->c = plan->tb.c;
     out->p = plan->tb.p;
     out->nf = plan->tb.nf;
-    out->n0 = plan->tb.n0;
+    out->n0 = plan->kernel == DMK_LOG2D ? plan->t2.n0 : plan->tb.n0;
     out->leaf_cap = plan->leaf_cap;
     out->max_level = plan->max_level;
     out->precision = plan->precision;
@@ -532,7 +623,21 @@ int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
 int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len) {
     if (!plan || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
     std::vector<double> v;
+    if (plan->kernel == DMK_LOG2D && which >= 1) {
+        switch (which) {
+        case 1: v = plan->t2.w; break;
+        case 2:
+            v.push_back(plan->t2.hW);
+            v.insert(v.end(), plan->t2.wW.begin(), plan->t2.wW.end());
+            break;
+        case 3: v = plan->t2.g; break;
+        case 4: v.push_back(plan->t2.G0); break;
+        default: return fail(DMK_ERR_INVALID_ARG, "unknown table");
+        }
+        which = -1;
+    }
     switch (which) {
+    case -1: break;
     case 0: v = plan->tb.psi_grid; break;
     case 1: v = plan->tb.w; break;
     case 2:

@@ -54,6 +54,18 @@ struct YukawaTables {
 };
 int build_yukawa_tables(const Tables &tb, double lam, int nlev, YukawaTables &yt, std::string &err);
 
+// The 2D Laplace kernel log r (Sec. 3.7 at lambda = 0 in the plane), on top of
+// the dimension-free parts of Tables (t, A, Fr, Fi): translation weights
+// w(|m|^2), the same at every level, the root window's spacing, modes, F
+// matrix and weights, and the Chebyshev coefficients g (in x = 2t - 1) of the
+// smooth part G of the residual, R_l(r) = log(r / R_l) + G(r^2 / R_l^2).
+struct Log2dTables {
+    double hW = 0, G0 = 0;
+    int n0 = 0;
+    std::vector<double> w, FWr, FWi, wW, g;  // [2 nf^2 + 1], [NW][p] x 2, [2 n0^2 + 1], [gdeg + 1]
+};
+int build_log2d_tables(const Tables &tb, Log2dTables &t2, std::string &err);
+
 // ---------------------------------------------------------------- device views
 // Plan tables on the device, in the working precision T.
 template <typename T>

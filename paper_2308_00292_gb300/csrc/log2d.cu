@@ -1,0 +1,513 @@
+// log2d.cu -- the DMK evaluation pass for the 2D Laplace kernel log r
+// (Sec. 3.7 at lambda = 0 in the plane; Steps 0-5 of Sec. 3.4 in two
+// dimensions), FP64 throughout.
+//
+// The tree is the library's 3D builder run on the points lifted to z = 0: the
+// builder only creates cells that hold points and only forces splits of
+// non-empty cells, so every box lies in the z = 0 layer and the octree is the
+// quad-tree of the points (octants 0-3 are the quadrants, colleagues with
+// dz = 0 are the 2D colleagues, and the near lists are the 2D ones).
+//
+// Per box the expansions are p^2 Chebyshev moments / local coefficients and
+// (2 nf + 1)^2 plane waves.  At these sizes a box's transforms are a few
+// hundred thousand flops, far below a tensor-core tile, so every kernel is a
+// block per box on the CUDA cores with the box's arrays in shared memory.
+//   k2_moments   Step 2: M[a][b] = sum_j q_j T_a(xi_j) T_b(eta_j) of a leaf
+//   k2_c2p       Step 2: parent moments from the children (coefficient shifts)
+//   k2_outgoing  Step 3: Phi[m] = sum F[mx][a] F[my][b] M[a][b] (F_out boxes)
+//   k2_local     Step 3: p2c of the parent's coefficients, the incoming
+//                expansion of the colleagues (translation phases are cube
+//                roots of unity), the root window at level 0
+//   k2_eval      Step 3: local expansions at the targets
+//   k2_near      Step 4-5: residual kernel log(r / R) + G(r^2 / R^2) over the
+//                near lists; coincident pairs remove rho S_L(0)
+//   k2_finalize  input order; log|x - y| = log S + log|u - v| adds log S times
+//                the charge of the non-coincident sources
+#include "dmk_internal.h"
+#include "dev_util.h"
+#include "log2d.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace dmk {
+namespace {
+
+constexpr int kT = 256;                       // threads per block
+constexpr int kPer = (kMaxP * kMaxP + kT - 1) / kT;  // p^2 entries per thread
+
+#define L2CK(x)                                                              \
+    do {                                                                     \
+        cudaError_t e_ = (x);                                                \
+        if (e_ != cudaSuccess) {                                             \
+            err = std::string("CUDA: ") + cudaGetErrorString(e_);            \
+            return DMK_ERR_CUDA;                                             \
+        }                                                                    \
+    } while (0)
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ void cell2(const TreeView &tv, int b, int &ix, int &iy) {
+    int iz;
+    box_decode_d(tv.bkey[b], tv.blevel[b], ix, iy, iz);
+}
+
+// Chebyshev polynomials T_0 .. T_{p-1} at x
+__device__ __forceinline__ void cheb_row(double x, int p, double *T) {
+    T[0] = 1.0;
+    if (p > 1) T[1] = x;
+    for (int n = 2; n < p; ++n) T[n] = 2.0 * x * T[n - 1] - T[n - 2];
+}
+
+// ---- Step 2: moments of the source leaves -----------------------------------
+__global__ void __launch_bounds__(kT) k2_moments(TreeView tv, Log2dDev d, double *mom) {
+    const int b = blockIdx.x;
+    if (!(tv.bflags[b] & BF_LEAF) || tv.bnsrc[b] == 0) return;
+    __shared__ double Tx[32][kMaxP], Ty[32][kMaxP], qs[32];
+    const int p = d.p, pp = p * p, tid = threadIdx.x;
+    int ix, iy;
+    cell2(tv, b, ix, iy);
+    const double R = level_R(tv.blevel[b]), cx = (ix + 0.5) * R, cy = (iy + 0.5) * R;
+    double acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
+    const int s0 = tv.bstart[b], n = tv.bcount[b];
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        if (tid < 32) {
+            const int k = s0 + c0 + tid;
+            if (c0 + tid < n) {
+                qs[tid] = tv.q[k];
+                cheb_row(2.0 * (tv.ux[k] - cx) / R, p, Tx[tid]);
+                cheb_row(2.0 * (tv.uy[k] - cy) / R, p, Ty[tid]);
+            } else {
+                qs[tid] = 0.0;
+                for (int a = 0; a < p; ++a) Tx[tid][a] = Ty[tid][a] = 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kT;
+            if (e < pp) {
+                const int a = e / p, bb = e - a * p;
+                double s = 0.0;
+                for (int i = 0; i < 32; ++i) s += qs[i] * Tx[i][a] * Ty[i][bb];
+                acc[j] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kT;
+        if (e < pp) mom[(size_t)b * pp + e] = acc[j];
+    }
+}
+
+// ---- Step 2: parent moments from the children ------------------------------
+// T_n((xi + s) / 2) = sum_m A_s[n][m] T_m(xi): M_P[n][n'] = sum A_sx[n][k] A_sy[n'][k'] M_C[k][k']
+__global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart, double *mom) {
+    const int b = lstart + blockIdx.x;
+    if ((tv.bflags[b] & BF_LEAF) || tv.bnsrc[b] == 0) return;
+    __shared__ double MC[kMaxP * kMaxP], Y[kMaxP * kMaxP];
+    const int p = d.p, pp = p * p, tid = threadIdx.x;
+    double acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
+    const uint8_t mask = tv.bcmask[b];
+    int ci = tv.bchild0[b];
+    for (int oc = 0; oc < 8; ++oc) {
+        if (!(mask & (1u << oc))) continue;
+        const int c = ci++;
+        if (tv.bnsrc[c] == 0) continue;
+        const double *Ax = d.A + (size_t)(oc & 1) * pp, *Ay = d.A + (size_t)((oc >> 1) & 1) * pp;
+        for (int e = tid; e < pp; e += kT) MC[e] = mom[(size_t)c * pp + e];
+        __syncthreads();
+        // Y[k][n'] = sum_k' A_sy[n'][k'] M_C[k][k']
+        for (int e = tid; e < pp; e += kT) {
+            const int k = e / p, n2 = e - k * p;
+            double s = 0.0;
+            for (int k2 = 0; k2 < p; ++k2) s += Ay[n2 * p + k2] * MC[k * p + k2];
+            Y[e] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kT;
+            if (e < pp) {
+                const int n1 = e / p, n2 = e - n1 * p;
+                double s = 0.0;
+                for (int k = 0; k < p; ++k) s += Ax[n1 * p + k] * Y[k * p + n2];
+                acc[j] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kT;
+        if (e < pp) mom[(size_t)b * pp + e] = acc[j];
+    }
+}
+
+// Phi[mx][my] = sum_a sum_b F[mx][a] F[my][b] M[a][b] with F = Fr + i Fi ([N][p]),
+// into phi (N^2 complex, interleaved); M and the workspace Y (N x p complex)
+// in shared memory
+__device__ void pw_from_moments(const double *M, const double *Fr, const double *Fi, int p, int N, double *Yr,
+                                double *Yi, double *phi) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < N * p; e += kT) {
+        const int mx = e / p, bb = e - mx * p;
+        double sr = 0.0, si = 0.0;
+        for (int a = 0; a < p; ++a) {
+            const double m = M[a * p + bb];
+            sr += Fr[mx * p + a] * m;
+            si += Fi[mx * p + a] * m;
+        }
+        Yr[e] = sr;
+        Yi[e] = si;
+    }
+    __syncthreads();
+    for (int e = tid; e < N * N; e += kT) {
+        const int mx = e / N, my = e - mx * N;
+        double sr = 0.0, si = 0.0;
+        for (int bb = 0; bb < p; ++bb) {
+            const double fr = Fr[my * p + bb], fi = Fi[my * p + bb];
+            const double yr = Yr[mx * p + bb], yi = Yi[mx * p + bb];
+            sr += fr * yr - fi * yi;
+            si += fr * yi + fi * yr;
+        }
+        phi[2 * e] = sr;
+        phi[2 * e + 1] = si;
+    }
+    __syncthreads();
+}
+
+// c[n][n'] = Re sum_mx sum_my conj(F[mx][n]) conj(F[my][n']) Psi[mx][my]; Psi (N^2
+// complex interleaved) and the workspace Z (p x N complex) in shared memory
+__device__ void coef_from_pw(const double *Psi, const double *Fr, const double *Fi, int p, int N, double *Zr,
+                             double *Zi, double *acc /* kPer per thread */) {
+    const int tid = threadIdx.x;
+    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]
+    for (int e = tid; e < p * N; e += kT) {
+        const int n = e / N, my = e - n * N;
+        double sr = 0.0, si = 0.0;
+        for (int mx = 0; mx < N; ++mx) {
+            const double fr = Fr[mx * p + n], fi = -Fi[mx * p + n];
+            const double pr = Psi[2 * (mx * N + my)], pi = Psi[2 * (mx * N + my) + 1];
+            sr += fr * pr - fi * pi;
+            si += fr * pi + fi * pr;
+        }
+        Zr[e] = sr;
+        Zi[e] = si;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kT;
+        if (e < p * p) {
+            const int n = e / p, n2 = e - n * p;
+            double s = 0.0;
+            for (int my = 0; my < N; ++my) {
+                // Re(conj(F[my][n2]) Z[n][my])
+                s += Fr[my * p + n2] * Zr[n * N + my] + Fi[my * p + n2] * Zi[n * N + my];
+            }
+            acc[j] += s;
+        }
+    }
+    __syncthreads();
+}
+
+// ---- Step 3: outgoing expansions of the F_out boxes -------------------------
+__global__ void __launch_bounds__(kT) k2_outgoing(TreeView tv, Log2dDev d, const double *mom, double *phi) {
+    const int b = blockIdx.x;
+    if (!(tv.bflags[b] & BF_FOUT)) return;
+    extern __shared__ double sm[];
+    const int p = d.p, pp = p * p, N = d.N1;
+    double *M = sm, *Yr = M + pp, *Yi = Yr + N * p, *P = Yi + N * p;
+    for (int e = threadIdx.x; e < pp; e += kT) M[e] = mom[(size_t)b * pp + e];
+    __syncthreads();
+    pw_from_moments(M, d.Fr, d.Fi, p, N, Yr, Yi, P);
+    double *out = phi + (size_t)tv.bslot[b] * 2 * N * N;
+    for (int e = threadIdx.x; e < 2 * N * N; e += kT) out[e] = P[e];
+}
+
+// ---- Step 3: local expansions of the boxes of one level ---------------------
+__global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int level, int lstart, const double *mom,
+                                               const double *phi, double *loc) {
+    const int b = lstart + blockIdx.x;
+    if (tv.bntgt[b] == 0) return;
+    extern __shared__ double sm[];
+    const int p = d.p, pp = p * p, N = d.N1, NW = d.NW, NM = N > NW ? N : NW;
+    double *CP = sm, *Y = CP + pp, *Psi = Y + pp, *Zr = Psi + 2 * NM * NM, *Zi = Zr + p * NM;
+    const int tid = threadIdx.x;
+    double acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
+    int ix, iy;
+    cell2(tv, b, ix, iy);
+    // the parent's expansion in this box's coordinates: c[k][k'] = sum A_sx[n][k] A_sy[n'][k'] c_P[n][n']
+    if (level > 0) {
+        const int P = tv.bparent[b];
+        const double *Ax = d.A + (size_t)(ix & 1) * pp, *Ay = d.A + (size_t)(iy & 1) * pp;
+        for (int e = tid; e < pp; e += kT) CP[e] = loc[(size_t)P * pp + e];
+        __syncthreads();
+        for (int e = tid; e < pp; e += kT) {  // Y[n][k'] = sum_n' A_sy[n'][k'] c_P[n][n']
+            const int n = e / p, k2 = e - n * p;
+            double s = 0.0;
+            for (int n2 = 0; n2 < p; ++n2) s += Ay[n2 * p + k2] * CP[n * p + n2];
+            Y[e] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kT;
+            if (e < pp) {
+                const int k = e / p, k2 = e - k * p;
+                double s = 0.0;
+                for (int n = 0; n < p; ++n) s += Ax[n * p + k] * Y[n * p + k2];
+                acc[j] += s;
+            }
+        }
+        __syncthreads();
+    }
+    // incoming plane waves from the F_out colleagues: w(|m|^2) omega^{m . delta}
+    if (tv.bflags[b] & BF_FIN) {
+        const int nf = d.nf;
+        for (int e = tid; e < N * N; e += kT) Psi[2 * e] = Psi[2 * e + 1] = 0.0;
+        __syncthreads();
+        const int32_t *col = tv.bcol + (size_t)b * 27;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int S = col[9 * (dx + 1) + 3 * (dy + 1) + 1];
+                if (S < 0 || !(tv.bflags[S] & BF_FOUT)) continue;
+                const double *ph = phi + (size_t)tv.bslot[S] * 2 * N * N;
+                // delta = c_B - c_S = -(dx, dy) R; phase exp(i (2 pi / 3) m . delta / R)
+                for (int e = tid; e < N * N; e += kT) {
+                    const int mx = e / N - nf, my = e % N - nf;
+                    int r = (-(mx * dx + my * dy)) % 3;
+                    if (r < 0) r += 3;
+                    const double cr = r == 0 ? 1.0 : -0.5, ci = r == 0 ? 0.0 : (r == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
+                    const double w = d.w[mx * mx + my * my];
+                    const double pr = ph[2 * e], pi = ph[2 * e + 1];
+                    Psi[2 * e] += w * (cr * pr - ci * pi);
+                    Psi[2 * e + 1] += w * (cr * pi + ci * pr);
+                }
+            }
+        __syncthreads();
+        coef_from_pw(Psi, d.Fr, d.Fi, p, N, Zr, Zi, acc);
+    }
+    // the windowed root kernel over the unit square
+    if (level == 0 && tv.bnsrc[b] > 0) {
+        for (int e = tid; e < pp; e += kT) CP[e] = mom[(size_t)b * pp + e];
+        __syncthreads();
+        pw_from_moments(CP, d.FWr, d.FWi, p, NW, Zr, Zi, Psi);
+        const int n0 = d.n0;
+        for (int e = tid; e < NW * NW; e += kT) {
+            const int mx = e / NW - n0, my = e % NW - n0;
+            const double w = d.wW[mx * mx + my * my];
+            Psi[2 * e] *= w;
+            Psi[2 * e + 1] *= w;
+        }
+        __syncthreads();
+        coef_from_pw(Psi, d.FWr, d.FWi, p, NW, Zr, Zi, acc);
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kT;
+        if (e < pp) loc[(size_t)b * pp + e] = acc[j];
+    }
+}
+
+// ---- Step 3: local expansions at the targets ---------------------------------
+__global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int32_t *pleaf, const double *loc,
+                                              double *ufar) {
+    const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (k >= tv.n) return;
+    if (!(tv.pflag[k] & 2)) { ufar[k] = 0.0; return; }
+    const int b = pleaf[k], p = d.p;
+    int ix, iy;
+    cell2(tv, b, ix, iy);
+    const double R = level_R(tv.blevel[b]);
+    const double xi = 2.0 * (tv.ux[k] - (ix + 0.5) * R) / R, eta = 2.0 * (tv.uy[k] - (iy + 0.5) * R) / R;
+    double Ty[kMaxP];
+    cheb_row(eta, p, Ty);
+    const double *c = loc + (size_t)b * p * p;
+    double acc = 0.0, t0 = 1.0, t1 = xi;
+    for (int a = 0; a < p; ++a) {
+        const double ta = a == 0 ? 1.0 : (a == 1 ? xi : 2.0 * xi * t1 - t0);
+        if (a >= 2) { t0 = t1; t1 = ta; }
+        double s = 0.0;
+        for (int bb = 0; bb < p; ++bb) s += c[a * p + bb] * Ty[bb];
+        acc += ta * s;
+    }
+    ufar[k] = acc;
+}
+
+// ---- Steps 4-5: residual kernels over the near lists ------------------------
+constexpr int kNT = 128;
+__global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const int32_t *tleaves, const int32_t *nl_off,
+                                               const int32_t *nl_src, double *unear, double *qco) {
+    const int i = blockIdx.x, T = tleaves[i], tid = threadIdx.x;
+    __shared__ double sx[kNT], sy[kNT], sq[kNT], g[64];
+    const int gdeg = d.gdeg;
+    for (int e = tid; e <= gdeg; e += kNT) g[e] = d.g[e];
+    __syncthreads();
+    const int t0 = tv.bstart[T], nt = tv.bcount[T];
+    for (int tc = 0; tc < nt; tc += kNT) {
+        const int k = t0 + tc + tid;
+        const bool act = tc + tid < nt && (tv.pflag[k] & 2);
+        const double xt = act ? tv.ux[k] : 0.0, yt = act ? tv.uy[k] : 0.0;
+        double acc = 0.0, qc = 0.0;
+        for (int li = nl_off[i]; li < nl_off[i + 1]; ++li) {
+            const int S = nl_src[li];
+            const double R = level_R(tv.blevel[S]), inv2 = 1.0 / (R * R);
+            const double S0 = log(R) - d.G0;  // mollified kernel at r = 0
+            const int s0 = tv.bstart[S], ns = tv.bcount[S];
+            for (int sc = 0; sc < ns; sc += kNT) {
+                __syncthreads();
+                if (sc + tid < ns) {
+                    sx[tid] = tv.ux[s0 + sc + tid];
+                    sy[tid] = tv.uy[s0 + sc + tid];
+                    sq[tid] = tv.q[s0 + sc + tid];
+                }
+                __syncthreads();
+                const int m = min(kNT, ns - sc);
+                if (!act) continue;
+                for (int j = 0; j < m; ++j) {
+                    const double dx = xt - sx[j], dy = yt - sy[j], r2 = dx * dx + dy * dy, t = r2 * inv2;
+                    if (!(t < 1.0)) continue;
+                    const double q = sq[j];
+                    if (r2 == 0.0) {
+                        acc -= q * S0;
+                        qc += q;
+                        continue;
+                    }
+                    // G(t) by Clenshaw in x = 2 t - 1
+                    const double x = 2.0 * t - 1.0;
+                    double b1 = 0.0, b2 = 0.0;
+                    for (int n = gdeg; n >= 1; --n) {
+                        const double b0 = 2.0 * x * b1 - b2 + g[n];
+                        b2 = b1;
+                        b1 = b0;
+                    }
+                    acc += q * (0.5 * log(t) + x * b1 - b2 + g[0]);
+                }
+            }
+        }
+        if (act) {
+            unear[k] = acc;
+            qco[k] = qc;
+        }
+    }
+}
+
+__global__ void k2_lift(const double *x2, int64_t n, double *x3) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x3[3 * i] = x2[2 * i];
+    x3[3 * i + 1] = x2[2 * i + 1];
+    x3[3 * i + 2] = 0.0;
+}
+
+// total source charge in a fixed order (one block)
+__global__ void k2_qsum(const double *q, const uint8_t *pflag, int64_t n, double *out) {
+    __shared__ double s[1024];
+    double a = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += 1024) a += (pflag[k] & 1) ? q[k] : 0.0;
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void k2_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout, const double *ufar,
+                            const double *unear, const double *qco, const double *qtot, const Frame *frame,
+                            double *pot) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || !(pflag[k] & 2)) return;
+    pot[pout[k]] = ufar[k] + unear[k] + log(frame->S) * (*qtot - qco[k]);
+}
+
+}  // namespace
+
+int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf, const double *src, int64_t ns,
+              const double *charges, const double *tgt, int64_t nt, int leaf_cap, int max_level, double *pot,
+              cudaStream_t st, std::string &err) {
+    if (nt == 0) return DMK_OK;
+    const bool same = (tgt == src && nt == ns);
+    if (ws.ensure(bf.x3, std::max<int64_t>(ns, 1) * 24) || (!same && ws.ensure(bf.t3, nt * 24))) {
+        err = "device allocation failed (2D points)";
+        return DMK_ERR_OOM;
+    }
+    if (ns > 0) {
+        k2_lift<<<nblk(ns, 256), 256, 0, st>>>(src, ns, (double *)bf.x3.p);
+        launch_tick();
+    }
+    if (!same) {
+        k2_lift<<<nblk(nt, 256), 256, 0, st>>>(tgt, nt, (double *)bf.t3.p);
+        launch_tick();
+    }
+    L2CK(cudaGetLastError());
+    const double *x3 = (const double *)bf.x3.p, *t3 = same ? x3 : (const double *)bf.t3.p;
+    int rc = tree.build(x3, ns, charges, same ? nullptr : t3, same ? 0 : nt, same, leaf_cap, max_level, 0, st, err);
+    if (rc) return rc;
+    const TreeView tv = tree.view();
+    const int p = d.p, pp = p * p, N = d.N1, NW = d.NW, NM = std::max(N, NW);
+    const int64_t n = tv.n;
+    if (ws.ensure(bf.mom, (int64_t)tv.nb * pp * 8) || ws.ensure(bf.loc, (int64_t)tv.nb * pp * 8) ||
+        ws.ensure(bf.phi, (int64_t)std::max(tree.nslots, 1) * 2 * N * N * 8) || ws.ensure(bf.ufar, n * 8) ||
+        ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8)) {
+        err = "device allocation failed (2D expansions)";
+        return DMK_ERR_OOM;
+    }
+    double *mom = (double *)bf.mom.p, *loc = (double *)bf.loc.p, *phi = (double *)bf.phi.p;
+    double *ufar = (double *)bf.ufar.p, *unear = (double *)bf.unear.p, *qco = (double *)bf.qco.p;
+    L2CK(cudaMemsetAsync(unear, 0, n * 8, st));
+    L2CK(cudaMemsetAsync(qco, 0, n * 8, st));
+    // Step 2
+    k2_moments<<<tv.nb, kT, 0, st>>>(tv, d, mom);
+    launch_tick();
+    for (int l = tv.nlev - 2; l >= 0; --l) {
+        if (tv.lev_count[l] == 0) continue;
+        k2_c2p<<<tv.lev_count[l], kT, 0, st>>>(tv, d, tv.lev_start[l], mom);
+        launch_tick();
+    }
+    L2CK(cudaGetLastError());
+    // Step 3
+    const size_t smo = (size_t)(pp + 2 * N * p + 2 * N * N) * 8;
+    const size_t sml = (size_t)(2 * pp + 2 * NM * NM + 2 * p * NM) * 8;
+    L2CK(cudaFuncSetAttribute(k2_outgoing, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smo));
+    L2CK(cudaFuncSetAttribute(k2_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
+    if (tree.nslots > 0) {
+        k2_outgoing<<<tv.nb, kT, smo, st>>>(tv, d, mom, phi);
+        launch_tick();
+    }
+    for (int l = 0; l < tv.nlev; ++l) {
+        if (tv.lev_count[l] == 0) continue;
+        k2_local<<<tv.lev_count[l], kT, sml, st>>>(tv, d, l, tv.lev_start[l], mom, phi, loc);
+        launch_tick();
+    }
+    k2_eval<<<nblk(n, kT), kT, 0, st>>>(tv, d, (const int32_t *)tree.pleaf.p, loc, ufar);
+    launch_tick();
+    L2CK(cudaGetLastError());
+    // Steps 4-5
+    if (tree.ntleaves > 0) {
+        k2_near<<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p, (const int32_t *)tree.nl_off.p,
+                                              (const int32_t *)tree.nl_src.p, unear, qco);
+        launch_tick();
+    }
+    k2_qsum<<<1, 1024, 0, st>>>(tv.q, tv.pflag, n, (double *)bf.qtot.p);
+    k2_finalize<<<nblk(n, 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)tree.pout.p, ufar, unear, qco,
+                                              (const double *)bf.qtot.p, (const Frame *)tree.frame.p, pot);
+    launch_tick();
+    launch_tick();
+    L2CK(cudaGetLastError());
+    return DMK_OK;
+}
+
+}  // namespace dmk

@@ -1,0 +1,34 @@
+// log2d.h -- the 2D Laplace kernel log r (internal).
+#pragma once
+
+#include <string>
+
+#include "dmk_internal.h"
+#include "tree.h"
+
+namespace dmk {
+
+// Plan tables of the 2D pass on the device (FP64).
+struct Log2dDev {
+    int p, nf, N1, n0, NW, gdeg;
+    const double *A;          // [2][p][p]: T_n((xi + s) / 2) = sum_m A_s[n][m] T_m(xi), s = -1, +1
+    const double *Fr, *Fi;    // [N1][p]: moments -> plane waves, theta = pi / 3
+    const double *FWr, *FWi;  // [NW][p]: the same for the root window
+    const double *w;          // [2 nf^2 + 1]: translation weights (every level)
+    const double *wW;         // [2 n0^2 + 1]: root window weights
+    const double *g;          // [gdeg + 1]: Chebyshev coefficients of G(t), x = 2 t - 1
+    double G0;                // G(0)
+};
+
+struct Log2dBufs {
+    DBuf x3, t3, mom, loc, phi, ufar, unear, qco, qtot;
+};
+
+// One evaluation: sources [ns][2], charges [ns], targets [nt][2] (targets ==
+// sources with nt == ns: every source is a target), potentials [nt]; all
+// device pointers, work on stream st.  Returns a DMK_* code.
+int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf, const double *src, int64_t ns,
+              const double *charges, const double *tgt, int64_t nt, int leaf_cap, int max_level, double *pot,
+              cudaStream_t st, std::string &err);
+
+}  // namespace dmk

@@ -534,4 +534,97 @@ int build_yukawa_tables(const Tables &tb, double lam, int nlev, YukawaTables &yt
     return 0;
 }
 
+// ---- 2D Laplace kernel log r (Sec. 3.7 at lambda = 0, in the plane) -----------
+// log r transforms to -2 pi / k^2 in two dimensions, so (psi(0) = 1)
+//   Dhat_l(k) = -2 pi [psi(k R_{l+1} / c) - psi(k R_l / c)] / k^2, Dhat_l(0) = -pi (c2 / c0) (R_l^2 - R_{l+1}^2),
+// and with h_l = 2 pi / (3 R_l) the weight (h_l / 2 pi)^2 Dhat_l(h_l |m|) is the
+// same at every level.  The residual's transform -2 pi (1 - psi(k R / c)) / k^2
+// inverts to R_l(r) = F(r / R_l), F(rho) = -int_0^inf (1 - psi(k / c)) J_0(k rho) / k dk;
+// the integral of (J_0(t) - [t < 1]) / t over (0, inf) is log 2 - gamma, which
+// leaves F(rho) = log rho + G(rho^2) with
+//   G(t) = log(K / 2) + gamma - int_0^K (1 - psi(k / c) J_0(k sqrt t)) / k dk,
+// psi negligible beyond K = 4 c.  The root window is the kernel cut at
+// R_t = 1 + sqrt 2 times psi(k / c):
+//   What(k) = psi(k / c) 2 pi (R_t log R_t J_1(k R_t) / k - (1 - J_0(k R_t)) / k^2).
+int build_log2d_tables(const Tables &tb, Log2dTables &t2, std::string &err) {
+    const int p = tb.p, nf = tb.nf;
+    const double c = tb.c;
+    Pswf psi(c);
+    // translation weights at R = 1: (1/3)^2 Dhat((2 pi / 3) sqrt s)
+    t2.w.resize(2 * nf * nf + 1);
+    for (int s = 0; s <= 2 * nf * nf; ++s) {
+        double dhat;
+        if (s == 0) {
+            dhat = -M_PI * psi.c2 / psi.c0 * 0.75;
+        } else {
+            const double k = 2.0 * M_PI / 3.0 * std::sqrt((double)s);
+            dhat = -2.0 * M_PI * psi.diff(k / (2.0 * c), k / c) / (k * k);
+        }
+        t2.w[s] = dhat / 9.0;
+    }
+    // root window
+    const double Rt = 1.0 + std::sqrt(2.0);
+    t2.hW = 2.0 * M_PI / (2.0 + Rt);
+    t2.n0 = (int)std::ceil(c / t2.hW) + 1;
+    if (t2.n0 > kMaxNf) { err = "root mode count above the library limit"; return -1; }
+    const int NW = 2 * t2.n0 + 1;
+    t2.FWr.assign((size_t)NW * p, 0.0);
+    t2.FWi.assign((size_t)NW * p, 0.0);
+    for (int mi = 0; mi < NW; ++mi) {
+        const int m = mi - t2.n0;
+        for (int n = 0; n < p; ++n) {
+            std::complex<double> acc = 0.0;
+            for (int j = 0; j < p; ++j) {
+                // V^{-1}[n][j] = (n ? 2 : 1) / p T_n(t_j), T_n(cos a) = cos(n a)
+                const double vinv = (n == 0 ? 1.0 : 2.0) / p * std::cos(n * M_PI * (j + 0.5) / p);
+                acc += std::polar(1.0, -0.5 * t2.hW * m * tb.t[j]) * vinv;
+            }
+            t2.FWr[(size_t)mi * p + n] = acc.real();
+            t2.FWi[(size_t)mi * p + n] = acc.imag();
+        }
+    }
+    t2.wW.resize(2 * t2.n0 * t2.n0 + 1);
+    const double scW = (t2.hW / (2.0 * M_PI)) * (t2.hW / (2.0 * M_PI));
+    for (int s = 0; s <= 2 * t2.n0 * t2.n0; ++s) {
+        const double k = t2.hW * std::sqrt((double)s);
+        double what;
+        if (s == 0)
+            what = M_PI * Rt * Rt * (std::log(Rt) - 0.5);
+        else
+            what = 2.0 * M_PI * (Rt * std::log(Rt) * std::cyl_bessel_j(1.0, k * Rt) / k -
+                                 (1.0 - std::cyl_bessel_j(0.0, k * Rt)) / (k * k)) * psi(k / c);
+        t2.wW[s] = scW * what;
+    }
+    // G(t) on [0, 1]: 16 Gauss-Legendre panels of 24 nodes on [0, K], then a
+    // Chebyshev interpolant at 64 points in t, cut where its tail is below
+    // 1e-3 eps of max(1, |G|)
+    const double K = 4.0 * c, gamma = 0.57721566490153286061;
+    std::vector<double> gx, gw, kk, wk, ps;
+    gl_rule(24, gx, gw);
+    const int panels = 16;
+    for (int q = 0; q < panels; ++q)
+        for (int i = 0; i < 24; ++i) {
+            const double k = K / panels * (q + 0.5 * (gx[i] + 1.0));
+            kk.push_back(k);
+            wk.push_back(0.5 * K / panels * gw[i] / k);
+            ps.push_back(psi(k / c));
+        }
+    auto G = [&](double t) {
+        const double r = std::sqrt(t);
+        double acc = 0.0;
+        for (size_t j = 0; j < kk.size(); ++j) acc += wk[j] * (1.0 - ps[j] * std::cyl_bessel_j(0.0, kk[j] * r));
+        return std::log(0.5 * K) + gamma - acc;
+    };
+    const int nc = 64;
+    std::vector<double> vals(nc);
+    double gmax = 1.0;
+    for (int j = 0; j < nc; ++j) {
+        vals[j] = G(cheb_node01(j, nc));
+        gmax = std::max(gmax, std::fabs(vals[j]));
+    }
+    t2.g = cheb_fit(vals, 1e-3 * tb.eps * gmax);
+    t2.G0 = G(0.0);
+    return 0;
+}
+
 }  // namespace dmk

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libdmk.so")
 
 DMK_LAPLACE = 0
 DMK_YUKAWA = 1
+DMK_LOG2D = 2       # log r in the plane (dim 2, FP64)
 DMK_FP64 = 0
 DMK_MIXED = 1
 FLAG_FAR_ONLY = 1
@@ -120,8 +121,10 @@ class Plan:
 
     def __init__(self, eps=1e-6, precision=DMK_FP64, leaf_cap=0, flags=0, max_level=0, p=0, nf=0, kernel=DMK_LAPLACE,
                  dim=3, lam=0.0):
-        """lam: the Yukawa parameter (kernel DMK_YUKAWA, exp(-lam r)/r)."""
+        """lam: the Yukawa parameter (kernel DMK_YUKAWA, exp(-lam r)/r).
+        kernel DMK_LOG2D takes dim=2: coordinates are (n, 2)."""
         self._h = ctypes.c_void_p()
+        self._dim = dim
         o = Opts(leaf_cap, precision, float(lam), flags, max_level, p, nf)
         _check(lib().dmk_plan(kernel, dim, eps, ctypes.byref(o), ctypes.byref(self._h)))
 
@@ -227,9 +230,9 @@ class Plan:
         return best.value, dict(zip(tried, list(times)))
 
     def eval_host(self, sources, charges, targets=None, out=None, stream=0):
-        src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+        src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, self._dim)
         q = np.ascontiguousarray(charges, dtype=np.float64)
-        tgt = src if targets is None else np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+        tgt = src if targets is None else np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, self._dim)
         if out is None:
             out = np.empty(tgt.shape[0])
         dp = ctypes.POINTER(ctypes.c_double)

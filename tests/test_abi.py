@@ -51,8 +51,15 @@ def test_argument_validation_without_device(dmk):
     assert L.dmk_plan(0, 3, 1.0, ctypes.byref(o), ctypes.byref(h)) == 1      # eps out of range
     assert L.dmk_plan(0, 3, float("nan"), ctypes.byref(o), ctypes.byref(h)) == 1
     assert L.dmk_plan(1, 3, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 1      # Yukawa without lambda
-    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # kernel not implemented
+    assert L.dmk_plan(3, 3, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # kernel not implemented
     assert L.dmk_plan(0, 2, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # dimension
+    assert L.dmk_plan(2, 3, 1e-6, ctypes.byref(o), ctypes.byref(h)) == 2      # log r is a 2D kernel
+    ho = dmk.Opts(flags=dmk.FLAG_HOST_ONLY)
+    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(ho), ctypes.byref(h)) == 0
+    L.dmk_plan_destroy(h)
+    h = ctypes.c_void_p()
+    mixed = dmk.Opts(precision=1, flags=dmk.FLAG_HOST_ONLY)
+    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(mixed), ctypes.byref(h)) == 2  # the 2D pass is FP64
     assert L.dmk_plan(0, 3, 1e-6, ctypes.byref(o), None) == 1
     bad = dmk.Opts(p=17)
     assert L.dmk_plan(0, 3, 1e-6, ctypes.byref(bad), ctypes.byref(h)) == 1

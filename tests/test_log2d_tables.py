@@ -1,0 +1,69 @@
+"""The library's 2D tables for log r (host plan math, no device) against the
+oracle's independent implementation of the same formulas (Sec. 3.7 at
+lambda = 0 in the plane): translation weights, root weights, and the
+residual R_l(r) = log(r / R_l) + G(r^2 / R_l^2) with its value at r = 0.
+"""
+import numpy as np
+import pytest
+
+from numpy.polynomial import chebyshev
+
+
+@pytest.fixture(scope="module")
+def dmk():
+    from paper_2308_00292_gb300 import build, dmk as m
+    build.build()
+    m.lib()
+    return m
+
+
+def plan(dmk, eps):
+    return dmk.Plan(eps, flags=dmk.FLAG_HOST_ONLY, kernel=dmk.DMK_LOG2D, dim=2)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9, 1e-12])
+def test_weights(dmk, oracle_mod, eps):
+    pl = plan(dmk, eps)
+    prm = pl.params()
+    op = oracle_mod.params_log2d(eps=eps)
+    nf = prm["nf"]
+    s = np.arange(2 * nf * nf + 1)
+    h = 2 * np.pi / 3
+    ref = (h / (2 * np.pi)) ** 2 * oracle_mod.kernel_log2d(op, 3, 0, h * np.sqrt(s))
+    w = pl.table(1)
+    assert np.abs(w - ref).max() <= 1e-12 * np.abs(ref).max()
+    # level independence: (h_l / 2 pi)^2 Dhat_l(h_l |m|) at level 5
+    h5 = h * 32
+    ref5 = (h5 / (2 * np.pi)) ** 2 * oracle_mod.kernel_log2d(op, 3, 5, h5 * np.sqrt(s))
+    assert np.abs(w - ref5).max() <= 1e-12 * np.abs(ref).max()
+    t2 = pl.table(2)
+    hW, wW = t2[0], t2[1:]
+    assert hW == pytest.approx(oracle_mod.hW_log2d(op), rel=1e-15)
+    n0 = prm["n0"]
+    assert n0 == oracle_mod.n0_log2d(op) and len(wW) == 2 * n0 * n0 + 1
+    sW = np.arange(2 * n0 * n0 + 1)
+    refW = (hW / (2 * np.pi)) ** 2 * oracle_mod.kernel_log2d(op, 4, 0, hW * np.sqrt(sW))
+    assert np.abs(wW - refW).max() <= 1e-12 * np.abs(refW).max()
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9, 1e-12])
+def test_residual(dmk, oracle_mod, eps):
+    pl = plan(dmk, eps)
+    op = oracle_mod.params_log2d(eps=eps)
+    g = pl.table(3)
+    assert len(g) <= 64
+    G0 = pl.table(4)[0]
+    t = np.linspace(1e-6, 1.0, 57)
+    lib = 0.5 * np.log(t) + chebyshev.chebval(2 * t - 1, g)
+    ref = oracle_mod.kernel_log2d(op, 1, 0, np.sqrt(t))
+    # the fit tolerance (1e-3 eps of max(1, |G|)) plus the rounding of two FP64
+    # codes that reach |R| ~ 5
+    bar = 5e-3 * eps + 4e-15 * max(1.0, np.abs(ref).max())
+    assert np.abs(lib - ref).max() <= bar
+    # scale-free: level 4 is the same function of r / R_4
+    ref4 = oracle_mod.kernel_log2d(op, 1, 4, np.sqrt(t) / 16)
+    assert np.abs(lib - ref4).max() <= bar
+    # S_l(0) = log R_l - G(0)
+    s0 = oracle_mod.kernel_log2d(op, 0, 3, np.zeros(1))[0]
+    assert np.log(1 / 8) - G0 == pytest.approx(s0, abs=1e-12)
+    assert chebyshev.chebval(-1.0, g) == pytest.approx(G0, abs=bar)
