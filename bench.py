@@ -53,6 +53,10 @@ def parse():
                     help="time the batched workload (4096 independent systems, leaf capacity autotuned) instead")
     ap.add_argument("--yukawa", action="store_true",
                     help="time the Yukawa kernel exp(-10 r)/r on 4e6 uniform points instead")
+    ap.add_argument("--log2d", action="store_true",
+                    help="time the 2D kernel log r on 8e6 points (circle and disk) at eps 1e-8 instead")
+    ap.add_argument("--leaf-cap", type=int, default=0,
+                    help="--log2d: this leaf capacity instead of the autotuner's (profiling runs)")
     return ap.parse_args()
 
 
@@ -417,6 +421,75 @@ def run_yukawa(args):
     print(json.dumps(line), flush=True)
 
 
+def run_log2d(args):
+    """log |x - y| in the plane, 8e6 points (half on the unit circle, half in the
+    disk), eps 1e-8: the FP64 path (the 2D pass has no mixed path), leaf
+    capacity chosen by the autotuner; e2e through dmk_eval_host from pinned
+    host buffers."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2308_00292_gb300 import dmk, inputs
+    name = "log2d_circle_disk_n8e6"
+    cfg = inputs.CONFIGS[name]
+    x, q = inputs.make(cfg["gen"], cfg["n"], cfg["seed"])
+    n = x.shape[0]
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    oracle.build()
+    sample = np.sort(np.random.default_rng(cfg["seed"] + 11).choice(n, 128, replace=False))
+    ref = oracle.direct_log2d(x, q, x[sample])
+    stream = torch.cuda.current_stream()
+    plan = dmk.Plan(cfg["eps"], kernel=dmk.DMK_LOG2D, dim=2, leaf_cap=args.leaf_cap)
+    if args.leaf_cap > 0:
+        best, tune_ms = args.leaf_cap, {}
+    else:
+        best, tune_ms = plan.tune_leaf_cap(xd, qd, candidates=[80, 120, 160, 240, 320], reps=1)
+    for _ in range(args.warmup):
+        plan.eval(xd, qd, out=out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.eval(xd, qd, out=out)
+        launches += plan.stats()["n_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = plan.stats()
+    u = out.cpu().numpy()[sample]
+    e2e = None
+    if not args.skip_e2e:
+        hx = torch.from_numpy(x).pin_memory().numpy()
+        hq = torch.from_numpy(q).pin_memory().numpy()
+        hu = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+        plan.eval_host(hx, hq, out=hu)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.eval_host(hx, hq, out=hu)
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e = {"value": n / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": n * 8,
+               "ms_per_step": e_ms}
+    plan.close()
+    line = {"metric": "2D log|x-y| DMK points/s at eps 1e-8 (FP64 path), 1 GB300",
+            "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "n_points": n, "distribution": cfg["gen"], "eps": cfg["eps"],
+                       "leaf_cap": best, "precision": "fp64", "seed": cfg["seed"],
+                       "l2": "inputs larger than L2 (%.0f MB of points and charges)" % (n * 24 / 1e6)},
+            "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+            "rel_l2_vs_direct_128_targets": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+            "tree": {"levels": st["n_levels"], "boxes": st["n_boxes"], "leaves": st["n_leaves"],
+                     "near_pairs": st["near_pairs"]},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -566,6 +639,8 @@ def main():
         run_batch(args)
     elif args.yukawa:
         run_yukawa(args)
+    elif args.log2d:
+        run_log2d(args)
     else:
         run_ours(args, rank, world, local_rank)
 

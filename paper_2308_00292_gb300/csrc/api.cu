@@ -158,7 +158,8 @@ int upload_log2d(dmk_plan_s *pl) {
     std::vector<double> A2(tb.A[0]);
     A2.insert(A2.end(), tb.A[1].begin(), tb.A[1].end());
     const size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(pl->t2.FWr),
-                 oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW), og = push(pl->t2.g);
+                 oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW),
+                 og = push(pl->t2.gmono.empty() ? pl->t2.g : pl->t2.gmono);
     if (pl->ws.ensure(pl->tab2, (int64_t)h.size() * 8)) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
     if (cudaMemcpy(pl->tab2.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(DMK_ERR_CUDA, "copying the plan tables to the device failed");
@@ -170,6 +171,7 @@ int upload_log2d(dmk_plan_s *pl) {
     d.n0 = pl->t2.n0;
     d.NW = 2 * pl->t2.n0 + 1;
     d.gdeg = (int)pl->t2.g.size() - 1;
+    d.gmono = pl->t2.gmono.empty() ? 0 : 1;
     d.A = base + oA;
     d.Fr = base + oFr;
     d.Fi = base + oFi;

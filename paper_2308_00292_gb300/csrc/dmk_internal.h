@@ -63,6 +63,9 @@ struct Log2dTables {
     double hW = 0, G0 = 0;
     int n0 = 0;
     std::vector<double> w, FWr, FWi, wW, g;  // [2 nf^2 + 1], [NW][p] x 2, [2 n0^2 + 1], [gdeg + 1]
+    // g as monomials in 2 t - 1 (Horner) where that form keeps its accuracy,
+    // else empty (the device then sums the Chebyshev series)
+    std::vector<double> gmono;
 };
 int build_log2d_tables(const Tables &tb, Log2dTables &t2, std::string &err);
 

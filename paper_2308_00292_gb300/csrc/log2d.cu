@@ -346,7 +346,11 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 }
 
 // ---- Steps 4-5: residual kernels over the near lists ------------------------
-constexpr int kNT = 128;
+// A thread per target: 64 threads per leaf (leaves hold about half their
+// capacity, so wider blocks would leave most lanes idle).  MONO: G by Horner
+// in monomials, else by Clenshaw in Chebyshev polynomials.
+constexpr int kNT = 64;
+template <bool MONO>
 __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const int32_t *tleaves, const int32_t *nl_off,
                                                const int32_t *nl_src, double *unear, double *qco) {
     const int i = blockIdx.x, T = tleaves[i], tid = threadIdx.x;
@@ -384,15 +388,21 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
                         qc += q;
                         continue;
                     }
-                    // G(t) by Clenshaw in x = 2 t - 1
                     const double x = 2.0 * t - 1.0;
-                    double b1 = 0.0, b2 = 0.0;
-                    for (int n = gdeg; n >= 1; --n) {
-                        const double b0 = 2.0 * x * b1 - b2 + g[n];
-                        b2 = b1;
-                        b1 = b0;
+                    double G;
+                    if (MONO) {
+                        G = g[gdeg];
+                        for (int n = gdeg - 1; n >= 0; --n) G = fma(G, x, g[n]);
+                    } else {
+                        double b1 = 0.0, b2 = 0.0;
+                        for (int n = gdeg; n >= 1; --n) {
+                            const double b0 = 2.0 * x * b1 - b2 + g[n];
+                            b2 = b1;
+                            b1 = b0;
+                        }
+                        G = x * b1 - b2 + g[0];
                     }
-                    acc += q * (0.5 * log(t) + x * b1 - b2 + g[0]);
+                    acc += q * (0.5 * log(t) + G);
                 }
             }
         }
@@ -497,8 +507,14 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     L2CK(cudaGetLastError());
     // Steps 4-5
     if (tree.ntleaves > 0) {
-        k2_near<<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p, (const int32_t *)tree.nl_off.p,
-                                              (const int32_t *)tree.nl_src.p, unear, qco);
+        if (d.gmono)
+            k2_near<true><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
+                                                        (const int32_t *)tree.nl_off.p,
+                                                        (const int32_t *)tree.nl_src.p, unear, qco);
+        else
+            k2_near<false><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
+                                                         (const int32_t *)tree.nl_off.p,
+                                                         (const int32_t *)tree.nl_src.p, unear, qco);
         launch_tick();
     }
     k2_qsum<<<1, 1024, 0, st>>>(tv.q, tv.pflag, n, (double *)bf.qtot.p);

@@ -16,7 +16,8 @@ struct Log2dDev {
     const double *FWr, *FWi;  // [NW][p]: the same for the root window
     const double *w;          // [2 nf^2 + 1]: translation weights (every level)
     const double *wW;         // [2 n0^2 + 1]: root window weights
-    const double *g;          // [gdeg + 1]: Chebyshev coefficients of G(t), x = 2 t - 1
+    const double *g;          // [gdeg + 1]: G(t) in x = 2 t - 1, monomials if gmono else Chebyshev
+    int gmono;
     double G0;                // G(0)
 };
 

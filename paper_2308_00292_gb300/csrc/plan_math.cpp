@@ -624,6 +624,24 @@ int build_log2d_tables(const Tables &tb, Log2dTables &t2, std::string &err) {
     }
     t2.g = cheb_fit(vals, 1e-3 * tb.eps * gmax);
     t2.G0 = G(0.0);
+    // the monomial form costs one FMA per degree instead of two; keep it if it
+    // reproduces the Chebyshev sum within 1e-4 eps (its coefficients grow with
+    // the degree, about 6e7 at the 1e-12 row, where it does not)
+    std::vector<double> mono = cheb_to_mono(t2.g);
+    double dev = 0.0;
+    for (int j = 0; j <= 256; ++j) {
+        const double x = -1.0 + j / 128.0;
+        double b1 = 0.0, b2 = 0.0, h = 0.0;
+        for (int k = (int)t2.g.size() - 1; k >= 1; --k) {
+            const double b0 = 2.0 * x * b1 - b2 + t2.g[k];
+            b2 = b1;
+            b1 = b0;
+        }
+        for (int k = (int)mono.size() - 1; k >= 0; --k) h = h * x + mono[k];
+        dev = std::max(dev, std::fabs(x * b1 - b2 + t2.g[0] - h));
+    }
+    t2.gmono.clear();
+    if (dev <= 1e-4 * tb.eps * gmax) t2.gmono = mono;
     return 0;
 }
 

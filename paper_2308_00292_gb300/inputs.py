@@ -16,6 +16,8 @@ Workloads:
                    uniform in the cube or one Gaussian cluster   (batched)
   disk2d        -- points uniform in the unit disk, charges U[-1,1]  (2D log)
   circle2d      -- points on the unit circle, charges U[-1,1]    (2D log, Table 3 shape)
+  circle_disk2d -- half on the unit circle, half uniform in the unit disk
+                                                                 (2D log workload)
 """
 from __future__ import annotations
 
@@ -124,6 +126,17 @@ def circle2d(n: int, seed: int = 9):
     return np.stack([np.cos(th), np.sin(th)], axis=1), q
 
 
+def circle_disk2d(n: int, seed: int = 10):
+    """n // 2 points on the unit circle and the rest uniform in the unit disk,
+    charges uniform in [-1, 1]; coordinates (n, 2)."""
+    rng = np.random.default_rng(seed)
+    nc = n // 2
+    th = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    r = np.concatenate([np.ones(nc), np.sqrt(rng.random(n - nc))])
+    q = rng.uniform(-1.0, 1.0, size=n)
+    return np.stack([r * np.cos(th), r * np.sin(th)], axis=1), q
+
+
 CONFIGS = {
     "laplace3d_uniform_n2e4": dict(gen="uniform_cube", n=20000, seed=1, eps=1e-6, leaf_cap=280),
     "laplace3d_clustered_n1e7": dict(gen="clustered", n=10_000_000, seed=2, eps=1e-6, leaf_cap=200),
@@ -137,8 +150,11 @@ CONFIGS = {
     "laplace3d_batched_4096": dict(gen="batch", nsys=4096, seed=6, eps=1e-6, leaf_cap=0),
     # the Yukawa kernel exp(-10 r)/r on 4e6 uniform points at eps 1e-8
     "yukawa3d_uniform_n4e6": dict(gen="uniform_cube", n=4_000_000, seed=7, eps=1e-8, lam=10.0, leaf_cap=0),
+    # the 2D log r workload: 8e6 points, half on the unit circle, half in the disk
+    "log2d_circle_disk_n8e6": dict(gen="circle_disk2d", n=8_000_000, seed=10, eps=1e-8, leaf_cap=0),
 }
 
 
 def make(gen: str, n: int, seed: int, **_):
-    return {"uniform_cube": uniform_cube, "clustered": clustered, "sphere": sphere}[gen](n, seed=seed)
+    return {"uniform_cube": uniform_cube, "clustered": clustered, "sphere": sphere, "disk2d": disk2d,
+            "circle2d": circle2d, "circle_disk2d": circle_disk2d}[gen](n, seed=seed)
