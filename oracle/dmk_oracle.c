@@ -1798,6 +1798,10 @@ double oracle_hW(const oracle_params *prm)
  * The unit-box map (the 3D one restricted to two coordinates) turns
  * log |x - y| into log S + log |u - v|: the potential in input units adds
  * log S times the charge of the sources not coincident with the target.
+ * The Gaussian splitting (Sec. 3.2 in the plane) serves as a cross-check:
+ * with sigma_l = R_l / delta the same transforms with exp(-k^2 sigma^2 / 4) in
+ * place of psi give the residual -E_1(r^2 / sigma_l^2) / 2 and the self value
+ * log sigma_l - gamma / 2 in closed form.
  */
 
 #define L2_PANELS 10
@@ -1813,10 +1817,53 @@ typedef struct {
     double G0;                                /* F(rho) - log rho at rho = 0 */
 } split2_t;
 
+/* Exponential integral E_1(x), x > 0: the power series
+ * -gamma - log x - sum_k (-x)^k / (k k!) for x <= 1, and beyond it the
+ * continued fraction E_1(x) = e^{-x} / (x + 1 - 1 / (x + 3 - 4 / (x + 5 - ...)))
+ * by the modified Lentz method (Abramowitz & Stegun 5.1.11 and 5.1.22). */
+static double expint_e1(double x)
+{
+    if (x <= 1.0) {
+        double sum = 0.0, term = 1.0;
+        for (int k = 1; k < 60; ++k) {
+            term *= -x / k; /* (-x)^k / k! */
+            double add = -term / k;
+            sum += add;
+            if (fabs(add) < 1e-18 * fabs(sum)) break;
+        }
+        return -L2_EULER_GAMMA - log(x) + sum;
+    }
+    double b = x + 1.0, c = 1e300, d = 1.0 / b, h = d;
+    for (int i = 1; i < 500; ++i) {
+        double an = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (an * d + b);
+        c = b + an / c;
+        double del = c * d;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * exp(-x);
+}
+
 static int split2_init(split2_t *sp, const oracle_params *in)
 {
     memset(sp, 0, sizeof(*sp));
     sp->prm = *in;
+    if (sp->prm.splitting == ORACLE_GAUSSIAN) {
+        /* the cross-check splitting, sigma_l = R_l / delta: Dhat_l, the window
+         * and the residual -E_1(r^2 / sigma_L^2) / 2 in closed form */
+        oracle_params tmp = sp->prm;
+        tmp.n0 = 1;
+        oracle_default_params(&tmp);
+        double sg = 1.0 / tmp.delta;
+        sp->Rt = sqrt(2.0) + tmp.gauss_b * sg;
+        sp->hW = 2.0 * M_PI / (2.0 + sp->Rt);
+        if (sp->prm.n0 <= 0) sp->prm.n0 = (int)ceil(2.0 * sqrt(log(100.0 / tmp.eps)) / sg / sp->hW);
+        tmp.n0 = sp->prm.n0;
+        sp->prm = tmp;
+        return 0;
+    }
     if (sp->prm.splitting != ORACLE_PSWF) return -1;
     sp->Rt = 1.0 + sqrt(2.0);
     sp->hW = 2.0 * M_PI / (2.0 + sp->Rt);
@@ -1852,20 +1899,33 @@ static void split2_free(split2_t *sp)
     sp->pswf = NULL;
 }
 
-/* residual kernel R_l(r) = F(r / R_l), r > 0 */
+/* residual kernel R_l(r) = F(r / R_l), r > 0; Gaussian: -E_1(r^2 / sigma_l^2) / 2 */
 static double split2_R(const split2_t *sp, int l, double r)
 {
+    if (sp->prm.splitting == ORACLE_GAUSSIAN) {
+        double sg = level_R(l) / sp->prm.delta;
+        return -0.5 * expint_e1(r * r / (sg * sg));
+    }
     double rho = r / level_R(l), acc = 0.0;
     for (int j = 0; j < L2_NQ; ++j) acc += sp->qw[j] * (1.0 - sp->qpsi[j] * j0(sp->qk[j] * rho));
     return log(rho * 0.5 * sp->K) + L2_EULER_GAMMA - acc;
 }
 
-/* mollified kernel at r = 0: lim (log r - R_l(r)) */
-static double split2_S0(const split2_t *sp, int l) { return log(level_R(l)) - sp->G0; }
+/* mollified kernel at r = 0: lim (log r - R_l(r)); Gaussian: log sigma_l - gamma / 2 */
+static double split2_S0(const split2_t *sp, int l)
+{
+    if (sp->prm.splitting == ORACLE_GAUSSIAN) return log(level_R(l) / sp->prm.delta) - 0.5 * L2_EULER_GAMMA;
+    return log(level_R(l)) - sp->G0;
+}
 
 static double split2_Dhat(const split2_t *sp, int l, double k)
 {
     double R = level_R(l), R1 = level_R(l + 1);
+    if (sp->prm.splitting == ORACLE_GAUSSIAN) {
+        double s0 = R / sp->prm.delta, s1 = R1 / sp->prm.delta;
+        if (k == 0.0) return -0.5 * M_PI * (s0 * s0 - s1 * s1);
+        return -2.0 * M_PI * (exp(-k * k * s1 * s1 / 4.0) - exp(-k * k * s0 * s0 / 4.0)) / (k * k);
+    }
     const pswf_t *s = sp->pswf;
     if (k == 0.0) return -M_PI * s->c2 / s->c0 * (R * R - R1 * R1);
     return -2.0 * M_PI * pswf_diff(s, k * R1 / s->c, k * R / s->c) / (k * k);
@@ -1873,7 +1933,13 @@ static double split2_Dhat(const split2_t *sp, int l, double k)
 
 static double split2_What(const split2_t *sp, double k)
 {
-    double Rt = sp->Rt, win = pswf_eval(sp->pswf, k / sp->pswf->c);
+    double Rt = sp->Rt, win;
+    if (sp->prm.splitting == ORACLE_GAUSSIAN) {
+        double sg = 1.0 / sp->prm.delta;
+        win = exp(-k * k * sg * sg / 4.0);
+    } else {
+        win = pswf_eval(sp->pswf, k / sp->pswf->c);
+    }
     if (k == 0.0) return M_PI * Rt * Rt * (log(Rt) - 0.5) * win;
     return 2.0 * M_PI * (Rt * log(Rt) * j1(k * Rt) / k - (1.0 - j0(k * Rt)) / (k * k)) * win;
 }

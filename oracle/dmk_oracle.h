@@ -121,8 +121,9 @@ double oracle_hW(const oracle_params *prm);
 
 /* ---- the 2D Laplace kernel log r (Sec. 3.7 at lambda = 0, in the plane) ----
  * u_i = sum_{j : y_j != x_i} rho_j log |x_i - y_j|; coordinates row-major
- * [n][2]; the PSWF splitting only (prm->splitting must be ORACLE_PSWF; c, p,
- * nf from Table 1 as in 3D, n0 from the 2D root window).  The unit-box map
+ * [n][2]; the PSWF splitting (c, p, nf from Table 1 as in 3D, n0 from the
+ * 2D root window) or, as an independent cross-check, the Gaussian one
+ * (sigma_l = R_l / delta, residual -E_1(r^2 / sigma_l^2) / 2 in closed form).  The unit-box map
  * is the 3D one on two coordinates; pot is in input units (it includes
  * log S times the charge of the sources not coincident with the target),
  * pot_far / pot_near (may be NULL) are the unit-box far and near parts. */

@@ -32,6 +32,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def plan_p(dmk, eps):
+    """The Chebyshev order the library takes (19 at the 1e-6 row in 2D)."""
+    with dmk.Plan(kernel=dmk.DMK_LOG2D, dim=2, eps=eps, flags=dmk.FLAG_HOST_ONLY) as plan:
+        return plan.params()["p"]
+
+
 def run(dmk, x, q, y=None, **kw):
     with dmk.Plan(kernel=dmk.DMK_LOG2D, dim=2, **kw) as plan:
         return plan.eval(dev(x), dev(q), None if y is None else dev(y)).cpu().numpy()
@@ -48,7 +54,7 @@ CASES = {
 def test_matches_oracle_and_direct(dmk, oracle_mod, case, eps, leaf_cap):
     x, q = CASES[case]()
     u = run(dmk, x, q, eps=eps, leaf_cap=leaf_cap)
-    ref = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=leaf_cap)
+    ref = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=leaf_cap, p=plan_p(dmk, eps))
     assert rel(u, ref) < 1e-2 * eps
     assert rel(u, oracle_mod.direct_log2d(x, q)) < eps
 
@@ -82,11 +88,12 @@ def test_small_inputs_and_host_entry(dmk, oracle_mod):
         # cancels the removed S_L(0) to the method's accuracy, as in the oracle
         one = plan.eval(dev(x[:1]), dev(q[:1])).cpu().numpy()
         assert abs(one[0]) < 1e-6 * abs(q[0])
-        assert one == pytest.approx(oracle_mod.dmk_log2d(x[:1], q[:1], eps=1e-6), abs=1e-12)
+        p6 = plan_p(dmk, 1e-6)
+        assert one == pytest.approx(oracle_mod.dmk_log2d(x[:1], q[:1], eps=1e-6, p=p6), abs=1e-12)
         two = plan.eval(dev(x[:2]), dev(q[:2])).cpu().numpy()
         r = np.linalg.norm(x[0] - x[1])
         assert two == pytest.approx([q[1] * np.log(r), q[0] * np.log(r)], abs=1e-6)
-        assert two == pytest.approx(oracle_mod.dmk_log2d(x[:2], q[:2], eps=1e-6), abs=1e-12)
+        assert two == pytest.approx(oracle_mod.dmk_log2d(x[:2], q[:2], eps=1e-6, p=p6), abs=1e-12)
         empty = plan.eval(dev(x[:0]), dev(q[:0]), dev(x[:5])).cpu().numpy()
         assert np.all(empty == 0.0)
     assert rel(ud, oracle_mod.direct_log2d(x, q)) < 1e-6

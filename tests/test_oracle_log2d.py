@@ -5,8 +5,9 @@ Laplacian of the residual kernel (a general-purpose quadrature of the
 mollifier's Hankel transform), the residual's support and its log r
 singularity, the difference kernels as the difference of two residuals
 (numerical Hankel inversion of Dhat_l), the truncated-kernel transform of the
-root window (numerical integration), the direct sum within eps, and the
-log S term of the unit-box map.
+root window (numerical integration), the direct sum within eps, the log S
+term of the unit-box map, and an independent Gaussian splitting (closed-form
+residual -E_1(r^2 / sigma^2) / 2) that must agree with the PSWF one.
 """
 import numpy as np
 import pytest
@@ -162,7 +163,55 @@ def test_log_of_the_scale(oracle_mod):
     assert rel(u2 - np.log(s) * (q.sum() - q), u1) < 1e-12
 
 
-def test_gaussian_splitting_is_refused(oracle_mod):
-    x, q = inputs.disk2d(100, seed=816)
-    with pytest.raises(RuntimeError):
-        oracle_mod.dmk_log2d(x, q, splitting=oracle_mod.GAUSSIAN)
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_gaussian_residual(oracle_mod, eps):
+    """The cross-check splitting sigma_l = R_l / delta: its residual has the
+    transform -2 pi (1 - exp(-k^2 sigma^2 / 4)) / k^2, i.e. -E_1(r^2 / sigma^2) / 2
+    (SciPy's exp1), whose radial Laplacian is -(2 / sigma^2) exp(-r^2 / sigma^2);
+    S_l(0) = log sigma_l - gamma / 2 is the limit of log r - R_l(r)."""
+    prm = oracle_mod.params_log2d(eps=eps, splitting=oracle_mod.GAUSSIAN)
+    delta = oracle_mod.params(eps=eps, splitting=oracle_mod.GAUSSIAN).delta
+    for level in (0, 3):
+        sg = 2.0 ** -level / delta
+        r = np.array([1e-7, 0.01, 0.2, 0.7, 1.0]) * 2.0 ** -level
+        got = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, r)
+        assert got == pytest.approx(-0.5 * special.exp1(r ** 2 / sg ** 2), rel=1e-13, abs=1e-300)
+        hh = 1e-3 * sg
+        for rr in (0.3 * sg, 0.8 * sg, 1.5 * sg):
+            f = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, rr + hh * np.arange(-2, 3))
+            d1 = (f[0] - 8 * f[1] + 8 * f[3] - f[4]) / (12 * hh)
+            d2 = (-f[0] + 16 * f[1] - 30 * f[2] + 16 * f[3] - f[4]) / (12 * hh * hh)
+            lap = -2.0 / sg ** 2 * np.exp(-rr ** 2 / sg ** 2)
+            assert d2 + d1 / rr == pytest.approx(lap, rel=1e-6)
+        s0 = oracle_mod.kernel_log2d(prm, S_ZERO, level, np.zeros(1))[0]
+        assert s0 == pytest.approx(np.log(sg) - 0.5 * np.euler_gamma, abs=1e-14)
+        v = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, np.array([1e-9 * sg]))[0]
+        assert np.log(1e-9 * sg) - v == pytest.approx(s0, abs=1e-12)
+        # below eps beyond the support R_l = delta sigma_l
+        out = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, np.array([1.0, 1.3]) * 2.0 ** -level)
+        assert np.all(np.abs(out) < eps)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_gaussian_and_pswf_splittings_agree(oracle_mod, case, eps):
+    """Two independent splittings of log r (Fourier-space PSWF and Gaussian),
+    each within eps of the direct sum, agree with each other within 2 eps."""
+    x, q = CASES[case]()
+    ref = oracle_mod.direct_log2d(x, q)
+    ug = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=120, splitting=oracle_mod.GAUSSIAN)
+    up = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=120)
+    assert rel(ug, ref) < eps
+    assert rel(up, ref) < eps
+    assert rel(ug, up) < 2 * eps
+
+
+def test_pswf_p18_at_the_1e6_row(oracle_mod):
+    """Table 1's p = 18 at the 1e-6 row leaves some uniform disks just above
+    eps (the reason the library takes p = 19 in 2D there); p = 19 stays below."""
+    x, q = inputs.disk2d(3000, seed=22)
+    ref = oracle_mod.direct_log2d(x, q)
+    e18 = rel(oracle_mod.dmk_log2d(x, q, eps=1e-6, leaf_cap=120), ref)
+    e19 = rel(oracle_mod.dmk_log2d(x, q, eps=1e-6, leaf_cap=120, p=19), ref)
+    assert 1e-6 < e18 < 1.2e-6
+    assert e19 < 0.8e-6
