@@ -104,6 +104,9 @@ def _load():
             lib.oracle_hW_log2d.restype = ctypes.c_double
             lib.oracle_n0_log2d.argtypes = [ctypes.POINTER(Params)]
             lib.oracle_n0_log2d.restype = ctypes.c_int
+            lib.oracle_tree_log2d.argtypes = [ctypes.POINTER(Params), dp, i64, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+            lib.oracle_tree_log2d.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -317,3 +320,19 @@ def hW_log2d(prm: Params) -> float:
 
 def n0_log2d(prm: Params) -> int:
     return _load().oracle_n0_log2d(ctypes.byref(prm))
+
+
+def tree_log2d(src, prm: Params | None = None, **kw):
+    """The 2D quad-tree: per point (level, ix, iy) of its leaf, and the box count."""
+    prm = prm if prm is not None else params_log2d(**kw)
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    n = src.shape[0]
+    lev = np.zeros(max(n, 1), dtype=np.int32)
+    ix = np.zeros(max(n, 1), dtype=np.int64)
+    iy = np.zeros(max(n, 1), dtype=np.int64)
+    nb = _load().oracle_tree_log2d(ctypes.byref(prm), _dp(src), n, lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   iy.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if nb < 0:
+        raise RuntimeError("oracle_tree_log2d failed with code %d" % nb)
+    return lev[:n], ix[:n], iy[:n], nb

@@ -2637,3 +2637,33 @@ int oracle_n0_log2d(const oracle_params *prm)
     split2_free(&sp);
     return n0;
 }
+
+int64_t oracle_tree_log2d(const oracle_params *prm_in, const double *src, int64_t ns,
+                          int32_t *leaf_level, int64_t *leaf_ix, int64_t *leaf_iy)
+{
+    split2_t sp;
+    if (split2_init(&sp, prm_in) != 0) { split2_free(&sp); return -1; }
+    double *dummy = (double *)calloc((size_t)(ns > 0 ? ns : 1), sizeof(double));
+    opoints2 P;
+    otree2 t;
+    memset(&t, 0, sizeof(t));
+    int rc = points2_init(&P, src, dummy, ns, src, ns);
+    if (rc == 0) rc = tree2_make(&t, &P, &sp.prm);
+    int64_t nb = rc == 0 ? t.nb : rc;
+    if (rc == 0)
+        for (int i = 0; i < t.nb; ++i) {
+            const obox2 *b = &t.b[i];
+            if (!b->leaf) continue;
+            for (int64_t k = b->start; k < b->start + b->count; ++k) {
+                int64_t pi = t.ord[k];
+                leaf_level[pi] = b->level;
+                leaf_ix[pi] = b->ix;
+                leaf_iy[pi] = b->iy;
+            }
+        }
+    tree2_free(&t);
+    points2_free(&P);
+    free(dummy);
+    split2_free(&sp);
+    return nb;
+}

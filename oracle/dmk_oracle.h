@@ -138,6 +138,10 @@ int oracle_dmk_log2d(const oracle_params *prm,
  * 4 = What_0(k). */
 void oracle_kernel_log2d(const oracle_params *prm, int what, int level,
                          const double *r, int64_t n, double *out);
+/* The quad-tree of the points src [ns][2] (every point a source and a target):
+ * per point its leaf's level and cell (ix, iy).  Returns the box count or < 0. */
+int64_t oracle_tree_log2d(const oracle_params *prm, const double *src, int64_t ns,
+                          int32_t *leaf_level, int64_t *leaf_ix, int64_t *leaf_iy);
 /* Root spacing h_W and mode count n0 of the 2D window. */
 double oracle_hW_log2d(const oracle_params *prm);
 int oracle_n0_log2d(const oracle_params *prm);

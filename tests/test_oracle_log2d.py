@@ -215,3 +215,29 @@ def test_pswf_p18_at_the_1e6_row(oracle_mod):
     e19 = rel(oracle_mod.dmk_log2d(x, q, eps=1e-6, leaf_cap=120, p=19), ref)
     assert 1e-6 < e18 < 1.2e-6
     assert e19 < 0.8e-6
+
+
+def _decode3(m):
+    ix = iy = iz = 0
+    for b in range(21):
+        ix |= ((m >> (3 * b)) & 1) << b
+        iy |= ((m >> (3 * b + 1)) & 1) << b
+        iz |= ((m >> (3 * b + 2)) & 1) << b
+    return ix, iy, iz
+
+
+@pytest.mark.parametrize("gen", ["disk2d", "circle2d", "circle_disk2d"])
+def test_lifted_octree_is_the_quadtree(oracle_mod, gen):
+    """The library builds the 2D tree with its octree builder on the points
+    lifted to z = 0.  The oracle's octree of the lifted points (which the GPU
+    tree matches bit for bit on 3D clouds) has the same boxes as the oracle's
+    quad-tree, every box in the z = 0 layer, and the same leaf per point."""
+    x, _ = inputs.make(gen, 5000, 31)
+    lev2, ix2, iy2, nb2 = oracle_mod.tree_log2d(x, leaf_cap=40)
+    lev3, cell3, (bl, bc, bf) = oracle_mod.tree(np.c_[x, np.zeros(len(x))], leaf_cap=40, with_boxes=True)
+    assert len(bl) == nb2
+    assert np.array_equal(lev2, lev3)
+    d = np.array([_decode3(int(c)) for c in cell3])
+    assert np.array_equal(d[:, 0], ix2) and np.array_equal(d[:, 1], iy2)
+    assert np.all(d[:, 2] == 0)
+    assert all(_decode3(int(c))[2] == 0 for c in bc)
