@@ -475,6 +475,18 @@ def run_log2d(args):
         e2e = {"value": n / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": n * 8,
                "ms_per_step": e_ms}
     plan.close()
+    cpu = None
+    if not args.skip_cpu_baseline:
+        # the oracle's 2D pass on 50 000 points of the same recipe, the leaf
+        # capacity the GPU used
+        xs, qs = inputs.make(cfg["gen"], 50_000, cfg["seed"] + 1000)
+        t0 = time.perf_counter()
+        oracle.dmk_log2d(xs, qs, eps=cfg["eps"], leaf_cap=best)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 50_000 / dt, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+               "kind": "oracle",
+               "sample": "50000 points of the %s workload (seed %d), eps %g, leaf cap %d, plain FP64 C oracle "
+                         "2D DMK, %.1f s" % (cfg["gen"], cfg["seed"] + 1000, cfg["eps"], best, dt)}
     line = {"metric": "2D log|x-y| DMK points/s at eps 1e-8 (FP64 path), 1 GB300",
             "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -486,7 +498,7 @@ def run_log2d(args):
             "rel_l2_vs_direct_128_targets": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
             "tree": {"levels": st["n_levels"], "boxes": st["n_boxes"], "leaves": st["n_leaves"],
                      "near_pairs": st["near_pairs"]},
-            "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
