@@ -268,7 +268,8 @@ typedef struct {
     double eps, c;          /* precision, PSWF bandwidth */
     int p, nf, n0;          /* Chebyshev order, difference / root Fourier half-widths */
     int leaf_cap, max_level, precision;
-    int q_degree;           /* degree of the residual-kernel polynomial in r^2 */
+    int q_degree;           /* degree of the residual-kernel polynomial in r^2
+                               (DMK_LOG2D: of G, R_l(r) = log(r / R_l) + G(r^2 / R_l^2)) */
     double psi0_over_c0;    /* psi(0)/c_0: the self term at R = 1 */
 } dmk_plan_params;
 

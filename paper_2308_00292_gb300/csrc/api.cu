@@ -620,7 +620,7 @@ int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
     out->leaf_cap = plan->leaf_cap;
     out->max_level = plan->max_level;
     out->precision = plan->precision;
-    out->q_degree = plan->qdeg;
+    out->q_degree = plan->kernel == DMK_LOG2D ? (int)plan->t2.g.size() - 1 : plan->qdeg;
     out->psi0_over_c0 = plan->tb.psi0_over_c0;
     return DMK_OK;
 }

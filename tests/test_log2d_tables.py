@@ -51,7 +51,7 @@ def test_residual(dmk, oracle_mod, eps):
     pl = plan(dmk, eps)
     op = oracle_mod.params_log2d(eps=eps)
     g = pl.table(3)
-    assert len(g) <= 64
+    assert len(g) <= 64 and pl.params()["q_degree"] == len(g) - 1
     G0 = pl.table(4)[0]
     t = np.linspace(1e-6, 1.0, 57)
     lib = 0.5 * np.log(t) + chebyshev.chebval(2 * t - 1, g)
