@@ -114,3 +114,26 @@ def test_refused_options(dmk):
         with pytest.raises(dmk.DMKError) as e:
             plan.eval_batch(dev(x), dev(q), [0, 100, 300])
         assert e.value.code == 2
+
+
+def _decode3(m):
+    ix = iy = iz = 0
+    for b in range(21):
+        ix |= ((m >> (3 * b)) & 1) << b
+        iy |= ((m >> (3 * b + 1)) & 1) << b
+        iz |= ((m >> (3 * b + 2)) & 1) << b
+    return ix, iy, iz
+
+
+def test_tree_is_the_oracle_quadtree(dmk, oracle_mod):
+    """The points lifted to z = 0 give, through the library's tree builder,
+    the oracle's quad-tree: the same leaf level and cell for every point."""
+    x, q = inputs.make("circle_disk2d", 6000, 827)
+    with dmk.Plan(kernel=dmk.DMK_LOG2D, dim=2, eps=1e-6, leaf_cap=40) as plan:
+        plan.eval(dev(x), dev(q))
+        lev, cell = plan.tree()
+    olev, oix, oiy, _ = oracle_mod.tree_log2d(x, leaf_cap=40)
+    assert np.array_equal(lev, olev)
+    d = np.array([_decode3(int(c)) for c in cell])
+    assert np.array_equal(d[:, 0], oix) and np.array_equal(d[:, 1], oiy)
+    assert np.all(d[:, 2] == 0)
