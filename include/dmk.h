@@ -100,7 +100,8 @@ typedef struct dmk_plan_s *dmk_plan_t;
  * windowed root kernel weights (Sec. 3.6, eq. windowedkernelft2), and copy
  * them to the current CUDA device.
  *
- *   kernel  must be DMK_LAPLACE and dim must be 3 (else DMK_ERR_UNSUPPORTED);
+ *   kernel  DMK_LAPLACE or DMK_YUKAWA with dim 3, or DMK_LOG2D with dim 2
+ *           (else DMK_ERR_UNSUPPORTED);
  *   eps     in [1e-12, 1e-2] (else DMK_ERR_INVALID_ARG);
  *   opts    may be NULL (defaults);
  *   out     receives the plan; the caller releases it with dmk_plan_destroy.
@@ -252,7 +253,11 @@ DMK_API int dmk_tune_leaf_cap_batch(dmk_plan_t plan,
                                     int n_systems, const int *candidates, int n_candidates, int reps,
                                     int *best_leaf_cap, float *times_ms, void *cuda_stream);
 
-/* Release a plan and all its device memory.  NULL is accepted. */
+/* Release a plan and all its device memory.  NULL is accepted.  Every call
+ * that takes a plan checks that it is a live handle (a marker word that
+ * dmk_plan sets and dmk_plan_destroy clears) and returns DMK_ERR_INVALID_ARG
+ * for anything else, without reading further; a handle whose memory was
+ * already freed cannot be detected reliably. */
 DMK_API int dmk_plan_destroy(dmk_plan_t plan);
 
 /* Static description of a status code. */

@@ -31,7 +31,12 @@ int fail(int code, const std::string &msg) {
 }
 }  // namespace
 
+// plans carry this word while they live; an entry point handed anything
+// else (a destroyed or foreign handle) refuses it instead of reading through it
+constexpr uint64_t kPlanMagic = 0x646d6b2d706c616eull;
+
 struct dmk_plan_s {
+    uint64_t magic = kPlanMagic;
     int kernel = 0, dim = 3;
     double eps = 0;
     dmk_opts opts{};
@@ -67,6 +72,7 @@ struct dmk_plan_s {
     size_t smem_limit = 0;
     int num_sms = 0;
     ~dmk_plan_s() {
+        magic = 0;
         if (events) {
             for (auto &e : ev) cudaEventDestroy(e);
             for (auto &e : nev) cudaEventDestroy(e);
@@ -78,6 +84,9 @@ struct dmk_plan_s {
 };
 
 namespace {
+
+// a live plan handle: a destroyed or foreign pointer is refused, not used
+bool bad_plan(const dmk_plan_s *plan) { return !plan || plan->magic != kPlanMagic; }
 
 template <typename T>
 int upload_tables(dmk_plan_s *pl, dmk::DevTables<T> &dt) {
@@ -444,6 +453,8 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
 }
 
 int dmk_plan_destroy(dmk_plan_t plan) {
+    if (!plan) return DMK_OK;
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "not a live plan handle");
     delete plan;
     return DMK_OK;
 }
@@ -451,7 +462,7 @@ int dmk_plan_destroy(dmk_plan_t plan) {
 int dmk_eval(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges, const double *targets,
              int64_t n_tgt, double *potentials, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials)))
@@ -463,7 +474,7 @@ int dmk_eval(dmk_plan_t plan, const double *sources, int64_t n_src, const double
 int dmk_eval_grad(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
                   const double *targets, int64_t n_tgt, double *potentials, double *gradients, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials || !gradients)))
@@ -475,7 +486,7 @@ int dmk_eval_grad(dmk_plan_t plan, const double *sources, int64_t n_src, const d
 int dmk_eval_batch(dmk_plan_t plan, const double *points, const double *charges, const int64_t *offsets,
                    int n_systems, double *potentials, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (!offsets || n_systems < 1 || n_systems > (1 << 24))
         return fail(DMK_ERR_INVALID_ARG, "n_systems must lie in 1..2^24 with an offsets array");
@@ -492,7 +503,7 @@ int dmk_eval_batch(dmk_plan_t plan, const double *points, const double *charges,
 int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const double *charges,
                   const double *targets, int64_t n_tgt, double *potentials, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && (!targets || !potentials)))
@@ -573,7 +584,7 @@ int dmk_tune_leaf_cap(dmk_plan_t plan, const double *sources, int64_t n_src, con
                       const double *targets, int64_t n_tgt, const int *candidates, int n_candidates, int reps,
                       int *best_leaf_cap, float *times_ms, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if ((n_src > 0 && (!sources || !charges)) || (n_tgt > 0 && !targets))
@@ -591,7 +602,7 @@ int dmk_tune_leaf_cap_batch(dmk_plan_t plan, const double *points, const double 
                             int n_systems, const int *candidates, int n_candidates, int reps, int *best_leaf_cap,
                             float *times_ms, void *cuda_stream) {
     g_detail.clear();
-    if (!plan) return fail(DMK_ERR_INVALID_ARG, "plan is NULL");
+    if (bad_plan(plan)) return fail(DMK_ERR_INVALID_ARG, "plan is NULL or not a live plan handle");
     if (plan->host_only) return fail(DMK_ERR_INVALID_ARG, "plan was built with DMK_FLAG_HOST_ONLY");
     if (!offsets || n_systems < 1 || n_systems > (1 << 24) || offsets[0] != 0)
         return fail(DMK_ERR_INVALID_ARG, "n_systems must lie in 1..2^24 with offsets from 0");
@@ -611,7 +622,7 @@ int dmk_tune_leaf_cap_batch(dmk_plan_t plan, const double *points, const double 
 }
 
 int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
-    if (!plan || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (bad_plan(plan) || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument or not a live plan handle");
     out->eps = plan->eps;
     out->c = plan->tb.c;
     out->p = plan->tb.p;
@@ -626,7 +637,7 @@ int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
 }
 
 int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64_t *len) {
-    if (!plan || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (bad_plan(plan) || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument or not a live plan handle");
     std::vector<double> v;
     if (plan->kernel == DMK_LOG2D && which >= 1) {
         switch (which) {
@@ -662,7 +673,7 @@ int dmk_plan_get_table(dmk_plan_t plan, int which, double *out, int64_t n, int64
 
 int dmk_plan_get_yukawa_table(dmk_plan_t plan, double lambda_unit, int level, int which, double *out, int64_t n,
                               int64_t *len) {
-    if (!plan || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (bad_plan(plan) || !len) return fail(DMK_ERR_INVALID_ARG, "NULL argument or not a live plan handle");
     if (plan->kernel != DMK_YUKAWA) return fail(DMK_ERR_INVALID_ARG, "not a DMK_YUKAWA plan");
     if (!(lambda_unit > 0.0) || level < 0 || level > dmk::kMaxLevel || which < 0 || which > 2)
         return fail(DMK_ERR_INVALID_ARG, "argument out of range");
@@ -689,13 +700,14 @@ int dmk_plan_get_yukawa_table(dmk_plan_t plan, double lambda_unit, int level, in
 }
 
 int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out) {
-    if (!plan || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (bad_plan(plan) || !out) return fail(DMK_ERR_INVALID_ARG, "NULL argument or not a live plan handle");
     *out = plan->stats;
     return DMK_OK;
 }
 
 int dmk_get_tree(dmk_plan_t plan, int32_t *leaf_level, int64_t *leaf_cell, int64_t n_points) {
-    if (!plan || !leaf_level || !leaf_cell) return fail(DMK_ERR_INVALID_ARG, "NULL argument");
+    if (bad_plan(plan) || !leaf_level || !leaf_cell)
+        return fail(DMK_ERR_INVALID_ARG, "NULL argument or not a live plan handle");
     if (!plan->tree || plan->tree->n != n_points)
         return fail(DMK_ERR_INVALID_ARG, "n_points does not match the last evaluation");
     std::string err;

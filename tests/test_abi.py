@@ -130,3 +130,24 @@ def test_batch_argument_validation_without_device(dmk):
     assert L.dmk_eval_batch(None, None, None, off, 2, None, None) == 1
     p = dmk.Plan(1e-6, flags=dmk.FLAG_HOST_ONLY)
     assert L.dmk_eval_batch(p._h, None, None, off, 2, None, None) == 1
+
+
+def test_foreign_plan_handles_are_refused(dmk):
+    """Host-side fault injection: a handle that is not a live plan (here a
+    zeroed buffer standing in for a corrupt or foreign pointer) is refused
+    with DMK_ERR_INVALID_ARG by every entry point that takes a plan; a live
+    host-only plan still answers."""
+    L = dmk.lib()
+    fake = ctypes.create_string_buffer(4096)
+    h = ctypes.cast(fake, ctypes.c_void_p)
+    dp = ctypes.POINTER(ctypes.c_double)
+    n = ctypes.c_int64()
+    assert L.dmk_eval(h, None, 0, None, None, 0, None, None) == 1
+    assert L.dmk_eval_host(h, None, 0, None, None, 0, None, None) == 1
+    assert L.dmk_plan_get_params(h, ctypes.byref(dmk.PlanParams())) == 1
+    assert L.dmk_plan_get_table(h, 1, None, 0, ctypes.byref(n)) == 1
+    assert L.dmk_get_stats(h, ctypes.byref(dmk.Stats())) == 1
+    assert L.dmk_plan_destroy(h) == 1
+    assert "live plan" in L.dmk_last_error_detail().decode()
+    with dmk.Plan(1e-6, flags=dmk.FLAG_HOST_ONLY) as plan:
+        assert plan.params()["p"] == 18
