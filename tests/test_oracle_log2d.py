@@ -173,9 +173,15 @@ def test_gaussian_residual(oracle_mod, eps):
     delta = oracle_mod.params(eps=eps, splitting=oracle_mod.GAUSSIAN).delta
     for level in (0, 3):
         sg = 2.0 ** -level / delta
-        r = np.array([1e-7, 0.01, 0.2, 0.7, 1.0]) * 2.0 ** -level
+        # both branches of E_1 (series below x = 1, continued fraction above)
+        # and the tail beyond the support
+        x = np.array([1e-14, 1e-6, 0.3, 0.999, 1.0, 1.001, 2.5, 9.0, 30.0, 80.0, 200.0])
+        r = sg * np.sqrt(x)
         got = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, r)
-        assert got == pytest.approx(-0.5 * special.exp1(r ** 2 / sg ** 2), rel=1e-13, abs=1e-300)
+        # x = r^2 / sigma^2 is recomputed from r, and E_1 ~ e^{-x} / x turns
+        # its rounding into a relative change of about x * 2e-16
+        ref = -0.5 * special.exp1(x)
+        assert np.all(np.abs(got - ref) <= (1e-14 + 1e-15 * x) * np.abs(ref))
         hh = 1e-3 * sg
         for rr in (0.3 * sg, 0.8 * sg, 1.5 * sg):
             f = oracle_mod.kernel_log2d(prm, R_RESIDUAL, level, rr + hh * np.arange(-2, 3))
