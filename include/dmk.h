@@ -193,6 +193,28 @@ DMK_API int dmk_eval_grad(dmk_plan_t plan,
                           void *cuda_stream);
 
 /*
+ * dmk_adjoint_combine -- the chain-rule products of the adjoint pass:
+ * out_i = w1_i g1_i + w2_i g2_i for rows g of three doubles.  The paper gives no
+ * gradients; the adjoint follows from the symmetry of the kernel (eq.
+ * discretesum with K(x - y) = K(y - x)): for L(u), u_i = sum_j K(x_i - y_j) rho_j,
+ * the gradient with respect to source y_j is rho_j grad v(y_j), v the potential
+ * of the charges dL/du placed at the targets, and the gradient with respect to
+ * target x_i is (dL/du_i) grad u(x_i); both are such products, and where
+ * sources and targets coincide they add.  dmk_eval_grad supplies grad v and
+ * grad u.
+ *
+ *   n         rows (>= 0)
+ *   w1, g1    device pointers: n weights and n x 3 gradients (row-major); both
+ *             NULL to omit the term
+ *   w2, g2    the same for the second term
+ *   out       device pointer, n x 3 doubles, caller-allocated, overwritten (may
+ *             alias g1 or g2)
+ *   stream    asynchronous with respect to the host; runs on cuda_stream
+ */
+DMK_API int dmk_adjoint_combine(int64_t n, const double *w1, const double *g1, const double *w2,
+                                const double *g2, double *out, void *cuda_stream);
+
+/*
  * dmk_direct_noalloc -- the direct sum u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j|
  * in double precision, performing no device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate while
@@ -207,9 +229,10 @@ DMK_API int dmk_eval_grad(dmk_plan_t plan,
  *               cost O(n_src * n_tgt)
  *   scratch     a fixed 2 MiB device array inside the library, shared by all
  *               calls: calls that overlap on the device race and must be
- *               serialised by the caller.  The first call on each device looks
- *               up the array's address (no allocation); make that first call
- *               before any stream capture.
+ *               serialised by the caller.  Every call looks up the array's
+ *               address on the current device (no allocation); the first call
+ *               on a device loads the library's module there, so make it before
+ *               any stream capture.
  *   stream      asynchronous with respect to the host; runs on cuda_stream
  */
 DMK_API int dmk_direct_noalloc(const double *sources, int64_t n_src, const double *charges,

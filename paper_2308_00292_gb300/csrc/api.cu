@@ -537,6 +537,40 @@ int dmk_eval_host(dmk_plan_t plan, const double *sources, int64_t n_src, const d
 }  // extern "C"
 
 namespace {
+// out[i][d] = w1[i] g1[i][d] + w2[i] g2[i][d], either term absent when its
+// weight pointer is null
+__global__ void k_adjoint_combine(int64_t n, const double *w1, const double *g1, const double *w2,
+                                  const double *g2, double *out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * n) return;
+    const int64_t i = k / 3;
+    double v = 0.0;
+    if (w1) v += w1[i] * g1[k];
+    if (w2) v += w2[i] * g2[k];
+    out[k] = v;
+}
+}  // namespace
+
+extern "C" {
+
+int dmk_adjoint_combine(int64_t n, const double *w1, const double *g1, const double *w2, const double *g2,
+                        double *out, void *cuda_stream) {
+    g_detail.clear();
+    if (n < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
+    if (n == 0) return DMK_OK;
+    if (!out || (w1 && !g1) || (w2 && !g2)) return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
+    if (n > ((int64_t)1 << 40)) return fail(DMK_ERR_INVALID_ARG, "n too large");
+    ::dmk::launch_tick();
+    k_adjoint_combine<<<(unsigned)((3 * n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(n, w1, g1, w2, g2,
+                                                                                             out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DMK_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return DMK_OK;
+}
+
+}  // extern "C"
+
+namespace {
 // time plan evaluations at each candidate leaf capacity; keep the fastest
 template <typename Eval>
 int tune_leaf_cap(dmk_plan_s *plan, const int *candidates, int n_candidates, int reps, int *best_leaf_cap,

@@ -20,15 +20,15 @@
 // The scratch is the file-scope array g_noalloc_scratch below
 // (kSplits * kMaxTargets doubles = 2 MiB), resident on every device that loads
 // the library until the process exits.  Host code cannot use the array's name
-// as a device address, so the first call on each device (with that device
-// current) looks the address up with cudaGetSymbolAddress and caches it; that
-// first call should therefore happen before any stream capture begins.  All
-// calls share the array: each call overwrites every partial it later reads,
-// so nothing has to be cleared, but calls that overlap on the device (other
-// streams, other host threads) race on it and must be serialised by the
-// caller.
+// as a device address, so every call looks the address up on the current
+// device with cudaGetSymbolAddress (no allocation; a device reset that reloads
+// the module cannot leave a stale address behind).  The first call on a device
+// loads the module there, so it should happen before any stream capture
+// begins.  All calls share the array: each call overwrites every partial it
+// later reads, so nothing has to be cleared, but calls that overlap on the
+// device (other streams, other host threads) race on it and must be
+// serialised by the caller.
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "dmk.h"
@@ -42,10 +42,6 @@ constexpr int kThreadsN = 128;
 constexpr int kChunk = 256;
 
 __device__ __align__(256) double g_noalloc_scratch[kSplits * kMaxTargets];
-
-std::mutex g_mu;
-void *g_addr[256] = {nullptr};
-thread_local std::string g_msg;
 
 // partial sums of targets [blockIdx.x * kThreadsN, ...) over source range blockIdx.y
 __global__ void __launch_bounds__(kThreadsN) k_direct_partial(const double *src, int64_t ns, const double *q,
@@ -89,7 +85,6 @@ __global__ void k_direct_reduce(const double *part, int64_t nt, double *pot) {
 }
 
 int fail(int code, const std::string &m) {
-    g_msg = m;
     ::dmk::set_error_detail(m);
     return code;
 }
@@ -99,6 +94,7 @@ int fail(int code, const std::string &m) {
 extern "C" DMK_API int dmk_direct_noalloc(const double *sources, int64_t n_src, const double *charges,
                                           const double *targets, int64_t n_tgt, double *potentials,
                                           void *cuda_stream) {
+    ::dmk::set_error_detail("");
     if (n_src < 0 || n_tgt < 0) return fail(DMK_ERR_INVALID_ARG, "negative size");
     if (n_tgt > kMaxTargets)
         return fail(DMK_ERR_INVALID_ARG, "dmk_direct_noalloc: n_tgt exceeds its fixed scratch (16384 targets)");
@@ -106,21 +102,18 @@ extern "C" DMK_API int dmk_direct_noalloc(const double *sources, int64_t n_src, 
         return fail(DMK_ERR_INVALID_ARG, "NULL array with a nonzero size");
     if (n_tgt == 0) return DMK_OK;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return fail(DMK_ERR_CUDA, "no current CUDA device");
     }
+    // the device address of the array on the current device
     void *scratch = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return fail(DMK_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-            g_addr[dev] = p;
+        const cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+        if (e != cudaSuccess || !scratch) {
+            cudaGetLastError();
+            return fail(DMK_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
         }
-        scratch = g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     dim3 grid((unsigned)((n_tgt + kThreadsN - 1) / kThreadsN), kSplits);

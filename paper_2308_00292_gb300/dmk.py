@@ -34,7 +34,7 @@ ERRORS = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_UNSUPPORTED", 3: "D
 EXPORTED = ["dmk_plan", "dmk_eval", "dmk_eval_grad", "dmk_eval_host", "dmk_plan_destroy", "dmk_error_string",
             "dmk_last_error_detail", "dmk_plan_get_params", "dmk_plan_get_table", "dmk_get_stats", "dmk_get_tree",
             "dmk_direct_noalloc", "dmk_tune_leaf_cap", "dmk_eval_batch",
-            "dmk_tune_leaf_cap_batch", "dmk_plan_get_yukawa_table"]
+            "dmk_tune_leaf_cap_batch", "dmk_plan_get_yukawa_table", "dmk_adjoint_combine"]
 
 
 class Opts(ctypes.Structure):
@@ -98,6 +98,7 @@ def lib():
             L.dmk_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
             L.dmk_get_tree.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), i64]
             L.dmk_direct_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+            L.dmk_adjoint_combine.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.dmk_tune_leaf_cap.argtypes = [vp, vp, i64, vp, vp, i64, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float), vp]
@@ -114,6 +115,28 @@ def _check(rc):
     if rc != 0:
         detail = lib().dmk_last_error_detail().decode()
         raise DMKError(rc, detail)
+
+
+def _dev(t, name, shape, device=None):
+    """Raise ValueError unless t is a contiguous float64 CUDA tensor of the given
+    shape (None entries match any size) on `device` (when given).  The library
+    reads and writes exactly that many doubles through the raw pointer, so a
+    wrong dtype, length or device would be an out-of-bounds access."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+    if len(t.shape) != len(shape) or any(w is not None and w != g for w, g in zip(shape, t.shape)):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape),
+                                                         tuple("*" if w is None else w for w in shape)))
+    return t
 
 
 class Plan:
@@ -154,13 +177,15 @@ class Plan:
         if isinstance(sources, np.ndarray):
             return self.eval_host(sources, charges, targets, out)
         import torch
-        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
-        ns = sources.shape[0]
-        tgt = sources if targets is None else targets
+        _dev(sources, "sources", (None, self._dim))
+        dev, ns = sources.device, sources.shape[0]
+        _dev(charges, "charges", (ns,), dev)
+        tgt = sources if targets is None else _dev(targets, "targets", (None, self._dim), dev)
         nt = tgt.shape[0]
         if out is None:
-            out = torch.empty(nt, dtype=torch.float64, device=sources.device)
-        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+            out = torch.empty(nt, dtype=torch.float64, device=dev)
+        _dev(out, "out", (nt,), dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().dmk_eval(self._h, sources.data_ptr(), ns, charges.data_ptr(), tgt.data_ptr(), nt,
                               out.data_ptr(), st))
         return out
@@ -168,15 +193,18 @@ class Plan:
     def eval_grad(self, sources, charges, targets=None, out=None, gout=None, stream=None):
         """Potentials and their gradients (n_tgt x 3) at the targets, torch CUDA tensors."""
         import torch
-        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
-        ns = sources.shape[0]
-        tgt = sources if targets is None else targets
+        _dev(sources, "sources", (None, 3))
+        dev, ns = sources.device, sources.shape[0]
+        _dev(charges, "charges", (ns,), dev)
+        tgt = sources if targets is None else _dev(targets, "targets", (None, 3), dev)
         nt = tgt.shape[0]
         if out is None:
-            out = torch.empty(nt, dtype=torch.float64, device=sources.device)
+            out = torch.empty(nt, dtype=torch.float64, device=dev)
         if gout is None:
-            gout = torch.empty(nt, 3, dtype=torch.float64, device=sources.device)
-        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+            gout = torch.empty(nt, 3, dtype=torch.float64, device=dev)
+        _dev(out, "out", (nt,), dev)
+        _dev(gout, "gout", (nt, 3), dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().dmk_eval_grad(self._h, sources.data_ptr(), ns, charges.data_ptr(), tgt.data_ptr(), nt,
                                    out.data_ptr(), gout.data_ptr(), st))
         return out, gout
@@ -185,12 +213,16 @@ class Plan:
         """Potentials of independent systems: system s is points[offsets[s]:offsets[s+1]]
         (torch CUDA float64 tensors; offsets a host sequence of n_systems + 1 ints)."""
         import torch
-        assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
-        assert charges.is_cuda and charges.dtype == torch.float64 and charges.is_contiguous()
+        _dev(points, "points", (None, 3))
+        dev, n = points.device, points.shape[0]
+        _dev(charges, "charges", (n,), dev)
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if off.ndim != 1 or off.size < 1 or off[0] != 0 or off[-1] != n:
+            raise ValueError("offsets must run from 0 to the number of points (%d)" % n)
         if out is None:
-            out = torch.empty(points.shape[0], dtype=torch.float64, device=points.device)
-        st = stream if stream is not None else torch.cuda.current_stream(points.device).cuda_stream
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+        _dev(out, "out", (n,), dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().dmk_eval_batch(self._h, points.data_ptr(), charges.data_ptr(),
                                     off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
                                     out.data_ptr(), st))
@@ -200,13 +232,15 @@ class Plan:
         """Time the given problem at each candidate leaf capacity and keep the
         fastest in the plan; returns (best, {candidate: ms})."""
         import torch
-        assert sources.is_cuda and sources.dtype == torch.float64 and sources.is_contiguous()
-        tgt = sources if targets is None else targets
+        _dev(sources, "sources", (None, self._dim))
+        dev = sources.device
+        _dev(charges, "charges", (sources.shape[0],), dev)
+        tgt = sources if targets is None else _dev(targets, "targets", (None, self._dim), dev)
         cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
         ncand = 0 if candidates is None else len(candidates)
         times = (ctypes.c_float * (7 if candidates is None else max(ncand, 1)))()
         best = ctypes.c_int()
-        st = stream if stream is not None else torch.cuda.current_stream(sources.device).cuda_stream
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().dmk_tune_leaf_cap(self._h, sources.data_ptr(), sources.shape[0], charges.data_ptr(),
                                        tgt.data_ptr(), tgt.shape[0], cand, ncand, reps, ctypes.byref(best),
                                        times, st))
@@ -216,14 +250,18 @@ class Plan:
     def tune_leaf_cap_batch(self, points, charges, offsets, candidates=None, reps=0, stream=None):
         """tune_leaf_cap for a batch of systems (as in eval_batch)."""
         import torch
-        assert points.is_cuda and points.dtype == torch.float64 and points.is_contiguous()
+        _dev(points, "points", (None, 3))
+        dev, n = points.device, points.shape[0]
+        _dev(charges, "charges", (n,), dev)
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        if off.ndim != 1 or off.size < 1 or off[0] != 0 or off[-1] != n:
+            raise ValueError("offsets must run from 0 to the number of points (%d)" % n)
         cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
         ncand = 0 if candidates is None else len(candidates)
         tried = list(candidates) if candidates is not None else [64, 100, 140, 200, 280, 400, 560]
         times = (ctypes.c_float * len(tried))()
         best = ctypes.c_int()
-        st = stream if stream is not None else torch.cuda.current_stream(points.device).cuda_stream
+        st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
         _check(lib().dmk_tune_leaf_cap_batch(self._h, points.data_ptr(), charges.data_ptr(),
                                              off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
                                              cand, ncand, reps, ctypes.byref(best), times, st))
@@ -231,10 +269,15 @@ class Plan:
 
     def eval_host(self, sources, charges, targets=None, out=None, stream=0):
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, self._dim)
-        q = np.ascontiguousarray(charges, dtype=np.float64)
+        q = np.ascontiguousarray(charges, dtype=np.float64).reshape(-1)
+        if q.shape[0] != src.shape[0]:
+            raise ValueError("charges has %d entries for %d sources" % (q.shape[0], src.shape[0]))
         tgt = src if targets is None else np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, self._dim)
         if out is None:
             out = np.empty(tgt.shape[0])
+        if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+                and out.size == tgt.shape[0]):
+            raise ValueError("out must be a contiguous float64 array of %d entries" % tgt.shape[0])
         dp = ctypes.POINTER(ctypes.c_double)
         _check(lib().dmk_eval_host(self._h, src.ctypes.data_as(dp), src.shape[0], q.ctypes.data_as(dp),
                                    tgt.ctypes.data_as(dp), tgt.shape[0], out.ctypes.data_as(dp), stream))
@@ -278,6 +321,26 @@ class Plan:
         return lev, cell
 
 
+def adjoint_combine(w1, g1, w2=None, g2=None, out=None, stream=None):
+    """out_i = w1_i g1_i (+ w2_i g2_i) for n x 3 gradients, on the device
+    (dmk_adjoint_combine); the terms take float64 CUDA tensors."""
+    import torch
+    n = g1.shape[0]
+    _dev(g1, "g1", (n, 3))
+    dev = g1.device
+    _dev(w1, "w1", (n,), dev)
+    if w2 is not None:
+        _dev(w2, "w2", (n,), dev)
+        _dev(g2, "g2", (n, 3), dev)
+    if out is None:
+        out = torch.empty(n, 3, dtype=torch.float64, device=dev)
+    _dev(out, "out", (n, 3), dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    _check(lib().dmk_adjoint_combine(n, w1.data_ptr(), g1.data_ptr(), None if w2 is None else w2.data_ptr(),
+                                     None if g2 is None else g2.data_ptr(), out.data_ptr(), st))
+    return out
+
+
 def potential(plan: Plan, sources, charges, targets=None):
     """Differentiable potentials: u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j| at the
     targets (every source when targets is None), with gradients with respect
@@ -285,44 +348,54 @@ def potential(plan: Plan, sources, charges, targets=None):
 
     The backward pass is two more evaluations of the same plan: the kernel is
     symmetric, so dL/drho_j = v(y_j) and dL/dy_j = rho_j grad v(y_j) for the
-    potential v of charges dL/du at the targets, and dL/dx_i = dL/du_i grad u(x_i).
+    potential v of charges dL/du at the targets, and dL/dx_i = dL/du_i grad u(x_i);
+    the products run in the library (dmk_adjoint_combine).
+
+    float32 inputs are widened to float64 at the boundary (exactly) and their
+    gradients are returned in float32; the potentials are float64.
     """
     import torch
+
+    def f64(t):
+        return t.detach().to(torch.float64).contiguous()
 
     class _Potential(torch.autograd.Function):
         @staticmethod
         def forward(ctx, src, rho, tgt):
             same = tgt is None
-            t = src if same else tgt
+            s64, r64 = f64(src), f64(rho)
+            t64 = s64 if same else f64(tgt)
             need_pos = ctx.needs_input_grad[0] or (not same and ctx.needs_input_grad[2])
             if need_pos:
-                u, gu = plan.eval_grad(src.detach().contiguous(), rho.detach().contiguous(),
-                                       None if same else t.detach().contiguous())
+                u, gu = plan.eval_grad(s64, r64, None if same else t64)
             else:
-                u = plan.eval(src.detach().contiguous(), rho.detach().contiguous(),
-                              None if same else t.detach().contiguous())
+                u = plan.eval(s64, r64, None if same else t64)
                 gu = None
             ctx.same = same
-            ctx.save_for_backward(src, rho, t, gu if gu is not None else torch.empty(0, device=src.device))
+            ctx.dtypes = (src.dtype, rho.dtype, None if same else tgt.dtype)
+            ctx.save_for_backward(s64, r64, t64, gu if gu is not None else torch.empty(0, device=src.device))
             ctx.has_gu = gu is not None
             return u
 
         @staticmethod
         def backward(ctx, g):
-            src, rho, t, gu = ctx.saved_tensors
-            g = g.contiguous()
+            s64, r64, t64, gu = ctx.saved_tensors
+            g = g.detach().to(torch.float64).contiguous()
             # the potential of charges g at the targets, and its gradient, at the sources
             if ctx.same:
-                v, gv = plan.eval_grad(src.detach().contiguous(), g)
+                v, gv = plan.eval_grad(s64, g)
             else:
-                v, gv = plan.eval_grad(t.detach().contiguous(), g, src.detach().contiguous())
-            d_rho = v if ctx.needs_input_grad[1] else None
-            d_src = rho[:, None] * gv if ctx.needs_input_grad[0] else None
-            d_tgt = None
-            if ctx.same and d_src is not None and ctx.has_gu:
-                d_src = d_src + g[:, None] * gu
-            elif not ctx.same and ctx.needs_input_grad[2] and ctx.has_gu:
-                d_tgt = g[:, None] * gu
+                v, gv = plan.eval_grad(t64, g, s64)
+            d_rho = v.to(ctx.dtypes[1]) if ctx.needs_input_grad[1] else None
+            d_src = d_tgt = None
+            if ctx.needs_input_grad[0]:
+                if ctx.same and ctx.has_gu:
+                    d_src = adjoint_combine(r64, gv, g, gu)
+                else:
+                    d_src = adjoint_combine(r64, gv)
+                d_src = d_src.to(ctx.dtypes[0])
+            if not ctx.same and ctx.needs_input_grad[2] and ctx.has_gu:
+                d_tgt = adjoint_combine(g, gu).to(ctx.dtypes[2])
             return d_src, d_rho, d_tgt
 
     return _Potential.apply(sources, charges, targets)

@@ -119,3 +119,56 @@ def test_autograd_central_differences(dmk):
     ad = gx[pts, dims]
     assert np.linalg.norm(np.array(fd) - ad) < 1e-4 * np.linalg.norm(ad)
     plan.close()
+
+
+def test_autograd_float32_inputs(dmk, oracle_mod):
+    """The differentiable workload takes FP32 positions and charges: they are
+    widened exactly at the boundary, the gradients come back in FP32 and match
+    the direct sums of the widened inputs (mixed path, eps 1e-6)."""
+    x32 = inputs.uniform_cube(4000, seed=421)[0].astype(np.float32)
+    q32 = inputs.uniform_cube(4000, seed=422)[1].astype(np.float32)
+    x, q = x32.astype(np.float64), q32.astype(np.float64)
+    w = np.random.default_rng(423).standard_normal(len(x))
+    plan = dmk.Plan(1e-6, precision=dmk.DMK_MIXED, leaf_cap=80)
+    xt = torch.from_numpy(x32).cuda().requires_grad_(True)
+    qt = torch.from_numpy(q32).cuda().requires_grad_(True)
+    u = dmk.potential(plan, xt, qt)
+    assert u.dtype == torch.float64
+    (torch.from_numpy(w).cuda() * u).sum().backward()
+    assert xt.grad.dtype == torch.float32 and qt.grad.dtype == torch.float32
+    assert rel(u.detach().cpu().numpy(), oracle_mod.direct(x, q)) < 1e-6
+    assert rel(qt.grad.cpu().numpy().astype(np.float64), oracle_mod.direct(x, w)) < 2e-6
+    gx_ref = w[:, None] * oracle_mod.direct_grad(x, q) + q[:, None] * oracle_mod.direct_grad(x, w)
+    assert rel(xt.grad.cpu().numpy().astype(np.float64), gx_ref) < 3e-6
+    plan.close()
+
+
+def test_autograd_separate_targets(dmk, oracle_mod):
+    """Separate targets: dL/dy_j = rho_j grad v(y_j) at the sources and
+    dL/dx_i = w_i grad u(x_i) at the targets, both formed by
+    dmk_adjoint_combine (FP64, eps 1e-9)."""
+    y, q = inputs.clustered(3000, seed=431, nclusters=3)
+    x, _ = inputs.uniform_cube(800, seed=432)
+    w = np.random.default_rng(433).standard_normal(len(x))
+    plan = dmk.Plan(1e-9, precision=0, leaf_cap=80)
+    yt = torch.from_numpy(y).cuda().requires_grad_(True)
+    qt = torch.from_numpy(q).cuda().requires_grad_(True)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    (torch.from_numpy(w).cuda() * dmk.potential(plan, yt, qt, xt)).sum().backward()
+    assert rel(qt.grad.cpu().numpy(), oracle_mod.direct(x, w, y)) < 3e-9
+    assert rel(yt.grad.cpu().numpy(), q[:, None] * oracle_mod.direct_grad(x, w, y)) < 3e-9
+    assert rel(xt.grad.cpu().numpy(), w[:, None] * oracle_mod.direct_grad(y, q, x)) < 3e-9
+    plan.close()
+
+
+def test_adjoint_combine_rows(dmk):
+    """out_i = w1_i g1_i + w2_i g2_i, and each term alone, bit for bit."""
+    rng = np.random.default_rng(441)
+    n = 1001
+    w1, w2 = rng.standard_normal(n), rng.standard_normal(n)
+    g1, g2 = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+    T = [torch.from_numpy(a).cuda() for a in (w1, g1, w2, g2)]
+    both = dmk.adjoint_combine(*T).cpu().numpy()
+    one = dmk.adjoint_combine(T[0], T[1]).cpu().numpy()
+    assert np.array_equal(one, w1[:, None] * g1)
+    assert np.allclose(both, w1[:, None] * g1 + w2[:, None] * g2, rtol=1e-15, atol=1e-15)
