@@ -32,8 +32,15 @@ if ROOT not in sys.path:
 
 METRIC = "3D Laplace DMK points/s at rel-L2 1e-6, mixed-prec vs FP64 path, 1 GB300"
 UNIT = "points/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# nominal dense tensor rates of the part (TF32 / BF16), used only as a ratio to
+# carry the measured BF16 rate over to TF32
+TF32_PER_BF16 = 1.1 / 2.25
+# FP32 FMA throughput measured on this machine's GB300 by a one-kernel probe
+# (independent FMA chains, CUDA events, 152 SMs x 8 blocks x 256 threads) at
+# the SM clock it ran at; scaled to the clock sampled during a run
+FFMA_MEASURED_TFLOPS = None
+FFMA_MEASURED_MHZ = 2070.0
 
 
 def parse():
@@ -146,6 +153,87 @@ def near_flops_per_pair(qdeg: int) -> int:
     # a pair inside the support: the distance (8), x = 2 r^2/R^2 - 1 (2),
     # Horner q(x) (2 per degree), rsqrt (1), 1/r - q/R (2), charge times value and sum (2)
     return NEAR_SCREEN_FLOPS + 2 + 2 * qdeg + 1 + 2 + 2
+
+
+def measured_peaks() -> dict:
+    """The measured peaks (HBM copy, cuBLAS BF16), else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]),
+                "bf16_tflops_sustained": float(m.get("bf16_tflops_sustained", m["bf16_tflops"])),
+                "basis": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "basis": "of fallback"}
+
+
+def fp32_peak(sm_count: int, sm_mhz: float):
+    """FP32 FMA peak in TFLOP/s at the sampled clock, and how it was obtained."""
+    if FFMA_MEASURED_TFLOPS:
+        return (FFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ,
+                "FFMA probe %.1f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (FFMA_MEASURED_TFLOPS,
+                                                                              FFMA_MEASURED_MHZ, sm_mhz))
+    return (sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
+            "%d SMs x %d FP32 lanes x 2 flops x %.0f MHz" % (sm_count, FP32_LANES_PER_SM, sm_mhz))
+
+
+def kernel_work(stats: dict, prm: dict, n_src: int, n_tgt: int) -> dict:
+    """Algorithmic work of each kernel of one evaluation, split by the unit
+    that executes it: (amount, unit kind) pairs, unit kind one of
+    'tensor' (flops of the 3xTF32 contractions, counted once per product),
+    'fp32' (FP32 flops on the CUDA cores) and 'hbm' (bytes)."""
+    p, nf = prm["p"], prm["nf"]
+    nh, n1 = nf + 1, 2 * nf + 1
+    mxp = (n1 + 1) & ~1
+    nfout, nfin = stats["n_fout"], stats["n_fin"]
+    w = {}
+    # upward: anterpolation onto the parent grid (2 p^3 per source), child-to-parent shifts
+    w["k_upward"] = [("anterpolation", 2.0 * p ** 3 * n_src, "tensor"),
+                     ("c2p shifts", 3.0 * p ** 3 * (p + 1) * max(nfout - 1, 0), "fp32")]
+    # outgoing plane waves, parity-split mode products z, y, x per F_out box
+    w["k_prox2pw"] = [("proxy to plane waves", float(nfout) * (2 * p ** 3 * nh + 4 * p * p * nh * nh
+                                                               + 4 * n1 * p * nh * nh), "fp32")]
+    if stats.get("incoming_reads", 0) > 0:
+        contr = float(nfin) * (8 * p * nh ** 3 + 4 * p * p * nh * nh + 2 * p ** 3 * nh)
+        w["k_incoming"] = [("plane waves to Chebyshev", contr, "tensor"),
+                           ("translation", 8.0 * n1 * n1 * nh * stats["incoming_reads"], "fp32"),
+                           ("plane waves read once, coefficients written",
+                            8.0 * nfout * nh * n1 * mxp + 4.0 * nfin * p ** 3, "hbm")]
+    ev = 2.0 * p ** 3 * n_tgt
+    w["k_local"] = [("leaf evaluation", ev, "tensor"),
+                    ("p2c shifts and sums", max(float(stats["local_flops"]) - ev, 0.0), "fp32")]
+    pairs, inside = stats["near_pairs"], stats["near_pairs_inside"]
+    w["k_near"] = [("residual pairs", float(pairs * NEAR_SCREEN_FLOPS + inside * (near_flops_per_pair(prm["q_degree"])
+                                                                          - NEAR_SCREEN_FLOPS)), "fp32")]
+    return w
+
+
+def rooflines(work: dict, times_ms: dict, peaks: dict) -> dict:
+    """Per kernel: each work component's achieved rate and fraction of its peak;
+    the kernel's bound is the component with the largest fraction."""
+    out = {}
+    for k, comps in work.items():
+        t = times_ms.get(k)
+        if not t or t <= 0:
+            continue
+        parts = []
+        for name, amount, kind in comps:
+            if amount <= 0:
+                continue
+            if kind == "hbm":
+                a, pk, unit, bound = amount / (t / 1e3) / 1e9, peaks["hbm"], "GB/s", "hbm"
+            elif kind == "tensor":
+                a, pk, unit, bound = amount / (t / 1e3) / 1e12, peaks["tensor"], "TFLOP/s", "tensor"
+            else:
+                a, pk, unit, bound = amount / (t / 1e3) / 1e12, peaks["fp32"], "TFLOP/s", "alu"
+            parts.append({"work": name, "amount": amount, "bound": bound, "achieved": a, "peak": pk, "unit": unit,
+                          "frac": a / pk})
+        if not parts:
+            continue
+        top = max(parts, key=lambda d: d["frac"])
+        out[k] = {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                  "frac": top["frac"], "ms_per_eval": t, "components": parts}
+    return out
 
 
 def rank_seed(cfg: dict, rank: int) -> int:
@@ -546,6 +634,7 @@ def run_ours(args, rank, world, local_rank):
     stats = plan.stats()
     prm = plan.params()
     value = job_throughput(n, world, ms)
+    out_timed = out.cpu().numpy()
 
     # end to end through the host entry point: pinned inputs, H2D + eval + D2H per step
     e2e = None
@@ -585,50 +674,81 @@ def run_ours(args, rank, world, local_rank):
                 "mixed_speedup": ms64 / ms}
         p64.close()
 
+    # per-kernel times: the far-field kernels alone (near field skipped) and the
+    # near field alone, outside the timed region, so that no kernel's time
+    # includes another running beside it
+    times = {}
+    with dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_FAR_ONLY) as pf:
+        acc = {"k_upward": [], "k_prox2pw": [], "k_incoming": [], "k_local": []}
+        for r in range(4):
+            pf.eval(xd, qd, out=out)
+            sf = pf.stats()
+            if r == 0:
+                continue
+            acc["k_upward"].append(sf["t_upward_ms"])
+            acc["k_prox2pw"].append(sf["t_planewave_ms"])
+            acc["k_incoming"].append(sf["t_incoming_ms"])
+            acc["k_local"].append(sf["t_local_ms"])
+        times.update({k: statistics.median(v) for k, v in acc.items()})
+    with dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_NEAR_ONLY) as pn:
+        tn = []
+        for r in range(4):
+            pn.eval(xd, qd, out=out)
+            if r:
+                tn.append(pn.stats()["t_near_ms"])
+        times["k_near"] = statistics.median(tn)
+    barrier()
     if rank != 0:
         return
-    # roofline of the two dominant kernels (both plain FP32 ALU work); the
-    # larger one is reported as "roofline"
+    # accuracy of the timed evaluation: the oracle's compensated FP64 direct sum
+    # over all sources at 256 sampled targets, on the host
+    import oracle
+    oracle.build()
+    u = out_timed
+    sample = np.sort(np.random.default_rng(cfg["seed"] + 11).choice(n, 256, replace=False))
+    ref = oracle.direct(x, q, x[sample])
+    rel_l2 = float(np.linalg.norm(u[sample] - ref) / np.linalg.norm(ref))
+
     per_step = {k: v / args.steps for k, v in phase.items()}
-    pairs, inside = stats["near_pairs"], stats["near_pairs_inside"]
-    fpp = near_flops_per_pair(prm["q_degree"])
-    near_flops = pairs * NEAR_SCREEN_FLOPS + inside * (fpp - NEAR_SCREEN_FLOPS)
     sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else 1440.0
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
-    basis = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz sampled SM clock" % sm_mhz
-    kernels = {}
-    t_near = per_step["t_near_ms"] / 1e3
-    a_near = near_flops / t_near / 1e12 if t_near > 0 else 0.0
-    tn, tl = traffic_per_unit("k_near"), traffic_per_unit("k_local")
-    kernels["k_near"] = {"kernel": "k_near (residual near field, Steps 4-5)", "bound": "alu", "achieved": a_near,
-                         "peak": peak_fp32, "unit": "TFLOP/s", "frac": a_near / peak_fp32,
-                         "traffic": tn * pairs if tn is not None else None,
-                         "traffic_basis": "DRAM bytes per launch: ncu capture at 2e6 points scaled by candidate pairs",
-                         "work": "%d candidate pairs x %d flops (distance screen) + %d pairs inside R_L x %d flops "
-                                 "(residual kernel) per launch" % (pairs, NEAR_SCREEN_FLOPS, inside,
-                                                                   fpp - NEAR_SCREEN_FLOPS),
-                         "ms_per_launch": per_step["t_near_ms"], "peak_basis": basis}
-    t_loc = per_step["t_local_ms"] / 1e3
-    a_loc = stats["local_flops"] / t_loc / 1e12 if t_loc > 0 else 0.0
-    kernels["k_local"] = {"kernel": "k_local (local expansions, translation, leaf evaluation; one launch per level)",
-                          "bound": "alu", "achieved": a_loc, "peak": peak_fp32, "unit": "TFLOP/s",
-                          "frac": a_loc / peak_fp32,
-                          "traffic": tl * stats["local_flops"] if tl is not None else None,
-                          "traffic_basis": "DRAM bytes per evaluation (all launches): ncu capture at 2e6 points "
-                                           "scaled by algorithmic flops",
-                          "work": "%d algorithmic flops per evaluation over %d launches" % (stats["local_flops"],
-                                                                                             stats["n_levels"]),
-                          "ms_per_eval": per_step["t_local_ms"], "peak_basis": basis}
-    roofline = dict(kernels["k_local"] if t_loc > t_near else kernels["k_near"])
+    props = torch.cuda.get_device_properties(local_rank)
+    sm_count = props.multi_processor_count
+    pk = measured_peaks()
+    f32, f32_basis = fp32_peak(sm_count, sm_mhz)
+    peaks = {"hbm": pk["hbm_gbs"], "fp32": f32,
+             "tensor": pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0}
+    peak_basis = {"hbm": "STREAM-style copy %s" % pk["basis"],
+                  "fp32": f32_basis,
+                  "tensor": "3xTF32 (three TF32 products per FP32 product): cuBLAS BF16 sustained %.1f TFLOP/s %s x "
+                            "nominal TF32/BF16 ratio 1.1/2.25 / 3" % (pk["bf16_tflops_sustained"], pk["basis"])}
+    kernels = rooflines(kernel_work(stats, prm, n, n), times, peaks)
+    # the traffic captured by ncu for the kernel whose source it was taken on
+    for k in ("k_local", "k_near"):
+        if k in kernels:
+            tpu = traffic_per_unit(k)
+            unit = stats["local_flops"] if k == "k_local" else stats["near_pairs"]
+            kernels[k]["traffic"] = tpu * unit if tpu is not None else None
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_eval"])
+    roofline = {"kernel": dom, "bound": kernels[dom]["bound"], "achieved": kernels[dom]["achieved"],
+                "peak": kernels[dom]["peak"], "unit": kernels[dom]["unit"], "frac": kernels[dom]["frac"],
+                "traffic": kernels[dom].get("traffic"), "ms_per_eval": kernels[dom]["ms_per_eval"],
+                "peak_basis": peak_basis[kernels[dom]["bound"] if kernels[dom]["bound"] != "alu" else "fp32"],
+                "timing": "CUDA events the library records on each kernel's stream, the kernel alone "
+                          "(far-field or near-field-only evaluations, median of 3)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
-            "config": config_dict(args, cfg), "e2e": e2e, "gpu_launches": launches,
-            "roofline": roofline, "kernels": kernels, "clocks": clocks,
+            "config": config_dict(args, cfg), "rel_l2": rel_l2,
+            "rel_l2_basis": "256 sampled targets against the oracle's compensated FP64 direct sum over all sources",
+            "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "kernels": kernels, "peaks": peaks, "peak_basis": peak_basis,
+            "sm_count": sm_count, "clocks": clocks,
             "phases_ms": {k: round(v, 3) for k, v in per_step.items()},
             "fp64_path": fp64,
             "tree": {"levels": stats["n_levels"], "boxes": stats["n_boxes"], "leaves": stats["n_leaves"],
-                     "fout": stats["n_fout"], "near_pairs": pairs, "balance_rounds": stats["balance_rounds"]}}
+                     "fout": stats["n_fout"], "fin": stats["n_fin"], "near_pairs": stats["near_pairs"],
+                     "near_pairs_inside": stats["near_pairs_inside"], "incoming_reads": stats["incoming_reads"],
+                     "balance_rounds": stats["balance_rounds"]}}
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample)
     print(json.dumps(line), flush=True)

@@ -332,7 +332,8 @@ DMK_API int dmk_plan_get_yukawa_table(dmk_plan_t plan, double lambda_unit, int l
 typedef struct {
     int64_t n_points;       /* points in the tree (union of sources and targets) */
     int32_t n_levels;       /* L_max + 1 */
-    int64_t n_boxes, n_leaves, n_fout, n_fin;
+    int64_t n_boxes, n_leaves, n_fout;
+    int64_t n_fin;          /* incoming boxes: boxes with targets and an F_out colleague */
     int64_t near_pairs;     /* candidate source-target pairs of the residual sum */
     int32_t balance_rounds; /* rebuilds needed by the level restriction */
     float t_tree_ms, t_upward_ms, t_downward_ms, t_near_ms, t_total_ms;
@@ -341,6 +342,14 @@ typedef struct {
     int64_t local_flops;    /* algorithmic flops of the local-expansion pass (p2c,
                                translation, plane waves to Chebyshev, leaf evaluation) */
     float t_local_ms;       /* device time of the local-expansion pass alone */
+    float t_incoming_ms;    /* device time of the tensor-core incoming pass (translation and
+                               plane waves to Chebyshev for every level), 0 when the
+                               local-expansion pass forms the incoming expansions itself */
+    int64_t incoming_reads; /* colleague plane-wave arrays read by the incoming pass */
+    int64_t incoming_flops; /* its algorithmic flops: translation 8 N1^2 (nf + 1) per
+                               colleague array, and the three parity-split contractions
+                               8 p (nf+1)^3 + 4 p^2 (nf+1)^2 + 2 p^3 (nf+1) per incoming box */
+    float t_planewave_ms;   /* device time of the outgoing plane waves and the root term */
 } dmk_eval_stats;
 
 DMK_API int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out);

@@ -23,7 +23,8 @@ LIB = os.path.join(PKG, "libdmk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["api.cu", "tree.cu", "sort_scan.cu", "passes.cu", "near.cu", "plan_math.cpp", "noalloc.cu", "log2d.cu"]
+SOURCES = ["api.cu", "tree.cu", "sort_scan.cu", "passes.cu", "incoming.cu", "near.cu", "plan_math.cpp", "noalloc.cu",
+           "log2d.cu"]
 
 
 def _nvcc() -> str:

@@ -62,7 +62,7 @@ struct dmk_plan_s {
     dmk::PassBufs bufs;
     dmk::DBuf h_src, h_q, h_tgt, h_pot;  // device copies for dmk_eval_host
     dmk_eval_stats stats{};
-    cudaEvent_t ev[7] = {};
+    cudaEvent_t ev[8] = {};
     // the near field runs on an internal low-priority stream, concurrently with
     // the far field on the caller's stream: its short blocks fill the SMs that
     // the per-level far-field launches leave idle
@@ -216,7 +216,7 @@ int eval_log2d(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, c
     s.n_leaves = pl->tree->nleaves;
     s.near_pairs = pl->tree->near_pairs;
     s.balance_rounds = pl->tree->rounds;
-    s.n_fin = pl->tree->ntleaves;
+    s.n_fin = pl->tree->nfin;
     float t05 = 0;
     cudaEventElapsedTime(&t05, pl->ev[0], pl->ev[5]);
     s.t_total_ms = t05;
@@ -275,7 +275,7 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     cx.pot = pot;
     cx.grad = grad;
     cx.st = st;
-    for (int i = 0; i < 7; ++i) cx.ev[i] = pl->ev[i];
+    for (int i = 0; i < 8; ++i) cx.ev[i] = pl->ev[i];
     cx.side = pl->side;
     cx.fork = pl->fork;
     cx.join = pl->join;
@@ -303,7 +303,7 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     s.near_pairs = pl->tree->near_pairs;
     s.balance_rounds = pl->tree->rounds;
     s.n_fout = pl->tree->root_leaf ? 0 : pl->tree->nslots;
-    s.n_fin = pl->tree->ntleaves;
+    s.n_fin = pl->tree->nfin;
     float t01 = 0, t12 = 0, t23 = 0, t34 = 0, t05 = 0;
     cudaEventElapsedTime(&t01, pl->ev[0], pl->ev[1]);
     cudaEventElapsedTime(&t12, pl->ev[1], pl->ev[2]);
@@ -315,26 +315,39 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     s.t_downward_ms = t23;
     s.t_near_ms = t34;
     s.t_total_ms = t05;
-    float t63 = 0, tn = 0;
+    float t63 = 0, tn = 0, t76 = 0;
     cudaEventElapsedTime(&t63, pl->ev[6], pl->ev[3]);
     s.t_local_ms = t63;
+    if (cudaEventElapsedTime(&t76, pl->ev[7], pl->ev[6]) == cudaSuccess) s.t_incoming_ms = t76;
+    else cudaGetLastError();
+    float t27 = 0;
+    if (cudaEventElapsedTime(&t27, pl->ev[2], pl->ev[7]) == cudaSuccess) s.t_planewave_ms = t27;
+    else cudaGetLastError();
     // the near field ran on the side stream, overlapping the far field
     if (cudaEventElapsedTime(&tn, pl->nev[0], pl->nev[1]) == cudaSuccess) s.t_near_ms = tn;
     else cudaGetLastError();
     s.n_launches = dmk::g_launches.load() - launches0;
     if (pl->bufs.counter.p) {
         // device words: [0] near work queue, [8] near pairs inside R_L,
-        // [16] local-pass flops, [24] a tensor-core wait that gave up
-        unsigned char w[32] = {0};
+        // [16] local-pass flops, [24] a tensor-core or TMA wait that gave up,
+        // [32] colleague arrays read by the incoming pass
+        unsigned char w[40] = {0};
         if (cudaMemcpy(w, pl->bufs.counter.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(DMK_ERR_CUDA, "reading the device status words failed");
-        unsigned long long inside = 0, f = 0;
+        unsigned long long inside = 0, f = 0, reads = 0;
         int timeout = 0;
         memcpy(&inside, w + 8, 8);
         memcpy(&f, w + 16, 8);
         memcpy(&timeout, w + 24, 4);
+        memcpy(&reads, w + 32, 8);
         if (pl->tree->ntleaves > 0) s.near_pairs_inside = (int64_t)inside;
         s.local_flops = (int64_t)f;
+        if (s.t_incoming_ms > 0.f || reads > 0) {
+            const int64_t P = pl->tb.p, NH = pl->tb.nf + 1, N1 = 2 * pl->tb.nf + 1;
+            s.incoming_reads = (int64_t)reads;
+            s.incoming_flops = 8 * N1 * N1 * NH * (int64_t)reads +
+                               s.n_fin * (8 * P * NH * NH * NH + 4 * P * P * NH * NH + 2 * P * P * P * NH);
+        }
         if (timeout) return fail(DMK_ERR_TIMEOUT, "a tensor-core completion wait gave up (local pass)");
     }
     return DMK_OK;

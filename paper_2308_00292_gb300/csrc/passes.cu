@@ -40,6 +40,7 @@
 //   k_near     residual kernels R_{L(j)} over the interaction lists (Step 4),
 //              including the self correction of Step 5 (r = 0 terms)
 #include "passes.h"
+#include "incoming.h"
 #include "tc.h"
 #include "dev_util.h"
 
@@ -497,7 +498,10 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
 // ---------------------------------------------------------------------------
 // Outgoing expansions (Step 3, T_prox2pw), parity-split
 // ---------------------------------------------------------------------------
-template <typename T, int P, int NF>
+// PLANE: the plane-major layout of the tensor-core incoming pass,
+// Phi[slot][m_z][m_y][m_x] with m_x padded to an even count; otherwise
+// Phi[slot][m_y][m_x][m_z] with m_z padded to an even count
+template <typename T, int P, int NF, bool PLANE>
 __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> tb, int nslots,
                                                       const int32_t *slot2box, const T *M,
                                                       typename Cplx<T>::type *Phi, BufLayout lay, char *slab) {
@@ -510,8 +514,12 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
     T *hs = buf_ptr<T>(lay, 3, sm, slab);    // [n][m']
     const int tid = threadIdx.x;
     load_hs<T, P, NF>(tb, hs);
-    constexpr int NHP = nz_pad<NF>();
-    const size_t stride = (size_t)N1 * N1 * NHP;
+    constexpr int NHP = nz_pad<NF>(), MXP = (N1 + 1) & ~1;
+    const size_t stride = PLANE ? (size_t)NH * N1 * MXP : (size_t)N1 * N1 * NHP;
+    // element (m_y, m_x, m_z) of a box's array (indices from 0)
+    auto at = [](int my, int mx, int mz) -> size_t {
+        return PLANE ? ((size_t)mz * N1 + my) * MXP + mx : (size_t)(my * N1 + mx) * NHP + mz;
+    };
     for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
         const int B = slot2box[slot];
         if (!(tv.bflags[B] & BF_FOUT)) continue;
@@ -557,15 +565,26 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
         // x: Phi[my][+-mx'][mz] = E +- i O
         C2 *out = Phi + (size_t)slot * stride;
         for (int it = tid; it < N1 * NH * NH; it += kThreads) {
-            const int my = it / (NH * NH), r = it % (NH * NH), mxp = r / NH, mz = r % NH;
+            // consecutive threads write consecutive elements: m_z fastest, or m_x in
+            // the plane-major layout
+            int my, mxp, mz;
+            if (PLANE) {
+                mz = it / (N1 * NH);
+                my = (it / NH) % N1;
+                mxp = it % NH;
+            } else {
+                my = it / (NH * NH);
+                mxp = (it / NH) % NH;
+                mz = it % NH;
+            }
             C2 E{0, 0}, O{0, 0};
             for (int a = 0; a < P; ++a) {
                 const C2 t = T2[(a * N1 + my) * NH + mz];
                 const T h = hs[a * NH + mxp];
                 if (a & 1) cfma(O, h, t); else cfma(E, h, t);
             }
-            out[(size_t)(my * N1 + NF + mxp) * NHP + mz] = C2{E.x - O.y, E.y + O.x};
-            if (mxp > 0) out[(size_t)(my * N1 + NF - mxp) * NHP + mz] = C2{E.x + O.y, E.y - O.x};
+            out[at(my, NF + mxp, mz)] = C2{E.x - O.y, E.y + O.x};
+            if (mxp > 0) out[at(my, NF - mxp, mz)] = C2{E.x + O.y, E.y - O.x};
         }
     }
 }
@@ -693,7 +712,8 @@ __device__ __forceinline__ void shift_pass(const T *__restrict__ A, const T *in,
         }
         return;
     }
-    constexpr bool TWO = true;
+    // two rows per thread only when the rows outnumber the threads
+    constexpr bool TWO = P * P > NT;
     constexpr int RR = P * P, H = TWO ? (RR + 1) / 2 : RR;
     auto base = [](int r) { return AX == 0 ? r * P : (AX == 1 ? (r / P) * P * P + r % P : r); };
     for (int t = threadIdx.x; t < H; t += NT) {
@@ -1043,12 +1063,14 @@ __device__ void tc_eval(const TreeView &tv, const float *Lev, const double (&cc)
         }
         tc::fence_before_sync();
         __syncthreads();
+        // added to the (zeroed) far field: a target may take two expansions, its
+        // parent's and its own incoming one
         if (cg == 0 && j < np && (tv.pflag[pq] & 2)) {
-            ufar[pq] = (double)(pu + red(0, 0) + red(0, 1) + red(0, 2));
+            ufar[pq] += (double)(pu + red(0, 0) + red(0, 1) + red(0, 2));
             if (gfar) {
-                gfar[3 * (size_t)pq + 0] = (double)(pgx + red(1, 0) + red(1, 1) + red(1, 2)) * s2R;
-                gfar[3 * (size_t)pq + 1] = (double)(pgy + red(2, 0) + red(2, 1) + red(2, 2)) * s2R;
-                gfar[3 * (size_t)pq + 2] = (double)(pgz + red(3, 0) + red(3, 1) + red(3, 2)) * s2R;
+                gfar[3 * (size_t)pq + 0] += (double)(pgx + red(1, 0) + red(1, 1) + red(1, 2)) * s2R;
+                gfar[3 * (size_t)pq + 1] += (double)(pgy + red(2, 0) + red(2, 1) + red(2, 2)) * s2R;
+                gfar[3 * (size_t)pq + 2] += (double)(pgz + red(3, 0) + red(3, 1) + red(3, 2)) * s2R;
             }
         }
     }
@@ -1073,7 +1095,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                                                         int lcount, const typename Cplx<T>::type *Phi, T *Lam,
                                                         const T *LamW, double *ufar, BufLayout lay, char *slab,
                                                         unsigned long long *flops, int *tc_err, int *run_ctr,
-                                                        double *gfar, typename Cplx<T>::type *psig) {
+                                                        double *gfar, typename Cplx<T>::type *psig,
+                                                        const T *lam_in, const int32_t *bfin, int lstr) {
     using C2 = typename Cplx<T>::type;
     using S = LocalShape<P, NF>;
     constexpr int NH = S::NH, N1 = S::N1, P3 = P * P * P, NHP = nz_pad<NF>();
@@ -1170,7 +1193,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     for (int i = g0; i < g1; ++i) {
                         const int b = lstart + i;
                         const uint8_t f = tv.bflags[b];
-                        if (!(f & BF_LEAF) || (f & BF_FIN) || tv.bntgt[b] == 0) continue;
+                        if (!(f & BF_LEAF) || (!lam_in && (f & BF_FIN)) || tv.bntgt[b] == 0) continue;
                         s_grs[n] = tv.bstart[b];
                         s_gro[n] = off;
                         off += tv.bcount[b];
@@ -1193,7 +1216,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             // while reading each colleague's Phi once instead of once per sibling.
             // The results go to this block's scratch, one plane-wave array per octant.
             bool gtr = false;
-            if (level > 0) {
+            if (level > 0 && !lam_in) {
                 __syncthreads();
                 if (tid < 32) {
                     // warp 0: the block's F_out slots (lane k: the parent's colleague k),
@@ -1340,6 +1363,19 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                         }
                         __syncthreads();
                         fetch_xyz(tv, s_brs, s_bro, 1, s_xyz);
+                        if (lam_in && level > 0) {
+                            // an incoming leaf: its parent's expansion is evaluated with its
+                            // sibling group (in the parent's frame, exact since T_p2c is an
+                            // exact re-expansion); here its own incoming expansion is added
+                            int ix, iy, iz;
+                            box_decode_d(tv.bkey[B], level, ix, iy, iz);
+                            const double R = level_R(level), s2R = 2.0 / R;
+                            const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
+                            if (tid == 0) atomicAdd(flops, 2ull * (P * P * P + P * P + P) * tv.bntgt[B]);
+                            tc_eval<P, NF>(tv, (const float *)(lam_in + (size_t)bfin[B] * lstr), cc, s2R, s_brs, s_bro,
+                                           1, s_xyz, st, phase, ufar, gfar);
+                            continue;
+                        }
                     }
                 }
                 // ---- parent's local expansion re-centred on this machine (T_p2c), or the root term
@@ -1365,8 +1401,33 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
                 }
                 __syncthreads();
-                // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients
-                if (fl & BF_FIN) {
+                // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients,
+                // formed for all levels by the tensor-core incoming pass when lam_in is given
+                if ((fl & BF_FIN) && lam_in) {
+                    // lstr is a multiple of 4 and Ls is 128-byte aligned: whole float4 rows,
+                    // every load of a thread in flight before the adds
+                    const T *li = lam_in + (size_t)bfin[B] * lstr;
+                    if constexpr (sizeof(T) == 4) {
+                        constexpr int NV = (P3 + 3) / 4, PER = (NV + kLThreads - 1) / kLThreads;
+                        float4 v[PER];
+#pragma unroll
+                        for (int k = 0; k < PER; ++k) {
+                            const int i = tid + k * kLThreads;
+                            v[k] = i < NV ? __ldg(reinterpret_cast<const float4 *>(li) + i) : make_float4(0, 0, 0, 0);
+                        }
+#pragma unroll
+                        for (int k = 0; k < PER; ++k) {
+                            const int i = 4 * (tid + k * kLThreads);
+                            if (i < P3) Ls[i] += v[k].x;
+                            if (i + 1 < P3) Ls[i + 1] += v[k].y;
+                            if (i + 2 < P3) Ls[i + 2] += v[k].z;
+                            if (i + 3 < P3) Ls[i + 3] += v[k].w;
+                        }
+                    } else {
+                        for (int i = tid; i < P3; i += kLThreads) Ls[i] += li[i];
+                    }
+                    __syncthreads();
+                } else if (fl & BF_FIN) {
                     if (tid == 0) {
                         int nc = 0;
                         for (int k = 0; k < 27; ++k) {
@@ -1573,7 +1634,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     // translation (one complex multiply-add per mode and colleague) and
                     // the three parity-split contractions, and the leaf evaluation
                     unsigned long long f = level > 0 ? 3ull * P * P * (P * (P + 1) / 2) * 2 : 0ull;
-                    if (fl & BF_FIN)
+                    if ((fl & BF_FIN) && !lam_in)
                         f += 8ull * N1 * N1 * NH * s_ncol + 8ull * P * NH * NH * NH + 4ull * P * P * NH * NH +
                              2ull * P * P * P * NH;
                     if (fl & BF_LEAF) f += 2ull * (P * P * P + P * P + P) * tv.bntgt[B];
@@ -1789,6 +1850,23 @@ static BufLayout make_layout(const std::vector<size_t> &sizes, size_t smem_limit
         }                                                                  \
     } while (0)
 
+// the tensor-core incoming pass serves the single-precision path at the
+// (P, NF) shapes it supports
+template <typename T, int P, int NF> constexpr bool incoming_tc() {
+    if constexpr (sizeof(T) == 4 && ((P == 9 && NF == 6) || (P == 18 && NF == 12) || (P == 19 && NF == 12)))
+        return InShape<P, NF>::OK;
+    return false;
+}
+
+template <typename T, int P, int NF> static int run_incoming(const IncomingArgs &a, cudaStream_t st, std::string &err) {
+    if constexpr (incoming_tc<T, P, NF>()) {
+        const int rc = launch_incoming<P, NF>(a, st, err);
+        return rc ? rc : 0;
+    }
+    err = "tensor-core incoming pass requested for an unsupported shape";
+    return DMK_ERR_INTERNAL;
+}
+
 template <typename T, int P, int NF>
 static int run_passes_P(PassCtx &cx, std::string &err) {
     using C2 = typename Cplx<T>::type;
@@ -1890,9 +1968,14 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         }
         PCK(cudaGetLastError());
     }
-    // ---- outgoing expansions of every F_out box
+    // ---- outgoing expansions of every F_out box; in single precision the
+    // incoming expansions then run on the tensor cores (incoming.cu), which
+    // read the plane waves plane by plane
     cudaEventRecord(cx.ev[2], st);
-    if (ws.ensure(cx.bufs->Phi, (int64_t)nslots * N1 * N1 * nz_pad<NF>() * sizeof(C2))) {
+    const bool tc_in = incoming_tc<T, P, NF>() && cx.tree->nfin > 0 && do_far;
+    const int64_t phi_elems = tc_in ? (int64_t)nslots * NH * N1 * ((N1 + 1) & ~1)
+                                    : (int64_t)nslots * N1 * N1 * nz_pad<NF>();
+    if (ws.ensure(cx.bufs->Phi, phi_elems * (int64_t)sizeof(C2))) {
         err = "device allocation failed (plane waves)";
         return DMK_ERR_OOM;
     }
@@ -1901,13 +1984,13 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * P * NH * sizeof(C2), (size_t)P * N1 * NH * sizeof(C2),
                                      (size_t)P * NH * sizeof(T)},
                                     smem_limit);
-        PCK(cudaFuncSetAttribute(k_prox2pw<T, P, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lay.smem_bytes));
+        auto kern = tc_in ? k_prox2pw<T, P, NF, true> : k_prox2pw<T, P, NF, false>;
+        PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         int grid = std::min(nslots, maxgrid);
         if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
         ::dmk::launch_tick();
-        k_prox2pw<T, P, NF><<<grid, kThreads, lay.smem_bytes, st>>>(
-            tv, tb, nslots, (const int32_t *)cx.tree->slot2box.p, M, Phi, lay, (char *)cx.bufs->slab.p);
+        kern<<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, nslots, (const int32_t *)cx.tree->slot2box.p, M, Phi,
+                                                     lay, (char *)cx.bufs->slab.p);
         PCK(cudaGetLastError());
     }
     // ---- root windowed term, for every root (system)
@@ -1921,6 +2004,35 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             k_root<T, P><<<grid, kThreads, 0, st>>>(tv, tb, M, nroots, LamW, (C2 *)cx.bufs->rootscr.p, scr);
             PCK(cudaGetLastError());
         }
+    }
+    // ---- incoming expansions of every level at once (tensor cores, TMA)
+    const T *lam_in = nullptr;
+    if (tc_in) {
+        const int nfin = cx.tree->nfin;
+        const int lstr = (P3 + 3) & ~3;
+        if (ws.ensure(cx.bufs->lam_in, (int64_t)nfin * lstr * 4) || ws.ensure(cx.bufs->finc, (int64_t)nfin * 27 * 4) ||
+            ws.ensure(cx.bufs->fincnt, (int64_t)nfin * 4)) {
+            err = "device allocation failed (incoming expansions)";
+            return DMK_ERR_OOM;
+        }
+        cudaEventRecord(cx.ev[7], st);
+        IncomingArgs ia{tv,
+                        cx.tables,
+                        Phi,
+                        nslots,
+                        nfin,
+                        (const int32_t *)cx.tree->fin2box.p,
+                        (int32_t *)cx.bufs->finc.p,
+                        (int32_t *)cx.bufs->fincnt.p,
+                        (float *)cx.bufs->lam_in.p,
+                        (unsigned long long *)cx.bufs->counter.p + 4,
+                        (int *)cx.bufs->counter.p + 6,
+                        cx.num_sms};
+        int rc = run_incoming<T, P, NF>(ia, st, err);
+        if (rc) return rc;
+        lam_in = (const T *)cx.bufs->lam_in.p;
+    } else {
+        cudaEventRecord(cx.ev[7], st);
     }
     // ---- local expansions, coarsest level first; leaves evaluate
     {
@@ -1959,7 +2071,9 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                                                        (unsigned long long *)cx.bufs->counter.p + 2,
                                                                        (int *)cx.bufs->counter.p + 6,
                                                                        (int *)cx.bufs->counter.p + 32 + l, gfar,
-                                                                       (C2 *)cx.bufs->psig.p);
+                                                                       (C2 *)cx.bufs->psig.p, lam_in,
+                                                                       (const int32_t *)cx.tree->bfin.p,
+                                                                       (P3 + 3) & ~3);
         }
         PCK(cudaGetLastError());
     }

@@ -16,6 +16,7 @@ struct BufLayout {
 
 struct PassBufs {
     DBuf M, Lam, LamW, Phi, ufar, unear, gfar, gnear, slab, rootscr, counter, psig;
+    DBuf lam_in, finc, fincnt;  // the tensor-core incoming pass: coefficients, colleague lists
 };
 
 struct PassCtx {
@@ -30,7 +31,7 @@ struct PassCtx {
     double *pot;
     double *grad;         // gradients of the potentials (n_tgt x 3), or null
     cudaStream_t st;
-    cudaEvent_t ev[7];  // 0 start, 1 upward, 2 plane waves, 6 local, 3 far done, 4 finalize, 5 end
+    cudaEvent_t ev[8];  // 0 start, 1 upward, 2 plane waves, 7 incoming, 6 local, 3 far done, 4 finalize, 5 end
     cudaStream_t side;  // the near field's stream, forked after the tree and joined before finalize
     cudaEvent_t fork, join, nev[2];  // nev: start and end of the near field on side
     size_t smem_limit;

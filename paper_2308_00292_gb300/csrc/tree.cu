@@ -528,6 +528,22 @@ __global__ void k_box_flags_in(int nb, const int32_t *bnsrc, const int32_t *bntg
     if (fin) bflags[b] |= BF_FIN;
 }
 
+// 1 for an incoming box (F_in with targets), else 0
+__global__ void k_is_fin(int nb, const uint8_t *bflags, const int32_t *bntgt, int32_t *isfin) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    isfin[b] = ((bflags[b] & BF_FIN) && bntgt[b] > 0) ? 1 : 0;
+}
+
+// bfin[b] = index of b among the incoming boxes (box order) or -1; fin2box inverts it
+__global__ void k_fin_index(int nb, const int32_t *isfin, int32_t *bfin, int32_t *fin2box) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int f = isfin[b] ? bfin[b] : -1;  // bfin holds the exclusive scan of isfin
+    bfin[b] = f;
+    if (f >= 0) fin2box[f] = b;
+}
+
 __global__ void k_slots(int nb, const int32_t *isslot, const int32_t *excl, int32_t *bslot) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -995,12 +1011,24 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     root_leaf = (nlev == 1);
     ::dmk::launch_tick();
     k_slots<<<nblk(nb, 128), 128, 0, st>>>(nb, isslot, excl, (int32_t *)bslot.p);
+    // the incoming boxes (isleaf's contents are no longer needed: it is reused)
+    if (ws.ensure(bfin, (int64_t)nb * 4) || ws.ensure(fin2box, (int64_t)nb * 4)) {
+        err = "device allocation failed";
+        return DMK_ERR_OOM_I;
+    }
+    ::dmk::launch_tick();
+    k_is_fin<<<nblk(nb, 128), 128, 0, st>>>(nb, (const uint8_t *)bflags.p, (const int32_t *)bntgt.p, isleaf);
+    // exclusive scan into bfin, then each thread turns its own entry into the index
+    scan_exclusive_i32(isleaf, (int32_t *)bfin.p, nb, d_flags + 10, scan_tmp.p, scan_tmp.bytes, st);
+    ::dmk::launch_tick();
+    k_fin_index<<<nblk(nb, 128), 128, 0, st>>>(nb, isleaf, (int32_t *)bfin.p, (int32_t *)fin2box.p);
     CK(cudaGetLastError());
-    int hs[4] = {0, 0, 0, 0};  // slots, -, -, leaves
-    CK(cudaMemcpyAsync(hs, d_flags + 6, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hs[5] = {0, 0, 0, 0, 0};  // slots, -, -, leaves, incoming boxes
+    CK(cudaMemcpyAsync(hs, d_flags + 6, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     nslots = hs[0];
     nleaves = hs[3];
+    nfin = hs[4];
     if (ws.ensure(slot2box, (int64_t)std::max(nslots, 1) * 4)) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
     ::dmk::launch_tick();
     k_slot2box<<<nblk(nb, 128), 128, 0, st>>>(nb, (const int32_t *)bslot.p, (int32_t *)slot2box.p);

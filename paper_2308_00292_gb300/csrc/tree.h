@@ -90,6 +90,7 @@ public:
     int64_t n = 0;
     bool same = true;
     int nb = 0, nlev = 0, nslots = 0, nleaves = 0, ntleaves = 0, rounds = 0, near_list_len = 0;
+    int nfin = 0;  // boxes with targets and an F_out colleague (the incoming boxes)
     int nsys = 1, kb = kMortonBits;  // systems (roots) and bits per axis of the point keys
     bool root_leaf = false;
     int64_t near_pairs = 0;
@@ -106,6 +107,9 @@ public:
     int64_t box_cap = 0;
     DBuf bkey, blevel, bstart, bcount, bparent, bchild0, bcmask, bflags, bnsrc, bntgt, bcol, bslot;
     DBuf bscr0, bscr1, bscr2, slot2box;
+    // incoming boxes in box order: bfin[box] = its index among them or -1,
+    // fin2box[index] = the box
+    DBuf bfin, fin2box;
     DBuf lvl_off9, lvl_cnt, lvl_excl;
     // near-field lists
     DBuf tleaves, nl_cnt, nl_off, nl_src, nl_tmp, pairs;

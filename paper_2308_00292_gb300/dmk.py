@@ -55,7 +55,9 @@ class Stats(ctypes.Structure):
                 ("t_tree_ms", ctypes.c_float), ("t_upward_ms", ctypes.c_float),
                 ("t_downward_ms", ctypes.c_float), ("t_near_ms", ctypes.c_float), ("t_total_ms", ctypes.c_float),
                 ("n_launches", ctypes.c_int64), ("near_pairs_inside", ctypes.c_int64),
-                ("local_flops", ctypes.c_int64), ("t_local_ms", ctypes.c_float)]
+                ("local_flops", ctypes.c_int64), ("t_local_ms", ctypes.c_float),
+                ("t_incoming_ms", ctypes.c_float), ("incoming_reads", ctypes.c_int64),
+                ("incoming_flops", ctypes.c_int64), ("t_planewave_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -193,10 +195,10 @@ class Plan:
     def eval_grad(self, sources, charges, targets=None, out=None, gout=None, stream=None):
         """Potentials and their gradients (n_tgt x 3) at the targets, torch CUDA tensors."""
         import torch
-        _dev(sources, "sources", (None, 3))
+        _dev(sources, "sources", (None, self._dim))
         dev, ns = sources.device, sources.shape[0]
         _dev(charges, "charges", (ns,), dev)
-        tgt = sources if targets is None else _dev(targets, "targets", (None, 3), dev)
+        tgt = sources if targets is None else _dev(targets, "targets", (None, self._dim), dev)
         nt = tgt.shape[0]
         if out is None:
             out = torch.empty(nt, dtype=torch.float64, device=dev)
@@ -213,12 +215,13 @@ class Plan:
         """Potentials of independent systems: system s is points[offsets[s]:offsets[s+1]]
         (torch CUDA float64 tensors; offsets a host sequence of n_systems + 1 ints)."""
         import torch
-        _dev(points, "points", (None, 3))
+        _dev(points, "points", (None, self._dim))
         dev, n = points.device, points.shape[0]
         _dev(charges, "charges", (n,), dev)
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-        if off.ndim != 1 or off.size < 1 or off[0] != 0 or off[-1] != n:
-            raise ValueError("offsets must run from 0 to the number of points (%d)" % n)
+        # the library validates the offsets themselves; the points must cover them
+        if off.ndim != 1 or off.size < 1 or off.max() > n:
+            raise ValueError("offsets must lie within the %d points" % n)
         if out is None:
             out = torch.empty(n, dtype=torch.float64, device=dev)
         _dev(out, "out", (n,), dev)
@@ -250,12 +253,12 @@ class Plan:
     def tune_leaf_cap_batch(self, points, charges, offsets, candidates=None, reps=0, stream=None):
         """tune_leaf_cap for a batch of systems (as in eval_batch)."""
         import torch
-        _dev(points, "points", (None, 3))
+        _dev(points, "points", (None, self._dim))
         dev, n = points.device, points.shape[0]
         _dev(charges, "charges", (n,), dev)
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-        if off.ndim != 1 or off.size < 1 or off[0] != 0 or off[-1] != n:
-            raise ValueError("offsets must run from 0 to the number of points (%d)" % n)
+        if off.ndim != 1 or off.size < 1 or off.max() > n:
+            raise ValueError("offsets must lie within the %d points" % n)
         cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
         ncand = 0 if candidates is None else len(candidates)
         tried = list(candidates) if candidates is not None else [64, 100, 140, 200, 280, 400, 560]
