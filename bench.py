@@ -39,8 +39,10 @@ TF32_PER_BF16 = 1.1 / 2.25
 # FP32 FMA throughput measured on this machine's GB300 by a one-kernel probe
 # (independent FMA chains, CUDA events, 152 SMs x 8 blocks x 256 threads) at
 # the SM clock it ran at; scaled to the clock sampled during a run
-FFMA_MEASURED_TFLOPS = None
+FFMA_MEASURED_TFLOPS = 78.52
 FFMA_MEASURED_MHZ = 2070.0
+# FP64 FMA throughput from the same probe with double chains
+DFMA_MEASURED_TFLOPS = 1.26
 
 
 def parse():
@@ -187,8 +189,11 @@ def kernel_work(stats: dict, prm: dict, n_src: int, n_tgt: int) -> dict:
     mxp = (n1 + 1) & ~1
     nfout, nfin = stats["n_fout"], stats["n_fin"]
     w = {}
-    # upward: anterpolation onto the parent grid (2 p^3 per source), child-to-parent shifts
-    w["k_upward"] = [("anterpolation", 2.0 * p ** 3 * n_src, "tensor"),
+    # upward: anterpolation onto the parent grid (2 p^3 per source), child-to-parent shifts;
+    # the single-precision anterpolation is register-tiled FFMA while one CTA's threads
+    # cover p x ceil(p/2) (a, b) pairs, else 3xTF32 on the tensor cores
+    anterp_unit = "fp32" if p * ((p + 1) // 2) <= ANTERP_FFMA_THREADS else "tensor"
+    w["k_upward"] = [("anterpolation", 2.0 * p ** 3 * n_src, anterp_unit),
                      ("c2p shifts", 3.0 * p ** 3 * (p + 1) * max(nfout - 1, 0), "fp32")]
     # outgoing plane waves, parity-split mode products z, y, x per F_out box
     w["k_prox2pw"] = [("proxy to plane waves", float(nfout) * (2 * p ** 3 * nh + 4 * p * p * nh * nh
@@ -224,6 +229,8 @@ def rooflines(work: dict, times_ms: dict, peaks: dict) -> dict:
                 a, pk, unit, bound = amount / (t / 1e3) / 1e9, peaks["hbm"], "GB/s", "hbm"
             elif kind == "tensor":
                 a, pk, unit, bound = amount / (t / 1e3) / 1e12, peaks["tensor"], "TFLOP/s", "tensor"
+            elif kind == "fp64":
+                a, pk, unit, bound = amount / (t / 1e3) / 1e12, peaks["fp64"], "TFLOP/s", "alu"
             else:
                 a, pk, unit, bound = amount / (t / 1e3) / 1e12, peaks["fp32"], "TFLOP/s", "alu"
             parts.append({"work": name, "amount": amount, "bound": bound, "achieved": a, "peak": pk, "unit": unit,
@@ -297,9 +304,15 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def config_precision(cfg: dict) -> str:
+    """The path a workload runs on: single precision with FP64 accumulation
+    wherever it can reach its eps (eps >= 1e-7), else FP64."""
+    return cfg.get("precision", "mixed" if cfg["eps"] >= 1e-7 else "fp64")
+
+
 def config_dict(args, cfg):
     return {"workload": args.config, "n_points": cfg["n"], "distribution": cfg["gen"], "eps": cfg["eps"],
-            "leaf_cap": cfg["leaf_cap"], "precision": "mixed", "seed": cfg["seed"],
+            "leaf_cap": cfg["leaf_cap"], "precision": config_precision(cfg), "seed": cfg["seed"],
             "l2": "inputs larger than L2 (%.0f MB of points and charges per rank)" % (cfg["n"] * 32 / 1e6),
             "parallelism": "independent replica per GPU" if args.gpus > 1 else "single GPU"}
 
@@ -609,7 +622,9 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    plan = dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"])
+    mixed = config_precision(cfg) == "mixed"
+    prec = dmk.DMK_MIXED if mixed else dmk.DMK_FP64
+    plan = dmk.Plan(cfg["eps"], precision=prec, leaf_cap=cfg["leaf_cap"])
     for _ in range(args.warmup):
         plan.eval(xd, qd, out=out)
     barrier()
@@ -656,7 +671,7 @@ def run_ours(args, rank, world, local_rank):
 
     # the FP64 path on the same input
     fp64 = None
-    if not args.skip_fp64:
+    if not args.skip_fp64 and mixed:
         p64 = dmk.Plan(cfg["eps"], precision=dmk.DMK_FP64, leaf_cap=cfg["leaf_cap"])
         p64.eval(xd, qd, out=out)
         barrier()
@@ -678,8 +693,8 @@ def run_ours(args, rank, world, local_rank):
     # near field alone, outside the timed region, so that no kernel's time
     # includes another running beside it
     times = {}
-    with dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_FAR_ONLY) as pf:
-        acc = {"k_upward": [], "k_prox2pw": [], "k_incoming": [], "k_local": []}
+    with dmk.Plan(cfg["eps"], precision=prec, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_FAR_ONLY) as pf:
+        acc = {"k_upward": [], "k_prox2pw": [], "k_incoming": [], "k_local": [], "tree": []}
         for r in range(4):
             pf.eval(xd, qd, out=out)
             sf = pf.stats()
@@ -689,8 +704,13 @@ def run_ours(args, rank, world, local_rank):
             acc["k_prox2pw"].append(sf["t_planewave_ms"])
             acc["k_incoming"].append(sf["t_incoming_ms"])
             acc["k_local"].append(sf["t_local_ms"])
+            acc["tree"].append(sf["t_tree_ms"])
         times.update({k: statistics.median(v) for k, v in acc.items()})
-    with dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_NEAR_ONLY) as pn:
+    t_tree = times.pop("tree")
+    if not mixed:
+        # the FP64 path forms the incoming expansions inside the local pass
+        times.pop("k_incoming", None)
+    with dmk.Plan(cfg["eps"], precision=prec, leaf_cap=cfg["leaf_cap"], flags=dmk.FLAG_NEAR_ONLY) as pn:
         tn = []
         for r in range(4):
             pn.eval(xd, qd, out=out)
@@ -721,7 +741,14 @@ def run_ours(args, rank, world, local_rank):
                   "fp32": f32_basis,
                   "tensor": "3xTF32 (three TF32 products per FP32 product): cuBLAS BF16 sustained %.1f TFLOP/s %s x "
                             "nominal TF32/BF16 ratio 1.1/2.25 / 3" % (pk["bf16_tflops_sustained"], pk["basis"])}
-    kernels = rooflines(kernel_work(stats, prm, n, n), times, peaks)
+    work = kernel_work(stats, prm, n, n)
+    if not mixed:
+        # the FP64 path runs every contraction in double precision on the CUDA cores
+        peaks["fp64"] = DFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
+        peak_basis["fp64"] = "DFMA probe %.2f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (
+            DFMA_MEASURED_TFLOPS, FFMA_MEASURED_MHZ, sm_mhz)
+        work = {k: [(nm, a, "hbm" if kd == "hbm" else "fp64") for nm, a, kd in v] for k, v in work.items()}
+    kernels = rooflines(work, times, peaks)
     # the traffic captured by ncu for the kernel whose source it was taken on
     for k in ("k_local", "k_near"):
         if k in kernels:
@@ -732,13 +759,20 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"kernel": dom, "bound": kernels[dom]["bound"], "achieved": kernels[dom]["achieved"],
                 "peak": kernels[dom]["peak"], "unit": kernels[dom]["unit"], "frac": kernels[dom]["frac"],
                 "traffic": kernels[dom].get("traffic"), "ms_per_eval": kernels[dom]["ms_per_eval"],
-                "peak_basis": peak_basis[kernels[dom]["bound"] if kernels[dom]["bound"] != "alu" else "fp32"],
+                "peak_basis": peak_basis[kernels[dom]["bound"] if kernels[dom]["bound"] != "alu"
+                                         else ("fp32" if mixed else "fp64")],
                 "timing": "CUDA events the library records on each kernel's stream, the kernel alone "
                           "(far-field or near-field-only evaluations, median of 3)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64acc" if mixed else "f64", "data": "synthetic",
             "config": config_dict(args, cfg), "rel_l2": rel_l2,
+            # the phases of the paper's timing breakdown (Table 2): tree, plane-wave
+            # (Fourier) work, residual near field (direct), each kernel alone
+            "paper_phases_ms": {"t_tree": t_tree,
+                                "t_fourier": times.get("k_prox2pw", 0.0) + times.get("k_incoming", 0.0),
+                                "t_direct": times.get("k_near", 0.0),
+                                "t_other_far": times.get("k_upward", 0.0) + times.get("k_local", 0.0)},
             "rel_l2_basis": "256 sampled targets against the oracle's compensated FP64 direct sum over all sources",
             "e2e": e2e, "gpu_launches": launches,
             "roofline": roofline, "kernels": kernels, "peaks": peaks, "peak_basis": peak_basis,

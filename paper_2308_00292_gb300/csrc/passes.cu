@@ -57,10 +57,24 @@ template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
 
 
-template <typename U>
+// A buffer of a kernel's layout.  With SM (the single-precision kernels, whose
+// buffers the host checks to lie in shared memory) the pointer is formed from
+// the shared array alone, so that the compiler emits shared-memory accesses
+// instead of generic ones.
+template <typename U, bool SM = false>
 __device__ __forceinline__ U *buf_ptr(const BufLayout &lay, int i, char *sm, char *slab) {
+    if constexpr (SM) return reinterpret_cast<U *>(sm + lay.off[i]);
     return lay.in_smem[i] ? reinterpret_cast<U *>(sm + lay.off[i])
                           : reinterpret_cast<U *>(slab + (size_t)blockIdx.x * lay.slab_bytes + lay.off[i]);
+}
+
+// the kernels whose buffers must all lie in shared memory
+template <typename T, int P> constexpr bool all_smem() { return sizeof(T) == 4 && P <= 20; }
+
+static bool layout_in_smem(const BufLayout &lay) {
+    for (int i = 0; i < lay.n; ++i)
+        if (!lay.in_smem[i]) return false;
+    return true;
 }
 
 // the stored half spectrum pads m_z to an even count so that two adjacent
@@ -329,16 +343,172 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
     if (!ok && (tid & 31) == 0) atomicExch(tc_err, 1);
 }
 
+// FP32 anterpolation with register tiles: thread (a, b pair) adds, point by
+// point, rho T_a(x) T_b(y) T_c(z) to its 2 P moments M[a][b][c], M[a][b + 1][c]
+// held in registers for a chunk of kCH points (one FMA per moment and point,
+// with rho T_a(x) T_b(y) formed once per (a, b)), two points per step; the
+// chunk's sums are then added to acc in shared memory, so every moment is a sum
+// of chunk sums (rounding like a per-chunk flush).  The T rows of a chunk are
+// staged by 3 kCH threads, whose coordinates are loaded one chunk ahead.  acc
+// must be zero on entry; called by the whole CTA.
+template <int P>
+__device__ __forceinline__ void anterpolate_ffma(const TreeView &tv, const double (&cc)[3], double s2R, const int *lstart,
+                                 const int *lpre, int ntot, float *stg, float *acc) {
+    constexpr int PS = UpShape<P>::PS, NBP = (P + 1) / 2, NIT = P * NBP;
+    static_assert(NIT <= kThreads, "one (a, b pair) item per thread");
+    const int tid = threadIdx.x;
+    const bool has = tid < NIT;
+    const int a = has ? tid / NBP : 0, b0 = has ? 2 * (tid % NBP) : 0;
+    const bool has1 = has && b0 + 1 < P;
+    // the coordinate (and charge) that thread tid < 3 kCH stages for point p
+    auto fetch = [&](int p, double &u, double &w) {
+        const int ax = tid / kCH;
+        u = 0.0;
+        w = 1.0;
+        if (p < ntot) {
+            int seg = 0;
+            while (seg < 7 && lpre[seg + 1] <= p) ++seg;
+            const int kk = lstart[seg] + (p - lpre[seg]);
+            u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
+            if (ax == 0) w = tv.q[kk];
+        }
+    };
+    double un = 0.0, wn = 1.0;
+    if (tid < 3 * kCH) fetch(tid % kCH, un, wn);
+    for (int p0 = 0; p0 < ntot; p0 += kCH) {
+        const int np = min(kCH, ntot - p0);
+        if (tid < 3 * kCH) {
+            // T_0 .. T_{P-1} of one coordinate of one point, times the charge for x
+            const int ax = tid / kCH, j = tid % kCH;
+            const double u = un, wq = wn;
+            if (p0 + kCH < ntot) fetch(p0 + kCH + j, un, wn);
+            float *o = stg + (ax * kCH + j) * PS;
+            if (j < np) {
+                const float xi = (float)((u - cc[ax]) * s2R);
+                const float w = (float)wq;
+                float t0 = 1.f, t1 = xi;
+                o[0] = w;
+                if (P > 1) o[1] = w * xi;
+#pragma unroll
+                for (int n = 2; n < P; ++n) {
+                    const float t2 = 2.f * xi * t1 - t0;
+                    o[n] = w * t2;
+                    t0 = t1;
+                    t1 = t2;
+                }
+            } else {
+#pragma unroll
+                for (int n = 0; n < PS; ++n) o[n] = 0.f;
+            }
+        }
+        __syncthreads();
+        if (has) {
+            float c0[P], c1[P];
+#pragma unroll
+            for (int c = 0; c < P; ++c) c0[c] = c1[c] = 0.f;
+            // two points per step (a zero row pads an odd count: staged as zeros)
+            for (int j = 0; j < np; j += 2) {
+                const float *X0 = stg + j * PS, *Y0 = stg + (kCH + j) * PS;
+                const float4 *Z0 = reinterpret_cast<const float4 *>(stg + (2 * kCH + j) * PS);
+                const float4 *Z1 = reinterpret_cast<const float4 *>(stg + (2 * kCH + j + 1) * PS);
+                const float xa0 = X0[a], xa1 = X0[PS + a];
+                const float s00 = xa0 * Y0[b0], s01 = has1 ? xa0 * Y0[b0 + 1] : 0.f;
+                const float s10 = xa1 * Y0[PS + b0], s11 = has1 ? xa1 * Y0[PS + b0 + 1] : 0.f;
+#pragma unroll
+                for (int c4 = 0; c4 < PS / 4; ++c4) {
+                    const float4 z = Z0[c4], y = Z1[c4];
+                    const float za[4] = {z.x, z.y, z.z, z.w}, zb[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = 4 * c4 + q;
+                        if (c < P) {
+                            c0[c] = fmaf(s10, zb[q], fmaf(s00, za[q], c0[c]));
+                            c1[c] = fmaf(s11, zb[q], fmaf(s01, za[q], c1[c]));
+                        }
+                    }
+                }
+            }
+            float *r0 = acc + (a * P + b0) * P;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                r0[c] += c0[c];
+                if (has1) r0[P + c] += c1[c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Single-precision anterpolation of every box of every level in one launch
+// (its boxes depend on no other level): persistent CTAs take the expansion
+// slots from a work counter, so that no level waits for its heaviest box; the
+// moments of the leaf children's sources go to M[slot].  The child-to-parent
+// shifts follow level by level (k_upward with c2p_only).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_anterp(TreeView tv, int nslots, const int32_t *slot2box, float *M,
+                                                     int *ctr) {
+    extern __shared__ __align__(128) char sm[];
+    using U = UpShape<P>;
+    constexpr int P3 = P * P * P;
+    float *acc = reinterpret_cast<float *>(sm);
+    float *stg = acc + (P3 + 31) / 32 * 32;  // [3][kCH][PS]
+    __shared__ int s_item, s_lstart[8], s_lpre[9];
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int slot = s_item;
+        if (slot >= nslots) break;
+        const int B = slot2box[slot];
+        const bool selfleaf = (tv.bflags[B] & BF_LEAF) != 0;
+        // a leaf's sources go to its parent's grid; a root that is a leaf
+        // anterpolates onto its own grid (for the windowed term W_0)
+        if ((selfleaf && tv.blevel[B] != 0) || tv.bnsrc[B] == 0) continue;
+        const int l = tv.blevel[B];
+        int ix, iy, iz;
+        box_decode_d(tv.bkey[B], l, ix, iy, iz);
+        const double R = level_R(l), s2R = 2.0 / R;
+        const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
+        for (int i = tid; i < P3; i += kThreads) acc[i] = 0.f;
+        const int c0 = tv.bchild0[B];
+        const unsigned cm = selfleaf ? 1u : tv.bcmask[B];
+        // point ranges of the leaf children (with sources), streamed as one sequence
+        if (tid == 0) {
+            int k = 0, nl = 0, tot = 0;
+            for (int oc = 0; oc < 8; ++oc) {
+                if (!(cm & (1u << oc))) continue;
+                const int D = selfleaf ? B : c0 + k;
+                ++k;
+                if (tv.bnsrc[D] == 0 || !(selfleaf || (tv.bflags[D] & BF_LEAF))) continue;
+                s_lstart[nl] = tv.bstart[D];
+                s_lpre[nl] = tot;
+                tot += tv.bcount[D];
+                ++nl;
+            }
+            for (int q = nl; q < 9; ++q) s_lpre[q] = tot;
+        }
+        __syncthreads();
+        const int ntot = s_lpre[8];
+        if (ntot > 0) anterpolate_ffma<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, stg, acc);
+        float *Mo = M + (size_t)slot * P3;
+        for (int i = tid; i < P3; i += kThreads) Mo[i] = acc[i];
+        __syncthreads();
+    }
+    (void)sizeof(U);
+}
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> tb, int lstart, int lcount, T *M,
-                                                     BufLayout lay, char *slab, int *tc_err) {
+                                                     BufLayout lay, char *slab, int *tc_err, int c2p_only) {
     extern __shared__ __align__(128) char sm[];
     using U = UpShape<P>;
     constexpr int P3 = P * P * P;
     constexpr int PS = U::PS, YS = U::YS;
     constexpr int NAG = (P + 3) / 4, NBCG = (P * P + 3) / 4;
-    // single precision anterpolates on the tensor cores (3xTF32)
-    constexpr bool kTC = sizeof(T) == 4 && U::TC_OK;
+    // single precision anterpolates with register-tiled FP32 FMAs (the orders of
+    // the single-precision plans); the tensor-core form stays for others
+    constexpr bool kFF = sizeof(T) == 4 && P * ((P + 1) / 2) <= kThreads;
+    constexpr bool kTC = !kFF && sizeof(T) == 4 && U::TC_OK;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     uint32_t phase = 0;
@@ -349,11 +519,11 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         __syncthreads();
         tc::fence_after_sync();
     }
-    T *acc = buf_ptr<T>(lay, 0, sm, slab);
+    T *acc = buf_ptr<T, all_smem<T, P>()>(lay, 0, sm, slab);
     // scratch shared by the two phases: staging + Y for the sources of leaf
     // children, then two P^3 buffers for the moment shifts of non-leaf children
-    T *scr = buf_ptr<T>(lay, 1, sm, slab);
-    T *As = buf_ptr<T>(lay, 2, sm, slab);   // shift matrices A_{-1}, A_{+1}
+    T *scr = buf_ptr<T, all_smem<T, P>()>(lay, 1, sm, slab);
+    T *As = buf_ptr<T, all_smem<T, P>()>(lay, 2, sm, slab);   // shift matrices A_{-1}, A_{+1}
     T *stg = scr;                           // [3][kCH][PS]
     T *Y = scr + 3 * kCH * PS;              // [kCH][YS]
     T *b0 = scr, *b1 = scr + P3;
@@ -367,7 +537,22 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         // anterpolates onto its own grid (for the windowed term W_0)
         if (selfleaf && tv.blevel[B] != 0) continue;
         if (tv.bnsrc[B] == 0) continue;
-        for (int i = tid; i < P3; i += kThreads) acc[i] = (T)0;
+        if (c2p_only) {
+            // the moments of the leaf children are in M already (k_anterp): only
+            // boxes with non-leaf children that hold sources have work here
+            bool any = false;
+            const unsigned cmk = selfleaf ? 0u : tv.bcmask[B];
+            for (int oc = 0, k = 0; oc < 8; ++oc) {
+                if (!(cmk & (1u << oc))) continue;
+                const int D = tv.bchild0[B] + k++;
+                any = any || (tv.bnsrc[D] > 0 && !(tv.bflags[D] & BF_LEAF));
+            }
+            if (!any) continue;
+            const T *Mi = M + (size_t)tv.bslot[B] * P3;
+            for (int i = tid; i < P3; i += kThreads) acc[i] = Mi[i];
+        } else {
+            for (int i = tid; i < P3; i += kThreads) acc[i] = (T)0;
+        }
         const int l = tv.blevel[B];
         int ix, iy, iz;
         box_decode_d(tv.bkey[B], l, ix, iy, iz);
@@ -392,8 +577,12 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
             for (int q = nl; q < 9; ++q) s_lpre[q] = tot;
         }
         __syncthreads();
-        const int ntot = s_lpre[8];
-        if constexpr (kTC) {
+        const int ntot = c2p_only ? 0 : s_lpre[8];
+        if constexpr (kFF) {
+            if (ntot > 0)
+                anterpolate_ffma<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, reinterpret_cast<float *>(stg),
+                                    reinterpret_cast<float *>(acc));
+        } else if constexpr (kTC) {
             if (ntot > 0) anterpolate_tc<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, scr, s_tmem, &s_bar, phase, acc,
                                              tc_err);
         } else {
@@ -508,10 +697,10 @@ __global__ void __launch_bounds__(kThreads) k_prox2pw(TreeView tv, DevTables<T> 
     using C2 = typename Cplx<T>::type;
     extern __shared__ __align__(128) char sm[];
     constexpr int P3 = P * P * P, NH = NF + 1, N1 = 2 * NF + 1;
-    T *Mb = buf_ptr<T>(lay, 0, sm, slab);
-    C2 *T1 = buf_ptr<C2>(lay, 1, sm, slab);  // [a][b][mz]
-    C2 *T2 = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my + NF][mz]
-    T *hs = buf_ptr<T>(lay, 3, sm, slab);    // [n][m']
+    T *Mb = buf_ptr<T, all_smem<T, P>()>(lay, 0, sm, slab);
+    C2 *T1 = buf_ptr<C2, all_smem<T, P>()>(lay, 1, sm, slab);  // [a][b][mz]
+    C2 *T2 = buf_ptr<C2, all_smem<T, P>()>(lay, 2, sm, slab);  // [a][my + NF][mz]
+    T *hs = buf_ptr<T, all_smem<T, P>()>(lay, 3, sm, slab);    // [n][m']
     const int tid = threadIdx.x;
     load_hs<T, P, NF>(tb, hs);
     constexpr int NHP = nz_pad<NF>(), MXP = (N1 + 1) & ~1;
@@ -1103,15 +1292,15 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     // single precision evaluates the leaves on the tensor cores (3xTF32)
     constexpr bool kTC = sizeof(T) == 4 && S::TC_OK;
     extern __shared__ __align__(128) char sm[];
-    T *Ls = buf_ptr<T>(lay, 0, sm, slab);
-    C2 *PsE = buf_ptr<C2>(lay, 1, sm, slab);  // [my + NF][mx'][mz]; PsO follows
+    T *Ls = buf_ptr<T, all_smem<T, P>()>(lay, 0, sm, slab);
+    C2 *PsE = buf_ptr<C2, all_smem<T, P>()>(lay, 1, sm, slab);  // [my + NF][mx'][mz]; PsO follows
     C2 *PsO = PsE + N1 * NH * NHP;
     C2 *T2 = PsE;                              // [a][b][mz], reuses the Psi buffers
-    C2 *T1e = buf_ptr<C2>(lay, 2, sm, slab);  // [a][my'][mz]; T1o follows
+    C2 *T1e = buf_ptr<C2, all_smem<T, P>()>(lay, 2, sm, slab);  // [a][my'][mz]; T1o follows
     C2 *T1o = T1e + P * NH * NH;
-    T *hs = buf_ptr<T>(lay, 3, sm, slab);
-    T *ev = buf_ptr<T>(lay, 4, sm, slab);     // [2][3][kECH][P]: T_n and T_n' of the evaluation chunk
-    T *As = buf_ptr<T>(lay, 5, sm, slab);     // shift matrices A_{-1}, A_{+1}
+    T *hs = buf_ptr<T, all_smem<T, P>()>(lay, 3, sm, slab);
+    T *ev = buf_ptr<T, all_smem<T, P>()>(lay, 4, sm, slab);     // [2][3][kECH][P]: T_n and T_n' of the evaluation chunk
+    T *As = buf_ptr<T, all_smem<T, P>()>(lay, 5, sm, slab);     // shift matrices A_{-1}, A_{+1}
     __shared__ int s_ncol;
     __shared__ int s_cslot[27];
     __shared__ int s_cd[27][3];
@@ -1140,7 +1329,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
     const size_t pstride = (size_t)N1 * N1 * NHP;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
-    T *Pl = buf_ptr<T>(lay, 6, sm, slab);     // the parent's Lambda, kept for its next children
+    T *Pl = buf_ptr<T, all_smem<T, P>()>(lay, 6, sm, slab);     // the parent's Lambda, kept for its next children
     int cur_parent = -1;
     __shared__ int s_run;
     __shared__ int s_grs[8], s_gro[9], s_gnr, s_gntgt;  // a sibling group's leaves evaluated in the parent
@@ -1908,7 +2097,8 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         PCK(cudaMemsetAsync(gnear, 0, n * 24, st));
     }
     // device words: [0] near work queue, [2..3] pairs inside R_L, [4..5] local
-    // flops, [6] tensor-core wait error, [32 + l] level-l work queue of k_local
+    // flops, [6] tensor-core wait error, [8..9] incoming reads, [12] the
+    // anterpolation's work queue, [32 + l] level-l work queue of k_local
     PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 256, st));
 
     // ---- residual near field and self corrections, on the side stream: it
@@ -1950,21 +2140,38 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         size_t scr = std::max((size_t)2 * P3, (size_t)kCH * (3 * UpShape<P>::PS + UpShape<P>::YS)) * sizeof(T);
         if (sizeof(T) == 4 && UpShape<P>::TC_OK) scr = std::max(scr, (size_t)UpShape<P>::TC_SCR * sizeof(float));
         BufLayout lay = make_layout({P3 * sizeof(T), scr, (size_t)2 * P * P * sizeof(T)}, smem_limit - 1024);
+        if (all_smem<T, P>() && !layout_in_smem(lay)) {
+            err = "upward pass: buffers do not fit in shared memory";
+            return DMK_ERR_INTERNAL;
+        }
         if (sizeof(T) == 4 && UpShape<P>::TC_OK && !lay.in_smem[1]) {
             err = "tensor-core operands of the upward pass do not fit in shared memory";
             return DMK_ERR_INTERNAL;
         }
         PCK(cudaFuncSetAttribute(k_upward<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
+        // single precision: the anterpolation of every level in one launch, then
+        // the child-to-parent shifts level by level
+        constexpr bool all_level = sizeof(T) == 4 && P * ((P + 1) / 2) <= kThreads;
+        if constexpr (all_level) {
+            if (do_far && nslots > 0) {
+                const size_t asmem = ((size_t)(P3 + 31) / 32 * 32 + 3 * kCH * UpShape<P>::PS) * sizeof(float);
+                PCK(cudaFuncSetAttribute(k_anterp<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
+                ::dmk::launch_tick();
+                k_anterp<P><<<std::min(nslots, 2 * cx.num_sms), kThreads, asmem, st>>>(
+                    tv, nslots, (const int32_t *)cx.tree->slot2box.p, (float *)M, (int *)cx.bufs->counter.p + 12);
+            }
+        }
         const int lmax = tv.nlev - 1;
         for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0 && do_far; --l) {
             int lc = tv.lev_count[l];
             int grid = std::min(lc, maxgrid);
             if (grid <= 0) continue;
+            if (all_level && l == lmax) continue;  // the finest non-leaf boxes have no non-leaf children
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
             k_upward<T, P><<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, tv.lev_start[l], lc, M, lay,
                                                                    (char *)cx.bufs->slab.p,
-                                                                   (int *)cx.bufs->counter.p + 6);
+                                                                   (int *)cx.bufs->counter.p + 6, all_level ? 1 : 0);
         }
         PCK(cudaGetLastError());
     }
@@ -1984,6 +2191,10 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         BufLayout lay = make_layout({P3 * sizeof(T), (size_t)P * P * NH * sizeof(C2), (size_t)P * N1 * NH * sizeof(C2),
                                      (size_t)P * NH * sizeof(T)},
                                     smem_limit);
+        if (all_smem<T, P>() && !layout_in_smem(lay)) {
+            err = "plane waves: buffers do not fit in shared memory";
+            return DMK_ERR_INTERNAL;
+        }
         auto kern = tc_in ? k_prox2pw<T, P, NF, true> : k_prox2pw<T, P, NF, false>;
         PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
         int grid = std::min(nslots, maxgrid);
@@ -2050,6 +2261,10 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                      (size_t)6 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
                                      P3 * sizeof(T)},
                                     smem_limit - 20480);
+        if (all_smem<T, P>() && !layout_in_smem(lay)) {
+            err = "local pass: buffers do not fit in shared memory";
+            return DMK_ERR_INTERNAL;
+        }
         if (tcore && !(lay.in_smem[1] && lay.in_smem[2])) {
             err = "tensor-core operands do not fit in shared memory";
             return DMK_ERR_INTERNAL;

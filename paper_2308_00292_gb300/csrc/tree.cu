@@ -594,6 +594,36 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
     }
 }
 
+// octant ranges of every leaf one level below it (the refinement of Sec. 3.3):
+// a warp per leaf counts its points per octant digit of the point keys
+__global__ void k_leaf_octants(int nb, const int8_t *blevel, const int32_t *bstart, const int32_t *bcount,
+                               const uint8_t *bflags, const uint64_t *skeys, int kb, int32_t *loct) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nb || !(bflags[b] & BF_LEAF)) return;
+    const int lane = threadIdx.x & 31, l = blevel[b];
+    const int32_t s = bstart[b], e = s + bcount[b];
+    if (l + 1 > kb) {
+        // the key has no digit below this level: the leaf is not refined (-1)
+        if (lane < 8) loct[8 * (int64_t)b + lane] = lane == 0 ? -1 : e - s;
+        return;
+    }
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int32_t k = s + lane; k < e; k += 32) {
+        const int o = (int)((skeys[k] >> (3 * (kb - l - 1))) & 7ull);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) cnt[d] += o == d ? 1 : 0;
+    }
+    int run = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        int c = cnt[d];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        run += c;
+        if (lane == 0) loct[8 * (int64_t)b + d] = run;
+    }
+}
+
 // residual-kernel interaction lists (target-centric form of Step 4):
 // source leaf S (level b) acts on target leaf T (level a) when S is a leaf
 // colleague of T's level-b ancestor (b <= a), or S is a leaf at level a+1
@@ -1052,6 +1082,16 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
                                                   (const uint8_t *)pflag.p, (int32_t *)pleaf.p,
                                                   (double4_32a *)plocal.p, nullptr);
         }
+
+    // ---- octant ranges of the leaves (near-field refinement)
+    if (ws.ensure(loct, (int64_t)nb * 32)) {
+        err = "device allocation failed";
+        return DMK_ERR_OOM_I;
+    }
+    ::dmk::launch_tick();
+    k_leaf_octants<<<nblk(nb, 4), 128, 0, st>>>(nb, (const int8_t *)blevel.p, (const int32_t *)bstart.p,
+                                                (const int32_t *)bcount.p, (const uint8_t *)bflags.p, sorted_keys,
+                                                kb, (int32_t *)loct.p);
 
     // ---- near-field lists over target leaves
     int32_t *istl = isleaf;  // reuse: 1 for target leaves
