@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 METRIC = "3D Laplace DMK points/s at rel-L2 1e-6, mixed-prec vs FP64 path, 1 GB300"
 UNIT = "points/s"
 FP32_LANES_PER_SM = 128
+# threads of the anterpolation CTA: one (a, b pair) register tile each
+ANTERP_FFMA_THREADS = 256
 # nominal dense tensor rates of the part (TF32 / BF16), used only as a ratio to
 # carry the measured BF16 rate over to TF32
 TF32_PER_BF16 = 1.1 / 2.25
@@ -781,7 +783,8 @@ def run_ours(args, rank, world, local_rank):
             "fp64_path": fp64,
             "tree": {"levels": stats["n_levels"], "boxes": stats["n_boxes"], "leaves": stats["n_leaves"],
                      "fout": stats["n_fout"], "fin": stats["n_fin"], "near_pairs": stats["near_pairs"],
-                     "near_pairs_inside": stats["near_pairs_inside"], "incoming_reads": stats["incoming_reads"],
+                     "near_pairs_inside": stats["near_pairs_inside"],
+                     "near_pairs_screened": stats["near_pairs_screened"], "incoming_reads": stats["incoming_reads"],
                      "balance_rounds": stats["balance_rounds"]}}
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_sample)

@@ -128,6 +128,10 @@ DMK_API int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opt
  * plan, grows on demand and is reused by later calls.  A plan must not be
  * used by two calls at the same time.  The call synchronises cuda_stream
  * before it returns.  On error the potentials are unspecified.
+ *
+ * Environment: DMK_TREE_INITIAL_BOXES=n gives a new plan's tree a first box
+ * capacity of max(n, 4096) instead of the estimate 16 (N / n_s + 64); a
+ * diagnostic that makes the box arrays grow while the levels are built.
  */
 DMK_API int dmk_eval(dmk_plan_t plan,
              const double *sources, int64_t n_src, const double *charges,
@@ -218,10 +222,9 @@ DMK_API int dmk_adjoint_combine(int64_t n, const double *w1, const double *g1, c
  * dmk_direct_noalloc -- the direct sum u_i = sum_{j : y_j != x_i} rho_j / |x_i - y_j|
  * in double precision, performing no device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate while
- * they run -- work captured into a CUDA graph that must not call cudaMalloc,
- * applications that give all device memory to their own pool, loops that
- * cannot absorb the synchronisation an allocation can cause -- and that
- * therefore cannot use dmk_eval, whose scratch grows with the input.
+ * they run -- applications that give all device memory to their own pool,
+ * loops that cannot absorb the synchronisation an allocation can cause -- and
+ * that therefore cannot use dmk_eval, whose scratch grows with the input.
  *
  *   arguments   as in dmk_eval (device pointers, row-major points); targets
  *               may equal sources; coincident pairs contribute zero
@@ -350,6 +353,9 @@ typedef struct {
                                colleague array, and the three parity-split contractions
                                8 p (nf+1)^3 + 4 p^2 (nf+1)^2 + 2 p^3 (nf+1) per incoming box */
     float t_planewave_ms;   /* device time of the outgoing plane waves and the root term */
+    int64_t near_pairs_screened; /* pairs whose distance the near field tested: the sources
+                                    left after culling against each target group's bounding
+                                    box, times the group's targets */
 } dmk_eval_stats;
 
 DMK_API int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out);

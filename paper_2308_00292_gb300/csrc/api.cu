@@ -330,8 +330,9 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
     if (pl->bufs.counter.p) {
         // device words: [0] near work queue, [8] near pairs inside R_L,
         // [16] local-pass flops, [24] a tensor-core or TMA wait that gave up,
-        // [32] colleague arrays read by the incoming pass
-        unsigned char w[40] = {0};
+        // [32] colleague arrays read by the incoming pass, [40] pairs screened
+        // by the near field
+        unsigned char w[48] = {0};
         if (cudaMemcpy(w, pl->bufs.counter.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(DMK_ERR_CUDA, "reading the device status words failed");
         unsigned long long inside = 0, f = 0, reads = 0;
@@ -340,7 +341,12 @@ int eval_device(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, 
         memcpy(&f, w + 16, 8);
         memcpy(&timeout, w + 24, 4);
         memcpy(&reads, w + 32, 8);
-        if (pl->tree->ntleaves > 0) s.near_pairs_inside = (int64_t)inside;
+        unsigned long long screened = 0;
+        memcpy(&screened, w + 40, 8);
+        if (pl->tree->ntleaves > 0) {
+            s.near_pairs_inside = (int64_t)inside;
+            s.near_pairs_screened = (int64_t)screened;
+        }
         s.local_flops = (int64_t)f;
         if (s.t_incoming_ms > 0.f || reads > 0) {
             const int64_t P = pl->tb.p, NH = pl->tb.nf + 1, N1 = 2 * pl->tb.nf + 1;

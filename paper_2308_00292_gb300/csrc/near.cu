@@ -25,7 +25,8 @@ namespace dmk {
 //      closer than R_b; the marked pairs of the warp are compacted into a
 //      queue and evaluated 32 at a time, one pair per lane;
 //   4. values are summed per target by a segmented warp reduction (a fixed
-//      order: the result is deterministic) into double accumulators.
+//      order: the result is deterministic) into per-target accumulators
+//      (FP64, or an exact float pair hi + lo in single precision).
 // In single precision coordinates are hi + lo pairs relative to the leaf
 // centres; the exact dyadic offset between the two leaf centres is added to
 // the source with a TwoSum, so differences of nearby points keep their full
@@ -44,6 +45,24 @@ template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return
 constexpr int kNearThreads = 128;
 constexpr int kNC = 128;  // staged sources per chunk
 
+// Per-target sums.  The double pass sums in FP64.  The single-precision pass
+// keeps a float pair hi + lo made exact by TwoSum: GB300 issues FP64 adds and
+// conversions at 1/64 of the FP32 rate, so a double add per run cost more
+// than the pairs it sums.  hi + lo carries about 48 bits, as a double sum of
+// FP32 runs would.
+template <typename T> struct NearAcc { using type = double; };
+template <> struct NearAcc<float> { using type = float2; };
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(float2 &a) { a = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void acc_add(double &a, double v) { a += v; }
+__device__ __forceinline__ void acc_add(float2 &a, float v) {
+    const float s = a.x + v, bb = s - a.x;
+    a.y += (a.x - (s - bb)) + (v - bb);
+    a.x = s;
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(float2 a) { return (double)a.x + (double)a.y; }
+
 // per-warp shared memory of k_near
 template <typename T> struct NearWarp {
     using V4 = typename Vec4<T>::type;
@@ -53,7 +72,7 @@ template <typename T> struct NearWarp {
     T sq[kNC];         // double precision: the charge
     V4 th[32];         // the group's targets (hi) and
     float4 tl[32];     // their lo parts
-    double acc[32];    // per-target sums
+    typename NearAcc<T>::type acc[32];  // per-target sums
     T lox[32], loy[32], loz[32];            // kept source leaves: centre offset,
     int lb_[32];                            // level
     int lss[32], loff[33];                  // first point, offset in the stream
@@ -63,7 +82,7 @@ template <typename T> struct NearWarp {
 };
 // the gradient pass adds the per-target gradient sums
 template <typename T> struct NearWarpG : NearWarp<T> {
-    double gacc[3][32];
+    typename NearAcc<T>::type gacc[3][32];
 };
 template <typename T, bool GRAD> using NearWarpT = typename std::conditional<GRAD, NearWarpG<T>, NearWarp<T>>::type;
 
@@ -148,6 +167,9 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
     // pairs inside the support of the residual kernel (statistics); the
     // counter sits 8 bytes after the work counter
     unsigned inside32 = 0;
+    // pairs screened (staged sources times the group's targets), counted at
+    // counter + 10 as 64 bits
+    unsigned long long screened = 0;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(counter, 1);
@@ -157,6 +179,7 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(FULL, inside, o);
             if (lane == 0 && inside) atomicAdd(reinterpret_cast<unsigned long long *>(counter + 2), inside);
+            if (lane == 0 && screened) atomicAdd(reinterpret_cast<unsigned long long *>(counter + 10), screened);
             break;
         }
         const int Tb = tleaves[it];
@@ -186,8 +209,9 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                 bl[1] = bh[1] = v.y;
                 bl[2] = bh[2] = v.z;
             }
-            W.acc[lane] = 0.0;
-            if constexpr (GRAD) W.gacc[0][lane] = W.gacc[1][lane] = W.gacc[2][lane] = 0.0;
+            acc_zero(W.acc[lane]);
+            if constexpr (GRAD)
+                for (int d = 0; d < 3; ++d) acc_zero(W.gacc[d][lane]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -299,6 +323,7 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                     }
                     __syncwarp();
                     if (fill == 0) continue;
+                    screened += (unsigned long long)fill * (unsigned)ng;
                     // 3. screening, 32 candidates per lane: k = u0 + sub + G i
                     for (int u0 = 0; u0 < fill; u0 += 32 * G) {
                         unsigned mask = 0;
@@ -348,9 +373,9 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                                         fpart = part;
                                         if constexpr (GRAD) fpg[0] = pg[0], fpg[1] = pg[1], fpg[2] = pg[2];
                                     } else {
-                                        W.acc[cur] += (double)part;
+                                        acc_add(W.acc[cur], part);
                                         if constexpr (GRAD)
-                                            for (int d = 0; d < 3; ++d) W.gacc[d][cur] += (double)pg[d];
+                                            for (int d = 0; d < 3; ++d) acc_add(W.gacc[d][cur], pg[d]);
                                     }
                                 }
                                 cur = tt;
@@ -409,9 +434,9 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                                 fpart = part;
                                 if constexpr (GRAD) fpg[0] = pg[0], fpg[1] = pg[1], fpg[2] = pg[2];
                             } else {
-                                W.acc[cur] += (double)part;
+                                acc_add(W.acc[cur], part);
                                 if constexpr (GRAD)
-                                    for (int d = 0; d < 3; ++d) W.gacc[d][cur] += (double)pg[d];
+                                    for (int d = 0; d < 3; ++d) acc_add(W.gacc[d][cur], pg[d]);
                             }
                         }
                         // first runs: a segmented sum over lanes with the same target
@@ -434,9 +459,9 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                         const int kn = __shfl_down_sync(FULL, key, 1);
                         __syncwarp();
                         if (first >= 0 && (lane == 31 || kn != key)) {
-                            W.acc[key] += (double)v;
+                            acc_add(W.acc[key], v);
                             if constexpr (GRAD)
-                                for (int d = 0; d < 3; ++d) W.gacc[d][key] += (double)fpg[d];
+                                for (int d = 0; d < 3; ++d) acc_add(W.gacc[d][key], fpg[d]);
                         }
                         __syncwarp();
                     }
@@ -444,9 +469,10 @@ __global__ void __launch_bounds__(kNearThreads, 6) k_near(TreeView tv, int ntl, 
                 }
             }
             if (lane < ng && (tv.pflag[ts + j0 + lane] & 2)) {
-                unear[ts + j0 + lane] = W.acc[lane];
+                unear[ts + j0 + lane] = acc_value(W.acc[lane]);
                 if constexpr (GRAD)
-                    for (int d = 0; d < 3; ++d) gnear[3 * (size_t)(ts + j0 + lane) + d] = W.gacc[d][lane];
+                    for (int d = 0; d < 3; ++d)
+                        gnear[3 * (size_t)(ts + j0 + lane) + d] = acc_value(W.gacc[d][lane]);
             }
             __syncwarp();
         }

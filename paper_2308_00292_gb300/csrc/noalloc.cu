@@ -2,10 +2,9 @@
 // no device allocation.
 //
 // Who needs it: code that must not allocate device memory while it runs --
-// work recorded into a CUDA graph whose capture forbids cudaMalloc, an
-// application that hands all device memory to its own pool and does not allow
-// libraries to grow their footprint, or a latency-critical loop that cannot
-// afford the device-wide synchronisation an allocation may cause.  dmk_eval
+// an application that hands all device memory to its own pool and does not
+// allow libraries to grow their footprint, or a latency-critical loop that
+// cannot afford the device-wide synchronisation an allocation may cause.  dmk_eval
 // cannot serve them: its tree and expansions grow with the input and live in
 // plan scratch allocated on first use.
 //

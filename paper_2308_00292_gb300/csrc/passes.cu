@@ -343,74 +343,100 @@ __device__ void anterpolate_tc(const TreeView &tv, const double (&cc)[3], double
     if (!ok && (tid & 31) == 0) atomicExch(tc_err, 1);
 }
 
-// FP32 anterpolation with register tiles: thread (a, b pair) adds, point by
-// point, rho T_a(x) T_b(y) T_c(z) to its 2 P moments M[a][b][c], M[a][b + 1][c]
-// held in registers for a chunk of kCH points (one FMA per moment and point,
-// with rho T_a(x) T_b(y) formed once per (a, b)), two points per step; the
-// chunk's sums are then added to acc in shared memory, so every moment is a sum
-// of chunk sums (rounding like a per-chunk flush).  The T rows of a chunk are
-// staged by 3 kCH threads, whose coordinates are loaded one chunk ahead.  acc
-// must be zero on entry; called by the whole CTA.
+// ---------------------------------------------------------------------------
+// Single-precision upward pass of every level in one launch (k_anterp)
+// ---------------------------------------------------------------------------
+// Shapes: compute threads hold the register tiles of the anterpolation, one
+// (a, b pair) item each; three staging warps form the Chebyshev rows of the
+// next chunk of points meanwhile (double-buffered, one barrier per chunk).
+template <int P> struct AntShape {
+    static constexpr int PS = (P + 3) & ~3, NBP = (P + 1) / 2, NIT = P * NBP;
+    static constexpr int NC = (NIT + 31) / 32 * 32;  // compute threads
+    static constexpr int NS = 3 * kCH;               // staging threads: (axis, point)
+    static constexpr int NT = NC + NS;
+    static constexpr int P3 = P * P * P, P3P = (P3 + 31) / 32 * 32;
+    static constexpr int STG = 3 * kCH * PS;         // floats of one staging buffer
+    static constexpr int WRK = 2 * STG > P3P ? 2 * STG : P3P;  // staging buffers, or the shift scratch
+    static constexpr int NPEN = (P * P + 1) / 2;     // pencil pairs of one shift axis
+    static constexpr size_t SMEM = ((size_t)P3P + WRK + 2 * P * PS) * sizeof(float);
+    static constexpr bool OK = NPEN <= NT;
+};
+
+// Chebyshev row of one coordinate of one point, times the charge for x:
+// o[n] = w T_n(xi), n < P, zero-padded to PS
 template <int P>
-__device__ __forceinline__ void anterpolate_ffma(const TreeView &tv, const double (&cc)[3], double s2R, const int *lstart,
-                                 const int *lpre, int ntot, float *stg, float *acc) {
-    constexpr int PS = UpShape<P>::PS, NBP = (P + 1) / 2, NIT = P * NBP;
-    static_assert(NIT <= kThreads, "one (a, b pair) item per thread");
+__device__ __forceinline__ void cheb_row(float *o, float xi, float w) {
+    float t0 = 1.f, t1 = xi;
+    o[0] = w;
+    if (P > 1) o[1] = w * xi;
+#pragma unroll
+    for (int n = 2; n < P; ++n) {
+        const float t2 = 2.f * xi * t1 - t0;
+        o[n] = w * t2;
+        t0 = t1;
+        t1 = t2;
+    }
+#pragma unroll
+    for (int n = P; n < AntShape<P>::PS; ++n) o[n] = 0.f;
+}
+
+// acc[a][b][c] += sum_j rho_j T_a(x_j) T_b(y_j) T_c(z_j) over the ntot points
+// of the ranges (lstart, lpre) on the grid of centre cc and scale s2R.  A
+// compute thread keeps M[a][b][c] and M[a][b+1][c] for every c in registers and
+// adds point by point, two points per step (one FMA per moment and point, with
+// rho T_a(x) T_b(y) formed once per (a, b)); a chunk's sums go to acc in
+// shared memory, so every moment is a sum of chunk sums of kCH points.
+// Staging threads load coordinates one chunk ahead of the rows they form.
+// Called by the whole CTA after acc is zeroed; ends with a barrier.
+template <int P>
+__device__ __forceinline__ void anterpolate_pipe(const TreeView &tv, const double (&cc)[3], double s2R,
+                                                 const int *lstart, const int *lpre, int ntot, float *stg,
+                                                 float *acc) {
+    using S = AntShape<P>;
+    constexpr int PS = S::PS, NBP = S::NBP;
     const int tid = threadIdx.x;
-    const bool has = tid < NIT;
-    const int a = has ? tid / NBP : 0, b0 = has ? 2 * (tid % NBP) : 0;
-    const bool has1 = has && b0 + 1 < P;
-    // the coordinate (and charge) that thread tid < 3 kCH stages for point p
+    const bool stager = tid >= S::NC;
+    const int sidx = tid - S::NC, ax = sidx / kCH, j = sidx % kCH;
+    const double cax = ax == 0 ? cc[0] : (ax == 1 ? cc[1] : cc[2]);
+    // the coordinate (and, for x, the charge) of point p of the ranges
     auto fetch = [&](int p, double &u, double &w) {
-        const int ax = tid / kCH;
-        u = 0.0;
-        w = 1.0;
+        u = cax;
+        w = 0.0;
         if (p < ntot) {
             int seg = 0;
             while (seg < 7 && lpre[seg + 1] <= p) ++seg;
             const int kk = lstart[seg] + (p - lpre[seg]);
             u = ax == 0 ? tv.ux[kk] : (ax == 1 ? tv.uy[kk] : tv.uz[kk]);
-            if (ax == 0) w = tv.q[kk];
+            w = ax == 0 ? tv.q[kk] : 1.0;
         }
     };
-    double un = 0.0, wn = 1.0;
-    if (tid < 3 * kCH) fetch(tid % kCH, un, wn);
-    for (int p0 = 0; p0 < ntot; p0 += kCH) {
-        const int np = min(kCH, ntot - p0);
-        if (tid < 3 * kCH) {
-            // T_0 .. T_{P-1} of one coordinate of one point, times the charge for x
-            const int ax = tid / kCH, j = tid % kCH;
-            const double u = un, wq = wn;
-            if (p0 + kCH < ntot) fetch(p0 + kCH + j, un, wn);
-            float *o = stg + (ax * kCH + j) * PS;
-            if (j < np) {
-                const float xi = (float)((u - cc[ax]) * s2R);
-                const float w = (float)wq;
-                float t0 = 1.f, t1 = xi;
-                o[0] = w;
-                if (P > 1) o[1] = w * xi;
-#pragma unroll
-                for (int n = 2; n < P; ++n) {
-                    const float t2 = 2.f * xi * t1 - t0;
-                    o[n] = w * t2;
-                    t0 = t1;
-                    t1 = t2;
-                }
-            } else {
-#pragma unroll
-                for (int n = 0; n < PS; ++n) o[n] = 0.f;
+    double un = 0.0, wn = 0.0;
+    if (stager) {
+        fetch(j, un, wn);
+        cheb_row<P>(stg + (ax * kCH + j) * PS, (float)((un - cax) * s2R), (float)wn);
+        fetch(kCH + j, un, wn);
+    }
+    __syncthreads();
+    const int a = tid / NBP, b0 = 2 * (tid % NBP);
+    const bool has1 = b0 + 1 < P;
+    for (int c = 0, p0 = 0; p0 < ntot; ++c, p0 += kCH) {
+        const float *cur = stg + (c & 1) * S::STG;
+        if (stager) {
+            if (p0 + kCH < ntot) {
+                float *nxt = stg + ((c + 1) & 1) * S::STG;
+                cheb_row<P>(nxt + (ax * kCH + j) * PS, (float)((un - cax) * s2R), (float)wn);
+                fetch(p0 + 2 * kCH + j, un, wn);
             }
-        }
-        __syncthreads();
-        if (has) {
+        } else if (tid < S::NIT) {
+            const int np = min(kCH, ntot - p0);
             float c0[P], c1[P];
 #pragma unroll
-            for (int c = 0; c < P; ++c) c0[c] = c1[c] = 0.f;
-            // two points per step (a zero row pads an odd count: staged as zeros)
-            for (int j = 0; j < np; j += 2) {
-                const float *X0 = stg + j * PS, *Y0 = stg + (kCH + j) * PS;
-                const float4 *Z0 = reinterpret_cast<const float4 *>(stg + (2 * kCH + j) * PS);
-                const float4 *Z1 = reinterpret_cast<const float4 *>(stg + (2 * kCH + j + 1) * PS);
+            for (int k = 0; k < P; ++k) c0[k] = c1[k] = 0.f;
+            // two points per step (a row past np is staged as zeros)
+            for (int jj = 0; jj < np; jj += 2) {
+                const float *X0 = cur + jj * PS, *Y0 = cur + (kCH + jj) * PS;
+                const float4 *Z0 = reinterpret_cast<const float4 *>(cur + (2 * kCH + jj) * PS);
+                const float4 *Z1 = reinterpret_cast<const float4 *>(cur + (2 * kCH + jj + 1) * PS);
                 const float xa0 = X0[a], xa1 = X0[PS + a];
                 const float s00 = xa0 * Y0[b0], s01 = has1 ? xa0 * Y0[b0 + 1] : 0.f;
                 const float s10 = xa1 * Y0[PS + b0], s11 = has1 ? xa1 * Y0[PS + b0 + 1] : 0.f;
@@ -420,95 +446,219 @@ __device__ __forceinline__ void anterpolate_ffma(const TreeView &tv, const doubl
                     const float za[4] = {z.x, z.y, z.z, z.w}, zb[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int c = 4 * c4 + q;
-                        if (c < P) {
-                            c0[c] = fmaf(s10, zb[q], fmaf(s00, za[q], c0[c]));
-                            c1[c] = fmaf(s11, zb[q], fmaf(s01, za[q], c1[c]));
+                        const int k = 4 * c4 + q;
+                        if (k < P) {
+                            c0[k] = fmaf(s10, zb[q], fmaf(s00, za[q], c0[k]));
+                            c1[k] = fmaf(s11, zb[q], fmaf(s01, za[q], c1[k]));
                         }
                     }
                 }
             }
+            // this thread's own rows of acc: no other thread touches them
             float *r0 = acc + (a * P + b0) * P;
 #pragma unroll
-            for (int c = 0; c < P; ++c) {
-                r0[c] += c0[c];
-                if (has1) r0[P + c] += c1[c];
+            for (int k = 0; k < P; ++k) {
+                r0[k] += c0[k];
+                if (has1) r0[P + k] += c1[k];
             }
         }
         __syncthreads();
     }
 }
 
-// Single-precision anterpolation of every box of every level in one launch
-// (its boxes depend on no other level): persistent CTAs take the expansion
-// slots from a work counter, so that no level waits for its heaviest box; the
-// moments of the leaf children's sources go to M[slot].  The child-to-parent
-// shifts follow level by level (k_upward with c2p_only).
+// One axis of the exact child-to-parent shift (Lemma ctoplemma) on pencils:
+// out[.., n, ..] = sum_{m <= n} A[n][m] in[.., m, ..] along axis AX (0 = the
+// fastest index c, 1 = b, 2 = a), two pencils per thread, each read whole into
+// registers first (so out may be in).  A is P x PS in shared memory, zero above
+// the diagonal.  MODE 0: in from global memory (L2, bypassing L1); 1: in and
+// out in shared memory; 2: out += (accumulate).
+template <int P, int AX, int MODE>
+__device__ __forceinline__ void shift_pencils(const float *A, const float *in, float *out) {
+    using S = AntShape<P>;
+    constexpr int PS = S::PS;
+    constexpr int s = AX == 0 ? 1 : (AX == 1 ? P : P * P);
+    auto base = [](int r) { return AX == 0 ? r * P : (AX == 1 ? (r / P) * P * P + r % P : r); };
+    const int t = threadIdx.x;
+    if (t < S::NPEN) {
+        const int r0 = t, r1 = t + S::NPEN;
+        const bool has1 = r1 < P * P;
+        const int e0 = base(r0), e1 = has1 ? base(r1) : e0;
+        float v0[PS], v1[PS];
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            v0[m] = MODE == 0 ? __ldcg(in + e0 + m * s) : in[e0 + m * s];
+            v1[m] = MODE == 0 ? __ldcg(in + e1 + m * s) : in[e1 + m * s];
+        }
+#pragma unroll
+        for (int m = P; m < PS; ++m) v0[m] = v1[m] = 0.f;
+#pragma unroll
+        for (int n = 0; n < P; ++n) {
+            const float4 *Ar = reinterpret_cast<const float4 *>(A + n * PS);
+            float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+            for (int m4 = 0; m4 <= n / 4; ++m4) {
+                const float4 w = Ar[m4];
+                o0 = fmaf(w.x, v0[4 * m4], o0);
+                o1 = fmaf(w.x, v1[4 * m4], o1);
+                o0 = fmaf(w.y, v0[4 * m4 + 1], o0);
+                o1 = fmaf(w.y, v1[4 * m4 + 1], o1);
+                o0 = fmaf(w.z, v0[4 * m4 + 2], o0);
+                o1 = fmaf(w.z, v1[4 * m4 + 2], o1);
+                o0 = fmaf(w.w, v0[4 * m4 + 3], o0);
+                o1 = fmaf(w.w, v1[4 * m4 + 3], o1);
+            }
+            if (MODE == 2) {
+                out[e0 + n * s] += o0;
+                if (has1) out[e1 + n * s] += o1;
+            } else {
+                out[e0 + n * s] = o0;
+                if (has1) out[e1 + n * s] = o1;
+            }
+        }
+    }
+}
+
+// Persistent CTAs take the expansion slots from a work counter.  For its box B
+// a CTA anterpolates the sources of B's leaf children onto B's grid (a root
+// that is a leaf anterpolates its own sources, for the windowed term W_0) and
+// stores the result in M[slot(B)].  The child-to-parent shifts need no
+// per-level launch: a box counts arrivals in cnt[slot] -- its own
+// anterpolation and the completion of each non-leaf child holding sources --
+// and the CTA whose arrival completes the count adds the shifted moments of
+// those children to the box's own, then arrives at the parent.  No CTA waits
+// for another, and every box's sum is formed by one CTA in octant order, so
+// the result does not depend on scheduling.  cnt must be zero on entry.
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_anterp(TreeView tv, int nslots, const int32_t *slot2box, float *M,
-                                                     int *ctr) {
+__global__ void __launch_bounds__(AntShape<P>::NT, 3) k_anterp(TreeView tv, const float *Atab, int nslots,
+                                                            const int32_t *slot2box, float *M, int *ctr, int *cnt) {
+    using S = AntShape<P>;
+    constexpr int P3 = S::P3, PS = S::PS;
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) char sm[];
-    using U = UpShape<P>;
-    constexpr int P3 = P * P * P;
     float *acc = reinterpret_cast<float *>(sm);
-    float *stg = acc + (P3 + 31) / 32 * 32;  // [3][kCH][PS]
-    __shared__ int s_item, s_lstart[8], s_lpre[9];
-    const int tid = threadIdx.x;
+    float *wrk = acc + S::P3P;          // staging buffers [2][3][kCH][PS], or the shift scratch [P3]
+    float *As = wrk + S::WRK;           // shift matrices A_{-1}, A_{+1}: [2][P][PS]
+    __shared__ int s_item, s_lstart[8], s_lpre[9], s_nnl, s_last;
+    __shared__ int s_kids[8];           // non-leaf children with sources, in octant order (octant << 27 | box)
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < 2 * P * PS; i += S::NT) {
+        const int h = i / (P * PS), n = (i / PS) % P, m = i % PS;
+        As[i] = m <= n && m < P ? Atab[h * P * P + n * P + m] : 0.f;
+    }
+    // warp 0: the children of box X -- the point ranges of its leaf children
+    // with sources (when ranges is set) and its non-leaf children with sources
+    auto children = [&](int X, bool ranges) {
+        if (tid < 32) {
+            const bool selfleaf = (tv.bflags[X] & BF_LEAF) != 0;
+            const unsigned cm = selfleaf ? 0u : tv.bcmask[X];
+            const int c0 = tv.bchild0[X];
+            bool leafk = false, nonleaf = false;
+            int st = 0, ct = 0;
+            if (selfleaf) {
+                if (lane == 0 && tv.bnsrc[X] > 0) {
+                    leafk = true;
+                    st = tv.bstart[X];
+                    ct = tv.bcount[X];
+                }
+            } else if (lane < 8 && ((cm >> lane) & 1u)) {
+                const int D = c0 + __popc(cm & ((1u << lane) - 1u));
+                const bool src = tv.bnsrc[D] > 0, lf = (tv.bflags[D] & BF_LEAF) != 0;
+                leafk = src && lf;
+                nonleaf = src && !lf;
+                if (leafk) {
+                    st = tv.bstart[D];
+                    ct = tv.bcount[D];
+                }
+                if (nonleaf) st = D;
+            }
+            const unsigned nm = __ballot_sync(FULL, nonleaf);
+            if (nonleaf) s_kids[__popc(nm & ((1u << lane) - 1u))] = (lane << 27) | st;
+            if (lane == 0) s_nnl = __popc(nm);
+            if (ranges) {
+                const unsigned lm = __ballot_sync(FULL, leafk);
+                int pre = leafk ? ct : 0;
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    const int v = __shfl_up_sync(FULL, pre, o);
+                    if (lane >= o) pre += v;
+                }
+                const int tot = __shfl_sync(FULL, pre, 7);
+                const int k = __popc(lm & ((1u << lane) - 1u));
+                if (leafk) {
+                    s_lstart[k] = st;
+                    s_lpre[k] = pre - ct;
+                }
+                if (lane >= __popc(lm) && lane < 9) s_lpre[lane] = tot;
+            }
+        }
+        __syncthreads();
+    };
     for (;;) {
         if (tid == 0) s_item = atomicAdd(ctr, 1);
         __syncthreads();
         const int slot = s_item;
         if (slot >= nslots) break;
         const int B = slot2box[slot];
-        const bool selfleaf = (tv.bflags[B] & BF_LEAF) != 0;
-        // a leaf's sources go to its parent's grid; a root that is a leaf
-        // anterpolates onto its own grid (for the windowed term W_0)
-        if ((selfleaf && tv.blevel[B] != 0) || tv.bnsrc[B] == 0) continue;
+        if (((tv.bflags[B] & BF_LEAF) && tv.blevel[B] != 0) || tv.bnsrc[B] == 0) continue;
         const int l = tv.blevel[B];
         int ix, iy, iz;
         box_decode_d(tv.bkey[B], l, ix, iy, iz);
         const double R = level_R(l), s2R = 2.0 / R;
         const double cc[3] = {(ix + 0.5) * R, (iy + 0.5) * R, (iz + 0.5) * R};
-        for (int i = tid; i < P3; i += kThreads) acc[i] = 0.f;
-        const int c0 = tv.bchild0[B];
-        const unsigned cm = selfleaf ? 1u : tv.bcmask[B];
-        // point ranges of the leaf children (with sources), streamed as one sequence
-        if (tid == 0) {
-            int k = 0, nl = 0, tot = 0;
-            for (int oc = 0; oc < 8; ++oc) {
-                if (!(cm & (1u << oc))) continue;
-                const int D = selfleaf ? B : c0 + k;
-                ++k;
-                if (tv.bnsrc[D] == 0 || !(selfleaf || (tv.bflags[D] & BF_LEAF))) continue;
-                s_lstart[nl] = tv.bstart[D];
-                s_lpre[nl] = tot;
-                tot += tv.bcount[D];
-                ++nl;
-            }
-            for (int q = nl; q < 9; ++q) s_lpre[q] = tot;
-        }
-        __syncthreads();
+        for (int i = tid; i < P3; i += S::NT) acc[i] = 0.f;
+        children(B, true);
         const int ntot = s_lpre[8];
-        if (ntot > 0) anterpolate_ffma<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, stg, acc);
+        if (ntot > 0) anterpolate_pipe<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, wrk, acc);
         float *Mo = M + (size_t)slot * P3;
-        for (int i = tid; i < P3; i += kThreads) Mo[i] = acc[i];
-        __syncthreads();
+        for (int i = tid; i < P3; i += S::NT) Mo[i] = acc[i];
+        // arrivals, climbing while this CTA completes a box
+        int X = B;
+        bool own = true;  // acc holds X's own moments
+        for (;;) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(cnt + tv.bslot[X], 1) == s_nnl;
+            __syncthreads();
+            if (!s_last) break;
+            __threadfence();
+            const int nnl = s_nnl;
+            if (nnl > 0) {
+                float *MX = M + (size_t)tv.bslot[X] * P3;
+                if (!own)
+                    for (int i = tid; i < P3; i += S::NT) acc[i] = __ldcg(MX + i);
+                for (int k = 0; k < nnl; ++k) {
+                    const int e = s_kids[k], oc = e >> 27, D = e & ((1 << 27) - 1);
+                    const float *MD = M + (size_t)tv.bslot[D] * P3;
+                    __syncthreads();  // wrk and acc free (previous child done, acc loaded)
+                    shift_pencils<P, 0, 0>(As + ((oc >> 2) & 1) * P * PS, MD, wrk);
+                    __syncthreads();
+                    shift_pencils<P, 1, 1>(As + ((oc >> 1) & 1) * P * PS, wrk, wrk);
+                    __syncthreads();
+                    shift_pencils<P, 2, 2>(As + (oc & 1) * P * PS, wrk, acc);
+                }
+                __syncthreads();
+                for (int i = tid; i < P3; i += S::NT) MX[i] = acc[i];
+            }
+            const int par = tv.bparent[X];
+            if (par < 0) break;
+            X = par;
+            own = false;
+            children(X, false);
+        }
     }
-    (void)sizeof(U);
 }
 
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> tb, int lstart, int lcount, T *M,
-                                                     BufLayout lay, char *slab, int *tc_err, int c2p_only) {
+                                                     BufLayout lay, char *slab, int *tc_err) {
     extern __shared__ __align__(128) char sm[];
     using U = UpShape<P>;
     constexpr int P3 = P * P * P;
     constexpr int PS = U::PS, YS = U::YS;
     constexpr int NAG = (P + 3) / 4, NBCG = (P * P + 3) / 4;
-    // single precision anterpolates with register-tiled FP32 FMAs (the orders of
-    // the single-precision plans); the tensor-core form stays for others
-    constexpr bool kFF = sizeof(T) == 4 && P * ((P + 1) / 2) <= kThreads;
-    constexpr bool kTC = !kFF && sizeof(T) == 4 && U::TC_OK;
+    // the single-precision orders whose register tiles fit run in k_anterp; the
+    // tensor-core form stays for the other single-precision orders
+    constexpr bool kTC = sizeof(T) == 4 && U::TC_OK;
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     uint32_t phase = 0;
@@ -537,22 +687,7 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
         // anterpolates onto its own grid (for the windowed term W_0)
         if (selfleaf && tv.blevel[B] != 0) continue;
         if (tv.bnsrc[B] == 0) continue;
-        if (c2p_only) {
-            // the moments of the leaf children are in M already (k_anterp): only
-            // boxes with non-leaf children that hold sources have work here
-            bool any = false;
-            const unsigned cmk = selfleaf ? 0u : tv.bcmask[B];
-            for (int oc = 0, k = 0; oc < 8; ++oc) {
-                if (!(cmk & (1u << oc))) continue;
-                const int D = tv.bchild0[B] + k++;
-                any = any || (tv.bnsrc[D] > 0 && !(tv.bflags[D] & BF_LEAF));
-            }
-            if (!any) continue;
-            const T *Mi = M + (size_t)tv.bslot[B] * P3;
-            for (int i = tid; i < P3; i += kThreads) acc[i] = Mi[i];
-        } else {
-            for (int i = tid; i < P3; i += kThreads) acc[i] = (T)0;
-        }
+        for (int i = tid; i < P3; i += kThreads) acc[i] = (T)0;
         const int l = tv.blevel[B];
         int ix, iy, iz;
         box_decode_d(tv.bkey[B], l, ix, iy, iz);
@@ -577,12 +712,8 @@ __global__ void __launch_bounds__(kThreads) k_upward(TreeView tv, DevTables<T> t
             for (int q = nl; q < 9; ++q) s_lpre[q] = tot;
         }
         __syncthreads();
-        const int ntot = c2p_only ? 0 : s_lpre[8];
-        if constexpr (kFF) {
-            if (ntot > 0)
-                anterpolate_ffma<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, reinterpret_cast<float *>(stg),
-                                    reinterpret_cast<float *>(acc));
-        } else if constexpr (kTC) {
+        const int ntot = s_lpre[8];
+        if constexpr (kTC) {
             if (ntot > 0) anterpolate_tc<P>(tv, cc, s2R, s_lstart, s_lpre, ntot, scr, s_tmem, &s_bar, phase, acc,
                                              tc_err);
         } else {
@@ -2097,8 +2228,9 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
         PCK(cudaMemsetAsync(gnear, 0, n * 24, st));
     }
     // device words: [0] near work queue, [2..3] pairs inside R_L, [4..5] local
-    // flops, [6] tensor-core wait error, [8..9] incoming reads, [12] the
-    // anterpolation's work queue, [32 + l] level-l work queue of k_local
+    // flops, [6] tensor-core wait error, [8..9] incoming reads, [10..11] pairs
+    // screened by the near field, [12] the upward pass's work queue, [32 + l]
+    // level-l work queue of k_local
     PCK(cudaMemsetAsync(cx.bufs->counter.p, 0, 256, st));
 
     // ---- residual near field and self corrections, on the side stream: it
@@ -2149,29 +2281,36 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
             return DMK_ERR_INTERNAL;
         }
         PCK(cudaFuncSetAttribute(k_upward<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem_bytes));
-        // single precision: the anterpolation of every level in one launch, then
-        // the child-to-parent shifts level by level
+        // single precision: the whole upward pass (anterpolation and the
+        // child-to-parent shifts of every level) in one launch; otherwise level
+        // by level, finest first
         constexpr bool all_level = sizeof(T) == 4 && P * ((P + 1) / 2) <= kThreads;
         if constexpr (all_level) {
             if (do_far && nslots > 0) {
-                const size_t asmem = ((size_t)(P3 + 31) / 32 * 32 + 3 * kCH * UpShape<P>::PS) * sizeof(float);
-                PCK(cudaFuncSetAttribute(k_anterp<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
+                using AS = AntShape<P>;
+                static_assert(AS::OK, "pencil pairs of a shift exceed the CTA");
+                if (ws.ensure(cx.bufs->upcnt, (int64_t)nslots * 4)) { err = "oom upward counters"; return DMK_ERR_OOM; }
+                PCK(cudaMemsetAsync(cx.bufs->upcnt.p, 0, (size_t)nslots * 4, st));
+                PCK(cudaFuncSetAttribute(k_anterp<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS::SMEM));
+                int per_sm = 0;
+                PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_anterp<P>, AS::NT, AS::SMEM));
+                const int grid = std::min(nslots, std::max(per_sm, 1) * cx.num_sms);
                 ::dmk::launch_tick();
-                k_anterp<P><<<std::min(nslots, 2 * cx.num_sms), kThreads, asmem, st>>>(
-                    tv, nslots, (const int32_t *)cx.tree->slot2box.p, (float *)M, (int *)cx.bufs->counter.p + 12);
+                k_anterp<P><<<grid, AS::NT, AS::SMEM, st>>>(tv, reinterpret_cast<const float *>(tb.A), nslots,
+                                                            (const int32_t *)cx.tree->slot2box.p, (float *)M,
+                                                            (int *)cx.bufs->counter.p + 12, (int *)cx.bufs->upcnt.p);
             }
         }
         const int lmax = tv.nlev - 1;
-        for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0 && do_far; --l) {
+        for (int l = (tv.nlev == 1 ? 0 : lmax - 1); l >= 0 && do_far && !all_level; --l) {
             int lc = tv.lev_count[l];
             int grid = std::min(lc, maxgrid);
             if (grid <= 0) continue;
-            if (all_level && l == lmax) continue;  // the finest non-leaf boxes have no non-leaf children
             if (ws.ensure(cx.bufs->slab, (int64_t)grid * lay.slab_bytes + 128)) { err = "oom slab"; return DMK_ERR_OOM; }
             ::dmk::launch_tick();
             k_upward<T, P><<<grid, kThreads, lay.smem_bytes, st>>>(tv, tb, tv.lev_start[l], lc, M, lay,
                                                                    (char *)cx.bufs->slab.p,
-                                                                   (int *)cx.bufs->counter.p + 6, all_level ? 1 : 0);
+                                                                   (int *)cx.bufs->counter.p + 6);
         }
         PCK(cudaGetLastError());
     }

@@ -17,6 +17,7 @@ struct BufLayout {
 struct PassBufs {
     DBuf M, Lam, LamW, Phi, ufar, unear, gfar, gnear, slab, rootscr, counter, psig;
     DBuf lam_in, finc, fincnt;  // the tensor-core incoming pass: coefficients, colleague lists
+    DBuf upcnt;                 // the single-precision upward pass: arrivals per expansion slot
 };
 
 struct PassCtx {

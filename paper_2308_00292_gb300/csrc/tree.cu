@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 namespace dmk {
 
@@ -629,16 +630,22 @@ __global__ void k_leaf_octants(int nb, const int8_t *blevel, const int32_t *bsta
 // colleague of T's level-b ancestor (b <= a), or S is a leaf at level a+1
 // touching T (T is then a coarse neighbour of S); pairs can only interact if
 // the boxes are closer than R_b, the support of R_b.
-__device__ __forceinline__ double box_dist2(int la, int ax, int ay, int az, int lb, int bx, int by, int bz) {
-    double Ra = level_R(la), Rb = level_R(lb);
-    double d2 = 0.0;
-    double ca[3] = {(ax + 0.5) * Ra, (ay + 0.5) * Ra, (az + 0.5) * Ra};
-    double cb[3] = {(bx + 0.5) * Rb, (by + 0.5) * Rb, (bz + 0.5) * Rb};
+// Is the gap between box A (level la, cell a*) and box B (level lb, cell b*)
+// below R_lb?  Exact integer arithmetic in units of 2^-L, L = max(la, lb) + 1:
+// the centres are (2 i + 1) 2^(L - l - 1), the half sides 2^(L - l - 1) and
+// R_lb = 2^(L - lb) units (coordinates below 2^22, squares below 2^46).
+__device__ __forceinline__ bool box_within(int la, int ax, int ay, int az, int lb, int bx, int by, int bz) {
+    const int L = (la > lb ? la : lb) + 1, sa = L - la - 1, sb = L - lb - 1;
+    const long long half = (1ll << sa) + (1ll << sb);
+    long long d2 = 0;
+    const int ia[3] = {ax, ay, az}, ib[3] = {bx, by, bz};
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double g = fabs(ca[d] - cb[d]) - 0.5 * (Ra + Rb);
+        const long long ca = (2ll * ia[d] + 1) << sa, cb = (2ll * ib[d] + 1) << sb;
+        const long long g = (ca > cb ? ca - cb : cb - ca) - half;
         if (g > 0) d2 += g * g;
     }
-    return d2;
+    return d2 < (1ll << (2 * (L - lb)));
 }
 
 // FILL = false: count every list (cnt, pairs) and write it to tmp, kNearCap
@@ -662,13 +669,12 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
     long long np = 0;
     int B = T;
     for (int b = a; b >= 0; --b) {
-        double Rb = level_R(b);
         for (int k = 0; k < 27; ++k) {
             int C = bcol[(int64_t)B * 27 + k];
             if (C < 0 || !(bflags[C] & BF_LEAF) || bnsrc[C] == 0) continue;
             int cx, cy, cz;
             morton_decode(key_cell(bkey[C], b), cx, cy, cz);
-            if (box_dist2(a, tx, ty, tz, b, cx, cy, cz) >= Rb * Rb) continue;
+            if (!box_within(a, tx, ty, tz, b, cx, cy, cz)) continue;
             if (FILL || n < kNearCap) out[n] = C;
             np += bnsrc[C];
             ++n;
@@ -676,7 +682,6 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
         B = bparent[B];
         if (B < 0) break;
     }
-    double R1 = level_R(a + 1);
     for (int k = 0; k < 27; ++k) {
         int C = bcol[(int64_t)T * 27 + k];
         if (C < 0 || (bflags[C] & BF_LEAF)) continue;
@@ -689,7 +694,7 @@ __global__ void k_near_lists(int ntl, const int32_t *tleaves, const uint64_t *bk
             if (!(bflags[D] & BF_LEAF) || bnsrc[D] == 0) continue;
             int dx, dy, dz;
             morton_decode(key_cell(bkey[D], a + 1), dx, dy, dz);
-            if (box_dist2(a, tx, ty, tz, a + 1, dx, dy, dz) >= R1 * R1) continue;
+            if (!box_within(a, tx, ty, tz, a + 1, dx, dy, dz)) continue;
             if (FILL || n < kNearCap) out[n] = D;
             np += bnsrc[D];
             ++n;
@@ -754,20 +759,21 @@ __global__ void k_leaf_export(int nb, const uint64_t *bkey, const int8_t *blevel
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-int TreeBuilder::grow_boxes(int64_t need, cudaStream_t st, std::string &err) {
+int TreeBuilder::grow_boxes(int64_t need, cudaStream_t st, std::string &err, size_t keep) {
     if (need <= box_cap) return 0;
     int64_t cap = std::max<int64_t>(need, box_cap * 2);
     cap = std::max<int64_t>(cap, 4096);
-    // box arrays are rebuilt from the root on every pass, so contents need
-    // not survive; reallocate all of them
+    // the arrays a level split writes keep their first `keep` boxes (the
+    // levels built so far, copied device to device); the others are filled
+    // after the boxes are complete, so their contents need not survive
     int rc = 0;
-    rc |= ws.ensure(bkey, cap * sizeof(uint64_t));
-    rc |= ws.ensure(blevel, cap);
-    rc |= ws.ensure(bstart, cap * 4);
-    rc |= ws.ensure(bcount, cap * 4);
-    rc |= ws.ensure(bparent, cap * 4);
-    rc |= ws.ensure(bchild0, cap * 4);
-    rc |= ws.ensure(bcmask, cap);
+    rc |= ws.grow_keep(bkey, cap * sizeof(uint64_t), keep * sizeof(uint64_t), st);
+    rc |= ws.grow_keep(blevel, cap, keep, st);
+    rc |= ws.grow_keep(bstart, cap * 4, keep * 4, st);
+    rc |= ws.grow_keep(bcount, cap * 4, keep * 4, st);
+    rc |= ws.grow_keep(bparent, cap * 4, keep * 4, st);
+    rc |= ws.grow_keep(bchild0, cap * 4, keep * 4, st);
+    rc |= ws.grow_keep(bcmask, cap, keep, st);
     rc |= ws.ensure(bflags, cap);
     rc |= ws.ensure(bnsrc, cap * 4);
     rc |= ws.ensure(bntgt, cap * 4);
@@ -776,9 +782,9 @@ int TreeBuilder::grow_boxes(int64_t need, cudaStream_t st, std::string &err) {
     rc |= ws.ensure(bscr0, cap * 4);
     rc |= ws.ensure(bscr1, cap * 4);
     rc |= ws.ensure(bscr2, (cap + 1) * 4);
+    if (rc & 2) { err = "device-to-device copy of the box arrays failed"; return DMK_ERR_CUDA_I; }
     if (rc) { err = "device allocation failed (boxes)"; return DMK_ERR_OOM_I; }
     box_cap = cap;
-    (void)st;
     return 0;
 }
 
@@ -863,6 +869,12 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
     if (ws.ensure(forced, fcap * sizeof(uint64_t))) { err = "device allocation failed"; return DMK_ERR_OOM_I; }
     CK(cudaMemsetAsync(forced.p, 0, fcap * sizeof(uint64_t), st));
     int64_t est = std::max<int64_t>(4096, 16 * (N / std::max(leaf_cap, 1) + 64) + 2 * (int64_t)nsys);
+    // diagnostic: a smaller first capacity, so that the box arrays grow while
+    // the levels are built (the estimate above leaves that path to rare trees)
+    if (const char *e = std::getenv("DMK_TREE_INITIAL_BOXES")) {
+        const long long v = std::atoll(e);
+        if (v > 0 && box_cap == 0) est = std::max<int64_t>(4096, v);
+    }
     if (int rc = grow_boxes(est, st, err)) return rc;
     rounds = 0;
     bool pushed = false;  // the forced set has been completed on the cell sets
@@ -906,30 +918,9 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
             CK(cudaMemcpyAsync(&total, d_flags + 3, 4, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (total > 0 && nbox + total > box_cap) {
-                // grow and restart this pass with the larger capacity
-                std::vector<char> dummy;
-                int64_t need = (int64_t)(nbox + total) * 2;
-                // preserve the levels built so far by copying through the host
-                size_t nb0 = (size_t)nbox;
-                std::vector<uint64_t> h_key(nb0);
-                std::vector<int8_t> h_lev(nb0);
-                std::vector<int32_t> h_st(nb0), h_ct(nb0), h_par(nb0), h_c0(nb0);
-                std::vector<uint8_t> h_cm(nb0);
-                CK(cudaMemcpy(h_key.data(), bkey.p, nb0 * 8, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_lev.data(), blevel.p, nb0, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_st.data(), bstart.p, nb0 * 4, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_ct.data(), bcount.p, nb0 * 4, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_par.data(), bparent.p, nb0 * 4, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_c0.data(), bchild0.p, nb0 * 4, cudaMemcpyDeviceToHost));
-                CK(cudaMemcpy(h_cm.data(), bcmask.p, nb0, cudaMemcpyDeviceToHost));
-                if (int rc = grow_boxes(need, st, err)) return rc;
-                CK(cudaMemcpy(bkey.p, h_key.data(), nb0 * 8, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(blevel.p, h_lev.data(), nb0, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(bstart.p, h_st.data(), nb0 * 4, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(bcount.p, h_ct.data(), nb0 * 4, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(bparent.p, h_par.data(), nb0 * 4, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(bchild0.p, h_c0.data(), nb0 * 4, cudaMemcpyHostToDevice));
-                CK(cudaMemcpy(bcmask.p, h_cm.data(), nb0, cudaMemcpyHostToDevice));
+                // grow the box arrays, keeping the levels built so far (device to device)
+                const int64_t need = (int64_t)(nbox + total) * 2;
+                if (int rc = grow_boxes(need, st, err, (size_t)nbox)) return rc;
                 la.bkey = (uint64_t *)bkey.p;
                 la.blevel = (int8_t *)blevel.p;
                 la.bstart = (int32_t *)bstart.p;

@@ -1,6 +1,8 @@
 // tree.h -- device buffers and the tree builder of libdmk (internal).
 #pragma once
 
+#include <algorithm>
+
 #include "dmk.h"
 #include "dmk_internal.h"
 
@@ -45,6 +47,27 @@ struct Workspace {
         }
         b.bytes = want;
         live += want;
+        return 0;
+    }
+    // grows b to at least bytes keeping its first keep bytes: a new buffer,
+    // a device-to-device copy on st, then the old buffer is freed once the
+    // copy is done; returns 0 on success, 1 when allocation fails, 2 when the
+    // copy fails (b then keeps its old buffer)
+    int grow_keep(DBuf &b, int64_t bytes, size_t keep, cudaStream_t st) {
+        if (b.p && (int64_t)b.bytes >= bytes) return 0;
+        DBuf nb;
+        if (ensure(nb, bytes)) return 1;
+        keep = std::min(keep, b.bytes);
+        if (keep && (cudaMemcpyAsync(nb.p, b.p, keep, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess)) {
+            release(nb);
+            return 2;
+        }
+        release(b);
+        b.p = nb.p;
+        b.bytes = nb.bytes;
+        nb.p = nullptr;
+        nb.bytes = 0;
         return 0;
     }
     void release(DBuf &b) {
@@ -121,7 +144,7 @@ public:
     DBuf tleaves, nl_cnt, nl_off, nl_src, nl_tmp, pairs;
 
 private:
-    int grow_boxes(int64_t need, cudaStream_t st, std::string &err);
+    int grow_boxes(int64_t need, cudaStream_t st, std::string &err, size_t keep = 0);
 };
 
 }  // namespace dmk

@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("n_launches", ctypes.c_int64), ("near_pairs_inside", ctypes.c_int64),
                 ("local_flops", ctypes.c_int64), ("t_local_ms", ctypes.c_float),
                 ("t_incoming_ms", ctypes.c_float), ("incoming_reads", ctypes.c_int64),
-                ("incoming_flops", ctypes.c_int64), ("t_planewave_ms", ctypes.c_float)]
+                ("incoming_flops", ctypes.c_int64), ("t_planewave_ms", ctypes.c_float),
+                ("near_pairs_screened", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -76,6 +76,8 @@ def test_near_pair_count_matches_kdtree(dmk, oracle_mod, precision):
         assert got == expected
     else:
         assert abs(got - expected) <= 1e-6 * expected + 10
+    # screening tests a subset of the lists' pairs that holds every pair inside
+    assert got <= st["near_pairs_screened"] <= st["near_pairs"]
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -98,6 +100,23 @@ def test_tree_bit_exact_adversarial(dmk, oracle_mod):
     _, lev, cell, _ = run(dmk, x, q, eps=1e-6, leaf_cap=30)
     olev, ocell = oracle_mod.tree(x, eps=1e-6, leaf_cap=30)
     assert np.array_equal(lev, olev) and np.array_equal(cell, ocell)
+
+
+def test_tree_bit_exact_box_growth(dmk, oracle_mod, monkeypatch):
+    """8000 clustered points at leaf capacity 2 make about 9000 boxes.  With
+    the first box capacity lowered to its minimum (4096) the box arrays grow
+    while the levels are built; the levels built before the growth must
+    survive it, so the tree stays bit-exact and the potentials are the same
+    as with the estimated capacity."""
+    x, q = CASES["clustered"]()
+    u0, lev0, cell0, st0 = run(dmk, x, q, eps=1e-6, leaf_cap=2, precision=dmk.DMK_FP64)
+    monkeypatch.setenv("DMK_TREE_INITIAL_BOXES", "1")
+    u1, lev1, cell1, st1 = run(dmk, x, q, eps=1e-6, leaf_cap=2, precision=dmk.DMK_FP64)
+    assert st1["n_boxes"] > 4096
+    olev, ocell = oracle_mod.tree(x, eps=1e-6, leaf_cap=2)
+    assert np.array_equal(lev1, olev) and np.array_equal(cell1, ocell)
+    assert np.array_equal(lev0, olev) and np.array_equal(cell0, ocell)
+    assert np.max(np.abs(u1 - u0)) <= 1e-12 * np.max(np.abs(u0))
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
