@@ -37,13 +37,15 @@
 // that move a contraction's TMEM result into the next operand (a transpose of
 // m'_y and a) store into 32 distinct shared-memory banks.
 //
-// The plane waves of the colleagues are read plane by plane with coalesced
-// loads, eight colleagues in flight at a time; the contractions of plane p
-// overlap the translation of plane p + 1 (the MMAs are asynchronous), and two
-// CTAs share an SM so that one CTA's barriers and MMA waits overlap the other
-// CTA's work.  All threads of a CTA advance together between block barriers;
-// thread 0 issues the MMAs, and the box's coefficients leave through a TMA
-// bulk store (cp.async.bulk, shared to global).  Every wait is bounded.
+// Warps 0-6 read the plane waves of the colleagues plane by plane with
+// coalesced loads, eight colleagues in flight at a time.  Warp 7 issues the
+// MMAs (one thread: each tcgen05.mma takes tens of cycles to issue, so the
+// issue of plane p overlaps the translation of plane p + 1 instead of holding
+// up a translating warp) and asks for the colleagues' plane p + 2 in L2 with
+// bulk prefetches.  Two CTAs share an SM so that one CTA's barriers and MMA
+// waits overlap the other CTA's work.  All threads of a CTA advance together
+// between block barriers, and the box's coefficients leave through a TMA bulk
+// store (cp.async.bulk, shared to global).  Every wait is bounded.
 #include "incoming.h"
 #include "tc.h"
 
@@ -151,8 +153,8 @@ __global__ void __launch_bounds__(kIThreads, 2)
     bool mhas[S::NMODE];
 #pragma unroll
     for (int k = 0; k < S::NMODE; ++k) {
-        const int r = tid + k * kIThreads;
-        mhas[k] = r < N1 * N1;
+        const int r = tid + k * kIWorkers;
+        mhas[k] = tid < kIWorkers && r < N1 * N1;
         const int my = mhas[k] ? r / N1 : 0, mx = mhas[k] ? r % N1 : 0;
         moff[k] = my * MXP + mx;
         const int vx = mx - NF, vy = my - NF;
@@ -209,6 +211,13 @@ __global__ void __launch_bounds__(kIThreads, 2)
         if (tid < 27) s_slot[tid] = finc[(size_t)f * 27 + tid] >> 5;
         __syncthreads();
         const int ncol = s_ncol, level = s_level;
+        constexpr uint32_t kPlaneBytes = (uint32_t)(N1 * MXP * sizeof(float2));  // a multiple of 16
+        // warp 7 starts the first two planes of every colleague on their way to L2
+        if (warp == 7 && lane < ncol) {
+            const float2 *pb = phi + (size_t)s_slot[lane] * BOXFL2;
+            tc::prefetch_l2(pb, kPlaneBytes);
+            if (NH > 1) tc::prefetch_l2(pb + N1 * MXP, kPlaneBytes);
+        }
         // phase of colleague j for the mode residues r = (m_x, m_y, m_z) mod 3: omega^kk,
         // kk = r . delta_j mod 3 with delta = (c_B - c_S) / R, kept as (kk != 0, +1 / -1 / 0
         // for kk = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3 / 2) D
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(kIThreads, 2)
             float2 Ta[S::NMODE], Ua[S::NMODE], Da[S::NMODE];
 #pragma unroll
             for (int k = 0; k < S::NMODE; ++k) Ta[k] = Ua[k] = Da[k] = make_float2(0.f, 0.f);
-            if (it < NH) {
+            if (it < NH && tid < kIWorkers) {
                 const int rz9 = 9 * (it % 3);
                 for (int j0 = 0; j0 < ncol; j0 += CB) {
                     float2 v[CB][S::NMODE];
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kIThreads, 2)
                 for (int k = 0; k < S::NMODE; ++k) {
                     if (!mhas[k]) continue;
                     const float w = cz * wscale * wrow[msq[k] + it * it];
-                    psi[tid + k * kIThreads] = make_float2(w * (Ta[k].x - 1.5f * Ua[k].x - kH * Da[k].y),
+                    psi[tid + k * kIWorkers] = make_float2(w * (Ta[k].x - 1.5f * Ua[k].x - kH * Da[k].y),
                                                           w * (Ta[k].y - 1.5f * Ua[k].y + kH * Da[k].x));
                 }
             }
@@ -381,8 +390,12 @@ __global__ void __launch_bounds__(kIThreads, 2)
             tc::fence_proxy_async();
             tc::fence_before_sync();
             __syncthreads();
-            // ---- G. the contractions of this step (one thread)
-            if (tid == 0) {
+            // ---- G. the contractions of this step, issued by one thread of warp 7 while
+            // warps 0-6 go on to translate the next plane; warp 7 first prefetches the
+            // colleagues' plane it + 2 into L2
+            if (warp == 7 && it + 2 < NH && lane < ncol)
+                tc::prefetch_l2(phi + (size_t)s_slot[lane] * BOXFL2 + (size_t)(it + 2) * (N1 * MXP), kPlaneBytes);
+            if (warp == 7 && lane == 0) {
                 tc::fence_after_sync();
                 const uint32_t bH = tc::smem_addr(Bw), bL = bH + 32 * S::K * 4;
                 if (it < NH) {

@@ -9,6 +9,7 @@
 namespace dmk {
 
 constexpr int kIThreads = 256;  // threads of a CTA; two CTAs share an SM
+constexpr int kIWorkers = 224;  // warps 0-6 translate; warp 7 issues the MMAs and prefetches
 constexpr int kITmem = 256;     // TMEM columns of a CTA
 
 // Shapes of the tensor-core incoming pass for Chebyshev order P and Fourier
@@ -20,7 +21,7 @@ template <int P, int NF> struct InShape {
     static constexpr int K = 16;                        // contraction length: m' = 0..NF, padded
     static constexpr int NZ = 2 * P * P;                // rows (class, a, b) of the last contraction
     static constexpr int TILE_FL = 128 * K;             // one part (hi or lo) of a 128 x 16 operand
-    static constexpr int NMODE = (N1 * N1 + kIThreads - 1) / kIThreads;  // plane modes per thread
+    static constexpr int NMODE = (N1 * N1 + kIWorkers - 1) / kIWorkers;  // plane modes per translating thread
     static constexpr int CB = 8;                        // colleagues whose loads are in flight together
     static constexpr int LSTR = (P * P * P + 3) & ~3;   // floats per box of the output
     static constexpr size_t O_AX = 0;                                     // [hi, lo]
