@@ -209,9 +209,12 @@ def kernel_work(stats: dict, prm: dict, n_src: int, n_tgt: int) -> dict:
     ev = 2.0 * p ** 3 * n_tgt
     w["k_local"] = [("leaf evaluation", ev, "tensor"),
                     ("p2c shifts and sums", max(float(stats["local_flops"]) - ev, 0.0), "fp32")]
-    pairs, inside = stats["near_pairs"], stats["near_pairs_inside"]
-    w["k_near"] = [("residual pairs", float(pairs * NEAR_SCREEN_FLOPS + inside * (near_flops_per_pair(prm["q_degree"])
-                                                                          - NEAR_SCREEN_FLOPS)), "fp32")]
+    # the near field: the distance screen of every pair the kernel tests (the
+    # sources left after culling against each target group's bounding box),
+    # and the residual kernel of every pair inside R_L
+    screened, inside = stats["near_pairs_screened"], stats["near_pairs_inside"]
+    w["k_near"] = [("screened pairs and residual kernel", float(screened * NEAR_SCREEN_FLOPS + inside * (
+        near_flops_per_pair(prm["q_degree"]) - NEAR_SCREEN_FLOPS)), "fp32")]
     return w
 
 

@@ -289,37 +289,45 @@ __global__ void k_roots(int nsys, const int64_t *off, uint64_t *bkey, int8_t *bl
     bparent[s] = -1;
 }
 
+// eight threads per box: thread j > 0 finds by binary search the first point
+// of octant j in the box's sorted range, so the searches run side by side
 __global__ void k_level_split(LevelArgs a, int level, int lstart, int lcount, int leaf_cap, int max_level) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= lcount) return;
-    int b = lstart + i;
-    int32_t s = a.bstart[b], c = a.bcount[b], e = s + c;
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gi >> 3), j = (int)(gi & 7);
+    const bool valid = i < lcount;
+    int32_t s = 0, e = 0;
     bool split = false;
-    if (level < max_level) {
-        const uint64_t k = a.bkey[b];
-        if (c > leaf_cap && a.keys[s] != a.keys[e - 1]) split = true;
-        else if (hset_contains(a.forced, a.fcap, forced_key(level, key_cell(k, level), key_sys(k, level), a.kb)))
-            split = true;
-    }
-    int32_t *off = a.off9 + (int64_t)i * 9;
-    int n = 0;
-    if (split) {
-        int shift = 3 * (a.kb - 1 - level);
-        off[0] = s;
-        int32_t lo = s;
-        for (int oc = 1; oc < 8; ++oc) {
-            int32_t l = lo, h = e;  // first index with octant >= oc
-            while (l < h) {
-                int32_t m = (l + h) >> 1;
-                if ((int)((a.keys[m] >> shift) & 7ull) < oc) l = m + 1; else h = m;
-            }
-            off[oc] = l;
-            lo = l;
+    if (valid) {
+        const int b = lstart + i;
+        s = a.bstart[b];
+        e = s + a.bcount[b];
+        if (level < max_level) {
+            const uint64_t k = a.bkey[b];
+            if (e - s > leaf_cap && a.keys[s] != a.keys[e - 1]) split = true;
+            else if (hset_contains(a.forced, a.fcap, forced_key(level, key_cell(k, level), key_sys(k, level), a.kb)))
+                split = true;
         }
-        off[8] = e;
-        for (int oc = 0; oc < 8; ++oc) n += off[oc + 1] > off[oc];
     }
-    a.cnt[i] = n;
+    int32_t l = s;  // first index with octant >= j (j = 0: the box's start)
+    if (split && j > 0) {
+        const int shift = 3 * (a.kb - 1 - level);
+        int32_t h = e;
+        while (l < h) {
+            const int32_t m = (l + h) >> 1;
+            if ((int)((a.keys[m] >> shift) & 7ull) < j) l = m + 1; else h = m;
+        }
+    }
+    // octant j is non-empty when the next boundary lies beyond this one
+    int32_t next = __shfl_down_sync(0xffffffffu, l, 1, 8);
+    if (j == 7) next = e;
+    const unsigned ne = __ballot_sync(0xffffffffu, split && next > l);
+    if (!valid) return;
+    int32_t *off = a.off9 + (int64_t)i * 9;
+    if (split) {
+        off[j] = l;
+        if (j == 7) off[8] = e;
+    }
+    if (j == 0) a.cnt[i] = __popc((ne >> (threadIdx.x & 24)) & 0xffu);
 }
 
 __global__ void k_level_emit(LevelArgs a, int level, int lstart, int lcount, int next_start) {
@@ -592,36 +600,6 @@ __global__ void k_point_local(int nb, const uint64_t *bkey, const int8_t *blevel
             lo.w = 0.f;
             plocal_lo[k] = lo;
         }
-    }
-}
-
-// octant ranges of every leaf one level below it (the refinement of Sec. 3.3):
-// a warp per leaf counts its points per octant digit of the point keys
-__global__ void k_leaf_octants(int nb, const int8_t *blevel, const int32_t *bstart, const int32_t *bcount,
-                               const uint8_t *bflags, const uint64_t *skeys, int kb, int32_t *loct) {
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= nb || !(bflags[b] & BF_LEAF)) return;
-    const int lane = threadIdx.x & 31, l = blevel[b];
-    const int32_t s = bstart[b], e = s + bcount[b];
-    if (l + 1 > kb) {
-        // the key has no digit below this level: the leaf is not refined (-1)
-        if (lane < 8) loct[8 * (int64_t)b + lane] = lane == 0 ? -1 : e - s;
-        return;
-    }
-    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int32_t k = s + lane; k < e; k += 32) {
-        const int o = (int)((skeys[k] >> (3 * (kb - l - 1))) & 7ull);
-#pragma unroll
-        for (int d = 0; d < 8; ++d) cnt[d] += o == d ? 1 : 0;
-    }
-    int run = 0;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        int c = cnt[d];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-        run += c;
-        if (lane == 0) loct[8 * (int64_t)b + d] = run;
     }
 }
 
@@ -911,7 +889,7 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
                          (int32_t *)lvl_off9.p, (int32_t *)lvl_cnt.p, (int32_t *)lvl_excl.p,
                          (const uint64_t *)forced.p, fcap, kb};
             ::dmk::launch_tick();
-            k_level_split<<<nblk(lc, 128), 128, 0, st>>>(la, l, lt_start[l], lc, leaf_cap, max_level);
+            k_level_split<<<nblk((int64_t)lc * 8, 128), 128, 0, st>>>(la, l, lt_start[l], lc, leaf_cap, max_level);
             scan_exclusive_i32((int32_t *)lvl_cnt.p, (int32_t *)lvl_excl.p, lc, d_flags + 3, scan_tmp.p,
                                scan_tmp.bytes, st);
             int total = 0;
@@ -1075,14 +1053,6 @@ int TreeBuilder::build(const double *src, int64_t ns, const double *charges, con
         }
 
     // ---- octant ranges of the leaves (near-field refinement)
-    if (ws.ensure(loct, (int64_t)nb * 32)) {
-        err = "device allocation failed";
-        return DMK_ERR_OOM_I;
-    }
-    ::dmk::launch_tick();
-    k_leaf_octants<<<nblk(nb, 4), 128, 0, st>>>(nb, (const int8_t *)blevel.p, (const int32_t *)bstart.p,
-                                                (const int32_t *)bcount.p, (const uint8_t *)bflags.p, sorted_keys,
-                                                kb, (int32_t *)loct.p);
 
     // ---- near-field lists over target leaves
     int32_t *istl = isleaf;  // reuse: 1 for target leaves

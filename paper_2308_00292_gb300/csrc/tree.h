@@ -133,12 +133,6 @@ public:
     // incoming boxes in box order: bfin[box] = its index among them or -1,
     // fin2box[index] = the box
     DBuf bfin, fin2box;
-    // the leaves refined once more (Sec. 3.3): for leaf b, loct[8 b + o] is the
-    // number of its points in octants 0 .. o at level blevel[b] + 1 (points are
-    // in Morton order, so octant o is the range [loct[8 b + o - 1], loct[8 b + o])
-    // of the leaf's points); loct[8 b] = -1 marks a leaf whose keys have no
-    // digit below its level (it is not refined)
-    DBuf loct;
     DBuf lvl_off9, lvl_cnt, lvl_excl;
     // near-field lists
     DBuf tleaves, nl_cnt, nl_off, nl_src, nl_tmp, pairs;
