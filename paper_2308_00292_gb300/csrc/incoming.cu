@@ -219,13 +219,13 @@ __global__ void __launch_bounds__(kIThreads, 2)
             if (NH > 1) tc::prefetch_l2(pb + N1 * MXP, kPlaneBytes);
         }
         // phase of colleague j for the mode residues r = (m_x, m_y, m_z) mod 3: omega^kk,
-        // kk = r . delta_j mod 3 with delta = (c_B - c_S) / R, kept as (kk != 0, +1 / -1 / 0
-        // for kk = 1 / 2 / 0) for the sum T - 1.5 U + i (sqrt3 / 2) D
+        // kk = r . delta_j mod 3 with delta = (c_B - c_S) / R, as (cos, sin) of 2 pi kk / 3
         for (int t = tid; t < 27 * ncol; t += kIThreads) {
             const int j = t / 27, r = t % 27, k = finc[(size_t)f * 27 + j] & 31;
             const int dx = (4 - k / 9) % 3, dy = (4 - (k / 3) % 3) % 3, dz = (4 - k % 3) % 3;
             const int kk = ((r % 3) * dx + ((r / 3) % 3) * dy + (r / 9) * dz) % 3;
-            ud[t] = make_float2(kk ? 1.f : 0.f, kk == 1 ? 1.f : (kk == 2 ? -1.f : 0.f));
+            constexpr float kH = 0.86602540378443864676f;
+            ud[t] = kk == 0 ? make_float2(1.f, 0.f) : make_float2(-0.5f, kk == 1 ? kH : -kH);
         }
         const float *wrow = tb.wl ? tb.wl + (size_t)level * (3 * NF * NF + 1) : tb.w;
         const float wscale = tb.wl ? 1.f : (float)(1u << level);
@@ -234,10 +234,10 @@ __global__ void __launch_bounds__(kIThreads, 2)
         __syncthreads();
 
         for (int it = 0; it < NH + 2; ++it) {
-            // ---- A. translation of plane it: partial sums over the colleagues
-            float2 Ta[S::NMODE], Ua[S::NMODE], Da[S::NMODE];
+            // ---- A. translation of plane it: sum over the colleagues of omega^kk Phi
+            float2 Ps[S::NMODE];
 #pragma unroll
-            for (int k = 0; k < S::NMODE; ++k) Ta[k] = Ua[k] = Da[k] = make_float2(0.f, 0.f);
+            for (int k = 0; k < S::NMODE; ++k) Ps[k] = make_float2(0.f, 0.f);
             if (it < NH && tid < kIWorkers) {
                 const int rz9 = 9 * (it % 3);
                 for (int j0 = 0; j0 < ncol; j0 += CB) {
@@ -258,12 +258,8 @@ __global__ void __launch_bounds__(kIThreads, 2)
 #pragma unroll
                         for (int k = 0; k < S::NMODE; ++k) {
                             const float2 c = uj[mres[k]];
-                            Ta[k].x += v[jj][k].x;
-                            Ta[k].y += v[jj][k].y;
-                            Ua[k].x = fmaf(c.x, v[jj][k].x, Ua[k].x);
-                            Ua[k].y = fmaf(c.x, v[jj][k].y, Ua[k].y);
-                            Da[k].x = fmaf(c.y, v[jj][k].x, Da[k].x);
-                            Da[k].y = fmaf(c.y, v[jj][k].y, Da[k].y);
+                            Ps[k].x = fmaf(-c.y, v[jj][k].y, fmaf(c.x, v[jj][k].x, Ps[k].x));
+                            Ps[k].y = fmaf(c.y, v[jj][k].x, fmaf(c.x, v[jj][k].y, Ps[k].y));
                         }
                     }
                 }
@@ -276,13 +272,11 @@ __global__ void __launch_bounds__(kIThreads, 2)
             // of plane it - 2 -> the second contraction's plane it - 2
             if (it < NH) {
                 const float cz = it == 0 ? 1.f : 2.f;  // m_z < 0 through Hermitian symmetry
-                constexpr float kH = 0.86602540378443864676f;
 #pragma unroll
                 for (int k = 0; k < S::NMODE; ++k) {
                     if (!mhas[k]) continue;
                     const float w = cz * wscale * wrow[msq[k] + it * it];
-                    psi[tid + k * kIWorkers] = make_float2(w * (Ta[k].x - 1.5f * Ua[k].x - kH * Da[k].y),
-                                                          w * (Ta[k].y - 1.5f * Ua[k].y + kH * Da[k].x));
+                    psi[tid + k * kIWorkers] = make_float2(w * Ps[k].x, w * Ps[k].y);
                 }
             }
             {
