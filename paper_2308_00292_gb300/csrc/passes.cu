@@ -546,8 +546,12 @@ __global__ void __launch_bounds__(AntShape<P>::NT, 3) k_anterp(TreeView tv, cons
         As[i] = m <= n && m < P ? Atab[h * P * P + n * P + m] : 0.f;
     }
     // warp 0: the children of box X -- the point ranges of its leaf children
-    // with sources (when ranges is set) and its non-leaf children with sources
+    // with sources (when ranges is set) and its non-leaf children with sources.
+    // The leading barrier: every warp has read the previous box's s_nnl and
+    // s_kids (a box without non-leaf children reaches here with no barrier
+    // after that read) before warp 0 overwrites them
     auto children = [&](int X, bool ranges) {
+        __syncthreads();
         if (tid < 32) {
             const bool selfleaf = (tv.bflags[X] & BF_LEAF) != 0;
             const unsigned cm = selfleaf ? 0u : tv.bcmask[X];
@@ -594,6 +598,9 @@ __global__ void __launch_bounds__(AntShape<P>::NT, 3) k_anterp(TreeView tv, cons
         __syncthreads();
     };
     for (;;) {
+        // every thread has read the previous item (a skipped item comes straight
+        // back here) before thread 0 takes the next
+        __syncthreads();
         if (tid == 0) s_item = atomicAdd(ctr, 1);
         __syncthreads();
         const int slot = s_item;
@@ -1017,22 +1024,25 @@ constexpr int kECH = 32;  // targets per evaluation chunk
 
 // One axis of a Chebyshev re-expansion on a P^3 array: out[.., m, ..] =
 // sum_{n >= m} A[n][m] in[.., n, ..] along axis AX (0 = z, the fastest index,
-// 1 = y, 2 = x).  Each thread owns two rows (P outputs each) in registers and
-// reads A from shared memory once per pair of multiply-adds.
+// 1 = y, 2 = x).  A is P rows of PA = (P + 3) & ~3 entries, zero above the
+// diagonal (m > n), so single precision reads a row's entries four at a time.
+// Each thread owns one row (two when the rows outnumber the threads) of P
+// outputs in registers.
+template <typename T, int P> constexpr int shift_pad() { return (P + 3) & ~3; }
 template <typename T, int P, int AX, int NT>
 __device__ __forceinline__ void shift_pass(const T *__restrict__ A, const T *in, T *out) {
+    constexpr int PA = shift_pad<T, P>();
     constexpr int s = AX == 0 ? 1 : (AX == 1 ? P : P * P);
     if constexpr (P > 20) {  // large orders: one output per thread (registers)
         for (int i = threadIdx.x; i < P * P * P; i += NT) {
             const int m = AX == 0 ? i % P : (AX == 1 ? (i / P) % P : i / (P * P));
             const int b = i - m * s;
             T acc = 0;
-            for (int n = m; n < P; ++n) acc += A[n * P + m] * in[b + n * s];
+            for (int n = m; n < P; ++n) acc += A[n * PA + m] * in[b + n * s];
             out[i] = acc;
         }
         return;
     }
-    // two rows per thread only when the rows outnumber the threads
     constexpr bool TWO = P * P > NT;
     constexpr int RR = P * P, H = TWO ? (RR + 1) / 2 : RR;
     auto base = [](int r) { return AX == 0 ? r * P : (AX == 1 ? (r / P) * P * P + r % P : r); };
@@ -1040,17 +1050,35 @@ __device__ __forceinline__ void shift_pass(const T *__restrict__ A, const T *in,
         const int r0 = t, r1 = t + H;
         const bool has1 = TWO && r1 < RR;
         const int b0 = base(r0), b1 = has1 ? base(r1) : b0;
-        T o0[P], o1[P];
+        T o0[PA], o1[PA];
 #pragma unroll
-        for (int m = 0; m < P; ++m) o0[m] = o1[m] = (T)0;
+        for (int m = 0; m < PA; ++m) o0[m] = o1[m] = (T)0;
 #pragma unroll
         for (int n = 0; n < P; ++n) {
             const T v0 = in[b0 + n * s], v1 = in[b1 + n * s];
+            if constexpr (sizeof(T) == 4) {
+                const float4 *Ar = reinterpret_cast<const float4 *>(A + n * PA);
 #pragma unroll
-            for (int m = 0; m <= n; ++m) {
-                const T a = A[n * P + m];
-                o0[m] += a * v0;
-                if (TWO) o1[m] += a * v1;
+                for (int m4 = 0; m4 <= n / 4; ++m4) {
+                    const float4 w = Ar[m4];
+                    o0[4 * m4] += w.x * v0;
+                    o0[4 * m4 + 1] += w.y * v0;
+                    o0[4 * m4 + 2] += w.z * v0;
+                    o0[4 * m4 + 3] += w.w * v0;
+                    if (TWO) {
+                        o1[4 * m4] += w.x * v1;
+                        o1[4 * m4 + 1] += w.y * v1;
+                        o1[4 * m4 + 2] += w.z * v1;
+                        o1[4 * m4 + 3] += w.w * v1;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m <= n; ++m) {
+                    const T a = A[n * PA + m];
+                    o0[m] += a * v0;
+                    if (TWO) o1[m] += a * v1;
+                }
             }
         }
 #pragma unroll
@@ -1456,7 +1484,14 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
         tc::fence_after_sync();
     }
     load_hs<T, P, NF>(tb, hs);
-    for (int i = tid; i < 2 * P * P; i += kLThreads) As[i] = tb.A[i];
+    {
+        // the shift matrices with rows padded to shift_pad entries, zero above the diagonal
+        constexpr int PA = shift_pad<T, P>();
+        for (int i = tid; i < 2 * P * PA; i += kLThreads) {
+            const int h = i / (P * PA), n = (i / PA) % P, m = i % PA;
+            As[i] = (m < P && m <= n) ? tb.A[h * P * P + n * P + m] : (T)0;
+        }
+    }
     const size_t pstride = (size_t)N1 * N1 * NHP;
     const T invR = (T)(double)(1u << level);
     const T kH = (T)0.86602540378443864676;  // sqrt(3)/2
@@ -1508,21 +1543,41 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
             int gnr = 0;
             if (kTC && level > 0) {
                 __syncthreads();
-                if (tid == 0) {
-                    int n = 0, off = 0, nt = 0;
-                    for (int i = g0; i < g1; ++i) {
+                if (tid < 32) {
+                    // warp 0, a lane per sibling (at most eight): the leaves with
+                    // targets, their point ranges in sibling order
+                    const int i = g0 + tid;
+                    bool in = false;
+                    int st0 = 0, ct = 0, ntg = 0;
+                    if (tid < 8 && i < g1) {
                         const int b = lstart + i;
                         const uint8_t f = tv.bflags[b];
-                        if (!(f & BF_LEAF) || (!lam_in && (f & BF_FIN)) || tv.bntgt[b] == 0) continue;
-                        s_grs[n] = tv.bstart[b];
-                        s_gro[n] = off;
-                        off += tv.bcount[b];
-                        nt += tv.bntgt[b];
-                        ++n;
+                        ntg = tv.bntgt[b];
+                        in = (f & BF_LEAF) && !(!lam_in && (f & BF_FIN)) && ntg > 0;
+                        if (in) {
+                            st0 = tv.bstart[b];
+                            ct = tv.bcount[b];
+                        }
                     }
-                    s_gro[n] = off;
-                    s_gnr = n;
-                    s_gntgt = nt;
+                    const unsigned inm = __ballot_sync(0xffffffffu, in);
+                    int off = in ? ct : 0, nt = in ? ntg : 0;
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, off, o);
+                        if (tid >= o) off += v;
+                        nt += __shfl_xor_sync(0xffffffffu, nt, o);
+                    }
+                    const int k = __popc(inm & ((1u << tid) - 1u));
+                    if (in) {
+                        s_grs[k] = st0;
+                        s_gro[k] = off - ct;
+                    }
+                    if (tid == 7) {
+                        const int n = __popc(inm);
+                        s_gro[n] = off;
+                        s_gnr = n;
+                        s_gntgt = nt;
+                    }
                 }
                 __syncthreads();
                 gnr = s_gnr;
@@ -1714,11 +1769,12 @@ __global__ void __launch_bounds__(kLThreads, 1) k_local(TreeView tv, DevTables<T
                     }
                     const int oc = (int)(tv.bkey[B] & 7ull);
                     // child coefficient b_m = sum_{n >= m} A_s[n][m] a_n along z, then y, then x
-                    shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * P, Pl, b1);
+                    constexpr int PA = shift_pad<T, P>();
+                    shift_pass<T, P, 0, kLThreads>(As + ((oc >> 2) & 1) * P * PA, Pl, b1);
                     __syncthreads();
-                    shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * P, b1, b0);
+                    shift_pass<T, P, 1, kLThreads>(As + ((oc >> 1) & 1) * P * PA, b1, b0);
                     __syncthreads();
-                    shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * P, b0, Ls);
+                    shift_pass<T, P, 2, kLThreads>(As + (oc & 1) * P * PA, b0, Ls);
                 }
                 __syncthreads();
                 // ---- incoming expansion from F_out colleagues -> Chebyshev coefficients,
@@ -2397,7 +2453,7 @@ static int run_passes_P(PassCtx &cx, std::string &err) {
                                          tcore ? (size_t)LS::TC_BUF2 * sizeof(float) : (size_t)0);
         cudaEventRecord(cx.ev[6], st);
         BufLayout lay = make_layout({P3 * sizeof(T), psi_bytes, t1_bytes, (size_t)P * NH * sizeof(T),
-                                     (size_t)6 * kECH * P * sizeof(T), (size_t)2 * P * P * sizeof(T),
+                                     (size_t)6 * kECH * P * sizeof(T), (size_t)2 * P * shift_pad<T, P>() * sizeof(T),
                                      P3 * sizeof(T)},
                                     smem_limit - 20480);
         if (all_smem<T, P>() && !layout_in_smem(lay)) {
