@@ -241,6 +241,26 @@ def test_full_size_clustered_sampled(dmk, oracle_mod):
         assert rel(u[idx], ref) < 1e-6, (prec, rel(u[idx], ref))
 
 
+def test_full_size_repeated_evaluations_identical(dmk):
+    """The benchmark's 1e7-point clustered workload evaluated 24 times on one
+    mixed plan: every evaluation equals the first bit for bit (the pass is
+    deterministic).  Persistent kernels whose CTAs share work through
+    counters can race only now and then; repeated evaluations are where such
+    a race shows (one did, in about one evaluation in ten)."""
+    cfg = inputs.CONFIGS["laplace3d_clustered_n1e7"]
+    x, q = inputs.make(**cfg)
+    xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+    with dmk.Plan(cfg["eps"], precision=dmk.DMK_MIXED, leaf_cap=cfg["leaf_cap"]) as plan:
+        first = plan.eval(xd, qd)
+        out = torch.empty_like(first)
+        bad = []
+        for k in range(24):
+            plan.eval(xd, qd, out=out)
+            if not torch.equal(out, first):
+                bad.append(k)
+    assert not bad, bad
+
+
 def test_full_size_clustered_sampled_eps1e9(dmk, oracle_mod):
     """The same 1e7-point clustered cloud at eps = 1e-9 (the workload's second
     precision; the FP64 path, since single precision cannot reach it): rel-L2
