@@ -429,9 +429,12 @@ __device__ __forceinline__ void anterpolate_pipe(const TreeView &tv, const doubl
             }
         } else if (tid < S::NIT) {
             const int np = min(kCH, ntot - p0);
-            float c0[P], c1[P];
+            // the moments of rows b0 and b0 + 1 as pairs of consecutive c, so that
+            // the packed FMA (two lanes of a 64-bit register pair, each rounded
+            // like fmaf) takes the T_c(z) pairs as they come from shared memory
+            float2 c0[PS / 2], c1[PS / 2];
 #pragma unroll
-            for (int k = 0; k < P; ++k) c0[k] = c1[k] = 0.f;
+            for (int k = 0; k < PS / 2; ++k) c0[k] = c1[k] = make_float2(0.f, 0.f);
             // two points per step (a row past np is staged as zeros)
             for (int jj = 0; jj < np; jj += 2) {
                 const float *X0 = cur + jj * PS, *Y0 = cur + (kCH + jj) * PS;
@@ -440,26 +443,25 @@ __device__ __forceinline__ void anterpolate_pipe(const TreeView &tv, const doubl
                 const float xa0 = X0[a], xa1 = X0[PS + a];
                 const float s00 = xa0 * Y0[b0], s01 = has1 ? xa0 * Y0[b0 + 1] : 0.f;
                 const float s10 = xa1 * Y0[PS + b0], s11 = has1 ? xa1 * Y0[PS + b0 + 1] : 0.f;
+                const float2 d00 = make_float2(s00, s00), d01 = make_float2(s01, s01);
+                const float2 d10 = make_float2(s10, s10), d11 = make_float2(s11, s11);
 #pragma unroll
                 for (int c4 = 0; c4 < PS / 4; ++c4) {
                     const float4 z = Z0[c4], y = Z1[c4];
-                    const float za[4] = {z.x, z.y, z.z, z.w}, zb[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = 4 * c4 + q;
-                        if (k < P) {
-                            c0[k] = fmaf(s10, zb[q], fmaf(s00, za[q], c0[k]));
-                            c1[k] = fmaf(s11, zb[q], fmaf(s01, za[q], c1[k]));
-                        }
-                    }
+                    const float2 za0 = make_float2(z.x, z.y), za1 = make_float2(z.z, z.w);
+                    const float2 zb0 = make_float2(y.x, y.y), zb1 = make_float2(y.z, y.w);
+                    c0[2 * c4] = __ffma2_rn(d10, zb0, __ffma2_rn(d00, za0, c0[2 * c4]));
+                    c0[2 * c4 + 1] = __ffma2_rn(d10, zb1, __ffma2_rn(d00, za1, c0[2 * c4 + 1]));
+                    c1[2 * c4] = __ffma2_rn(d11, zb0, __ffma2_rn(d01, za0, c1[2 * c4]));
+                    c1[2 * c4 + 1] = __ffma2_rn(d11, zb1, __ffma2_rn(d01, za1, c1[2 * c4 + 1]));
                 }
             }
             // this thread's own rows of acc: no other thread touches them
             float *r0 = acc + (a * P + b0) * P;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
-                r0[k] += c0[k];
-                if (has1) r0[P + k] += c1[k];
+                r0[k] += (k & 1) ? c0[k >> 1].y : c0[k >> 1].x;
+                if (has1) r0[P + k] += (k & 1) ? c1[k >> 1].y : c1[k >> 1].x;
             }
         }
         __syncthreads();
@@ -529,7 +531,7 @@ __device__ __forceinline__ void shift_pencils(const float *A, const float *in, f
 // for another, and every box's sum is formed by one CTA in octant order, so
 // the result does not depend on scheduling.  cnt must be zero on entry.
 template <int P>
-__global__ void __launch_bounds__(AntShape<P>::NT, 3) k_anterp(TreeView tv, const float *Atab, int nslots,
+__global__ void __launch_bounds__(AntShape<P>::NT, 2) k_anterp(TreeView tv, const float *Atab, int nslots,
                                                             const int32_t *slot2box, float *M, int *ctr, int *cnt) {
     using S = AntShape<P>;
     constexpr int P3 = S::P3, PS = S::PS;
