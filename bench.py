@@ -123,19 +123,24 @@ class ClockSampler:
 NEAR_SCREEN_FLOPS = 8  # distance of a candidate pair: 3 differences, 3 squares, 2 adds
 
 
-# DRAM bytes per algorithmic unit, from one ncu capture of every k_local and
-# k_near launch of an evaluation of the 2e6-point clustered workload (profiles/
-# dram_traffic_laplace3d_clustered_n2e6.md), each valid only for the kernel
-# source it was taken on: kernel -> (source file, its sha256, bytes per unit)
+# DRAM bytes per unit of work, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of every kernel launch of an evaluation of the
+# 2e6-point clustered workload (profiles/dram_traffic_laplace3d_clustered_n2e6.md),
+# each valid only for the kernel source it was taken on:
+# kernel -> (source file, its sha256, bytes per unit, the unit)
 TRAFFIC = {
-    # bytes per algorithmic flop
-    "k_local": ("paper_2308_00292_gb300/csrc/passes.cu",
-                "6c5879d89bc324243013b044981eebeadc2bbadc368f8c5b0c170913fc313ed5",
-                (1413.1e6 + 1110.7e6) / 7.106e10),
-    # bytes per candidate pair
     "k_near": ("paper_2308_00292_gb300/csrc/near.cu",
-               "da5054e095dbfb3012a473a0d690619f48e9e42b21dd55c41fc453b0aadca925",
-               (74.25e6 + 7.45e6) / 4.693e9),
+               "112cd3947ab28d2b05e8f021493f6e6ff7889daaac1e6856d8eecea9b7998034",
+               (74050560 + 9337344) / 2296972300, "near_pairs_screened"),
+    "k_local": ("paper_2308_00292_gb300/csrc/passes.cu",
+                "0f4bf4204d6232a6b711d373f96deb4ffb1f235a578e7f7b72006c9f56c630c3",
+                (980.77e6 + 120.51e6) / 45739717602, "local_flops"),
+    "k_upward": ("paper_2308_00292_gb300/csrc/passes.cu",
+                 "0f4bf4204d6232a6b711d373f96deb4ffb1f235a578e7f7b72006c9f56c630c3",
+                 (127476992 + 192137984) / 2000000, "n_points"),
+    "k_incoming": ("paper_2308_00292_gb300/csrc/incoming.cu",
+                   "0ffb113e5a55fd71b119a1b20be0f6c40b1aba711c9d70abdd70a81941f26762",
+                   (747262208 + 652316928) / 1218832664, "hbm_bytes"),
 }
 
 
@@ -144,7 +149,7 @@ def traffic_per_unit(kernel: str):
     import hashlib
     if kernel not in TRAFFIC:
         return None
-    src, sha_want, per_unit = TRAFFIC[kernel]
+    src, sha_want, per_unit, _ = TRAFFIC[kernel]
     try:
         with open(os.path.join(ROOT, src), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -754,12 +759,14 @@ def run_ours(args, rank, world, local_rank):
             DFMA_MEASURED_TFLOPS, FFMA_MEASURED_MHZ, sm_mhz)
         work = {k: [(nm, a, "hbm" if kd == "hbm" else "fp64") for nm, a, kd in v] for k, v in work.items()}
     kernels = rooflines(work, times, peaks)
-    # the traffic captured by ncu for the kernel whose source it was taken on
-    for k in ("k_local", "k_near"):
-        if k in kernels:
+    # the traffic captured by ncu for the kernel whose source it was taken on,
+    # scaled by the kernel's units of work in this evaluation
+    units = {"near_pairs_screened": stats["near_pairs_screened"], "local_flops": stats["local_flops"],
+             "n_points": n, "hbm_bytes": sum(a for nm, a, kd in work.get("k_incoming", []) if kd == "hbm")}
+    for k in TRAFFIC:
+        if k in kernels and mixed:  # the captures are of the single-precision kernels
             tpu = traffic_per_unit(k)
-            unit = stats["local_flops"] if k == "k_local" else stats["near_pairs"]
-            kernels[k]["traffic"] = tpu * unit if tpu is not None else None
+            kernels[k]["traffic"] = tpu * units[TRAFFIC[k][3]] if tpu is not None else None
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_eval"])
     roofline = {"kernel": dom, "bound": kernels[dom]["bound"], "achieved": kernels[dom]["achieved"],
                 "peak": kernels[dom]["peak"], "unit": kernels[dom]["unit"], "frac": kernels[dom]["frac"],
