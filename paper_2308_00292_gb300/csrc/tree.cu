@@ -25,6 +25,7 @@
 #include "tree.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <cstdio>
 #include <cstdlib>
 
@@ -152,6 +153,7 @@ __global__ void k_bbox_final(const double *part, int nblk, Frame *frame) {
     if (!(S > 0.0)) S = 1.0;
     for (int d = 0; d < 3; ++d) frame->lo[d] = mn[d];
     frame->S = S;
+    frame->rS = 1.0 / S;
 }
 
 // one block per system of a batch: the bounding box of its points -> frame[s]
@@ -190,13 +192,25 @@ __global__ void k_bbox_sys(const double *src, const int64_t *off, Frame *frame, 
         if (!(S > 0.0)) S = 1.0;
         for (int d = 0; d < 3; ++d) frame[sy].lo[d] = b > a ? s[d][0] : 0.0;
         frame[sy].S = S;
+        frame[sy].rS = 1.0 / S;
     }
 }
 
 // ------------------------------------------------------------------ 2. keys
-__device__ __forceinline__ double unit_coord(double x, double lo, double S) {
-    // one IEEE subtraction and one IEEE division (nothing to contract)
-    return __ddiv_rn(__dsub_rn(x, lo), S);
+// (x - lo) / S correctly rounded, as one IEEE subtraction and one IEEE
+// division would give, without the division: with rS = RN(1 / S), the product
+// a rS is within two ulps of a / S; a Newton step on the exact remainder
+// a - q S (one FMA) brings it within one ulp, and a second step then yields
+// the correctly rounded quotient (Markstein, IBM J. Res. Dev. 34(1), 1990:
+// q + (a - q S) RN(1/S), rounded once, is RN(a / S) when q is within an ulp).
+// GB300 runs FP64 at 1/62 of its FP32 rate, and the division was most of the
+// key kernel's time.
+__device__ __forceinline__ double unit_coord(double x, double lo, double S, double rS) {
+    const double a = __dsub_rn(x, lo);
+    if (!(rS >= DBL_MIN && rS <= DBL_MAX)) return __ddiv_rn(a, S);  // 1 / S subnormal or infinite
+    double q = __dmul_rn(a, rS);
+    q = __fma_rn(__fma_rn(-q, S, a), rS, q);
+    return __fma_rn(__fma_rn(-q, S, a), rS, q);
 }
 // cell of u in [0, 1] at kb bits (exact scaling by 2^kb)
 __device__ __forceinline__ uint32_t fine_cell(double u, int kb) {
@@ -227,8 +241,8 @@ __global__ void k_make_keys(const double *src, int64_t ns, const double *tgt, in
     const double *x = i < ns ? src + 3 * i : tgt + 3 * (i - ns);
     const int sy = point_sys(off, nsys, i);
     const Frame f = frame[sy];
-    const double u0 = unit_coord(x[0], f.lo[0], f.S), u1 = unit_coord(x[1], f.lo[1], f.S),
-                 u2 = unit_coord(x[2], f.lo[2], f.S);
+    const double u0 = unit_coord(x[0], f.lo[0], f.S, f.rS), u1 = unit_coord(x[1], f.lo[1], f.S, f.rS),
+                 u2 = unit_coord(x[2], f.lo[2], f.S, f.rS);
     u[3 * i] = u0;
     u[3 * i + 1] = u1;
     u[3 * i + 2] = u2;

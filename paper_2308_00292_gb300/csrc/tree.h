@@ -83,6 +83,7 @@ struct Workspace {
 struct Frame {
     double lo[3];
     double S;
+    double rS;  // 1 / S, correctly rounded
 };
 
 template <typename T> struct Vec4;
