@@ -166,9 +166,20 @@ int upload_log2d(dmk_plan_s *pl) {
     };
     std::vector<double> A2(tb.A[0]);
     A2.insert(A2.end(), tb.A[1].begin(), tb.A[1].end());
+    const std::vector<double> &gv = pl->t2.gmono.empty() ? pl->t2.g : pl->t2.gmono;
+    // Tang's table-driven log for the residual kernel: t = m 2^e, m in [1, 2),
+    // log m = -log F_k + log1p(m F_k - 1) for the leading 8 fraction bits k of m.
+    // F_k is any double near 1 / (1 + (k + 1/2) / 256); -log F_k is taken for the
+    // stored F_k, in extended precision and rounded once.
+    std::vector<double> lgF(256), lgL(256), lgE(256);
+    for (int k = 0; k < 256; ++k) {
+        lgF[k] = 1.0 / (1.0 + (k + 0.5) / 256.0);
+        lgL[k] = (double)(-0.5L * std::log((long double)lgF[k]));
+        lgE[k] = (double)((long double)gv[0] - 0.5L * (long double)k * std::log(2.0L));
+    }
     const size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(pl->t2.FWr),
-                 oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW),
-                 og = push(pl->t2.gmono.empty() ? pl->t2.g : pl->t2.gmono);
+                 oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW), og = push(gv),
+                 olF = push(lgF), olL = push(lgL), olE = push(lgE);
     if (pl->ws.ensure(pl->tab2, (int64_t)h.size() * 8)) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
     if (cudaMemcpy(pl->tab2.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(DMK_ERR_CUDA, "copying the plan tables to the device failed");
@@ -189,6 +200,9 @@ int upload_log2d(dmk_plan_s *pl) {
     d.w = base + ow;
     d.wW = base + owW;
     d.g = base + og;
+    d.lgF = base + olF;
+    d.lgL = base + olL;
+    d.lgE = base + olE;
     d.G0 = pl->t2.G0;
     return DMK_OK;
 }

@@ -346,71 +346,186 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 }
 
 // ---- Steps 4-5: residual kernels over the near lists ------------------------
-// A thread per target: 64 threads per leaf (leaves hold about half their
-// capacity, so wider blocks would leave most lanes idle).  MONO: G by Horner
-// in monomials, else by Clenshaw in Chebyshev polynomials.
-constexpr int kNT = 64;
+// A block of kNW warps per target leaf.  The sources of the leaf's near list are
+// staged in shared memory, kCH at a time, with FP32 offsets from the leaf's
+// centre for screening.  A warp takes one target at a time: its lanes screen
+// 32 candidates per step in FP32 against a threshold that cannot reject a
+// pair inside the support, append the survivors to a queue, and evaluate the
+// queue 32 pairs at a time in FP64, so that the FP64 pipe (the bound: GB300
+// issues FP64 at 1/64 of its FP32 rate) only sees pairs that are evaluated.
+//
+// Per pair inside the support (t = r^2 / R^2 < 1, exact since 1/R^2 = 4^l):
+//   (1/2) log t + G(2t - 1),
+// with log t = e ln 2 + log m, t = m 2^e, m in [1, 2), by Tang's table-driven
+// method: log m = -log F_k + log1p(m F_k - 1), F_k ~ 1 / (1 + (k + 1/2)/256) for
+// the leading 8 bits k of m's fraction, so |m F_k - 1| <= 2^-9, and log1p by
+// its Taylor series to degree 5 (remainder below 5e-18).  The tables hold
+// -(1/2) log F_k and g_0 - (e/2) ln 2 (e = -1 ... -255; smaller t, and
+// subnormal r^2, take CUDA's log).  G by Horner in monomials (MONO) or by
+// Clenshaw in Chebyshev polynomials.  Coincident pairs remove q S_L(0) and
+// count their charge for the log S term.
+constexpr int kNW = 4, kNT = 32 * kNW;  // warps, threads per block
+constexpr int kCH = 512;                // sources staged per chunk
+constexpr int kLvl = 32;                // level table (levels 0 .. kMaxLevel, then the no-source mark)
+constexpr int kNoSrc = kLvl - 1;
+static_assert(kMaxLevel < kNoSrc, "level table");
+
 template <bool MONO>
 __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const int32_t *tleaves, const int32_t *nl_off,
                                                const int32_t *nl_src, double *unear, double *qco) {
-    const int i = blockIdx.x, T = tleaves[i], tid = threadIdx.x;
-    __shared__ double sx[kNT], sy[kNT], sq[kNT], g[64];
-    const int gdeg = d.gdeg;
+    __shared__ double sx[kCH], sy[kCH], sq[kCH];
+    __shared__ float sox[kCH], soy[kCH];
+    __shared__ uint8_t slev[kCH];
+    __shared__ uint16_t queue[kNW][64];
+    __shared__ double lgF[256], lgL[256], lgE[256], g[64];
+    __shared__ double l_x2[kLvl], l_S0[kLvl];
+    __shared__ long long l_R2[kLvl];
+    __shared__ float l_thr[kLvl];
+    const int i = blockIdx.x, T = tleaves[i], tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int gdeg = d.gdeg, a = tv.blevel[T];
+    int ix, iy;
+    cell2(tv, T, ix, iy);
+    const double Bt = level_R(a), cx = (ix + 0.5) * Bt, cy = (iy + 0.5) * Bt;
+    for (int e = tid; e < 256; e += kNT) {
+        lgF[e] = d.lgF[e];
+        lgL[e] = d.lgL[e];
+        lgE[e] = d.lgE[e];
+    }
     for (int e = tid; e <= gdeg; e += kNT) g[e] = d.g[e];
-    __syncthreads();
-    const int t0 = tv.bstart[T], nt = tv.bcount[T];
-    for (int tc = 0; tc < nt; tc += kNT) {
-        const int k = t0 + tc + tid;
-        const bool act = tc + tid < nt && (tv.pflag[k] & 2);
-        const double xt = act ? tv.ux[k] : 0.0, yt = act ? tv.uy[k] : 0.0;
-        double acc = 0.0, qc = 0.0;
-        for (int li = nl_off[i]; li < nl_off[i + 1]; ++li) {
-            const int S = nl_src[li];
-            const double R = level_R(tv.blevel[S]), inv2 = 1.0 / (R * R);
-            const double S0 = log(R) - d.G0;  // mollified kernel at r = 0
-            const int s0 = tv.bstart[S], ns = tv.bcount[S];
-            for (int sc = 0; sc < ns; sc += kNT) {
-                __syncthreads();
-                if (sc + tid < ns) {
-                    sx[tid] = tv.ux[s0 + sc + tid];
-                    sy[tid] = tv.uy[s0 + sc + tid];
-                    sq[tid] = tv.q[s0 + sc + tid];
-                }
-                __syncthreads();
-                const int m = min(kNT, ns - sc);
-                if (!act) continue;
-                for (int j = 0; j < m; ++j) {
-                    const double dx = xt - sx[j], dy = yt - sy[j], r2 = dx * dx + dy * dy, t = r2 * inv2;
-                    if (!(t < 1.0)) continue;
-                    const double q = sq[j];
-                    if (r2 == 0.0) {
-                        acc -= q * S0;
-                        qc += q;
-                        continue;
-                    }
-                    const double x = 2.0 * t - 1.0;
-                    double G;
-                    if (MONO) {
-                        G = g[gdeg];
-                        for (int n = gdeg - 1; n >= 0; --n) G = fma(G, x, g[n]);
-                    } else {
-                        double b1 = 0.0, b2 = 0.0;
-                        for (int n = gdeg; n >= 1; --n) {
-                            const double b0 = 2.0 * x * b1 - b2 + g[n];
-                            b2 = b1;
-                            b1 = b0;
-                        }
-                        G = x * b1 - b2 + g[0];
-                    }
-                    acc += q * (0.5 * log(t) + G);
-                }
-            }
-        }
-        if (act) {
-            unear[k] = acc;
-            qco[k] = qc;
+    if (tid < kLvl) {
+        if (tid <= kMaxLevel) {
+            const double R = level_R(tid);
+            l_x2[tid] = 2.0 / (R * R);                // x = 2 t - 1 = r^2 (2 / R^2) - 1
+            l_S0[tid] = log(R) - d.G0;                // mollified kernel at r = 0
+            l_R2[tid] = __double_as_longlong(R * R);  // r^2 < R^2 compared as bit patterns
+            // The FP32 offsets from the leaf's centre are off by at most
+            // 2^-24 (|x_t - c| + |x_s - c|) + 2^-24 |dx| per axis, below
+            // 2^-24 (4 R + B_t) for a pair inside the support; 2^-21 (4 R + B_t)
+            // per axis and the relative factor cover that and the rounding of
+            // the three FP32 operations with room.
+            const double rr = R + (4.0 * R + Bt) * 0x1p-21;
+            l_thr[tid] = __double2float_ru(rr * rr * (1.0 + 0x1p-20));
+        } else {
+            l_x2[tid] = l_S0[tid] = 0.0;
+            l_R2[tid] = 0;
+            l_thr[tid] = -1.0f;  // rejects every candidate
         }
     }
+    const int t0 = tv.bstart[T], nt = tv.bcount[T];
+    uint16_t *qw = queue[w];
+    const unsigned below = (1u << lane) - 1u;
+
+    // one pair (target xt, yt; staged source j) into acc, qc
+    auto pair = [&](int j, double xt, double yt, double &acc, double &qc) {
+        const double dx = xt - sx[j], dy = yt - sy[j];
+        const double r2 = fma(dy, dy, dx * dx);
+        const int l = slev[j];
+        const long long rb = __double_as_longlong(r2);
+        if (!(rb < l_R2[l])) return;  // outside the support (or NaN)
+        const double q = sq[j];
+        if (rb == 0) {
+            acc = fma(-q, l_S0[l], acc);
+            qc += q;
+            return;
+        }
+        const double x = fma(r2, l_x2[l], -1.0);
+        double G, b2 = 0.0;  // G(x) = G x + g_0 (monomials) or x b_1 - b_2 + g_0 (Clenshaw, b_1 in G)
+        if (MONO) {
+            G = g[gdeg];
+            for (int n = gdeg - 1; n >= 1; --n) G = fma(G, x, g[n]);
+        } else {
+            const double x2 = 2.0 * x;
+            G = 0.0;
+            for (int n = gdeg; n >= 1; --n) {
+                const double b0 = fma(x2, G, g[n] - b2);
+                b2 = G;
+                G = b0;
+            }
+        }
+        const int hi = __double2hiint(r2), be = (hi >> 20) & 0x7ff;
+        const int et = be - 1023 + 2 * l;  // exponent of t = r^2 4^l
+        double s;                          // g_0 + (1/2) log t
+        if (be != 0 && et >= -255) {
+            const int k = (hi >> 12) & 0xff;
+            const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(r2));
+            const double r = fma(m, lgF[k], -1.0);
+            double h = fma(r, 0.1, -0.125);  // (1/2) log1p(r) = r (1/2 - r/4 + r^2/6 - r^3/8 + r^4/10)
+            h = fma(h, r, 1.0 / 6.0);
+            h = fma(h, r, -0.25);
+            h = fma(h, r, 0.5);
+            s = lgE[-et] + (lgL[k] + h * r);
+        } else {
+            s = g[0] + 0.5 * log(r2 * (0.5 * l_x2[l]));
+        }
+        const double v = MONO ? fma(G, x, s) : fma(x, G, s - b2);
+        acc = fma(q, v, acc);
+    };
+
+    const int li0 = nl_off[i], li1 = nl_off[i + 1];
+    int nch = 0;  // sources staged (block-uniform)
+    auto process = [&]() {
+        __syncthreads();
+        for (int k = w; k < nt; k += kNW) {
+            const int pk = t0 + k;
+            if (!(tv.pflag[pk] & 2)) continue;
+            const double xt = tv.ux[pk], yt = tv.uy[pk];
+            const float tx = (float)(xt - cx), ty = (float)(yt - cy);
+            double acc = 0.0, qc = 0.0;
+            int qn = 0;
+            for (int j0 = 0; j0 < nch; j0 += 32) {
+                const int j = j0 + lane;
+                bool in = false;
+                if (j < nch) {
+                    const float ex = tx - sox[j], ey = ty - soy[j];
+                    in = fmaf(ey, ey, ex * ex) <= l_thr[slev[j]];
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) qw[qn + __popc(m & below)] = (uint16_t)j;
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    pair(qw[lane], xt, yt, acc, qc);
+                    qn -= 32;
+                    __syncwarp();
+                    if (lane < qn) qw[lane] = qw[32 + lane];
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+            if (lane < qn) pair(qw[lane], xt, yt, acc, qc);
+            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                qc += __shfl_xor_sync(0xffffffffu, qc, o);
+            }
+            if (lane == 0) {
+                unear[pk] += acc;
+                qco[pk] += qc;
+            }
+        }
+        __syncthreads();
+        nch = 0;
+    };
+    for (int li = li0; li < li1; ++li) {
+        const int S = nl_src[li], s0 = tv.bstart[S], ns = tv.bcount[S], l = tv.blevel[S];
+        for (int o = 0; o < ns;) {
+            const int take = min(ns - o, kCH - nch);
+            for (int e = tid; e < take; e += kNT) {
+                const int ks = s0 + o + e, js = nch + e;
+                const double xs = tv.ux[ks], ys = tv.uy[ks];
+                sx[js] = xs;
+                sy[js] = ys;
+                sq[js] = tv.q[ks];
+                sox[js] = (float)(xs - cx);
+                soy[js] = (float)(ys - cy);
+                slev[js] = (uint8_t)((tv.pflag[ks] & 1) ? l : kNoSrc);
+            }
+            nch += take;
+            o += take;
+            if (nch == kCH) process();
+        }
+    }
+    if (nch > 0) process();
 }
 
 __global__ void k2_lift(const double *x2, int64_t n, double *x3) {

@@ -17,6 +17,10 @@ struct Log2dDev {
     const double *w;          // [2 nf^2 + 1]: translation weights (every level)
     const double *wW;         // [2 n0^2 + 1]: root window weights
     const double *g;          // [gdeg + 1]: G(t) in x = 2 t - 1, monomials if gmono else Chebyshev
+    // the table-driven log of the residual kernel (Tang's method), [256] each:
+    const double *lgF;        // F_k ~ 1 / (1 + (k + 1/2) / 256)
+    const double *lgL;        // -(1/2) log F_k
+    const double *lgE;        // g[0] - (j/2) log 2 (j = 1 ... 255: t = m 2^-j)
     int gmono;
     double G0;                // G(0)
 };

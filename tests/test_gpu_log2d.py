@@ -77,6 +77,25 @@ def test_separate_targets_duplicates_and_scale(dmk, oracle_mod):
     assert rel(u2 - np.log(s) * (q.sum() - q), u1) < 1e-13
 
 
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_close_pairs_across_scales(dmk, oracle_mod, eps):
+    """Separations from 1e-3 down to 1e-150 at the corner of the unit box (the
+    map keeps them: x - lo is exact there), so that t = r^2 / R^2 spans the
+    residual kernel's table-driven log (t >= 2^-255) and its fallback below."""
+    x, q = inputs.disk2d(2000, seed=827)
+    x = x - x.min(axis=0) + 0.25
+    seps = [1e-3, 1e-8, 1e-20, 1e-35, 1e-45, 1e-80, 1e-150]
+    extra = [[0.0, 0.0]] + [[s, 0.0] for s in seps] + [[0.0, s] for s in seps[::2]]
+    x = np.r_[x, np.array(extra)]
+    q = np.r_[q, np.random.default_rng(828).uniform(-1, 1, len(extra))]
+    u = run(dmk, x, q, eps=eps, leaf_cap=60)
+    d = oracle_mod.direct_log2d(x, q)
+    assert rel(u, d) < eps
+    k = len(extra)
+    assert np.max(np.abs(u[-k:] - d[-k:]) / np.abs(d[-k:])) < eps
+    assert rel(u, oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=60, p=plan_p(dmk, eps))) < 1e-2 * eps
+
+
 def test_small_inputs_and_host_entry(dmk, oracle_mod):
     x, q = inputs.disk2d(2000, seed=825)
     with dmk.Plan(kernel=dmk.DMK_LOG2D, dim=2, eps=1e-6) as plan:
