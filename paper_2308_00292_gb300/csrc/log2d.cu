@@ -64,7 +64,7 @@ __device__ __forceinline__ void cheb_row(double x, int p, double *T) {
 __global__ void __launch_bounds__(kT) k2_moments(TreeView tv, Log2dDev d, double *mom) {
     const int b = blockIdx.x;
     if (!(tv.bflags[b] & BF_LEAF) || tv.bnsrc[b] == 0) return;
-    __shared__ double Tx[32][kMaxP], Ty[32][kMaxP], qs[32];
+    __shared__ double Tx[32][kMaxP], Ty[32][kMaxP];
     const int p = d.p, pp = p * p, tid = threadIdx.x;
     int ix, iy;
     cell2(tv, b, ix, iy);
@@ -77,11 +77,11 @@ __global__ void __launch_bounds__(kT) k2_moments(TreeView tv, Log2dDev d, double
         if (tid < 32) {
             const int k = s0 + c0 + tid;
             if (c0 + tid < n) {
-                qs[tid] = tv.q[k];
+                const double qk = tv.q[k];
                 cheb_row(2.0 * (tv.ux[k] - cx) / R, p, Tx[tid]);
                 cheb_row(2.0 * (tv.uy[k] - cy) / R, p, Ty[tid]);
+                for (int a = 0; a < p; ++a) Tx[tid][a] *= qk;  // q_j T_a(xi_j)
             } else {
-                qs[tid] = 0.0;
                 for (int a = 0; a < p; ++a) Tx[tid][a] = Ty[tid][a] = 0.0;
             }
         }
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kT) k2_moments(TreeView tv, Log2dDev d, double
             if (e < pp) {
                 const int a = e / p, bb = e - a * p;
                 double s = 0.0;
-                for (int i = 0; i < 32; ++i) s += qs[i] * Tx[i][a] * Ty[i][bb];
+                for (int i = 0; i < 32; ++i) s += Tx[i][a] * Ty[i][bb];
                 acc[j] += s;
             }
         }
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart
         for (int e = tid; e < pp; e += kT) {
             const int k = e / p, n2 = e - k * p;
             double s = 0.0;
-            for (int k2 = 0; k2 < p; ++k2) s += Ay[n2 * p + k2] * MC[k * p + k2];
+            for (int k2 = 0; k2 <= n2; ++k2) s += Ay[n2 * p + k2] * MC[k * p + k2];  // A_s[n][m] = 0 for m > n
             Y[e] = s;
         }
         __syncthreads();
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart
             if (e < pp) {
                 const int n1 = e / p, n2 = e - n1 * p;
                 double s = 0.0;
-                for (int k = 0; k < p; ++k) s += Ax[n1 * p + k] * Y[k * p + n2];
+                for (int k = 0; k <= n1; ++k) s += Ax[n1 * p + k] * Y[k * p + n2];
                 acc[j] += s;
             }
         }
@@ -151,32 +151,42 @@ __global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart
     }
 }
 
-// Phi[mx][my] = sum_a sum_b F[mx][a] F[my][b] M[a][b] with F = Fr + i Fi ([N][p]),
-// into phi (N^2 complex, interleaved); M and the workspace Y (N x p complex)
-// in shared memory
+// The moments are real, so the plane waves are Hermitian, Phi[-m] = conj(Phi[m]),
+// and only the half spectrum m_x = 0 ... nh (nh = (N - 1) / 2, rows nh + 1 of N
+// complex values) is formed, stored and translated.  F[m][a] approximates
+// exp(-i theta m xi) by T_0 ... T_{p-1}: its cosine part is even and its sine
+// part odd, so F is real for even a and imaginary for odd a (the other part
+// is rounding, taken as zero), and each complex product is a real one.
+
+// Phi[mx][my] = sum_a sum_b F[mx][a] F[my][b] M[a][b], mx = 0 ... nh, into phi
+// ((nh + 1) x N complex, interleaved); M and the workspace Y ((nh + 1) x p
+// complex) in shared memory
 __device__ void pw_from_moments(const double *M, const double *Fr, const double *Fi, int p, int N, double *Yr,
                                 double *Yi, double *phi) {
-    const int tid = threadIdx.x;
-    for (int e = tid; e < N * p; e += kT) {
+    const int tid = threadIdx.x, nh = (N - 1) / 2, NH = nh + 1;
+    // Y[mx][b] = sum_a F[mx][a] M[a][b]: real part over even a, imaginary over odd a
+    for (int e = tid; e < NH * p; e += kT) {
         const int mx = e / p, bb = e - mx * p;
+        const double *fr = Fr + (size_t)(mx + nh) * p, *fi = Fi + (size_t)(mx + nh) * p;
         double sr = 0.0, si = 0.0;
-        for (int a = 0; a < p; ++a) {
-            const double m = M[a * p + bb];
-            sr += Fr[mx * p + a] * m;
-            si += Fi[mx * p + a] * m;
-        }
+        for (int a = 0; a < p; a += 2) sr += fr[a] * M[a * p + bb];
+        for (int a = 1; a < p; a += 2) si += fi[a] * M[a * p + bb];
         Yr[e] = sr;
         Yi[e] = si;
     }
     __syncthreads();
-    for (int e = tid; e < N * N; e += kT) {
+    // Phi[mx][my] = sum_b F[my][b] Y[mx][b]: F[my][b] = Fr (b even) or i Fi (b odd)
+    for (int e = tid; e < NH * N; e += kT) {
         const int mx = e / N, my = e - mx * N;
+        const double *fr = Fr + (size_t)my * p, *fi = Fi + (size_t)my * p, *yr = Yr + mx * p, *yi = Yi + mx * p;
         double sr = 0.0, si = 0.0;
-        for (int bb = 0; bb < p; ++bb) {
-            const double fr = Fr[my * p + bb], fi = Fi[my * p + bb];
-            const double yr = Yr[mx * p + bb], yi = Yi[mx * p + bb];
-            sr += fr * yr - fi * yi;
-            si += fr * yi + fi * yr;
+        for (int bb = 0; bb < p; bb += 2) {
+            sr += fr[bb] * yr[bb];
+            si += fr[bb] * yi[bb];
+        }
+        for (int bb = 1; bb < p; bb += 2) {
+            sr -= fi[bb] * yi[bb];
+            si += fi[bb] * yr[bb];
         }
         phi[2 * e] = sr;
         phi[2 * e + 1] = si;
@@ -184,35 +194,43 @@ __device__ void pw_from_moments(const double *M, const double *Fr, const double 
     __syncthreads();
 }
 
-// c[n][n'] = Re sum_mx sum_my conj(F[mx][n]) conj(F[my][n']) Psi[mx][my]; Psi (N^2
-// complex interleaved) and the workspace Z (p x N complex) in shared memory
+// c[n][n'] = Re sum_{all m} conj(F[mx][n]) conj(F[my][n']) Psi[mx][my] from the
+// half spectrum Psi ((nh + 1) x N complex interleaved, the rows mx >= 1 already
+// doubled: the terms at m and -m are conjugate); the workspace Z (p x N
+// complex) in shared memory
 __device__ void coef_from_pw(const double *Psi, const double *Fr, const double *Fi, int p, int N, double *Zr,
                              double *Zi, double *acc /* kPer per thread */) {
-    const int tid = threadIdx.x;
-    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]
+    const int tid = threadIdx.x, nh = (N - 1) / 2, NH = nh + 1;
+    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]: conj(F) = Fr (n even) or -i Fi (n odd)
     for (int e = tid; e < p * N; e += kT) {
         const int n = e / N, my = e - n * N;
         double sr = 0.0, si = 0.0;
-        for (int mx = 0; mx < N; ++mx) {
-            const double fr = Fr[mx * p + n], fi = -Fi[mx * p + n];
-            const double pr = Psi[2 * (mx * N + my)], pi = Psi[2 * (mx * N + my) + 1];
-            sr += fr * pr - fi * pi;
-            si += fr * pi + fi * pr;
+        if (!(n & 1)) {
+            for (int mx = 0; mx < NH; ++mx) {
+                const double f = Fr[(mx + nh) * p + n];
+                sr += f * Psi[2 * (mx * N + my)];
+                si += f * Psi[2 * (mx * N + my) + 1];
+            }
+        } else {
+            for (int mx = 0; mx < NH; ++mx) {
+                const double f = Fi[(mx + nh) * p + n];
+                sr += f * Psi[2 * (mx * N + my) + 1];
+                si -= f * Psi[2 * (mx * N + my)];
+            }
         }
         Zr[e] = sr;
         Zi[e] = si;
     }
     __syncthreads();
+    // c[n][n'] = Re sum_my conj(F[my][n']) Z[n][my] = sum_my Fr Zr (n' even) or Fi Zi (n' odd)
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int e = tid + j * kT;
         if (e < p * p) {
             const int n = e / p, n2 = e - n * p;
+            const double *F = (n2 & 1) ? Fi : Fr, *Z = ((n2 & 1) ? Zi : Zr) + n * N;
             double s = 0.0;
-            for (int my = 0; my < N; ++my) {
-                // Re(conj(F[my][n2]) Z[n][my])
-                s += Fr[my * p + n2] * Zr[n * N + my] + Fi[my * p + n2] * Zi[n * N + my];
-            }
+            for (int my = 0; my < N; ++my) s += F[my * p + n2] * Z[my];
             acc[j] += s;
         }
     }
@@ -224,13 +242,13 @@ __global__ void __launch_bounds__(kT) k2_outgoing(TreeView tv, Log2dDev d, const
     const int b = blockIdx.x;
     if (!(tv.bflags[b] & BF_FOUT)) return;
     extern __shared__ double sm[];
-    const int p = d.p, pp = p * p, N = d.N1;
-    double *M = sm, *Yr = M + pp, *Yi = Yr + N * p, *P = Yi + N * p;
+    const int p = d.p, pp = p * p, N = d.N1, NH = d.nf + 1;
+    double *M = sm, *Yr = M + pp, *Yi = Yr + NH * p, *P = Yi + NH * p;
     for (int e = threadIdx.x; e < pp; e += kT) M[e] = mom[(size_t)b * pp + e];
     __syncthreads();
     pw_from_moments(M, d.Fr, d.Fi, p, N, Yr, Yi, P);
-    double *out = phi + (size_t)tv.bslot[b] * 2 * N * N;
-    for (int e = threadIdx.x; e < 2 * N * N; e += kT) out[e] = P[e];
+    double *out = phi + (size_t)tv.bslot[b] * 2 * NH * N;
+    for (int e = threadIdx.x; e < 2 * NH * N; e += kT) out[e] = P[e];
 }
 
 // ---- Step 3: local expansions of the boxes of one level ---------------------
@@ -240,7 +258,8 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
     if (tv.bntgt[b] == 0) return;
     extern __shared__ double sm[];
     const int p = d.p, pp = p * p, N = d.N1, NW = d.NW, NM = N > NW ? N : NW;
-    double *CP = sm, *Y = CP + pp, *Psi = Y + pp, *Zr = Psi + 2 * NM * NM, *Zi = Zr + p * NM;
+    // Psi holds a half spectrum, (NM + 1) / 2 rows of NM
+    double *CP = sm, *Y = CP + pp, *Psi = Y + pp, *Zr = Psi + NM * (NM + 1), *Zi = Zr + p * NM;
     const int tid = threadIdx.x;
     double acc[kPer];
 #pragma unroll
@@ -253,10 +272,10 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
         const double *Ax = d.A + (size_t)(ix & 1) * pp, *Ay = d.A + (size_t)(iy & 1) * pp;
         for (int e = tid; e < pp; e += kT) CP[e] = loc[(size_t)P * pp + e];
         __syncthreads();
-        for (int e = tid; e < pp; e += kT) {  // Y[n][k'] = sum_n' A_sy[n'][k'] c_P[n][n']
+        for (int e = tid; e < pp; e += kT) {  // Y[n][k'] = sum_n' A_sy[n'][k'] c_P[n][n'] (A_s[n'][k'] = 0 for k' > n')
             const int n = e / p, k2 = e - n * p;
             double s = 0.0;
-            for (int n2 = 0; n2 < p; ++n2) s += Ay[n2 * p + k2] * CP[n * p + n2];
+            for (int n2 = k2; n2 < p; ++n2) s += Ay[n2 * p + k2] * CP[n * p + n2];
             Y[e] = s;
         }
         __syncthreads();
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
             if (e < pp) {
                 const int k = e / p, k2 = e - k * p;
                 double s = 0.0;
-                for (int n = 0; n < p; ++n) s += Ax[n * p + k] * Y[n * p + k2];
+                for (int n = k; n < p; ++n) s += Ax[n * p + k] * Y[n * p + k2];
                 acc[j] += s;
             }
         }
@@ -274,22 +293,23 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
     }
     // incoming plane waves from the F_out colleagues: w(|m|^2) omega^{m . delta}
     if (tv.bflags[b] & BF_FIN) {
-        const int nf = d.nf;
-        for (int e = tid; e < N * N; e += kT) Psi[2 * e] = Psi[2 * e + 1] = 0.0;
+        const int nf = d.nf, NH = nf + 1;
+        for (int e = tid; e < NH * N; e += kT) Psi[2 * e] = Psi[2 * e + 1] = 0.0;
         __syncthreads();
         const int32_t *col = tv.bcol + (size_t)b * 27;
         for (int dx = -1; dx <= 1; ++dx)
             for (int dy = -1; dy <= 1; ++dy) {
                 const int S = col[9 * (dx + 1) + 3 * (dy + 1) + 1];
                 if (S < 0 || !(tv.bflags[S] & BF_FOUT)) continue;
-                const double *ph = phi + (size_t)tv.bslot[S] * 2 * N * N;
-                // delta = c_B - c_S = -(dx, dy) R; phase exp(i (2 pi / 3) m . delta / R)
-                for (int e = tid; e < N * N; e += kT) {
-                    const int mx = e / N - nf, my = e % N - nf;
+                const double *ph = phi + (size_t)tv.bslot[S] * 2 * NH * N;
+                // delta = c_B - c_S = -(dx, dy) R; phase exp(i (2 pi / 3) m . delta / R);
+                // half spectrum mx = 0 ... nf, the rows mx >= 1 doubled
+                for (int e = tid; e < NH * N; e += kT) {
+                    const int mx = e / N, my = e % N - nf;
                     int r = (-(mx * dx + my * dy)) % 3;
                     if (r < 0) r += 3;
                     const double cr = r == 0 ? 1.0 : -0.5, ci = r == 0 ? 0.0 : (r == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
-                    const double w = d.w[mx * mx + my * my];
+                    const double w = (mx ? 2.0 : 1.0) * d.w[mx * mx + my * my];
                     const double pr = ph[2 * e], pi = ph[2 * e + 1];
                     Psi[2 * e] += w * (cr * pr - ci * pi);
                     Psi[2 * e + 1] += w * (cr * pi + ci * pr);
@@ -304,9 +324,9 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
         __syncthreads();
         pw_from_moments(CP, d.FWr, d.FWi, p, NW, Zr, Zi, Psi);
         const int n0 = d.n0;
-        for (int e = tid; e < NW * NW; e += kT) {
-            const int mx = e / NW - n0, my = e % NW - n0;
-            const double w = d.wW[mx * mx + my * my];
+        for (int e = tid; e < (n0 + 1) * NW; e += kT) {
+            const int mx = e / NW, my = e % NW - n0;
+            const double w = (mx ? 2.0 : 1.0) * d.wW[mx * mx + my * my];
             Psi[2 * e] *= w;
             Psi[2 * e + 1] *= w;
         }
@@ -585,7 +605,7 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     const int p = d.p, pp = p * p, N = d.N1, NW = d.NW, NM = std::max(N, NW);
     const int64_t n = tv.n;
     if (ws.ensure(bf.mom, (int64_t)tv.nb * pp * 8) || ws.ensure(bf.loc, (int64_t)tv.nb * pp * 8) ||
-        ws.ensure(bf.phi, (int64_t)std::max(tree.nslots, 1) * 2 * N * N * 8) || ws.ensure(bf.ufar, n * 8) ||
+        ws.ensure(bf.phi, (int64_t)std::max(tree.nslots, 1) * 2 * (d.nf + 1) * N * 8) || ws.ensure(bf.ufar, n * 8) ||
         ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8)) {
         err = "device allocation failed (2D expansions)";
         return DMK_ERR_OOM;
@@ -604,8 +624,8 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     }
     L2CK(cudaGetLastError());
     // Step 3
-    const size_t smo = (size_t)(pp + 2 * N * p + 2 * N * N) * 8;
-    const size_t sml = (size_t)(2 * pp + 2 * NM * NM + 2 * p * NM) * 8;
+    const size_t smo = (size_t)(pp + (N + 1) * p + (N + 1) * N) * 8;  // half spectra: (N + 1) / 2 rows
+    const size_t sml = (size_t)(2 * pp + NM * (NM + 1) + 2 * p * NM) * 8;
     L2CK(cudaFuncSetAttribute(k2_outgoing, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smo));
     L2CK(cudaFuncSetAttribute(k2_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sml));
     if (tree.nslots > 0) {
