@@ -68,6 +68,8 @@ def parse():
                     help="time the 2D kernel log r on 8e6 points (circle and disk) at eps 1e-8 instead")
     ap.add_argument("--leaf-cap", type=int, default=0,
                     help="--log2d: this leaf capacity instead of the autotuner's (profiling runs)")
+    ap.add_argument("--log2d-points", type=int, default=0,
+                    help="--log2d: this many points of the same recipe instead of 8e6 (profiling runs)")
     return ap.parse_args()
 
 
@@ -539,8 +541,10 @@ def run_log2d(args):
     from paper_2308_00292_gb300 import dmk, inputs
     name = "log2d_circle_disk_n8e6"
     cfg = inputs.CONFIGS[name]
-    x, q = inputs.make(cfg["gen"], cfg["n"], cfg["seed"])
+    x, q = inputs.make(cfg["gen"], args.log2d_points or cfg["n"], cfg["seed"])
     n = x.shape[0]
+    if args.log2d_points:
+        name += "_points%d" % n
     xd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     oracle.build()
@@ -559,15 +563,36 @@ def run_log2d(args):
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
+    t_near = []
     e0.record(stream)
     for _ in range(args.steps):
         plan.eval(xd, qd, out=out)
-        launches += plan.stats()["n_launches"]
+        st = plan.stats()
+        launches += st["n_launches"]
+        t_near.append(st["t_near_ms"])
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     st = plan.stats()
+    prm = plan.params()
+    # k2_near, the dominant kernel, is bound by the FP64 pipe: per pair inside the
+    # support 24 flops (distance, log t by the table, the sums) and 2 per degree
+    # of the residual polynomial after the first (Horner, the form the plan takes
+    # at eps 1e-8); timed by the events the library records around it
+    sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else FFMA_MEASURED_MHZ
+    near_ms = float(np.median(t_near))
+    near_flops = st["near_pairs_inside"] * (24 + 2 * (prm["q_degree"] - 1))
+    f64_peak = DFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
+    achieved = near_flops / (near_ms * 1e-3) / 1e12
+    roofline = {"kernel": "k2_near", "bound": "fp64", "achieved": achieved, "peak": f64_peak, "unit": "TFLOP/s",
+                "frac": achieved / f64_peak, "traffic": None, "ms_per_eval": near_ms,
+                "peak_basis": "DFMA probe %.2f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (
+                    DFMA_MEASURED_TFLOPS, FFMA_MEASURED_MHZ, sm_mhz),
+                "work": "%d pairs inside the support x %d flops" % (st["near_pairs_inside"],
+                                                                    24 + 2 * (prm["q_degree"] - 1)),
+                "timing": "CUDA events the library records around the kernel on the evaluation's stream, "
+                          "median over the timed steps"}
     u = out.cpu().numpy()[sample]
     e2e = None
     if not args.skip_e2e:
@@ -604,7 +629,8 @@ def run_log2d(args):
             "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
             "rel_l2_vs_direct_128_targets": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
             "tree": {"levels": st["n_levels"], "boxes": st["n_boxes"], "leaves": st["n_leaves"],
-                     "near_pairs": st["near_pairs"]},
+                     "near_pairs": st["near_pairs"], "near_pairs_inside": st["near_pairs_inside"]},
+            "roofline": roofline,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 

@@ -355,7 +355,9 @@ typedef struct {
     float t_planewave_ms;   /* device time of the outgoing plane waves and the root term */
     int64_t near_pairs_screened; /* pairs whose distance the near field tested: the sources
                                     left after culling against each target group's bounding
-                                    box, times the group's targets */
+                                    box, times the group's targets (3D); every candidate
+                                    pair (2D log r, where t_near_ms times the near field on
+                                    the evaluation's stream) */
 } dmk_eval_stats;
 
 DMK_API int dmk_get_stats(dmk_plan_t plan, dmk_eval_stats *out);

@@ -215,7 +215,7 @@ int eval_log2d(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, c
     const long long launches0 = dmk::g_launches.load();
     cudaEventRecord(pl->ev[0], st);
     int rc = dmk::run_log2d(pl->d2, *pl->tree, pl->ws, pl->b2, src, ns, q, tgt, nt, pl->leaf_cap, pl->max_level,
-                            pot, st, err);
+                            pot, st, pl->nev, err);
     if (rc) return fail(rc, "2D pass: " + err);
     cudaEventRecord(pl->ev[5], st);
     cudaError_t ce = cudaStreamSynchronize(st);
@@ -231,10 +231,20 @@ int eval_log2d(dmk_plan_s *pl, const double *src, int64_t ns, const double *q, c
     s.near_pairs = pl->tree->near_pairs;
     s.balance_rounds = pl->tree->rounds;
     s.n_fin = pl->tree->nfin;
-    float t05 = 0;
+    float t05 = 0, tn = 0;
     cudaEventElapsedTime(&t05, pl->ev[0], pl->ev[5]);
     s.t_total_ms = t05;
+    if (cudaEventElapsedTime(&tn, pl->nev[0], pl->nev[1]) == cudaSuccess) s.t_near_ms = tn;
+    else cudaGetLastError();
     s.n_launches = dmk::g_launches.load() - launches0;
+    if (pl->tree->ntleaves > 0 && pl->b2.cnt.p) {
+        // every candidate pair is screened; the device counts those inside the support
+        unsigned long long inside = 0;
+        if (cudaMemcpy(&inside, pl->b2.cnt.p, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(DMK_ERR_CUDA, "reading the near-field counter failed");
+        s.near_pairs_inside = (int64_t)inside;
+        s.near_pairs_screened = s.near_pairs;
+    }
     return DMK_OK;
 }
 

@@ -368,11 +368,14 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 // ---- Steps 4-5: residual kernels over the near lists ------------------------
 // A block of kNW warps per target leaf.  The sources of the leaf's near list are
 // staged in shared memory, kCH at a time, with FP32 offsets from the leaf's
-// centre for screening.  A warp takes one target at a time: its lanes screen
+// centre for screening.  A warp takes kS targets at a time: its lanes screen
 // 32 candidates per step in FP32 against a threshold that cannot reject a
-// pair inside the support, append the survivors to a queue, and evaluate the
-// queue 32 pairs at a time in FP64, so that the FP64 pipe (the bound: GB300
-// issues FP64 at 1/64 of its FP32 rate) only sees pairs that are evaluated.
+// pair inside the support, append the survivors (target slot, source) to one
+// queue, and evaluate the queue 32 pairs at a time in FP64 into per-lane,
+// per-slot sums in shared memory, so that the FP64 pipe (the bound: GB300
+// issues FP64 at 1/64 of its FP32 rate) sees only pairs that are evaluated,
+// with one partly filled step per kS targets.  The lanes' sums of a target
+// are then added in a fixed butterfly order (results do not depend on timing).
 //
 // Per pair inside the support (t = r^2 / R^2 < 1, exact since 1/R^2 = 4^l):
 //   (1/2) log t + G(2t - 1),
@@ -386,21 +389,25 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 // count their charge for the log S term.
 constexpr int kNW = 4, kNT = 32 * kNW;  // warps, threads per block
 constexpr int kCH = 512;                // sources staged per chunk
+constexpr int kS = 4;                   // targets in flight per warp (one queue, one flush)
 constexpr int kLvl = 32;                // level table (levels 0 .. kMaxLevel, then the no-source mark)
 constexpr int kNoSrc = kLvl - 1;
 static_assert(kMaxLevel < kNoSrc, "level table");
 
 template <bool MONO>
 __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const int32_t *tleaves, const int32_t *nl_off,
-                                               const int32_t *nl_src, double *unear, double *qco) {
+                                               const int32_t *nl_src, double *unear, double *qco,
+                                               unsigned long long *n_inside) {
     __shared__ double sx[kCH], sy[kCH], sq[kCH];
     __shared__ float sox[kCH], soy[kCH];
     __shared__ uint8_t slev[kCH];
-    __shared__ uint16_t queue[kNW][64];
+    __shared__ uint16_t queue[kNW][64];           // (slot << 10) | source
+    __shared__ double accS[kNW][kS][32], qcS[kNW][kS][32], txS[kNW][kS], tyS[kNW][kS];
     __shared__ double lgF[256], lgL[256], lgE[256], g[64];
     __shared__ double l_x2[kLvl], l_S0[kLvl];
     __shared__ long long l_R2[kLvl];
     __shared__ float l_thr[kLvl];
+    __shared__ unsigned s_inside;
     const int i = blockIdx.x, T = tleaves[i], tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int gdeg = d.gdeg, a = tv.blevel[T];
     int ix, iy;
@@ -431,17 +438,22 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
             l_thr[tid] = -1.0f;  // rejects every candidate
         }
     }
+    if (tid == 0) s_inside = 0;
     const int t0 = tv.bstart[T], nt = tv.bcount[T];
     uint16_t *qw = queue[w];
+    unsigned inside = 0;  // pairs inside the support evaluated by this thread
     const unsigned below = (1u << lane) - 1u;
 
-    // one pair (target xt, yt; staged source j) into acc, qc
-    auto pair = [&](int j, double xt, double yt, double &acc, double &qc) {
-        const double dx = xt - sx[j], dy = yt - sy[j];
+    // one queued pair (target slot, staged source) into the lane's sums of the slot
+    auto pair = [&](int e) {
+        const int j = e & 1023, sl = e >> 10;
+        double &acc = accS[w][sl][lane], &qc = qcS[w][sl][lane];
+        const double dx = txS[w][sl] - sx[j], dy = tyS[w][sl] - sy[j];
         const double r2 = fma(dy, dy, dx * dx);
         const int l = slev[j];
         const long long rb = __double_as_longlong(r2);
         if (!(rb < l_R2[l])) return;  // outside the support (or NaN)
+        ++inside;
         const double q = sq[j];
         if (rb == 0) {
             acc = fma(-q, l_S0[l], acc);
@@ -482,49 +494,69 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
     };
 
     const int li0 = nl_off[i], li1 = nl_off[i + 1];
-    int nch = 0;  // sources staged (block-uniform)
+    int nch = 0, chunk = 0;  // sources staged, chunks processed (block-uniform)
     auto process = [&]() {
         __syncthreads();
-        for (int k = w; k < nt; k += kNW) {
-            const int pk = t0 + k;
-            if (!(tv.pflag[pk] & 2)) continue;
-            const double xt = tv.ux[pk], yt = tv.uy[pk];
-            const float tx = (float)(xt - cx), ty = (float)(yt - cy);
-            double acc = 0.0, qc = 0.0;
+        // warp w takes the targets w + kNW (s + kS g), s = 0 ... kS - 1, as group g
+        for (int k0 = w; k0 < nt; k0 += kNW * kS) {
+#pragma unroll
+            for (int sl = 0; sl < kS; ++sl) accS[w][sl][lane] = qcS[w][sl][lane] = 0.0;
+            if (lane < kS && k0 + kNW * lane < nt) {
+                txS[w][lane] = tv.ux[t0 + k0 + kNW * lane];
+                tyS[w][lane] = tv.uy[t0 + k0 + kNW * lane];
+            }
+            __syncwarp();
             int qn = 0;
-            for (int j0 = 0; j0 < nch; j0 += 32) {
-                const int j = j0 + lane;
-                bool in = false;
-                if (j < nch) {
-                    const float ex = tx - sox[j], ey = ty - soy[j];
-                    in = fmaf(ey, ey, ex * ex) <= l_thr[slev[j]];
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                if (in) qw[qn + __popc(m & below)] = (uint16_t)j;
-                qn += __popc(m);
-                if (qn >= 32) {
-                    __syncwarp();
-                    pair(qw[lane], xt, yt, acc, qc);
-                    qn -= 32;
-                    __syncwarp();
-                    if (lane < qn) qw[lane] = qw[32 + lane];
-                    __syncwarp();
+            for (int sl = 0; sl < kS; ++sl) {
+                const int k = k0 + kNW * sl;
+                if (k >= nt || !(tv.pflag[t0 + k] & 2)) continue;
+                const float tx = (float)(txS[w][sl] - cx), ty = (float)(tyS[w][sl] - cy);
+                for (int j0 = 0; j0 < nch; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool in = false;
+                    if (j < nch) {
+                        const float ex = tx - sox[j], ey = ty - soy[j];
+                        in = fmaf(ey, ey, ex * ex) <= l_thr[slev[j]];
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (in) qw[qn + __popc(m & below)] = (uint16_t)((sl << 10) | j);
+                    qn += __popc(m);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        pair(qw[lane]);
+                        qn -= 32;
+                        __syncwarp();
+                        if (lane < qn) qw[lane] = qw[32 + lane];
+                        __syncwarp();
+                    }
                 }
             }
             __syncwarp();
-            if (lane < qn) pair(qw[lane], xt, yt, acc, qc);
+            if (lane < qn) pair(qw[lane]);
             __syncwarp();
-            for (int o = 16; o > 0; o >>= 1) {
-                acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                qc += __shfl_xor_sync(0xffffffffu, qc, o);
+            for (int sl = 0; sl < kS; ++sl) {
+                const int k = k0 + kNW * sl, pk = t0 + k;
+                if (k >= nt || !(tv.pflag[pk] & 2)) continue;
+                double acc = accS[w][sl][lane], qc = qcS[w][sl][lane];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                // coincident sources (the target itself among them) are rare: one
+                // lane's charge is taken as it is, more are summed like acc
+                const unsigned mq = __ballot_sync(0xffffffffu, __double_as_longlong(qc) != 0);
+                if (__popc(mq) > 1) {
+                    for (int o = 16; o > 0; o >>= 1) qc += __shfl_xor_sync(0xffffffffu, qc, o);
+                } else {
+                    qc = __shfl_sync(0xffffffffu, qc, mq ? __ffs(mq) - 1 : 0);
+                }
+                if (lane == 0) {
+                    unear[pk] = chunk ? unear[pk] + acc : acc;
+                    qco[pk] = chunk ? qco[pk] + qc : qc;
+                }
             }
-            if (lane == 0) {
-                unear[pk] += acc;
-                qco[pk] += qc;
-            }
+            __syncwarp();
         }
         __syncthreads();
         nch = 0;
+        ++chunk;
     };
     for (int li = li0; li < li1; ++li) {
         const int S = nl_src[li], s0 = tv.bstart[S], ns = tv.bcount[S], l = tv.blevel[S];
@@ -546,6 +578,11 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
         }
     }
     if (nch > 0) process();
+    inside = __reduce_add_sync(0xffffffffu, inside);
+    __syncthreads();
+    if (lane == 0) atomicAdd(&s_inside, inside);
+    __syncthreads();
+    if (tid == 0) atomicAdd(n_inside, (unsigned long long)s_inside);
 }
 
 __global__ void k2_lift(const double *x2, int64_t n, double *x3) {
@@ -582,7 +619,7 @@ __global__ void k2_finalize(int64_t n, const uint8_t *pflag, const int32_t *pout
 
 int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf, const double *src, int64_t ns,
               const double *charges, const double *tgt, int64_t nt, int leaf_cap, int max_level, double *pot,
-              cudaStream_t st, std::string &err) {
+              cudaStream_t st, const cudaEvent_t near_ev[2], std::string &err) {
     if (nt == 0) return DMK_OK;
     const bool same = (tgt == src && nt == ns);
     if (ws.ensure(bf.x3, std::max<int64_t>(ns, 1) * 24) || (!same && ws.ensure(bf.t3, nt * 24))) {
@@ -606,7 +643,7 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     const int64_t n = tv.n;
     if (ws.ensure(bf.mom, (int64_t)tv.nb * pp * 8) || ws.ensure(bf.loc, (int64_t)tv.nb * pp * 8) ||
         ws.ensure(bf.phi, (int64_t)std::max(tree.nslots, 1) * 2 * (d.nf + 1) * N * 8) || ws.ensure(bf.ufar, n * 8) ||
-        ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8)) {
+        ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8) || ws.ensure(bf.cnt, 8)) {
         err = "device allocation failed (2D expansions)";
         return DMK_ERR_OOM;
     }
@@ -614,6 +651,7 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     double *ufar = (double *)bf.ufar.p, *unear = (double *)bf.unear.p, *qco = (double *)bf.qco.p;
     L2CK(cudaMemsetAsync(unear, 0, n * 8, st));
     L2CK(cudaMemsetAsync(qco, 0, n * 8, st));
+    L2CK(cudaMemsetAsync(bf.cnt.p, 0, 8, st));
     // Step 2
     k2_moments<<<tv.nb, kT, 0, st>>>(tv, d, mom);
     launch_tick();
@@ -641,17 +679,20 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     launch_tick();
     L2CK(cudaGetLastError());
     // Steps 4-5
+    if (near_ev[0]) L2CK(cudaEventRecord(near_ev[0], st));
     if (tree.ntleaves > 0) {
+        auto *cnt = (unsigned long long *)bf.cnt.p;
         if (d.gmono)
             k2_near<true><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
                                                         (const int32_t *)tree.nl_off.p,
-                                                        (const int32_t *)tree.nl_src.p, unear, qco);
+                                                        (const int32_t *)tree.nl_src.p, unear, qco, cnt);
         else
             k2_near<false><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
                                                          (const int32_t *)tree.nl_off.p,
-                                                         (const int32_t *)tree.nl_src.p, unear, qco);
+                                                         (const int32_t *)tree.nl_src.p, unear, qco, cnt);
         launch_tick();
     }
+    if (near_ev[1]) L2CK(cudaEventRecord(near_ev[1], st));
     k2_qsum<<<1, 1024, 0, st>>>(tv.q, tv.pflag, n, (double *)bf.qtot.p);
     k2_finalize<<<nblk(n, 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)tree.pout.p, ufar, unear, qco,
                                               (const double *)bf.qtot.p, (const Frame *)tree.frame.p, pot);

@@ -27,13 +27,15 @@ struct Log2dDev {
 
 struct Log2dBufs {
     DBuf x3, t3, mom, loc, phi, ufar, unear, qco, qtot;
+    DBuf cnt;  // pairs inside the support evaluated by the near field (u64)
 };
 
 // One evaluation: sources [ns][2], charges [ns], targets [nt][2] (targets ==
 // sources with nt == ns: every source is a target), potentials [nt]; all
-// device pointers, work on stream st.  Returns a DMK_* code.
+// device pointers, work on stream st; near_ev[0] and near_ev[1] (either may be
+// null) are recorded on st before and after the near field.  Returns a DMK_* code.
 int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf, const double *src, int64_t ns,
               const double *charges, const double *tgt, int64_t nt, int leaf_cap, int max_level, double *pot,
-              cudaStream_t st, std::string &err);
+              cudaStream_t st, const cudaEvent_t near_ev[2], std::string &err);
 
 }  // namespace dmk
