@@ -52,8 +52,11 @@ typedef enum {
                               split in Fourier space (Sec. 3.7); no batches, no
                               gradients */
     DMK_LOG2D = 2,         /* log r in 2D (dim 2), the Fourier-space splitting of
-                              Sec. 3.7 at lambda = 0; DMK_FP64 only, both parts
-                              (no FAR_ONLY / NEAR_ONLY), no batches, no gradients;
+                              Sec. 3.7 at lambda = 0; both parts (no FAR_ONLY /
+                              NEAR_ONLY), no batches, no gradients; DMK_MIXED
+                              (eps >= 1e-7) evaluates the residual pairs in single
+                              precision from hi/lo coordinates and keeps the far
+                              field and the sums in double;
                               dmk_eval and dmk_eval_host take n x 2 coordinates;
                               potentials sum rho_j log |x_i - y_j| over y_j != x_i */
     DMK_SQRTLAPLACE = 3    /* reserved: 1/r^2 in 3D (Sec. 4) */

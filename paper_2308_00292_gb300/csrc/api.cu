@@ -180,6 +180,11 @@ int upload_log2d(dmk_plan_s *pl) {
     const size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(pl->t2.FWr),
                  oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW), og = push(gv),
                  olF = push(lgF), olL = push(lgL), olE = push(lgE);
+    // the Chebyshev coefficients of G rounded to FP32, packed two to a double slot
+    std::vector<float> gcf(pl->t2.g.begin(), pl->t2.g.end());
+    std::vector<double> gcf_words((gcf.size() + 1) / 2, 0.0);
+    memcpy(gcf_words.data(), gcf.data(), gcf.size() * sizeof(float));
+    const size_t ogc = push(gcf_words);
     if (pl->ws.ensure(pl->tab2, (int64_t)h.size() * 8)) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
     if (cudaMemcpy(pl->tab2.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(DMK_ERR_CUDA, "copying the plan tables to the device failed");
@@ -204,6 +209,9 @@ int upload_log2d(dmk_plan_s *pl) {
     d.lgL = base + olL;
     d.lgE = base + olE;
     d.G0 = pl->t2.G0;
+    d.mixed = pl->precision == DMK_MIXED ? 1 : 0;
+    d.gcf = (const float *)(base + ogc);
+    d.gcdeg = (int)gcf.size() - 1;
     return DMK_OK;
 }
 
@@ -421,8 +429,8 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
         return fail(DMK_ERR_INVALID_ARG, "option out of range");
     if ((o.flags & DMK_FLAG_FAR_ONLY) && (o.flags & DMK_FLAG_NEAR_ONLY))
         return fail(DMK_ERR_INVALID_ARG, "DMK_FLAG_FAR_ONLY and DMK_FLAG_NEAR_ONLY are exclusive");
-    if (kernel == DMK_LOG2D && (o.precision == DMK_MIXED || (o.flags & (DMK_FLAG_FAR_ONLY | DMK_FLAG_NEAR_ONLY))))
-        return fail(DMK_ERR_UNSUPPORTED, "the 2D pass runs in FP64 and evaluates both parts");
+    if (kernel == DMK_LOG2D && (o.flags & (DMK_FLAG_FAR_ONLY | DMK_FLAG_NEAR_ONLY)))
+        return fail(DMK_ERR_UNSUPPORTED, "the 2D pass evaluates both parts");
     std::unique_ptr<dmk_plan_s> pl(new (std::nothrow) dmk_plan_s());
     if (!pl) return fail(DMK_ERR_OOM, "host allocation failed");
     pl->kernel = kernel;
@@ -443,7 +451,7 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     // clouds, so the mixed path takes p = 19 to leave room for its rounding.
     if (o.precision == DMK_MIXED && eps < 1e-7) return fail(DMK_ERR_UNSUPPORTED, "DMK_MIXED needs eps >= 1e-7");
     int p_req = o.p;
-    if (p_req == 0 && o.precision == DMK_MIXED && eps < 1e-3 * (1 - 1e-12)) p_req = 19;
+    if (p_req == 0 && o.precision == DMK_MIXED && kernel != DMK_LOG2D && eps < 1e-3 * (1 - 1e-12)) p_req = 19;
     // the Yukawa kernel at the 1e-6 row: p = 18 leaves its far field at ~1.0 eps
     // (lambda S = 10, uniform points), p = 19 at ~0.8 eps
     if (p_req == 0 && kernel == DMK_YUKAWA && eps < 1e-3 * (1 - 1e-12) && eps >= 1e-6 * (1 - 1e-12)) p_req = 19;

@@ -394,12 +394,16 @@ constexpr int kLvl = 32;                // level table (levels 0 .. kMaxLevel, t
 constexpr int kNoSrc = kLvl - 1;
 static_assert(kMaxLevel < kNoSrc, "level table");
 
-template <bool MONO>
+template <bool MONO, bool MIX>
 __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const int32_t *tleaves, const int32_t *nl_off,
                                                const int32_t *nl_src, double *unear, double *qco,
                                                unsigned long long *n_inside) {
     __shared__ double sx[kCH], sy[kCH], sq[kCH];
     __shared__ float sox[kCH], soy[kCH];
+    // MIX: leaf-unit offsets from the leaf's centre as FP32 (hi, lo) pairs, FP32 charges
+    __shared__ float sxh[MIX ? kCH : 1], sxl[MIX ? kCH : 1], syh[MIX ? kCH : 1], syl[MIX ? kCH : 1],
+        sqf[MIX ? kCH : 1], thl[MIX ? kNW : 1][kS][4], gf[MIX ? 64 : 1];
+    __shared__ float l_R2f[MIX ? kLvl : 1], l_s2f[MIX ? kLvl : 1], l_S0f[MIX ? kLvl : 1];
     __shared__ uint8_t slev[kCH];
     __shared__ uint16_t queue[kNW][64];           // (slot << 10) | source
     __shared__ double accS[kNW][kS][32], qcS[kNW][kS][32], txS[kNW][kS], tyS[kNW][kS];
@@ -419,6 +423,15 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
         lgE[e] = d.lgE[e];
     }
     for (int e = tid; e <= gdeg; e += kNT) g[e] = d.g[e];
+    if (MIX)
+        for (int e = tid; e <= d.gcdeg; e += kNT) gf[e] = d.gcf[e];
+    if (MIX && tid < kLvl) {
+        // leaf units: r^2 < R_l^2 as r_leaf^2 < 4^(a - l), t = r_leaf^2 4^(l - a)
+        const bool ok = tid <= kMaxLevel;
+        l_R2f[tid] = ok ? ldexpf(1.0f, 2 * (a - tid)) : -1.0f;
+        l_s2f[tid] = ok ? ldexpf(1.0f, 2 * (tid - a)) : 0.0f;
+        l_S0f[tid] = ok ? (float)(log(level_R(tid)) - d.G0) : 0.0f;
+    }
     if (tid < kLvl) {
         if (tid <= kMaxLevel) {
             const double R = level_R(tid);
@@ -444,8 +457,51 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
     unsigned inside = 0;  // pairs inside the support evaluated by this thread
     const unsigned below = (1u << lane) - 1u;
 
+    const double rBt = 1.0 / Bt;  // 2^a, exact
+    // MIX: one queued pair in FP32 (separations from the hi/lo offsets keep their
+    // relative accuracy however close the points), the lane's sums of the slot
+    // an unevaluated FP32 pair (hi, lo) updated by TwoSum
+    auto pair_mix = [&](int e) {
+        const int j = e & 1023, sl = e >> 10;
+        float2 &acc = reinterpret_cast<float2 *>(&accS[w][sl][0])[lane];
+        const float dx = (thl[w][sl][0] - sxh[j]) + (thl[w][sl][1] - sxl[j]);
+        const float dy = (thl[w][sl][2] - syh[j]) + (thl[w][sl][3] - syl[j]);
+        const float r2 = fmaf(dy, dy, dx * dx);
+        const int l = slev[j];
+        if (!(r2 < l_R2f[l])) return;  // outside the support (or NaN)
+        ++inside;
+        float term;
+        if (r2 < 0x1p-100f) {
+            // coincident, or so close that r^2 leaves the FP32 range: FP64
+            const double ddx = txS[w][sl] - sx[j], ddy = tyS[w][sl] - sy[j], r2d = fma(ddy, ddy, ddx * ddx);
+            if (r2d == 0.0) {
+                qcS[w][sl][lane] += sq[j];
+                term = -sqf[j] * l_S0f[l];
+            } else {
+                term = (float)(sq[j] * (0.5 * log(r2d * (0.5 * l_x2[l])) + d.G0));
+            }
+        } else {
+            const float t = r2 * l_s2f[l], x2 = fmaf(4.0f, t, -2.0f);  // 2 x, x = 2 t - 1
+            float b1 = 0.0f, b2 = 0.0f;
+            for (int n = d.gcdeg; n >= 1; --n) {
+                const float b0 = fmaf(x2, b1, gf[n] - b2);
+                b2 = b1;
+                b1 = b0;
+            }
+            const float G = fmaf(0.5f * x2, b1, gf[0] - b2);
+            term = sqf[j] * fmaf(0.5f, logf(t), G);
+        }
+        const float sum = acc.x + term, bv = sum - acc.x;
+        acc.y += (acc.x - (sum - bv)) + (term - bv);
+        acc.x = sum;
+    };
+
     // one queued pair (target slot, staged source) into the lane's sums of the slot
     auto pair = [&](int e) {
+        if (MIX) {
+            pair_mix(e);
+            return;
+        }
         const int j = e & 1023, sl = e >> 10;
         double &acc = accS[w][sl][lane], &qc = qcS[w][sl][lane];
         const double dx = txS[w][sl] - sx[j], dy = tyS[w][sl] - sy[j];
@@ -502,8 +558,17 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
 #pragma unroll
             for (int sl = 0; sl < kS; ++sl) accS[w][sl][lane] = qcS[w][sl][lane] = 0.0;
             if (lane < kS && k0 + kNW * lane < nt) {
-                txS[w][lane] = tv.ux[t0 + k0 + kNW * lane];
-                tyS[w][lane] = tv.uy[t0 + k0 + kNW * lane];
+                const double xt = tv.ux[t0 + k0 + kNW * lane], yt = tv.uy[t0 + k0 + kNW * lane];
+                txS[w][lane] = xt;
+                tyS[w][lane] = yt;
+                if (MIX) {
+                    const double ox = (xt - cx) * rBt, oy = (yt - cy) * rBt;
+                    const float hx = (float)ox, hy = (float)oy;
+                    thl[w][lane][0] = hx;
+                    thl[w][lane][1] = (float)(ox - hx);
+                    thl[w][lane][2] = hy;
+                    thl[w][lane][3] = (float)(oy - hy);
+                }
             }
             __syncwarp();
             int qn = 0;
@@ -537,8 +602,21 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
             for (int sl = 0; sl < kS; ++sl) {
                 const int k = k0 + kNW * sl, pk = t0 + k;
                 if (k >= nt || !(tv.pflag[pk] & 2)) continue;
-                double acc = accS[w][sl][lane], qc = qcS[w][sl][lane];
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                double acc, qc = qcS[w][sl][lane];
+                if (MIX) {
+                    float2 a2 = reinterpret_cast<const float2 *>(&accS[w][sl][0])[lane];
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, a2.x, o),
+                                    ol = __shfl_xor_sync(0xffffffffu, a2.y, o);
+                        const float sum = a2.x + oh, bv = sum - a2.x;
+                        a2.y = (a2.y + ol) + ((a2.x - (sum - bv)) + (oh - bv));
+                        a2.x = sum;
+                    }
+                    acc = (double)a2.x + (double)a2.y;
+                } else {
+                    acc = accS[w][sl][lane];
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                }
                 // coincident sources (the target itself among them) are rare: one
                 // lane's charge is taken as it is, more are summed like acc
                 const unsigned mq = __ballot_sync(0xffffffffu, __double_as_longlong(qc) != 0);
@@ -571,6 +649,15 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
                 sox[js] = (float)(xs - cx);
                 soy[js] = (float)(ys - cy);
                 slev[js] = (uint8_t)((tv.pflag[ks] & 1) ? l : kNoSrc);
+                if (MIX) {
+                    const double ox = (xs - cx) * rBt, oy = (ys - cy) * rBt;
+                    const float hx = (float)ox, hy = (float)oy;
+                    sxh[js] = hx;
+                    sxl[js] = (float)(ox - hx);
+                    syh[js] = hy;
+                    syl[js] = (float)(oy - hy);
+                    sqf[js] = (float)tv.q[ks];
+                }
             }
             nch += take;
             o += take;
@@ -593,14 +680,29 @@ __global__ void k2_lift(const double *x2, int64_t n, double *x3) {
     x3[3 * i + 2] = 0.0;
 }
 
-// total source charge in a fixed order (one block)
-__global__ void k2_qsum(const double *q, const uint8_t *pflag, int64_t n, double *out) {
-    __shared__ double s[1024];
+// total source charge in a fixed order: kQB blocks sum fixed ranges (threads
+// strided, then a tree), one block adds the partial sums
+constexpr int kQB = 304, kQT = 256;
+__global__ void __launch_bounds__(kQT) k2_qsum_part(const double *q, const uint8_t *pflag, int64_t n, double *part) {
+    __shared__ double s[kQT];
+    const int64_t per = (n + kQB - 1) / kQB, lo = per * blockIdx.x, hi = min(n, lo + per);
     double a = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += 1024) a += (pflag[k] & 1) ? q[k] : 0.0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += kQT) a += (pflag[k] & 1) ? q[k] : 0.0;
     s[threadIdx.x] = a;
     __syncthreads();
-    for (int h = 512; h > 0; h >>= 1) {
+    for (int h = kQT / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(kQB) k2_qsum(const double *part, double *out) {
+    __shared__ double s[512];
+    s[threadIdx.x] = part[threadIdx.x];
+    if (threadIdx.x + kQB < 512) s[threadIdx.x + kQB] = 0.0;
+    __syncthreads();
+    for (int h = 256; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
@@ -643,7 +745,8 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     const int64_t n = tv.n;
     if (ws.ensure(bf.mom, (int64_t)tv.nb * pp * 8) || ws.ensure(bf.loc, (int64_t)tv.nb * pp * 8) ||
         ws.ensure(bf.phi, (int64_t)std::max(tree.nslots, 1) * 2 * (d.nf + 1) * N * 8) || ws.ensure(bf.ufar, n * 8) ||
-        ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8) || ws.ensure(bf.cnt, 8)) {
+        ws.ensure(bf.unear, n * 8) || ws.ensure(bf.qco, n * 8) || ws.ensure(bf.qtot, 8) || ws.ensure(bf.cnt, 8) ||
+        ws.ensure(bf.qpart, kQB * 8)) {
         err = "device allocation failed (2D expansions)";
         return DMK_ERR_OOM;
     }
@@ -682,18 +785,20 @@ int run_log2d(const Log2dDev &d, TreeBuilder &tree, Workspace &ws, Log2dBufs &bf
     if (near_ev[0]) L2CK(cudaEventRecord(near_ev[0], st));
     if (tree.ntleaves > 0) {
         auto *cnt = (unsigned long long *)bf.cnt.p;
-        if (d.gmono)
-            k2_near<true><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
-                                                        (const int32_t *)tree.nl_off.p,
-                                                        (const int32_t *)tree.nl_src.p, unear, qco, cnt);
+        const int32_t *tl = (const int32_t *)tree.tleaves.p, *no = (const int32_t *)tree.nl_off.p,
+                      *ns_ = (const int32_t *)tree.nl_src.p;
+        if (d.mixed)
+            k2_near<false, true><<<tree.ntleaves, kNT, 0, st>>>(tv, d, tl, no, ns_, unear, qco, cnt);
+        else if (d.gmono)
+            k2_near<true, false><<<tree.ntleaves, kNT, 0, st>>>(tv, d, tl, no, ns_, unear, qco, cnt);
         else
-            k2_near<false><<<tree.ntleaves, kNT, 0, st>>>(tv, d, (const int32_t *)tree.tleaves.p,
-                                                         (const int32_t *)tree.nl_off.p,
-                                                         (const int32_t *)tree.nl_src.p, unear, qco, cnt);
+            k2_near<false, false><<<tree.ntleaves, kNT, 0, st>>>(tv, d, tl, no, ns_, unear, qco, cnt);
         launch_tick();
     }
     if (near_ev[1]) L2CK(cudaEventRecord(near_ev[1], st));
-    k2_qsum<<<1, 1024, 0, st>>>(tv.q, tv.pflag, n, (double *)bf.qtot.p);
+    k2_qsum_part<<<kQB, kQT, 0, st>>>(tv.q, tv.pflag, n, (double *)bf.qpart.p);
+    k2_qsum<<<1, kQB, 0, st>>>((const double *)bf.qpart.p, (double *)bf.qtot.p);
+    launch_tick();
     k2_finalize<<<nblk(n, 256), 256, 0, st>>>(n, tv.pflag, (const int32_t *)tree.pout.p, ufar, unear, qco,
                                               (const double *)bf.qtot.p, (const Frame *)tree.frame.p, pot);
     launch_tick();

@@ -23,11 +23,16 @@ struct Log2dDev {
     const double *lgE;        // g[0] - (j/2) log 2 (j = 1 ... 255: t = m 2^-j)
     int gmono;
     double G0;                // G(0)
+    // the mixed-precision near field (FP32 pairs, FP64 sums of the lanes)
+    int mixed;
+    const float *gcf;         // [gcdeg + 1]: G in Chebyshev polynomials of x, FP32
+    int gcdeg;
 };
 
 struct Log2dBufs {
     DBuf x3, t3, mom, loc, phi, ufar, unear, qco, qtot;
-    DBuf cnt;  // pairs inside the support evaluated by the near field (u64)
+    DBuf cnt;    // pairs inside the support evaluated by the near field (u64)
+    DBuf qpart;  // partial sums of the total charge
 };
 
 // One evaluation: sources [ns][2], charges [ns], targets [nt][2] (targets ==

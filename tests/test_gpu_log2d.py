@@ -3,8 +3,8 @@ plane) through the C ABI: the FP64 pass against the oracle's 2D pass on the
 same quad-tree (the two share the formulas, not the code; the residual's
 smooth part is a Chebyshev fit within 1e-3 eps) within 1e-2 eps, and against
 the direct sum within eps; separate targets, coincident points, the log S term
-of the unit-box map, empty and one-point inputs, the host entry point, and the
-options the 2D pass refuses.
+of the unit-box map, empty and one-point inputs, the host entry point, the
+mixed-precision near field, and the options the 2D pass refuses.
 """
 import numpy as np
 import pytest
@@ -118,9 +118,38 @@ def test_small_inputs_and_host_entry(dmk, oracle_mod):
     assert rel(ud, oracle_mod.direct_log2d(x, q)) < 1e-6
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("eps,leaf_cap", [(1e-6, 120), (1e-6, 40), (1e-7, 160)])
+def test_mixed_near_field(dmk, oracle_mod, case, eps, leaf_cap):
+    """The mixed path: FP32 residual pairs from hi/lo leaf-unit offsets, FP64
+    far field and sums; within eps of the direct sum, and within a fraction of
+    eps of the FP64 pass on the same tree."""
+    x, q = CASES[case]()
+    um = run(dmk, x, q, eps=eps, leaf_cap=leaf_cap, precision=dmk.DMK_MIXED)
+    ud = run(dmk, x, q, eps=eps, leaf_cap=leaf_cap)
+    assert rel(um, oracle_mod.direct_log2d(x, q)) < eps
+    assert rel(um, ud) < 0.3 * eps
+
+
+def test_mixed_close_pairs(dmk, oracle_mod):
+    """Separations from 1e-3 to 1e-150 on the mixed path: FP32 pairs down to
+    r^2 = 2^-100 in leaf units, FP64 below, coincident points exact."""
+    x, q = inputs.disk2d(2000, seed=829)
+    x = x - x.min(axis=0) + 0.25
+    seps = [1e-3, 1e-5, 1e-8, 1e-12, 1e-20, 1e-45, 1e-150]
+    extra = [[0.0, 0.0], [0.0, 0.0]] + [[s, 0.0] for s in seps] + [[0.0, s] for s in seps[::2]]
+    x = np.r_[x, np.array(extra)]
+    q = np.r_[q, np.random.default_rng(830).uniform(-1, 1, len(extra))]
+    um = run(dmk, x, q, eps=1e-6, leaf_cap=60, precision=dmk.DMK_MIXED)
+    d = oracle_mod.direct_log2d(x, q)
+    assert rel(um, d) < 1e-6
+    k = len(extra)
+    assert np.max(np.abs(um[-k:] - d[-k:]) / np.abs(d[-k:])) < 1e-6
+
+
 def test_refused_options(dmk):
     x, q = inputs.disk2d(300, seed=826)
-    for kw in (dict(precision=dmk.DMK_MIXED), dict(flags=dmk.FLAG_FAR_ONLY), dict(dim=3)):
+    for kw in (dict(precision=dmk.DMK_MIXED, eps=1e-8), dict(flags=dmk.FLAG_FAR_ONLY), dict(dim=3)):
         args = dict(kernel=dmk.DMK_LOG2D, dim=2, eps=1e-6)
         args.update(kw)
         with pytest.raises(dmk.DMKError) as e:

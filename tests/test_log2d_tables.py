@@ -67,3 +67,17 @@ def test_residual(dmk, oracle_mod, eps):
     s0 = oracle_mod.kernel_log2d(op, 0, 3, np.zeros(1))[0]
     assert np.log(1 / 8) - G0 == pytest.approx(s0, abs=1e-12)
     assert chebyshev.chebval(-1.0, g) == pytest.approx(G0, abs=bar)
+
+
+def test_mixed_plans(dmk):
+    """The mixed path (FP32 residual pairs) is taken at eps >= 1e-7 with the FP64
+    plan's tables, and refused below, where FP32 rounding reaches eps."""
+    for eps in (1e-6, 1e-7):
+        with dmk.Plan(eps, flags=dmk.FLAG_HOST_ONLY, kernel=dmk.DMK_LOG2D, dim=2,
+                      precision=dmk.DMK_MIXED) as pm, plan(dmk, eps) as pd:
+            a, b = pm.params(), pd.params()
+            assert a["precision"] == dmk.DMK_MIXED
+            assert all(a[k] == b[k] for k in ("p", "nf", "n0", "q_degree", "leaf_cap"))
+    with pytest.raises(dmk.DMKError) as e:
+        dmk.Plan(1e-8, flags=dmk.FLAG_HOST_ONLY, kernel=dmk.DMK_LOG2D, dim=2, precision=dmk.DMK_MIXED)
+    assert e.value.code == 2
