@@ -592,7 +592,7 @@ def run_log2d(args):
     sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else FFMA_MEASURED_MHZ
     near_ms = float(np.median(t_near))
     if args.log2d_mixed:
-        per_pair, unit_name = 34 + 3 * prm["q_degree"], "fp32"
+        per_pair, unit_name = 34 + 3 * prm["q_degree_f32"], "fp32"
         peak = FFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
         basis = "FFMA probe %.1f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (FFMA_MEASURED_TFLOPS,
                                                                              FFMA_MEASURED_MHZ, sm_mhz)

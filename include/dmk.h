@@ -305,6 +305,10 @@ typedef struct {
     int q_degree;           /* degree of the residual-kernel polynomial in r^2
                                (DMK_LOG2D: of G, R_l(r) = log(r / R_l) + G(r^2 / R_l^2)) */
     double psi0_over_c0;    /* psi(0)/c_0: the self term at R = 1 */
+    int q_degree_f32;       /* DMK_LOG2D: the degree at which the single-precision
+                               near field (DMK_MIXED) cuts G's Chebyshev series, where
+                               its tail falls below 1e-2 eps max(1, |G|); q_degree
+                               for the 3D kernels */
 } dmk_plan_params;
 
 DMK_API int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out);

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libdmk (include/dmk.h): plan construction (Step 1 of
 // Sec. 3.4), one evaluation pass (Steps 0 and 2-5), statistics and tree export.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -46,6 +47,7 @@ struct dmk_plan_s {
     int precision = 0;
     int leaf_cap = 280, max_level = 20;
     int qdeg = 0;
+    int gdeg_f32 = 0;           // DMK_LOG2D: degree of G's series on the FP32 near field
     double lambda = 0.0;        // Yukawa parameter (input units), 0 for Laplace
     dmk::YukawaTables yt;       // Yukawa tables at the last unit-box lambda
     dmk::Workspace ws;
@@ -155,6 +157,26 @@ int upload_yukawa(dmk_plan_s *pl, dmk::DevTables<T> &dt, double lam_unit, int nl
     return DMK_OK;
 }
 
+// The degree at which the FP32 near field of a DMK_LOG2D plan cuts G's
+// Chebyshev series: where the tail stays below 1e-2 eps max(1, |G|) (FP32
+// cannot resolve more), at least 3.
+static int log2d_f32_degree(const std::vector<double> &gc, double eps) {
+    double gmax = 1.0;
+    for (int j = 0; j <= 256; ++j) {
+        const double x = -1.0 + j / 128.0;
+        double b1 = 0.0, b2 = 0.0;
+        for (int k = (int)gc.size() - 1; k >= 1; --k) {
+            const double b0 = 2.0 * x * b1 - b2 + gc[k];
+            b2 = b1;
+            b1 = b0;
+        }
+        gmax = std::max(gmax, std::fabs(x * b1 - b2 + gc[0]));
+    }
+    int d = (int)gc.size() - 1;
+    for (double tail = 0.0; d > 3 && tail + std::fabs(gc[d]) <= 1e-2 * eps * gmax; --d) tail += std::fabs(gc[d]);
+    return d;
+}
+
 int upload_log2d(dmk_plan_s *pl) {
     const dmk::Tables &tb = pl->tb;
     std::vector<double> h;
@@ -180,9 +202,15 @@ int upload_log2d(dmk_plan_s *pl) {
     const size_t oA = push(A2), oFr = push(tb.Fr), oFi = push(tb.Fi), oFWr = push(pl->t2.FWr),
                  oFWi = push(pl->t2.FWi), ow = push(pl->t2.w), owW = push(pl->t2.wW), og = push(gv),
                  olF = push(lgF), olL = push(lgL), olE = push(lgE);
-    // the Chebyshev coefficients of G rounded to FP32, packed two to a double slot
-    std::vector<float> gcf(pl->t2.g.begin(), pl->t2.g.end());
-    std::vector<double> gcf_words((gcf.size() + 1) / 2, 0.0);
+    // The Chebyshev coefficients of G for the FP32 near field (degree
+    // gdeg_f32), rounded to FP32, zero-padded at the top to groups of four (zero
+    // leading coefficients leave Clenshaw's recurrence unchanged), packed two
+    // to a double slot.
+    const std::vector<double> &gc = pl->t2.g;
+    const int gdeg_f = pl->gdeg_f32;
+    std::vector<float> gcf((gdeg_f / 4 + 1) * 4, 0.0f);
+    for (int k = 0; k <= gdeg_f; ++k) gcf[k] = (float)gc[k];
+    std::vector<double> gcf_words(gcf.size() / 2, 0.0);
     memcpy(gcf_words.data(), gcf.data(), gcf.size() * sizeof(float));
     const size_t ogc = push(gcf_words);
     if (pl->ws.ensure(pl->tab2, (int64_t)h.size() * 8)) return fail(DMK_ERR_OOM, "device allocation failed (tables)");
@@ -211,7 +239,8 @@ int upload_log2d(dmk_plan_s *pl) {
     d.G0 = pl->t2.G0;
     d.mixed = pl->precision == DMK_MIXED ? 1 : 0;
     d.gcf = (const float *)(base + ogc);
-    d.gcdeg = (int)gcf.size() - 1;
+    d.gcdeg = gdeg_f;
+    d.gcn4 = (int)gcf.size() / 4;
     return DMK_OK;
 }
 
@@ -463,6 +492,7 @@ int dmk_plan(dmk_kernel kernel, int dim, double eps, const dmk_opts *opts, dmk_p
     if (kernel == DMK_LOG2D) {
         if (dmk::build_log2d_tables(pl->tb, pl->t2, err) != 0) return fail(DMK_ERR_UNSUPPORTED, err);
         if (pl->t2.g.size() > 64) return fail(DMK_ERR_INTERNAL, "2D residual polynomial degree above 63");
+        pl->gdeg_f32 = log2d_f32_degree(pl->t2.g, eps);
     }
     if (pl->qdeg >= 64) return fail(DMK_ERR_INTERNAL, "residual polynomial degree above 63");
     pl->host_only = (o.flags & DMK_FLAG_HOST_ONLY) != 0;
@@ -718,6 +748,7 @@ int dmk_plan_get_params(dmk_plan_t plan, dmk_plan_params *out) {
     out->precision = plan->precision;
     out->q_degree = plan->kernel == DMK_LOG2D ? (int)plan->t2.g.size() - 1 : plan->qdeg;
     out->psi0_over_c0 = plan->tb.psi0_over_c0;
+    out->q_degree_f32 = plan->kernel == DMK_LOG2D ? plan->gdeg_f32 : out->q_degree;
     return DMK_OK;
 }
 

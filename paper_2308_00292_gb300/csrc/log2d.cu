@@ -175,21 +175,30 @@ __device__ void pw_from_moments(const double *M, const double *Fr, const double 
         Yi[e] = si;
     }
     __syncthreads();
-    // Phi[mx][my] = sum_b F[my][b] Y[mx][b]: F[my][b] = Fr (b even) or i Fi (b odd)
-    for (int e = tid; e < NH * N; e += kT) {
-        const int mx = e / N, my = e - mx * N;
-        const double *fr = Fr + (size_t)my * p, *fi = Fi + (size_t)my * p, *yr = Yr + mx * p, *yi = Yi + mx * p;
-        double sr = 0.0, si = 0.0;
+    // Phi[mx][my] = sum_b F[my][b] Y[mx][b]: F[my][b] = Fr (b even) or i Fi (b odd),
+    // and F[-my] = conj(F[my]).  With E = sum_{b even} Fr[m][b] Y[mx][b] and
+    // O = sum_{b odd} Fi[m][b] Y[mx][b] (complex, m >= 0):
+    // Phi[mx][m] = E + i O and Phi[mx][-m] = E - i O
+    for (int e = tid; e < NH * NH; e += kT) {
+        const int mx = e / NH, m = e - mx * NH;
+        const double *fr = Fr + (size_t)(m + nh) * p, *fi = Fi + (size_t)(m + nh) * p, *yr = Yr + mx * p,
+                     *yi = Yi + mx * p;
+        double er = 0.0, ei = 0.0, orr = 0.0, oi = 0.0;
         for (int bb = 0; bb < p; bb += 2) {
-            sr += fr[bb] * yr[bb];
-            si += fr[bb] * yi[bb];
+            er += fr[bb] * yr[bb];
+            ei += fr[bb] * yi[bb];
         }
         for (int bb = 1; bb < p; bb += 2) {
-            sr -= fi[bb] * yi[bb];
-            si += fi[bb] * yr[bb];
+            orr += fi[bb] * yr[bb];
+            oi += fi[bb] * yi[bb];
         }
-        phi[2 * e] = sr;
-        phi[2 * e + 1] = si;
+        double *pp = phi + 2 * (mx * N + nh + m), *pm = phi + 2 * (mx * N + nh - m);
+        pp[0] = er - oi;
+        pp[1] = ei + orr;
+        if (m > 0) {
+            pm[0] = er + oi;
+            pm[1] = ei - orr;
+        }
     }
     __syncthreads();
 }
@@ -201,36 +210,46 @@ __device__ void pw_from_moments(const double *M, const double *Fr, const double 
 __device__ void coef_from_pw(const double *Psi, const double *Fr, const double *Fi, int p, int N, double *Zr,
                              double *Zi, double *acc /* kPer per thread */) {
     const int tid = threadIdx.x, nh = (N - 1) / 2, NH = nh + 1;
-    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]: conj(F) = Fr (n even) or -i Fi (n odd)
-    for (int e = tid; e < p * N; e += kT) {
-        const int n = e / N, my = e - n * N;
-        double sr = 0.0, si = 0.0;
+    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]: conj(F) = Fr (n even) or -i Fi (n odd),
+    // formed for my = +m and -m together.  The second contraction needs only
+    // Zs[n][m] = Re Z[n][m] + Re Z[n][-m] (n' even: Fr[-m] = Fr[m]) and
+    // Za[n][m] = Im Z[n][m] - Im Z[n][-m] (n' odd: Fi[-m] = -Fi[m]), m = 0 ... nh
+    // (Zs[n][0] = Re Z[n][0], Za[n][0] = 0), stored in Zr and Zi as p x (nh + 1)
+    for (int e = tid; e < p * NH; e += kT) {
+        const int n = e / NH, m = e - n * NH;
+        const double *pp = Psi + 2 * (nh + m), *pm = Psi + 2 * (nh - m);
+        double rp = 0.0, ip = 0.0, rm = 0.0, im = 0.0;
         if (!(n & 1)) {
             for (int mx = 0; mx < NH; ++mx) {
                 const double f = Fr[(mx + nh) * p + n];
-                sr += f * Psi[2 * (mx * N + my)];
-                si += f * Psi[2 * (mx * N + my) + 1];
+                rp += f * pp[2 * mx * N];
+                ip += f * pp[2 * mx * N + 1];
+                rm += f * pm[2 * mx * N];
+                im += f * pm[2 * mx * N + 1];
             }
         } else {
             for (int mx = 0; mx < NH; ++mx) {
                 const double f = Fi[(mx + nh) * p + n];
-                sr += f * Psi[2 * (mx * N + my) + 1];
-                si -= f * Psi[2 * (mx * N + my)];
+                rp += f * pp[2 * mx * N + 1];
+                ip -= f * pp[2 * mx * N];
+                rm += f * pm[2 * mx * N + 1];
+                im -= f * pm[2 * mx * N];
             }
         }
-        Zr[e] = sr;
-        Zi[e] = si;
+        Zr[e] = m ? rp + rm : rp;
+        Zi[e] = m ? ip - im : 0.0;
     }
     __syncthreads();
-    // c[n][n'] = Re sum_my conj(F[my][n']) Z[n][my] = sum_my Fr Zr (n' even) or Fi Zi (n' odd)
+    // c[n][n'] = Re sum_my conj(F[my][n']) Z[n][my] = sum_m Fr[m][n'] Zs[n][m] (n' even)
+    // or sum_m Fi[m][n'] Za[n][m] (n' odd), m = 0 ... nh
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int e = tid + j * kT;
         if (e < p * p) {
             const int n = e / p, n2 = e - n * p;
-            const double *F = (n2 & 1) ? Fi : Fr, *Z = ((n2 & 1) ? Zi : Zr) + n * N;
+            const double *F = ((n2 & 1) ? Fi : Fr) + (size_t)nh * p + n2, *Z = ((n2 & 1) ? Zi : Zr) + n * NH;
             double s = 0.0;
-            for (int my = 0; my < N; ++my) s += F[my * p + n2] * Z[my];
+            for (int m = 0; m < NH; ++m) s += F[m * p] * Z[m];
             acc[j] += s;
         }
     }
@@ -402,7 +421,8 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
     __shared__ float sox[kCH], soy[kCH];
     // MIX: leaf-unit offsets from the leaf's centre as FP32 (hi, lo) pairs, FP32 charges
     __shared__ float sxh[MIX ? kCH : 1], sxl[MIX ? kCH : 1], syh[MIX ? kCH : 1], syl[MIX ? kCH : 1],
-        sqf[MIX ? kCH : 1], thl[MIX ? kNW : 1][kS][4], gf[MIX ? 64 : 1];
+        sqf[MIX ? kCH : 1], thl[MIX ? kNW : 1][kS][4];
+    __shared__ float4 gf4[MIX ? 16 : 1];
     __shared__ float l_R2f[MIX ? kLvl : 1], l_s2f[MIX ? kLvl : 1], l_S0f[MIX ? kLvl : 1];
     __shared__ uint8_t slev[kCH];
     __shared__ uint16_t queue[kNW][64];           // (slot << 10) | source
@@ -424,7 +444,7 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
     }
     for (int e = tid; e <= gdeg; e += kNT) g[e] = d.g[e];
     if (MIX)
-        for (int e = tid; e <= d.gcdeg; e += kNT) gf[e] = d.gcf[e];
+        for (int e = tid; e < d.gcn4; e += kNT) gf4[e] = reinterpret_cast<const float4 *>(d.gcf)[e];
     if (MIX && tid < kLvl) {
         // leaf units: r^2 < R_l^2 as r_leaf^2 < 4^(a - l), t = r_leaf^2 4^(l - a)
         const bool ok = tid <= kMaxLevel;
@@ -482,13 +502,20 @@ __global__ void __launch_bounds__(kNT) k2_near(TreeView tv, Log2dDev d, const in
             }
         } else {
             const float t = r2 * l_s2f[l], x2 = fmaf(4.0f, t, -2.0f);  // 2 x, x = 2 t - 1
-            float b1 = 0.0f, b2 = 0.0f;
-            for (int n = d.gcdeg; n >= 1; --n) {
-                const float b0 = fmaf(x2, b1, gf[n] - b2);
-                b2 = b1;
-                b1 = b0;
+            // Clenshaw, four coefficients per shared-memory load
+            float b1 = 0.0f, b2 = 0.0f, b0;
+            for (int gi = d.gcn4 - 1; gi >= 1; --gi) {
+                const float4 c = gf4[gi];
+                b0 = fmaf(x2, b1, c.w - b2), b2 = b1, b1 = b0;
+                b0 = fmaf(x2, b1, c.z - b2), b2 = b1, b1 = b0;
+                b0 = fmaf(x2, b1, c.y - b2), b2 = b1, b1 = b0;
+                b0 = fmaf(x2, b1, c.x - b2), b2 = b1, b1 = b0;
             }
-            const float G = fmaf(0.5f * x2, b1, gf[0] - b2);
+            const float4 c = gf4[0];
+            b0 = fmaf(x2, b1, c.w - b2), b2 = b1, b1 = b0;
+            b0 = fmaf(x2, b1, c.z - b2), b2 = b1, b1 = b0;
+            b0 = fmaf(x2, b1, c.y - b2), b2 = b1, b1 = b0;
+            const float G = fmaf(0.5f * x2, b1, c.x - b2);
             term = sqf[j] * fmaf(0.5f, logf(t), G);
         }
         const float sum = acc.x + term, bv = sum - acc.x;

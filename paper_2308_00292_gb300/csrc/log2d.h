@@ -25,8 +25,8 @@ struct Log2dDev {
     double G0;                // G(0)
     // the mixed-precision near field (FP32 pairs, FP64 sums of the lanes)
     int mixed;
-    const float *gcf;         // [gcdeg + 1]: G in Chebyshev polynomials of x, FP32
-    int gcdeg;
+    const float *gcf;         // [4 gcn4]: G in Chebyshev polynomials of x, FP32, degree
+    int gcdeg, gcn4;          // gcdeg, zero above it (16-byte aligned)
 };
 
 struct Log2dBufs {

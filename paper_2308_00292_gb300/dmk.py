@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
 class PlanParams(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("c", ctypes.c_double), ("p", ctypes.c_int), ("nf", ctypes.c_int),
                 ("n0", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_level", ctypes.c_int),
-                ("precision", ctypes.c_int), ("q_degree", ctypes.c_int), ("psi0_over_c0", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("q_degree", ctypes.c_int), ("psi0_over_c0", ctypes.c_double),
+                ("q_degree_f32", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

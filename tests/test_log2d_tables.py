@@ -81,3 +81,21 @@ def test_mixed_plans(dmk):
     with pytest.raises(dmk.DMKError) as e:
         dmk.Plan(1e-8, flags=dmk.FLAG_HOST_ONLY, kernel=dmk.DMK_LOG2D, dim=2, precision=dmk.DMK_MIXED)
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-7])
+def test_f32_series_cut(dmk, eps):
+    """The FP32 near field's series for G: the Chebyshev coefficients cut where
+    their tail sum stays below 1e-2 eps max(1, |G|), so that the cut G is
+    within that bound of the full one everywhere on [-1, 1]."""
+    with plan(dmk, eps) as pl:
+        prm = pl.params()
+        g = pl.table(3)
+        d = prm["q_degree_f32"]
+        assert 3 <= d <= prm["q_degree"]
+        x = np.linspace(-1.0, 1.0, 1001)
+        full = chebyshev.chebval(x, g)
+        gmax = max(1.0, np.abs(full).max())
+        assert np.abs(full - chebyshev.chebval(x, g[:d + 1])).max() <= 1e-2 * eps * gmax * (1 + 1e-9)
+        if d < prm["q_degree"]:  # one more coefficient dropped would pass the bound
+            assert np.abs(g[d:]).sum() > 1e-2 * eps * gmax
