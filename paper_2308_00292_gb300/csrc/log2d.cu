@@ -112,24 +112,48 @@ __global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart
     if ((tv.bflags[b] & BF_LEAF) || tv.bnsrc[b] == 0) return;
     __shared__ double MC[kMaxP * kMaxP], Y[kMaxP * kMaxP];
     const int p = d.p, pp = p * p, tid = threadIdx.x;
-    double acc[kPer];
+    // M_P = sum_C A_sx(C) (M_C A_sy(C)^T): the children with the same x half share
+    // A_sx, so Y_C = M_C A_sy(C)^T is summed per x half (in the threads' registers,
+    // which own the same entries of Y and of M_P) and A_sx is applied once per half
+    double ys[2][kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kPer; ++j) ys[0][j] = ys[1][j] = 0.0;
     const uint8_t mask = tv.bcmask[b];
-    int ci = tv.bchild0[b];
+    int ci = tv.bchild0[b], halves = 0;
     for (int oc = 0; oc < 8; ++oc) {
         if (!(mask & (1u << oc))) continue;
         const int c = ci++;
         if (tv.bnsrc[c] == 0) continue;
-        const double *Ax = d.A + (size_t)(oc & 1) * pp, *Ay = d.A + (size_t)((oc >> 1) & 1) * pp;
+        const int hx = oc & 1;
+        halves |= 1 << hx;
+        const double *Ay = d.A + (size_t)((oc >> 1) & 1) * pp;
+        __syncthreads();
         for (int e = tid; e < pp; e += kT) MC[e] = mom[(size_t)c * pp + e];
         __syncthreads();
-        // Y[k][n'] = sum_k' A_sy[n'][k'] M_C[k][k']
-        for (int e = tid; e < pp; e += kT) {
-            const int k = e / p, n2 = e - k * p;
-            double s = 0.0;
-            for (int k2 = 0; k2 <= n2; ++k2) s += Ay[n2 * p + k2] * MC[k * p + k2];  // A_s[n][m] = 0 for m > n
-            Y[e] = s;
+        // Y[k][n'] = sum_k' A_sy[n'][k'] M_C[k][k'] (A_s[n][m] = 0 for m > n)
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kT;
+            if (e < pp) {
+                const int k = e / p, n2 = e - k * p;
+                double s = 0.0;
+                for (int k2 = 0; k2 <= n2; ++k2) s += Ay[n2 * p + k2] * MC[k * p + k2];
+                if (hx) ys[1][j] += s;
+                else ys[0][j] += s;
+            }
+        }
+    }
+    double acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
+    for (int hx = 0; hx < 2; ++hx) {
+        if (!(halves & (1 << hx))) continue;
+        const double *Ax = d.A + (size_t)hx * pp;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kT;
+            if (e < pp) Y[e] = hx ? ys[1][j] : ys[0][j];
         }
         __syncthreads();
 #pragma unroll
@@ -142,7 +166,6 @@ __global__ void __launch_bounds__(kT) k2_c2p(TreeView tv, Log2dDev d, int lstart
                 acc[j] += s;
             }
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
@@ -205,39 +228,47 @@ __device__ void pw_from_moments(const double *M, const double *Fr, const double 
 
 // c[n][n'] = Re sum_{all m} conj(F[mx][n]) conj(F[my][n']) Psi[mx][my] from the
 // half spectrum Psi ((nh + 1) x N complex interleaved, the rows mx >= 1 already
-// doubled: the terms at m and -m are conjugate); the workspace Z (p x N
-// complex) in shared memory
-__device__ void coef_from_pw(const double *Psi, const double *Fr, const double *Fi, int p, int N, double *Zr,
+// doubled: the terms at m and -m are conjugate; overwritten); the workspace Z
+// (p x (nh + 1), two real arrays) in shared memory
+__device__ void coef_from_pw(double *Psi, const double *Fr, const double *Fi, int p, int N, double *Zr,
                              double *Zi, double *acc /* kPer per thread */) {
     const int tid = threadIdx.x, nh = (N - 1) / 2, NH = nh + 1;
-    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]: conj(F) = Fr (n even) or -i Fi (n odd),
-    // formed for my = +m and -m together.  The second contraction needs only
-    // Zs[n][m] = Re Z[n][m] + Re Z[n][-m] (n' even: Fr[-m] = Fr[m]) and
-    // Za[n][m] = Im Z[n][m] - Im Z[n][-m] (n' odd: Fi[-m] = -Fi[m]), m = 0 ... nh
-    // (Zs[n][0] = Re Z[n][0], Za[n][0] = 0), stored in Zr and Zi as p x (nh + 1)
+    // Z[n][my] = sum_mx conj(F[mx][n]) Psi[mx][my]: conj(F) = Fr (n even) or -i Fi (n odd).
+    // The second contraction needs only Zs[n][m] = Re Z[n][m] + Re Z[n][-m] (n' even:
+    // Fr[-m] = Fr[m]) and Za[n][m] = Im Z[n][m] - Im Z[n][-m] (n' odd: Fi[-m] = -Fi[m]),
+    // m = 0 ... nh (Zs[n][0] = Re Z[n][0], Za[n][0] = 0).  So Psi's columns are first
+    // replaced in place by their sums (column +m) and differences (column -m), m >= 1,
+    // and each of Zs, Za is one real contraction over mx.  Stored in Zr and Zi as
+    // p x (nh + 1).
+    for (int e = tid; e < NH * nh; e += kT) {
+        const int mx = e / nh, m = e - mx * nh + 1;
+        double *pp = Psi + 2 * (mx * N + nh + m), *pm = Psi + 2 * (mx * N + nh - m);
+        const double ar = pp[0], ai = pp[1], br = pm[0], bi = pm[1];
+        pp[0] = ar + br;
+        pp[1] = ai + bi;
+        pm[0] = ar - br;
+        pm[1] = ai - bi;
+    }
+    __syncthreads();
     for (int e = tid; e < p * NH; e += kT) {
         const int n = e / NH, m = e - n * NH;
-        const double *pp = Psi + 2 * (nh + m), *pm = Psi + 2 * (nh - m);
-        double rp = 0.0, ip = 0.0, rm = 0.0, im = 0.0;
+        const double *ps = Psi + 2 * (nh + m), *pa = Psi + 2 * (nh - m);
+        double zs = 0.0, za = 0.0;
         if (!(n & 1)) {
             for (int mx = 0; mx < NH; ++mx) {
                 const double f = Fr[(mx + nh) * p + n];
-                rp += f * pp[2 * mx * N];
-                ip += f * pp[2 * mx * N + 1];
-                rm += f * pm[2 * mx * N];
-                im += f * pm[2 * mx * N + 1];
+                zs += f * ps[2 * mx * N];
+                za += f * pa[2 * mx * N + 1];
             }
         } else {
             for (int mx = 0; mx < NH; ++mx) {
                 const double f = Fi[(mx + nh) * p + n];
-                rp += f * pp[2 * mx * N + 1];
-                ip -= f * pp[2 * mx * N];
-                rm += f * pm[2 * mx * N + 1];
-                im -= f * pm[2 * mx * N];
+                zs += f * ps[2 * mx * N + 1];
+                za -= f * pa[2 * mx * N];
             }
         }
-        Zr[e] = m ? rp + rm : rp;
-        Zi[e] = m ? ip - im : 0.0;
+        Zr[e] = zs;
+        Zi[e] = m ? za : 0.0;
     }
     __syncthreads();
     // c[n][n'] = Re sum_my conj(F[my][n']) Z[n][my] = sum_m Fr[m][n'] Zs[n][m] (n' even)
@@ -313,27 +344,38 @@ __global__ void __launch_bounds__(kT) k2_local(TreeView tv, Log2dDev d, int leve
     // incoming plane waves from the F_out colleagues: w(|m|^2) omega^{m . delta}
     if (tv.bflags[b] & BF_FIN) {
         const int nf = d.nf, NH = nf + 1;
-        for (int e = tid; e < NH * N; e += kT) Psi[2 * e] = Psi[2 * e + 1] = 0.0;
+        __shared__ const double *s_ph[9];  // the colleague at (dx, dy) = (c / 3 - 1, c % 3 - 1), or null
+        if (tid < 9) {
+            const int S = tv.bcol[(size_t)b * 27 + 9 * (tid / 3) + 3 * (tid % 3) + 1];
+            s_ph[tid] = (S >= 0 && (tv.bflags[S] & BF_FOUT)) ? phi + (size_t)tv.bslot[S] * 2 * NH * N : nullptr;
+        }
         __syncthreads();
-        const int32_t *col = tv.bcol + (size_t)b * 27;
-        for (int dx = -1; dx <= 1; ++dx)
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int S = col[9 * (dx + 1) + 3 * (dy + 1) + 1];
-                if (S < 0 || !(tv.bflags[S] & BF_FOUT)) continue;
-                const double *ph = phi + (size_t)tv.bslot[S] * 2 * NH * N;
-                // delta = c_B - c_S = -(dx, dy) R; phase exp(i (2 pi / 3) m . delta / R);
-                // half spectrum mx = 0 ... nf, the rows mx >= 1 doubled
-                for (int e = tid; e < NH * N; e += kT) {
-                    const int mx = e / N, my = e % N - nf;
-                    int r = (-(mx * dx + my * dy)) % 3;
-                    if (r < 0) r += 3;
-                    const double cr = r == 0 ? 1.0 : -0.5, ci = r == 0 ? 0.0 : (r == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
-                    const double w = (mx ? 2.0 : 1.0) * d.w[mx * mx + my * my];
-                    const double pr = ph[2 * e], pi = ph[2 * e + 1];
-                    Psi[2 * e] += w * (cr * pr - ci * pi);
-                    Psi[2 * e + 1] += w * (cr * pi + ci * pr);
-                }
+        // delta = c_B - c_S = -(dx, dy) R: the phase exp(i (2 pi / 3) m . delta / R) is a
+        // cube root of unity, c + i s with c in {1, -1/2} and s in {0, +-sqrt(3)/2}, so
+        // Psi = w (U + i V) with U = sum c Phi_S and V = sum s Phi_S; half spectrum
+        // mx = 0 ... nf, the rows mx >= 1 doubled
+        for (int e = tid; e < NH * N; e += kT) {
+            const int mx = e / N, my = e % N - nf;
+            double ur = 0.0, ui = 0.0, vr = 0.0, vi = 0.0;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                const double *ph = s_ph[c];
+                if (!ph) continue;
+                const int dx = c / 3 - 1, dy = c % 3 - 1;
+                int r = (-(mx * dx + my * dy)) % 3;
+                if (r < 0) r += 3;
+                const double cr = r == 0 ? 1.0 : -0.5,
+                             ci = r == 0 ? 0.0 : (r == 1 ? 0.86602540378443864676 : -0.86602540378443864676);
+                const double pr = ph[2 * e], pi = ph[2 * e + 1];
+                ur = fma(cr, pr, ur);
+                ui = fma(cr, pi, ui);
+                vr = fma(ci, pr, vr);
+                vi = fma(ci, pi, vi);
             }
+            const double w = (mx ? 2.0 : 1.0) * d.w[mx * mx + my * my];
+            Psi[2 * e] = w * (ur - vi);
+            Psi[2 * e + 1] = w * (ui + vr);
+        }
         __syncthreads();
         coef_from_pw(Psi, d.Fr, d.Fi, p, N, Zr, Zi, acc);
     }

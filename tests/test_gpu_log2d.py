@@ -129,6 +129,8 @@ def test_mixed_near_field(dmk, oracle_mod, case, eps, leaf_cap):
     ud = run(dmk, x, q, eps=eps, leaf_cap=leaf_cap)
     assert rel(um, oracle_mod.direct_log2d(x, q)) < eps
     assert rel(um, ud) < 0.3 * eps
+    ref = oracle_mod.dmk_log2d(x, q, eps=eps, leaf_cap=leaf_cap, p=plan_p(dmk, eps))
+    assert rel(um, ref) < 0.3 * eps
 
 
 def test_mixed_close_pairs(dmk, oracle_mod):
