@@ -59,7 +59,12 @@ def test_argument_validation_without_device(dmk):
     L.dmk_plan_destroy(h)
     h = ctypes.c_void_p()
     mixed = dmk.Opts(precision=1, flags=dmk.FLAG_HOST_ONLY)
-    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(mixed), ctypes.byref(h)) == 2  # the 2D pass is FP64
+    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(mixed), ctypes.byref(h)) == 0  # 2D mixed near field
+    L.dmk_plan_destroy(h)
+    h = ctypes.c_void_p()
+    assert L.dmk_plan(2, 2, 1e-8, ctypes.byref(mixed), ctypes.byref(h)) == 2  # mixed below 1e-7
+    far = dmk.Opts(flags=dmk.FLAG_HOST_ONLY | dmk.FLAG_FAR_ONLY)
+    assert L.dmk_plan(2, 2, 1e-6, ctypes.byref(far), ctypes.byref(h)) == 2    # the 2D pass evaluates both parts
     assert L.dmk_plan(0, 3, 1e-6, ctypes.byref(o), None) == 1
     bad = dmk.Opts(p=17)
     assert L.dmk_plan(0, 3, 1e-6, ctypes.byref(bad), ctypes.byref(h)) == 1
