@@ -69,20 +69,24 @@ __global__ void __launch_bounds__(kT) k2_moments(TreeView tv, Log2dDev d, double
     int ix, iy;
     cell2(tv, b, ix, iy);
     const double R = level_R(tv.blevel[b]), cx = (ix + 0.5) * R, cy = (iy + 0.5) * R;
+    const double s2R = (double)(2u << tv.blevel[b]);  // 2 / R, a power of two
     double acc[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) acc[j] = 0.0;
     const int s0 = tv.bstart[b], n = tv.bcount[b];
     for (int c0 = 0; c0 < n; c0 += 32) {
-        if (tid < 32) {
-            const int k = s0 + c0 + tid;
-            if (c0 + tid < n) {
-                const double qk = tv.q[k];
-                cheb_row(2.0 * (tv.ux[k] - cx) / R, p, Tx[tid]);
-                cheb_row(2.0 * (tv.uy[k] - cy) / R, p, Ty[tid]);
-                for (int a = 0; a < p; ++a) Tx[tid][a] *= qk;  // q_j T_a(xi_j)
+        if (tid < 64) {  // warp 0 the x rows (times the charge), warp 1 the y rows
+            const int i = tid & 31, k = s0 + c0 + i;
+            double *row = tid < 32 ? Tx[i] : Ty[i];
+            if (c0 + i < n) {
+                // 2 (x - c) / R, an exact scaling
+                cheb_row(tid < 32 ? (tv.ux[k] - cx) * s2R : (tv.uy[k] - cy) * s2R, p, row);
+                if (tid < 32) {
+                    const double qk = tv.q[k];
+                    for (int a = 0; a < p; ++a) row[a] *= qk;  // q_j T_a(xi_j)
+                }
             } else {
-                for (int a = 0; a < p; ++a) Tx[tid][a] = Ty[tid][a] = 0.0;
+                for (int a = 0; a < p; ++a) row[a] = 0.0;
             }
         }
         __syncthreads();
@@ -411,7 +415,8 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
     int ix, iy;
     cell2(tv, b, ix, iy);
     const double R = level_R(tv.blevel[b]);
-    const double xi = 2.0 * (tv.ux[k] - (ix + 0.5) * R) / R, eta = 2.0 * (tv.uy[k] - (iy + 0.5) * R) / R;
+    const double s2R = (double)(2u << tv.blevel[b]);  // 2 / R, a power of two: exact scaling
+    const double xi = (tv.ux[k] - (ix + 0.5) * R) * s2R, eta = (tv.uy[k] - (iy + 0.5) * R) * s2R;
     double Ty[kMaxP];
     cheb_row(eta, p, Ty);
     const double *c = loc + (size_t)b * p * p;

@@ -149,6 +149,18 @@ def test_mixed_close_pairs(dmk, oracle_mod):
     assert np.max(np.abs(um[-k:] - d[-k:]) / np.abs(d[-k:])) < 1e-6
 
 
+def test_repeated_evaluations_identical(dmk):
+    """The near field's queues and per-lane sums are added in a fixed order, so
+    repeated evaluations agree bit for bit, on both paths."""
+    x, q = inputs.circle2d(20000, seed=831)
+    for prec, eps in ((dmk.DMK_FP64, 1e-8), (dmk.DMK_MIXED, 1e-6)):
+        with dmk.Plan(kernel=dmk.DMK_LOG2D, dim=2, eps=eps, precision=prec, leaf_cap=120) as plan:
+            xd, qd = dev(x), dev(q)
+            u0 = plan.eval(xd, qd).cpu().numpy()
+            for _ in range(4):
+                assert np.array_equal(plan.eval(xd, qd).cpu().numpy(), u0)
+
+
 def test_refused_options(dmk):
     x, q = inputs.disk2d(300, seed=826)
     for kw in (dict(precision=dmk.DMK_MIXED, eps=1e-8), dict(flags=dmk.FLAG_FAR_ONLY), dict(dim=3)):
