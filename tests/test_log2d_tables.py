@@ -99,3 +99,24 @@ def test_f32_series_cut(dmk, eps):
         assert np.abs(full - chebyshev.chebval(x, g[:d + 1])).max() <= 1e-2 * eps * gmax * (1 + 1e-9)
         if d < prm["q_degree"]:  # one more coefficient dropped would pass the bound
             assert np.abs(g[d:]).sum() > 1e-2 * eps * gmax
+
+
+def test_table_log_method():
+    """log t as the 2D near field forms it (Tang's table-driven method): t = m 2^e,
+    F_k = 1 / (1 + (k + 1/2)/256) for the leading 8 fraction bits k of m,
+    log m = -log F_k + log1p(m F_k - 1) with log1p by its Taylor series to degree
+    5; against the library log over t in [2^-255, 1), to a few units of rounding
+    of the result (the series remainder is below 5e-18)."""
+    rng = np.random.default_rng(41)
+    t = np.exp2(-rng.uniform(0.0, 255.0, 200000))
+    t = np.r_[t, 1.0 - np.exp2(-np.arange(1, 53, dtype=float)), np.exp2(-np.arange(1, 256, dtype=float))]
+    m, e = np.frexp(t)            # t = m 2^e, m in [1/2, 1)
+    m, e = 2.0 * m, e - 1         # m in [1, 2)
+    k = np.floor((m - 1.0) * 256.0).astype(int)
+    F = 1.0 / (1.0 + (k + 0.5) / 256.0)
+    r = m * F - 1.0               # (the kernel forms this with one FMA)
+    assert np.all(np.abs(r) <= 2.0 ** -9 * (1 + 1e-12))
+    h = ((((r * 0.2 - 0.25) * r + 1.0 / 3.0) * r - 0.5) * r + 1.0) * r   # log1p(r), degree 5
+    got = e * np.log(2.0) + (-np.log(F) + h)
+    ref = np.log(t)
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) < 8e-16
