@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 // pair inside the support, append the survivors (target slot, source) to one
 // queue, and evaluate the queue 32 pairs at a time in FP64 into per-lane,
 // per-slot sums in shared memory, so that the FP64 pipe (the bound: GB300
-// issues FP64 at 1/64 of its FP32 rate) sees only pairs that are evaluated,
+// issues FP64 at about 1/62 of its FP32 rate) sees only pairs that are evaluated,
 // with one partly filled step per kS targets.  The lanes' sums of a target
 // are then added in a fixed butterfly order (results do not depend on timing).
 //
@@ -453,6 +453,12 @@ __global__ void __launch_bounds__(kT) k2_eval(TreeView tv, Log2dDev d, const int
 // subnormal r^2, take CUDA's log).  G by Horner in monomials (MONO) or by
 // Clenshaw in Chebyshev polynomials.  Coincident pairs remove q S_L(0) and
 // count their charge for the log S term.
+//
+// MIX (the mixed path, eps >= 1e-7): the same staging, screening and queue;
+// each pair in FP32 from hi/lo offsets in leaf units (the separation keeps its
+// relative accuracy however close the points), logf, and Clenshaw on G's
+// Chebyshev series cut for FP32; per-lane sums (hi, lo) by TwoSum.  Pairs with
+// r^2 below 2^-100 leaf units squared (coincident ones among them) take FP64.
 constexpr int kNW = 4, kNT = 32 * kNW;  // warps, threads per block
 constexpr int kCH = 512;                // sources staged per chunk
 constexpr int kS = 4;                   // targets in flight per warp (one queue, one flush)
