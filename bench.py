@@ -532,6 +532,32 @@ def run_yukawa(args):
     print(json.dumps(line), flush=True)
 
 
+def log2d_near_roofline(inside: int, prm: dict, near_ms: float, sm_mhz: float, mixed: bool) -> dict:
+    """The 2D near field (k2_near) against its pipe's peak.  On the FP64 path
+    it is bound by the FP64 pipe: per pair inside the support 24 flops
+    (distance, log t by the table, the sums) and 2 per degree of the residual
+    polynomial after the first (Horner, the form the plan takes at eps 1e-8).
+    On the mixed path its pairs are FP32: 34 flops (distance from hi/lo
+    offsets and r^2 9, t and 2x 3, Clenshaw's last step 4, logf counted as 8,
+    the product 3, TwoSum 7) and 3 per degree of Clenshaw's recurrence, on the
+    series cut for FP32 (q_degree_f32).  Peaks: the FFMA / DFMA probes scaled
+    to the sampled SM clock."""
+    if mixed:
+        per_pair, unit = 34 + 3 * prm["q_degree_f32"], "fp32"
+        peak = FFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
+        basis = "FFMA probe %.1f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (FFMA_MEASURED_TFLOPS,
+                                                                             FFMA_MEASURED_MHZ, sm_mhz)
+    else:
+        per_pair, unit = 24 + 2 * (prm["q_degree"] - 1), "fp64"
+        peak = DFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
+        basis = "DFMA probe %.2f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (DFMA_MEASURED_TFLOPS,
+                                                                              FFMA_MEASURED_MHZ, sm_mhz)
+    achieved = inside * per_pair / (near_ms * 1e-3) / 1e12
+    return {"kernel": "k2_near", "bound": unit, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "ms_per_eval": near_ms, "peak_basis": basis,
+            "work": "%d pairs inside the support x %d flops" % (inside, per_pair)}
+
+
 def run_log2d(args):
     """log |x - y| in the plane, 8e6 points (half on the unit circle, half in the
     disk), eps 1e-8: the FP64 path (the 2D pass has no mixed path), leaf
@@ -582,31 +608,11 @@ def run_log2d(args):
     ms = e0.elapsed_time(e1) / args.steps
     st = plan.stats()
     prm = plan.params()
-    # k2_near is bound by the FP64 pipe on the FP64 path: per pair inside the
-    # support 24 flops (distance, log t by the table, the sums) and 2 per degree
-    # of the residual polynomial after the first (Horner, the form the plan takes
-    # at eps 1e-8).  On the mixed path its pairs are FP32: 34 flops (distance from
-    # hi/lo offsets and r^2 9, t and 2x 3, Clenshaw's last step 4, logf counted
-    # as 8, the product 3, TwoSum 7) and 3 per degree of Clenshaw's recurrence.
-    # Timed by the events the library records around it.
     sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else FFMA_MEASURED_MHZ
     near_ms = float(np.median(t_near))
-    if args.log2d_mixed:
-        per_pair, unit_name = 34 + 3 * prm["q_degree_f32"], "fp32"
-        peak = FFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
-        basis = "FFMA probe %.1f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (FFMA_MEASURED_TFLOPS,
-                                                                             FFMA_MEASURED_MHZ, sm_mhz)
-    else:
-        per_pair, unit_name = 24 + 2 * (prm["q_degree"] - 1), "fp64"
-        peak = DFMA_MEASURED_TFLOPS * sm_mhz / FFMA_MEASURED_MHZ
-        basis = "DFMA probe %.2f TFLOP/s at %.0f MHz, scaled to %.0f MHz" % (DFMA_MEASURED_TFLOPS,
-                                                                              FFMA_MEASURED_MHZ, sm_mhz)
-    achieved = st["near_pairs_inside"] * per_pair / (near_ms * 1e-3) / 1e12
-    roofline = {"kernel": "k2_near", "bound": unit_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "ms_per_eval": near_ms, "peak_basis": basis,
-                "work": "%d pairs inside the support x %d flops" % (st["near_pairs_inside"], per_pair),
-                "timing": "CUDA events the library records around the kernel on the evaluation's stream, "
-                          "median over the timed steps"}
+    roofline = log2d_near_roofline(st["near_pairs_inside"], prm, near_ms, sm_mhz, args.log2d_mixed)
+    roofline["timing"] = ("CUDA events the library records around the kernel on the evaluation's stream, "
+                          "median over the timed steps")
     u = out.cpu().numpy()[sample]
     e2e = None
     if not args.skip_e2e:

@@ -67,3 +67,19 @@ def test_fp32_peak_scales_with_the_clock():
     peak, basis = bench.fp32_peak(152, bench.FFMA_MEASURED_MHZ / 2)
     assert peak == pytest.approx(bench.FFMA_MEASURED_TFLOPS / 2)
     assert "FFMA probe" in basis
+
+
+def test_log2d_near_roofline():
+    """The 2D near field's roofline: 24 + 2 (q_degree - 1) FP64 flops per pair
+    inside the support against the DFMA probe, or 34 + 3 q_degree_f32 FP32
+    flops on the mixed path against the FFMA probe, both at the sampled clock."""
+    prm = {"q_degree": 15, "q_degree_f32": 11}
+    r = bench.log2d_near_roofline(1_000_000_000, prm, 100.0, bench.FFMA_MEASURED_MHZ, False)
+    assert r["bound"] == "fp64" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(1e9 * 52 / 0.1 / 1e12)
+    assert r["peak"] == pytest.approx(bench.DFMA_MEASURED_TFLOPS)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    m = bench.log2d_near_roofline(1_000_000_000, prm, 10.0, bench.FFMA_MEASURED_MHZ / 2, True)
+    assert m["bound"] == "fp32"
+    assert m["achieved"] == pytest.approx(1e9 * (34 + 33) / 0.01 / 1e12)
+    assert m["peak"] == pytest.approx(bench.FFMA_MEASURED_TFLOPS / 2)
